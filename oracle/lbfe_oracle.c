@@ -1,0 +1,436 @@
+/*
+ * Plain, slow FP64 CPU oracle of the forcing-based free-energy D2Q9 lattice
+ * Boltzmann step (Li, Yu & Huang, "Achieving thermodynamic consistency in a
+ * class of free-energy multiphase lattice Boltzmann models").
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link, load or
+ * call this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do. It shares no source with the CUDA library.
+ *
+ * The step is written as the paper states it, one literal stage at a time,
+ * over the whole periodic lattice, with no fusion:
+ *   1. rho = sum_a f_a                                   (Eq. 12)
+ *   2. lap = isotropic 9-point Laplacian of rho          (Eq. 2 needs it; the
+ *      paper prints no stencil: reading 6 * sum_a w_a (rho(x+e_a) - rho(x)))
+ *   3. mu_c = E_f'(rho) - kappa * lap                    (Eq. 2, Eq. 30 / CS)
+ *   4. grad_h of mu_c (and of rho for the standard form)  (Eq. 17)
+ *   5. F = grad_h(rho/3) - rho grad_h mu_c  (standard,  Eq. 13 right)
+ *      F = (1/3 - rho) grad_h mu_c         (improved,  Eq. 24)
+ *   6. u = (sum_a e_a f_a + F/2) / rho                   (Eq. 12)
+ *   7. improved only: p_m = (c0 + mu_c)/3, phi = rho/3 - p_m,
+ *      C1 = d_x(phi u_x) + d_y(phi u_y), C7 = d_x(phi u_x) - d_y(phi u_y),
+ *      derivatives by the Eq. 17 stencil                  (Eqs. 24, 29)
+ *   8. G_a from Eq. 14 for all nine a; S = M G; m = M f; m_eq from Eq. 11
+ *      (standard) or Eq. 27 (improved), all as dense 9x9 products
+ *   9. m* = m - Lambda (m - m_eq) + (I - Lambda/2)(S + C)  (Eqs. 9, 28, 8)
+ *  10. f* = M^-1 m*, with M^-1 obtained by Gauss-Jordan elimination
+ *  11. push streaming f_a(x + e_a) = f*_a(x), periodic     (Eq. 10)
+ *
+ * M is the Lallemand-Luo D2Q9 moment matrix with moments ordered
+ * (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy): the order of the relaxation
+ * vector of Eq. 8 and of the equilibria of Eqs. 11 and 27 (the paper cites
+ * the matrix but does not print it).
+ *
+ * Layout: populations f[a][y][x] (a = 0..8, x fastest); fields [y][x].
+ * Velocity order e0=(0,0), e1=(1,0), e2=(0,1), e3=(-1,0), e4=(0,-1),
+ * e5=(1,1), e6=(-1,1), e7=(-1,-1), e8=(1,-1); weights from Eq. 14.
+ *
+ * Compile with -O2 -ffp-contract=off so that no fused multiply-add changes
+ * the rounding of the literal expressions.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+
+static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WA[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0; /* c_s^2, Eq. 13 */
+
+/* Lallemand-Luo transformation matrix, rows = moments. */
+static const double MM[Q][Q] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},          /* rho  */
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},     /* e    */
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},      /* eps  */
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},       /* j_x  */
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},       /* q_x  */
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},       /* j_y  */
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},       /* q_y  */
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},        /* p_xx */
+    {0, 0, 0, 0, 0, 1, -1, 1, -1},        /* p_xy */
+};
+
+typedef struct {
+    int32_t nx, ny;
+    int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28) */
+    int32_t collision; /* 0 = BGK (all rates 1/tau_v), 1 = MRT (Eq. 8) */
+    int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
+    int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
+                          bit 0: drop the correction term C of Eq. 28
+                          bit 1: flip the sign of the F/2 shift in Eq. 12 */
+    double a, b, R, T, kappa;
+    double tau_v, tau_e, tau_s, tau_q; /* MRT rates of Eq. 8; tau_c = 1 */
+    double pm_c0;                      /* p_m = (c0 + mu_c)/3; the paper's c0 is 1 */
+    double nu;                         /* > 0: constant kinematic viscosity, tau_v set per
+                                          node from it (Sec. III below Eq. 29; Sec. II A) */
+} orc_case;
+
+/* ------------------------------------------------------------------ EOS */
+
+/* Bulk free-energy density E_f(rho). vdW: Eq. 30's E_f. CS: the
+ * Carnahan-Starling free energy E_f = RT rho ln rho + RT rho (4n - 3n^2)/(1-n)^2
+ * - a rho^2 with n = b rho / 4 (not in the paper). */
+double orc_Ef(const orc_case* c, double rho)
+{
+    if (c->eos == 0) return rho * c->R * c->T * log(rho / (1.0 - c->b * rho)) - c->a * rho * rho;
+    double n = c->b * rho / 4.0;
+    double om = 1.0 - n;
+    return c->R * c->T * rho * log(rho) + c->R * c->T * rho * (4.0 * n - 3.0 * n * n) / (om * om) -
+           c->a * rho * rho;
+}
+
+/* E_f'(rho), the bulk part of the chemical potential (Eq. 2; vdW Eq. 30). */
+double orc_dEf(const orc_case* c, double rho)
+{
+    if (c->eos == 0) {
+        double one_m = 1.0 - c->b * rho;
+        return c->R * c->T * (log(rho / one_m) + 1.0 / one_m) - 2.0 * c->a * rho;
+    }
+    double n = c->b * rho / 4.0;
+    double om = 1.0 - n;
+    return c->R * c->T *
+               (log(rho) + 1.0 + (4.0 * n - 3.0 * n * n) / (om * om) +
+                n * (4.0 - 2.0 * n) / (om * om * om)) -
+           2.0 * c->a * rho;
+}
+
+/* p_EOS = rho E_f' - E_f (the line after Eq. 4). */
+double orc_pEOS(const orc_case* c, double rho) { return rho * orc_dEf(c, rho) - orc_Ef(c, rho); }
+
+/* ------------------------------------------------------------- stencils */
+
+static inline int wrap(int i, int n) { return ((i % n) + n) % n; }
+
+/* Eq. 17: grad_h phi = (1/c_s^2) sum_a w_a phi(x + e_a) e_a, periodic. */
+void orc_grad(int nx, int ny, const double* phi, double* gx, double* gy)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double sx = 0.0, sy = 0.0;
+            for (int a = 0; a < Q; ++a) {
+                double v = phi[wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)];
+                sx += WA[a] * v * EX[a];
+                sy += WA[a] * v * EY[a];
+            }
+            gx[y * nx + x] = sx / CS2;
+            gy[y * nx + x] = sy / CS2;
+        }
+}
+
+/* Isotropic Laplacian: (2/c_s^2) sum_a w_a (phi(x + e_a) - phi(x)). The paper
+ * needs a Laplacian in Eq. 2 but does not print its stencil; this is the
+ * 9-point isotropic form built from the same weights as Eq. 17. */
+void orc_laplacian(int nx, int ny, const double* phi, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double c0 = phi[y * nx + x];
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a)
+                s += WA[a] * (phi[wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)] - c0);
+            out[y * nx + x] = 2.0 * s / CS2;
+        }
+}
+
+/* ------------------------------------------------------- moment algebra */
+
+void orc_M(double* out) { memcpy(out, MM, sizeof(MM)); }
+
+/* Gauss-Jordan inverse of M with partial pivoting. */
+void orc_Minv(double* out)
+{
+    double A[Q][2 * Q];
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < 2 * Q; ++j) A[i][j] = (j < Q) ? MM[i][j] : (j - Q == i ? 1.0 : 0.0);
+    for (int col = 0; col < Q; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < Q; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (piv != col)
+            for (int j = 0; j < 2 * Q; ++j) {
+                double t = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+        double d = A[col][col];
+        for (int j = 0; j < 2 * Q; ++j) A[col][j] /= d;
+        for (int r = 0; r < Q; ++r) {
+            if (r == col) continue;
+            double m = A[r][col];
+            if (m == 0.0) continue;
+            for (int j = 0; j < 2 * Q; ++j) A[r][j] -= m * A[col][j];
+        }
+    }
+    for (int i = 0; i < Q; ++i)
+        for (int j = 0; j < Q; ++j) out[i * Q + j] = A[i][Q + j];
+}
+
+static void matvec(const double* A, const double* v, double* out)
+{
+    for (int i = 0; i < Q; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < Q; ++j) s += A[i * Q + j] * v[j];
+        out[i] = s;
+    }
+}
+
+/* Moment-space equilibrium: Eq. 11 (standard) or Eq. 27 with
+ * gamma = 3 p_m / rho and p_m = (c0 + mu_c)/3 (improved, Eq. 24). */
+void orc_meq(const orc_case* c, double rho, double ux, double uy, double mu, double* meq)
+{
+    double u2 = ux * ux + uy * uy;
+    if (c->scheme == 0) {
+        meq[0] = rho;
+        meq[1] = rho * (-2.0 + 3.0 * u2);
+        meq[2] = rho * (1.0 - 3.0 * u2);
+        meq[3] = rho * ux;
+        meq[4] = -rho * ux;
+        meq[5] = rho * uy;
+        meq[6] = -rho * uy;
+    } else {
+        double pm = (c->pm_c0 + mu) / 3.0;
+        double g = 3.0 * pm / rho;
+        meq[0] = rho;
+        meq[1] = rho * (-4.0 + 3.0 * u2 + 2.0 * g);
+        meq[2] = rho * (4.0 - 3.0 * u2 - 3.0 * g);
+        meq[3] = rho * ux;
+        meq[4] = rho * (g - 2.0) * ux;
+        meq[5] = rho * uy;
+        meq[6] = rho * (g - 2.0) * uy;
+    }
+    meq[7] = rho * (ux * ux - uy * uy);
+    meq[8] = rho * ux * uy;
+}
+
+/* Population-space equilibrium f_eq = M^-1 m_eq. */
+void orc_feq(const orc_case* c, double rho, double ux, double uy, double mu, double* feq)
+{
+    double Mi[Q * Q], meq[Q];
+    orc_Minv(Mi);
+    orc_meq(c, rho, ux, uy, mu, meq);
+    matvec(Mi, meq, feq);
+}
+
+/* Eq. 14: G_a = w_a [ (e_a - u)/c_s^2 + (e_a . u) e_a / c_s^4 ] . F */
+void orc_guo(double ux, double uy, double Fx, double Fy, double* G)
+{
+    for (int a = 0; a < Q; ++a) {
+        double eu = EX[a] * ux + EY[a] * uy;
+        double vx = (EX[a] - ux) / CS2 + eu * EX[a] / (CS2 * CS2);
+        double vy = (EY[a] - uy) / CS2 + eu * EY[a] / (CS2 * CS2);
+        G[a] = WA[a] * (vx * Fx + vy * Fy);
+    }
+}
+
+/* Shear relaxation time at a node. With nu > 0 it follows from the dynamic
+ * viscosity: eta = p_m (tau_v - 1/2) for the improved scheme (below Eq. 29) and
+ * eta = rho c_s^2 (tau_v - 1/2) for the standard one (below Eq. 8), eta = nu rho. */
+double orc_tau_v(const orc_case* c, double rho, double mu)
+{
+    if (!(c->nu > 0.0)) return c->tau_v;
+    if (c->scheme == 1) return 0.5 + c->nu * rho / ((c->pm_c0 + mu) / 3.0);
+    return 0.5 + c->nu / CS2;
+}
+
+/* Diagonal of Lambda: Eq. 8 (tau_c = 1) for MRT, all 1/tau_v for BGK. */
+static void relax_rates(const orc_case* c, double tau_v, double* lam)
+{
+    if (c->collision == 0) {
+        for (int i = 0; i < Q; ++i) lam[i] = 1.0 / tau_v;
+        return;
+    }
+    lam[0] = 1.0;
+    lam[1] = 1.0 / c->tau_e;
+    lam[2] = 1.0 / c->tau_s;
+    lam[3] = 1.0;
+    lam[4] = 1.0 / c->tau_q;
+    lam[5] = 1.0;
+    lam[6] = 1.0 / c->tau_q;
+    lam[7] = 1.0 / tau_v;
+    lam[8] = 1.0 / tau_v;
+}
+
+/* ------------------------------------------------- macroscopic fields */
+
+/* Stages 1-6 (and p_m, C of stage 7) over the lattice, from the populations
+ * at the start of a step. Any output pointer may be NULL except as noted.
+ * Returns 0, or -1 when rho <= 0 or a value is not finite somewhere. */
+int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
+               double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double* rho = calloc(N, sizeof(double));
+    double* lap = calloc(N, sizeof(double));
+    double* mu = calloc(N, sizeof(double));
+    double* gmx = calloc(N, sizeof(double));
+    double* gmy = calloc(N, sizeof(double));
+    double* grx = calloc(N, sizeof(double));
+    double* gry = calloc(N, sizeof(double));
+    double* ux = calloc(N, sizeof(double));
+    double* uy = calloc(N, sizeof(double));
+    double* Fx = calloc(N, sizeof(double));
+    double* Fy = calloc(N, sizeof(double));
+    double* A = calloc(N, sizeof(double));
+    double* B = calloc(N, sizeof(double));
+    double* Ax = calloc(N, sizeof(double));
+    double* Ay = calloc(N, sizeof(double));
+    double* Bx = calloc(N, sizeof(double));
+    double* By = calloc(N, sizeof(double));
+    int bad = 0;
+
+    /* 1. density */
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int a = 0; a < Q; ++a) s += f[a * N + i];
+        rho[i] = s;
+        if (!(s > 0.0) || !isfinite(s)) bad = 1;
+    }
+    /* 2-3. chemical potential */
+    orc_laplacian(nx, ny, rho, lap);
+    for (int i = 0; i < N; ++i) mu[i] = orc_dEf(c, rho[i]) - c->kappa * lap[i];
+    /* 4-5. force */
+    orc_grad(nx, ny, mu, gmx, gmy);
+    if (c->scheme == 0) {
+        double* r3 = calloc(N, sizeof(double));
+        for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
+        orc_grad(nx, ny, r3, grx, gry);
+        free(r3);
+        for (int i = 0; i < N; ++i) {
+            Fx[i] = grx[i] - rho[i] * gmx[i];
+            Fy[i] = gry[i] - rho[i] * gmy[i];
+        }
+    } else {
+        for (int i = 0; i < N; ++i) {
+            Fx[i] = (CS2 - rho[i]) * gmx[i];
+            Fy[i] = (CS2 - rho[i]) * gmy[i];
+        }
+    }
+    /* 6. velocity */
+    double half = (c->flags & 2) ? -0.5 : 0.5;
+    for (int i = 0; i < N; ++i) {
+        double jx = 0.0, jy = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            jx += EX[a] * f[a * N + i];
+            jy += EY[a] * f[a * N + i];
+        }
+        ux[i] = (jx + half * Fx[i]) / rho[i];
+        uy[i] = (jy + half * Fy[i]) / rho[i];
+    }
+    /* 7. correction term (improved scheme) */
+    if (c->scheme == 1) {
+        for (int i = 0; i < N; ++i) {
+            double pm = (c->pm_c0 + mu[i]) / 3.0;
+            double phi = rho[i] * CS2 - pm;
+            A[i] = phi * ux[i];
+            B[i] = phi * uy[i];
+        }
+        orc_grad(nx, ny, A, Ax, Ay);
+        orc_grad(nx, ny, B, Bx, By);
+    }
+    for (int i = 0; i < N; ++i) {
+        if (!isfinite(mu[i]) || !isfinite(ux[i]) || !isfinite(uy[i])) bad = 1;
+        if (rho_o) rho_o[i] = rho[i];
+        if (ux_o) ux_o[i] = ux[i];
+        if (uy_o) uy_o[i] = uy[i];
+        if (mu_o) mu_o[i] = mu[i];
+        if (Fx_o) Fx_o[i] = Fx[i];
+        if (Fy_o) Fy_o[i] = Fy[i];
+        if (C1_o) C1_o[i] = (c->scheme == 1) ? Ax[i] + By[i] : 0.0;
+        if (C7_o) C7_o[i] = (c->scheme == 1) ? Ax[i] - By[i] : 0.0;
+    }
+    free(rho); free(lap); free(mu); free(gmx); free(gmy); free(grx); free(gry);
+    free(ux); free(uy); free(Fx); free(Fy); free(A); free(B);
+    free(Ax); free(Ay); free(Bx); free(By);
+    return bad ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------- step */
+
+/* Advance f (in place, f[a][y][x]) by nsteps time steps. Returns the number
+ * of steps completed; fewer than nsteps means the state became non-physical
+ * (rho <= 0 or a non-finite value) before the step that was not taken. */
+int64_t orc_step(const orc_case* c, double* f, int64_t nsteps)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double Mi[Q * Q], lam[Q];
+    orc_Minv(Mi);
+    double* rho = malloc(N * sizeof(double));
+    double* ux = malloc(N * sizeof(double));
+    double* uy = malloc(N * sizeof(double));
+    double* mu = malloc(N * sizeof(double));
+    double* Fx = malloc(N * sizeof(double));
+    double* Fy = malloc(N * sizeof(double));
+    double* C1 = malloc(N * sizeof(double));
+    double* C7 = malloc(N * sizeof(double));
+    double* fn = malloc((size_t)Q * N * sizeof(double));
+    int64_t done = 0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (orc_fields(c, f, rho, ux, uy, mu, Fx, Fy, C1, C7) != 0) break;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int i = y * nx + x;
+                double fl[Q], m[Q], meq[Q], G[Q], S[Q], Cv[Q], ms[Q], fs[Q];
+                for (int a = 0; a < Q; ++a) fl[a] = f[a * N + i];
+                /* 8. forcing, moments, equilibria */
+                orc_guo(ux[i], uy[i], Fx[i], Fy[i], G);
+                matvec(&MM[0][0], G, S);
+                matvec(&MM[0][0], fl, m);
+                orc_meq(c, rho[i], ux[i], uy[i], mu[i], meq);
+                for (int k = 0; k < Q; ++k) Cv[k] = 0.0;
+                if (c->scheme == 1 && !(c->flags & 1)) {
+                    Cv[1] = 9.0 * C1[i];
+                    Cv[7] = 3.0 * C7[i];
+                }
+                /* 9. collision in moment space */
+                relax_rates(c, orc_tau_v(c, rho[i], mu[i]), lam);
+                for (int k = 0; k < Q; ++k)
+                    ms[k] = m[k] - lam[k] * (m[k] - meq[k]) + (1.0 - 0.5 * lam[k]) * (S[k] + Cv[k]);
+                /* 10. back to populations */
+                matvec(Mi, ms, fs);
+                /* 11. push streaming */
+                for (int a = 0; a < Q; ++a)
+                    fn[a * N + wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)] = fs[a];
+            }
+        memcpy(f, fn, (size_t)Q * N * sizeof(double));
+        ++done;
+    }
+    free(rho); free(ux); free(uy); free(mu); free(Fx); free(Fy); free(C1); free(C7); free(fn);
+    return done;
+}
+
+/* Initial populations (no rule in the paper): f(0) = M^-1 m_eq(rho0, u0) of
+ * the running scheme, with mu_c (hence p_m) from rho0 through Eq. 2.
+ * ux0/uy0 may be NULL for a fluid at rest. Returns 0, or -1 if rho0 <= 0. */
+int orc_init(const orc_case* c, const double* rho0, const double* ux0, const double* uy0, double* f)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double* lap = malloc(N * sizeof(double));
+    double Mi[Q * Q];
+    orc_Minv(Mi);
+    orc_laplacian(nx, ny, rho0, lap);
+    int bad = 0;
+    for (int i = 0; i < N; ++i) {
+        if (!(rho0[i] > 0.0)) bad = 1;
+        double mu = orc_dEf(c, rho0[i]) - c->kappa * lap[i];
+        double meq[Q], fe[Q];
+        orc_meq(c, rho0[i], ux0 ? ux0[i] : 0.0, uy0 ? uy0[i] : 0.0, mu, meq);
+        matvec(Mi, meq, fe);
+        for (int a = 0; a < Q; ++a) f[a * N + i] = fe[a];
+    }
+    free(lap);
+    return bad ? -1 : 0;
+}
