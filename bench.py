@@ -1,0 +1,266 @@
+"""Throughput of the fused free-energy D2Q9 step on GB300 (MLUPS and HBM roofline).
+
+Workload: 4096 x 4096 periodic spinodal decomposition, improved scheme (Eqs. 24,
+27-29), MRT collision (Eq. 8), FP32 populations stored as deviations from
+w_a rho_ref. EOS: the paper's van der Waals set (a = 9/392, b = 2/21, kappa =
+0.02) at T = 0.8 T_c; initial density = mean of the Maxwell densities times
+(1 + U[-0.01, 0.01]) from the seeded SplitMix64 stream. One step = one time
+step of the whole lattice (one fused kernel launch). The populations (1.2 GB
+per step read + write) exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on a
+bounded 256 x 256 sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 free-energy LB MLUPS & % HBM roofline, FP32/batched vs plain FP64"
+N_SIDE = 4096
+T_RED = 0.8
+BYTES_PER_NODE = {"f32": 72, "f64": 144}  # 9 populations read + 9 written
+VDW = dict(a=9.0 / 392.0, b=2.0 / 21.0, R=1.0)
+SAMPLE_SIDE = 256
+WORKLOAD = (f"spinodal {N_SIDE}x{N_SIDE} periodic, improved scheme, MRT (tau_v 0.8, tau_e 1.0, tau_s 1.0, "
+            f"tau_q 1.1), vdW a=9/392 b=2/21 kappa=0.02 at T/Tc={T_RED}, FP32 deviation storage")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2008_01473_gb300 import build, inputs, lbfe
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    build.build()
+    tc, _ = lbfe.critical(lbfe.VDW, **VDW)
+    T = T_RED * tc
+    rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], T)
+    case = lbfe.Case(nx=N_SIDE, ny=N_SIDE, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, T=T,
+                     kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW)
+    nodes = N_SIDE * N_SIDE
+    rho0 = inputs.spinodal(N_SIDE, N_SIDE, 0.5 * (rg + rl), 0.01, seed=1 + rank)
+    rho0_pin = torch.from_numpy(rho0).pin_memory()
+    lat = lbfe.Lattice([case], precision=lbfe.FP32, device=f"cuda:{local}")
+    stream = lat.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    # ------------------------------------------------------ device-resident
+    lat.init_fields(0, rho0_pin)
+    lat.step(args.warmup)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(args.steps):
+            lat.step(1)
+            ev[k + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]  # ms, one kernel launch each
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    out, st = lat.reductions()
+    stable = bool(st[0] == 0)
+
+    # ------------------------------------------------------------ end to end
+    res = {k: torch.empty((N_SIDE, N_SIDE), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
+    barrier()
+    t0 = time.perf_counter()
+    lat.init_fields(0, rho0_pin)
+    lat.step(args.steps)
+    import ctypes as C
+
+    rc = lbfe.lib().lb_moments(lat._h, 0, C.c_void_p(res["rho"].data_ptr()), C.c_void_p(res["ux"].data_ptr()),
+                               C.c_void_p(res["uy"].data_ptr()), None, 0)
+    lbfe._check(rc, lat._h)
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    lat.close()
+
+    if rank == 0:
+        peak, src = _peaks()
+        mean_ms = sum(per) / len(per)
+        achieved = BYTES_PER_NODE["f32"] * nodes / (mean_ms * 1e-3) / 1e9
+        value = ws * nodes * args.steps / (total_ms * 1e-3) / 1e6
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "nodes_per_gpu": nodes,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": "populations 1.21 GB per step > 129 MB L2 (no flush needed)",
+                       "stable": stable},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak_source": src, "bytes_per_node": BYTES_PER_NODE["f32"],
+                         "kernel_ms_mean": round(mean_ms, 4), "kernel_ms_min": round(min(per), 4)},
+            "clocks": clk,
+            "e2e": {"value": round(ws * nodes * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+                    "h2d_bytes_per_step": int(8 * nodes / args.steps),
+                    "d2h_bytes_per_step": int((8 + 3 * 8) * nodes / args.steps),
+                    "includes": "lb_init_fields from pinned host rho0 (with its validation read-back), "
+                                "K lb_step calls, lb_moments of rho, ux, uy to pinned host"},
+            "gpu_launches": args.steps,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample():
+    import oracle as O
+    from oracle import thermo
+    from paper_2008_01473_gb300 import inputs
+
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, T_RED)
+    oc = O.Case(nx=SAMPLE_SIDE, ny=SAMPLE_SIDE, scheme=O.IMPROVED, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b,
+                T=T, kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
+    f = O.init(oc, inputs.spinodal(SAMPLE_SIDE, SAMPLE_SIDE, 0.5 * (rg + rl), 0.01, seed=1))
+    return O, oc, f
+
+
+def cpu_baseline(steps: int) -> dict:
+    """The FP64 oracle (single-threaded C) on a bounded sample of the workload."""
+    O, oc, f = _oracle_sample()
+    O.step(oc, f, 1)
+    t0 = time.perf_counter()
+    O.step(oc, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(SAMPLE_SIDE * SAMPLE_SIDE * steps / dt / 1e6, 3), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle", "sample": f"{SAMPLE_SIDE}x{SAMPLE_SIDE} sub-lattice of the same workload, "
+                                        f"{steps} steps, FP64 single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    O, oc, f = _oracle_sample()
+    O.step(oc, f, max(args.warmup, 1))
+    t0 = time.perf_counter()
+    O.step(oc, f, args.steps)
+    dt = time.perf_counter() - t0
+    v = SAMPLE_SIDE * SAMPLE_SIDE * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP32 deviation storage", "FP64 oracle")
+                       + f"; each step a {SAMPLE_SIDE}x{SAMPLE_SIDE} sample", "nx": SAMPLE_SIDE, "ny": SAMPLE_SIDE},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{SAMPLE_SIDE}x{SAMPLE_SIDE} sub-lattice, {args.steps} steps"},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=150)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * lbfe.h - C ABI of the GB300 (sm_103a) forcing-based free-energy D2Q9
+ * lattice Boltzmann library (Li, Yu & Huang, "Achieving thermodynamic
+ * consistency in a class of free-energy multiphase lattice Boltzmann models").
+ *
+ * One time step of one periodic case is, per node:
+ *   rho = sum_a f_a, rho u = sum_a e_a f_a + F/2                 (Eq. 12)
+ *   mu_c = E_f'(rho) - kappa lap(rho)                            (Eq. 2; vdW Eq. 30)
+ *   F = grad_h(rho/3) - rho grad_h mu_c   (standard scheme,       Eq. 13 right)
+ *   F = (1/3 - rho) grad_h mu_c           (improved scheme,       Eq. 24)
+ *   grad_h = isotropic gradient                                  (Eq. 17)
+ *   m* = m - Lambda (m - m_eq) + (I - Lambda/2)(S + C)           (Eqs. 9, 28)
+ *   m_eq from Eq. 11 (standard) or Eq. 27 (improved), S = M G with G of Eq. 14,
+ *   C = (0, 9 C1, 0, 0, 0, 0, 0, 3 C7, 0) of Eq. 29 (improved only),
+ *   Lambda from Eq. 8 (MRT) or 1/tau_v on every moment (BGK),
+ *   f* = M^-1 m*, streamed f_a(x + e_a, t + 1) = f*_a(x, t)      (Eq. 10).
+ * M is the Lallemand-Luo D2Q9 matrix, moments ordered (rho, e, eps, j_x, q_x,
+ * j_y, q_y, p_xx, p_xy); velocities e0=(0,0), e1=(1,0), e2=(0,1), e3=(-1,0),
+ * e4=(0,-1), e5=(1,1), e6=(-1,1), e7=(-1,-1), e8=(1,-1).
+ *
+ * Conventions for every entry point:
+ *  - Ownership: the caller allocates the device workspace (size from
+ *    lb_workspace_bytes) and every input/output buffer, and frees them after
+ *    lb_destroy. The library allocates host memory only (handle, tables,
+ *    captured graphs) and never frees caller memory.
+ *  - Streams: all device work is enqueued on the stream given to lb_create
+ *    (a cudaStream_t passed as void*; NULL = legacy default stream). Calls
+ *    that return data to host memory synchronise that stream before
+ *    returning.
+ *  - Fields: FP64, row-major [ny][nx], x fastest. A pointer flagged
+ *    on_device = 1 is a device address, otherwise a host address.
+ *  - Errors: every call returns an lb_status; nothing throws, exits or traps.
+ *    lb_last_error() gives a one-line description of the handle's last failure.
+ *  - A handle is not thread-safe; separate handles are independent.
+ */
+#ifndef LBFE_H
+#define LBFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_E_INVALID = 1,   /* bad argument or parameter set (nothing was enqueued) */
+    LB_E_CUDA = 2,      /* a CUDA runtime call failed; see lb_last_error */
+    LB_E_UNSTABLE = 3,  /* a case produced rho <= 0 or a non-finite value */
+    LB_E_TIMEOUT = 4,   /* reserved: a bounded device-side wait gave up */
+    LB_E_WORKSPACE = 5, /* workspace pointer misaligned or too small */
+    LB_E_STATE = 6      /* call out of order (e.g. step before init) */
+} lb_status;
+
+enum { LB_STANDARD = 0, LB_IMPROVED = 1 };  /* Eq. 13 right / Eqs. 24-29 */
+enum { LB_BGK = 0, LB_MRT = 1 };            /* single rate 1/tau_v / Eq. 8 */
+enum { LB_VDW = 0, LB_CS = 1 };             /* Eq. 30 / Carnahan-Starling */
+enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic */
+
+/* One independent periodic case. Eq. 30 (vdW):
+ *   E_f = rho R T ln[rho/(1 - b rho)] - a rho^2;
+ * Carnahan-Starling (not in the paper):
+ *   E_f = R T rho ln rho + R T rho (4n - 3n^2)/(1 - n)^2 - a rho^2, n = b rho/4.
+ * tau_e, tau_s, tau_q are the free MRT times of Eq. 8 (tau_c = 1); BGK uses
+ * tau_v alone. nu > 0 selects constant kinematic viscosity: tau_v at each
+ * node follows from eta = nu rho with eta = p_m (tau_v - 1/2) (improved,
+ * below Eq. 29) or rho c_s^2 (tau_v - 1/2) (standard, below Eq. 8).
+ * p_m = (pm_c0 + mu_c)/3 (Eq. 24 uses pm_c0 = 1). rho_ref is the reference
+ * density of FP32 storage (populations are stored as f_a - w_a rho_ref);
+ * rho_ref = 0 asks lb_init_fields to use the mean of the initial density. */
+typedef struct {
+    int32_t nx, ny;      /* >= 3 each */
+    int32_t scheme;      /* LB_STANDARD or LB_IMPROVED */
+    int32_t collision;   /* LB_BGK or LB_MRT */
+    int32_t eos;         /* LB_VDW or LB_CS */
+    int32_t reserved;    /* must be 0 */
+    double a, b, R, T;   /* EOS parameters; T absolute */
+    double kappa;        /* > 0, Eq. 1 */
+    double tau_v, tau_e, tau_s, tau_q; /* each > 1/2 */
+    double pm_c0;        /* Eq. 24 constant */
+    double nu;           /* 0 or > 0 */
+    double rho_ref;      /* FP32 storage reference, >= 0 */
+} lb_case;
+
+typedef struct lb_handle lb_handle;
+
+/* Bytes of device workspace that lb_create needs for these cases at this
+ * precision (LB_FP64 or LB_FP32). The workspace must be 256-byte aligned. */
+lb_status lb_workspace_bytes(const lb_case* cases, int32_t ncases, int32_t precision,
+                             size_t* bytes);
+
+/* Validate the cases, lay the workspace out and build the launch work-lists.
+ * d_workspace: device memory of at least lb_workspace_bytes bytes, owned by
+ * the caller and not touched by anyone else until lb_destroy. cuda_stream:
+ * cudaStream_t (void*). On LB_OK *out holds a new handle. */
+lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, void* d_workspace,
+                    size_t ws_bytes, void* cuda_stream, lb_handle** out);
+
+/* Set case case_id to f(0) = M^-1 m_eq(rho0, u0) of its scheme, with mu_c of
+ * Eq. 2 evaluated on rho0 (the paper gives no initialisation rule).
+ * rho0 [ny][nx] must be > 0; ux0/uy0 may be NULL (fluid at rest). Pointers
+ * are device addresses if on_device, else host (copied synchronously). */
+lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
+                         const double* uy0, int32_t on_device);
+
+/* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
+ * Eq. 10). Enqueued asynchronously; the last step of the call also records
+ * per-case mass, kinetic energy and max|u| for lb_reductions. */
+lb_status lb_step(lb_handle* h, int64_t nsteps);
+
+/* Macroscopic fields of case case_id at the current step: rho and u of
+ * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2; any output may be
+ * NULL. Device outputs if on_device, else host (stream synchronised). */
+lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy,
+                     double* mu, int32_t on_device);
+
+/* Per-case results of the last lb_step call, FP64 sums in a fixed order:
+ * out[5*c + {0,1,2,3,4}] = {mass sum rho, kinetic energy sum rho|u|^2/2,
+ * max |u|, step count, 0}; case_status[c] = LB_OK or LB_E_UNSTABLE.
+ * Host pointers; synchronises the stream. Returns LB_E_UNSTABLE if any case
+ * is unstable (the others keep their values). */
+lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
+
+/* Bytes of one case's snapshot (populations + step counter) for lb_save. */
+lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes);
+
+/* Copy case case_id's populations and step counter to / from host memory
+ * (bit-exact resume). host_buf must hold lb_snapshot_bytes bytes. */
+lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes);
+lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes);
+
+/* Host thermodynamics for set-up (FP64, Newton): critical point and the
+ * Maxwell equal-area coexistence densities rho_g < rho_l (Sec. IV A; Table II
+ * lists the vdW values). eos = LB_VDW or LB_CS. */
+lb_status lb_critical(int32_t eos, double a, double b, double R, double* Tc, double* rho_c);
+lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double* rho_g,
+                     double* rho_l);
+
+const char* lb_last_error(const lb_handle* h);
+void lb_destroy(lb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBFE_H */

@@ -1,0 +1,502 @@
+// C-ABI entry points of liblbfe (declared and documented in include/lbfe.h):
+// validation, workspace layout, work-list construction and the launches of
+// the step, initialisation, field-export and reduction kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbfe.h"
+#include "aux_kernels.cuh"
+#include "launch.h"
+
+using namespace lbfe;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMinRows = 8;  // smallest row segment of a work item
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+int halo_of(int scheme) { return scheme == LB_IMPROVED ? 3 : 2; }
+
+int strip_width(int scheme) { return kStepThreads - 2 * halo_of(scheme); }
+
+int64_t max_items_of(const lb_case& c)
+{
+    const int64_t ns = (c.nx + strip_width(c.scheme) - 1) / strip_width(c.scheme);
+    return ns * ((c.ny + kMinRows - 1) / kMinRows);
+}
+
+struct Layout {
+    size_t cases32, cases64, items, f[2], scratch, partials, red, total;
+    std::vector<int64_t> off;  // element offset of each case in a population buffer
+    int64_t max_items = 0, max_nodes = 0, max_parts = 0;
+};
+
+Layout layout_of(const lb_case* cs, int n, int prec)
+{
+    Layout L;
+    const size_t es = prec == LB_FP32 ? 4 : 8;
+    size_t p = 0;
+    L.cases32 = p;
+    p = align_up(p + n * sizeof(DevCase<float>), kAlign);
+    L.cases64 = p;
+    p = align_up(p + n * sizeof(DevCase<double>), kAlign);
+    int64_t elems = 0;
+    for (int i = 0; i < n; ++i) {
+        L.max_items += max_items_of(cs[i]);
+        L.max_nodes = std::max<int64_t>(L.max_nodes, (int64_t)cs[i].nx * cs[i].ny);
+        L.max_parts = std::max<int64_t>(L.max_parts, (int64_t)((cs[i].nx + 255) / 256) * cs[i].ny);
+        L.off.push_back(elems);
+        elems += (int64_t)align_up((size_t)kQ * cs[i].ny * pitch_of(cs[i].nx) * es, kAlign) / es;
+    }
+    L.items = p;
+    p = align_up(p + L.max_items * sizeof(Item), kAlign);
+    for (int b = 0; b < 2; ++b) {
+        L.f[b] = p;
+        p = align_up(p + elems * es, kAlign);
+    }
+    L.scratch = p;  // eight FP64 fields of the largest case
+    p = align_up(p + 8 * align_up(L.max_nodes * sizeof(double), kAlign), kAlign);
+    L.partials = p;
+    p = align_up(p + L.max_parts * sizeof(Partial), kAlign);
+    L.red = p;
+    p = align_up(p + n * 8 * sizeof(double), kAlign);
+    L.total = p;
+    return L;
+}
+
+std::string check_case(const lb_case& c, int i)
+{
+    char buf[160];
+    auto bad = [&](const char* what) {
+        snprintf(buf, sizeof buf, "case %d: %s", i, what);
+        return std::string(buf);
+    };
+    if (c.nx < 3 || c.ny < 3) return bad("nx and ny must be >= 3");
+    if ((int64_t)c.nx * c.ny > (int64_t)1 << 31) return bad("lattice too large");
+    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return bad("unknown scheme");
+    if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
+    if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");
+    if (c.reserved != 0) return bad("reserved must be 0");
+    const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.tau_v, c.tau_e, c.tau_s, c.tau_q, c.pm_c0,
+                        c.nu, c.rho_ref};
+    for (double x : v)
+        if (!std::isfinite(x)) return bad("non-finite parameter");
+    if (!(c.a > 0 && c.b > 0 && c.R > 0 && c.T > 0 && c.kappa > 0)) return bad("a, b, R, T, kappa must be > 0");
+    if (!(c.tau_v > 0.5 && c.tau_e > 0.5 && c.tau_s > 0.5 && c.tau_q > 0.5))
+        return bad("relaxation times must be > 1/2");
+    if (c.nu < 0 || c.rho_ref < 0) return bad("nu and rho_ref must be >= 0");
+    return std::string();
+}
+
+template <typename T>
+DevCase<T> dev_case(const lb_case& c, int64_t off, double rho_ref)
+{
+    DevCase<T> d{};
+    d.nx = c.nx;
+    d.ny = c.ny;
+    d.pitch = pitch_of(c.nx);
+    d.off = off;
+    d.plane = (int64_t)c.ny * d.pitch;
+    d.RT = (T)(c.R * c.T);
+    d.a = (T)c.a;
+    d.b = (T)c.b;
+    d.kappa = (T)c.kappa;
+    d.c0 = (T)c.pm_c0;
+    d.rho_ref = (T)rho_ref;
+    const bool bgk = c.collision == LB_BGK;
+    d.lam_v = (T)(1.0 / c.tau_v);
+    d.lam_e = (T)(1.0 / (bgk ? c.tau_v : c.tau_e));
+    d.lam_s = (T)(1.0 / (bgk ? c.tau_v : c.tau_s));
+    d.lam_q = (T)(1.0 / (bgk ? c.tau_v : c.tau_q));
+    d.nu = (T)c.nu;
+    return d;
+}
+
+struct Group {
+    int scheme, coll, eos;
+    bool nu;
+    int64_t first, count;  // slice of the item array
+};
+
+}  // namespace
+
+struct lb_handle {
+    std::vector<lb_case> cases;
+    int prec = LB_FP32;
+    cudaStream_t stream = nullptr;
+    uint8_t* ws = nullptr;
+    Layout L;
+    int cur = 0;
+    std::vector<double> rho_ref;
+    std::vector<int64_t> steps;
+    std::vector<char> inited;
+    std::vector<Group> groups;
+    std::vector<Item> items;
+    std::string err;
+
+    void* fbuf(int b) const { return ws + L.f[b]; }
+    DevCase<float>* dc32() const { return reinterpret_cast<DevCase<float>*>(ws + L.cases32); }
+    DevCase<double>* dc64() const { return reinterpret_cast<DevCase<double>*>(ws + L.cases64); }
+    Item* ditems() const { return reinterpret_cast<Item*>(ws + L.items); }
+    double* scratch(int k) const
+    {
+        return reinterpret_cast<double*>(ws + L.scratch +
+                                         k * align_up(L.max_nodes * sizeof(double), kAlign));
+    }
+    Partial* partials() const { return reinterpret_cast<Partial*>(ws + L.partials); }
+    double* red() const { return reinterpret_cast<double*>(ws + L.red); }
+
+    lb_status fail(lb_status s, const std::string& m)
+    {
+        err = m;
+        return s;
+    }
+    lb_status cuda(cudaError_t e, const char* where)
+    {
+        if (e == cudaSuccess) return LB_OK;
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return LB_E_CUDA;
+    }
+    lb_status upload_case(int i)
+    {
+        const DevCase<float> c32 = dev_case<float>(cases[i], L.off[i], rho_ref[i]);
+        const DevCase<double> c64 = dev_case<double>(cases[i], L.off[i], rho_ref[i]);
+        lb_status s = cuda(cudaMemcpyAsync(dc32() + i, &c32, sizeof c32, cudaMemcpyHostToDevice, stream),
+                           "upload case");
+        if (s != LB_OK) return s;
+        s = cuda(cudaMemcpyAsync(dc64() + i, &c64, sizeof c64, cudaMemcpyHostToDevice, stream), "upload case");
+        if (s != LB_OK) return s;
+        return cuda(cudaStreamSynchronize(stream), "upload case");
+    }
+};
+
+namespace {
+
+// Split every case into column strips and row segments so that one launch
+// fills the GPU about once: each case gets a share of the resident block
+// slots proportional to its node count.
+void build_items(lb_handle* h)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int n = (int)h->cases.size();
+    h->items.clear();
+    h->groups.clear();
+    for (int s = 0; s < 2; ++s)
+        for (int co = 0; co < 2; ++co)
+            for (int e = 0; e < 2; ++e)
+                for (int nu = 0; nu < 2; ++nu) {
+                    std::vector<int> members;
+                    double nodes = 0;
+                    for (int i = 0; i < n; ++i) {
+                        const lb_case& c = h->cases[i];
+                        if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1)) {
+                            members.push_back(i);
+                            nodes += (double)c.nx * c.ny;
+                        }
+                    }
+                    if (members.empty()) continue;
+                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1)
+                                                       : occupancy_step_f64(s, co, e, nu == 1);
+                    const double slots = (double)sms * occ;
+                    Group g{s, co, e, nu == 1, (int64_t)h->items.size(), 0};
+                    const int W = strip_width(s);
+                    for (int i : members) {
+                        const lb_case& c = h->cases[i];
+                        const int ns = (c.nx + W - 1) / W;
+                        const double share = slots * ((double)c.nx * c.ny) / nodes;
+                        int nseg = std::max(1, (int)std::floor(share / ns));
+                        nseg = std::min(nseg, std::max(1, c.ny / kMinRows));
+                        for (int k = 0; k < ns; ++k) {
+                            const int x0 = (int)((int64_t)c.nx * k / ns);
+                            const int x1 = (int)((int64_t)c.nx * (k + 1) / ns);
+                            for (int q = 0; q < nseg; ++q) {
+                                const int y0 = (int)((int64_t)c.ny * q / nseg);
+                                const int y1 = (int)((int64_t)c.ny * (q + 1) / nseg);
+                                h->items.push_back(Item{i, x0, x1 - x0, y0, y1 - y0, 0});
+                            }
+                        }
+                    }
+                    g.count = (int64_t)h->items.size() - g.first;
+                    h->groups.push_back(g);
+                }
+}
+
+lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
+
+// Pull-moment, chemical-potential and velocity passes for one case; outputs
+// may be device pointers or NULL. Partials of the case land in h->partials().
+lb_status fields_pass(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
+{
+    const lb_case& c = h->cases[i];
+    const DevCase<double> cd = dev_case<double>(c, h->L.off[i], h->rho_ref[i]);
+    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2), *s3 = h->scratch(3);
+    if (h->prec == LB_FP32) {
+        const DevCase<float> cf = dev_case<float>(c, h->L.off[i], h->rho_ref[i]);
+        pull_moments_kernel<float><<<grd, blk, 0, h->stream>>>(cf, (const float*)h->fbuf(h->cur), s0, s1, s2);
+    } else {
+        pull_moments_kernel<double><<<grd, blk, 0, h->stream>>>(cd, (const double*)h->fbuf(h->cur), s0, s1, s2);
+    }
+    if (c.eos == LB_VDW)
+        mu_field_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+    else
+        mu_field_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+    if (c.scheme == LB_IMPROVED)
+        velocity_kernel<1><<<grd, blk, 0, h->stream>>>(cd, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
+    else
+        velocity_kernel<0><<<grd, blk, 0, h->stream>>>(cd, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
+    return h->cuda(cudaGetLastError(), "fields pass");
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_workspace_bytes(const lb_case* cases, int32_t ncases, int32_t precision, size_t* bytes)
+{
+    if (!cases || ncases <= 0 || !bytes || (precision != LB_FP32 && precision != LB_FP64))
+        return LB_E_INVALID;
+    for (int i = 0; i < ncases; ++i)
+        if (!check_case(cases[i], i).empty()) return LB_E_INVALID;
+    *bytes = layout_of(cases, ncases, precision).total;
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, void* d_workspace,
+                    size_t ws_bytes, void* cuda_stream, lb_handle** out)
+{
+    if (!out) return LB_E_INVALID;
+    *out = nullptr;
+    if (!cases || ncases <= 0 || (precision != LB_FP32 && precision != LB_FP64)) return LB_E_INVALID;
+    for (int i = 0; i < ncases; ++i)
+        if (!check_case(cases[i], i).empty()) return LB_E_INVALID;
+    Layout L = layout_of(cases, ncases, precision);
+    if (!d_workspace || ((uintptr_t)d_workspace % kAlign) != 0 || ws_bytes < L.total) return LB_E_WORKSPACE;
+    lb_handle* h = new lb_handle();
+    h->cases.assign(cases, cases + ncases);
+    h->prec = precision;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->ws = (uint8_t*)d_workspace;
+    h->L = L;
+    h->rho_ref.assign(ncases, 0.0);
+    for (int i = 0; i < ncases; ++i) h->rho_ref[i] = precision == LB_FP32 ? cases[i].rho_ref : 0.0;
+    h->steps.assign(ncases, 0);
+    h->inited.assign(ncases, 0);
+    build_items(h);
+    lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
+                                          cudaMemcpyHostToDevice, h->stream),
+                          "upload items");
+    for (int i = 0; i < ncases && s == LB_OK; ++i) s = h->upload_case(i);
+    if (s != LB_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
+                         const double* uy0, int32_t on_device)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size() || !rho0)
+        return h->fail(LB_E_INVALID, "lb_init_fields: bad case id or null rho0");
+    const lb_case& c = h->cases[case_id];
+    const int64_t N = (int64_t)c.nx * c.ny;
+    const size_t bytes = N * sizeof(double);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2), *s3 = h->scratch(3);
+    lb_status s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
+    if (s == LB_OK && ux0) s = h->cuda(cudaMemcpyAsync(s1, ux0, bytes, kind, h->stream), "copy ux0");
+    if (s == LB_OK && uy0) s = h->cuda(cudaMemcpyAsync(s2, uy0, bytes, kind, h->stream), "copy uy0");
+    if (s != LB_OK) return s;
+    // validate on the host (init is a one-off)
+    std::vector<double> r(N);
+    s = h->cuda(cudaMemcpyAsync(r.data(), s0, bytes, cudaMemcpyDeviceToHost, h->stream), "check rho0");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "check rho0");
+    if (s != LB_OK) return s;
+    double sum = 0.0;
+    for (double v : r) {
+        if (!(v > 0.0) || !std::isfinite(v)) return h->fail(LB_E_INVALID, "rho0 must be finite and > 0");
+        if (c.eos == LB_VDW && !(c.b * v < 1.0)) return h->fail(LB_E_INVALID, "rho0 outside 0 < b rho < 1");
+        if (c.eos == LB_CS && !(0.25 * c.b * v < 1.0)) return h->fail(LB_E_INVALID, "rho0 outside b rho/4 < 1");
+        sum += v;
+    }
+    if (h->prec == LB_FP32) h->rho_ref[case_id] = c.rho_ref > 0 ? c.rho_ref : sum / (double)N;
+    if ((s = h->upload_case(case_id)) != LB_OK) return s;
+    const DevCase<double> cd = dev_case<double>(c, h->L.off[case_id], h->rho_ref[case_id]);
+    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    if (c.eos == LB_VDW)
+        mu_field_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+    else
+        mu_field_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+    const double* pux = ux0 ? s1 : nullptr;
+    const double* puy = uy0 ? s2 : nullptr;
+    if (h->prec == LB_FP32) {
+        const DevCase<float> cf = dev_case<float>(c, h->L.off[case_id], h->rho_ref[case_id]);
+        if (c.scheme == LB_IMPROVED)
+            init_kernel<float, 1><<<grd, blk, 0, h->stream>>>(cf, cd, s0, pux, puy, s3, (float*)h->fbuf(h->cur));
+        else
+            init_kernel<float, 0><<<grd, blk, 0, h->stream>>>(cf, cd, s0, pux, puy, s3, (float*)h->fbuf(h->cur));
+    } else {
+        if (c.scheme == LB_IMPROVED)
+            init_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, pux, puy, s3, (double*)h->fbuf(h->cur));
+        else
+            init_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, pux, puy, s3, (double*)h->fbuf(h->cur));
+    }
+    if ((s = h->cuda(cudaGetLastError(), "init kernels")) != LB_OK) return s;
+    h->steps[case_id] = 0;
+    h->inited[case_id] = 1;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_handle* h, int64_t nsteps)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (nsteps < 0) return h->fail(LB_E_INVALID, "lb_step: nsteps < 0");
+    for (size_t i = 0; i < h->cases.size(); ++i)
+        if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_step: every case needs lb_init_fields first");
+    for (int64_t n = 0; n < nsteps; ++n) {
+        for (const Group& g : h->groups) {
+            cudaError_t e;
+            if (h->prec == LB_FP32)
+                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, (int)g.count, h->stream,
+                                    (const float*)h->fbuf(h->cur), (float*)h->fbuf(h->cur ^ 1), h->dc32(),
+                                    h->ditems() + g.first);
+            else
+                e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, h->stream,
+                                    (const double*)h->fbuf(h->cur), (double*)h->fbuf(h->cur ^ 1), h->dc64(),
+                                    h->ditems() + g.first);
+            if (e != cudaSuccess) return h->cuda(e, "step launch");
+        }
+        h->cur ^= 1;
+    }
+    for (auto& s : h->steps) s += nsteps;
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy, double* mu,
+                     int32_t on_device)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size()) return h->fail(LB_E_INVALID, "lb_moments: bad case id");
+    if (!h->inited[case_id]) return h->fail(LB_E_STATE, "lb_moments: case not initialised");
+    const lb_case& c = h->cases[case_id];
+    const size_t bytes = (size_t)c.nx * c.ny * sizeof(double);
+    double* outs[4] = {rho, ux, uy, mu};
+    double* dst[4];
+    for (int k = 0; k < 4; ++k) dst[k] = outs[k] ? (on_device ? outs[k] : h->scratch(4 + k)) : nullptr;
+    lb_status s = fields_pass(h, case_id, dst[0], dst[1], dst[2], dst[3]);
+    if (s != LB_OK) return s;
+    if (!on_device) {
+        for (int k = 0; k < 4 && s == LB_OK; ++k)
+            if (outs[k]) s = h->cuda(cudaMemcpyAsync(outs[k], dst[k], bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
+        if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "moments sync");
+    }
+    return s;
+}
+
+lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (!out) return h->fail(LB_E_INVALID, "lb_reductions: null out");
+    const int n = (int)h->cases.size();
+    for (int i = 0; i < n; ++i)
+        if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_reductions: case not initialised");
+    for (int i = 0; i < n; ++i) {
+        lb_status s = fields_pass(h, i, nullptr, nullptr, nullptr, nullptr);
+        if (s != LB_OK) return s;
+        const lb_case& c = h->cases[i];
+        const int64_t parts = (int64_t)((c.nx + 255) / 256) * c.ny;
+        finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), parts, (double)h->steps[i], h->red() + 8 * i);
+        if ((s = h->cuda(cudaGetLastError(), "finalize")) != LB_OK) return s;
+    }
+    std::vector<double> red((size_t)n * 8);
+    lb_status s = h->cuda(cudaMemcpyAsync(red.data(), h->red(), red.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, h->stream),
+                          "copy reductions");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "reductions sync");
+    if (s != LB_OK) return s;
+    bool unstable = false;
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 5; ++k) out[5 * i + k] = red[8 * i + k];
+        const bool bad = red[8 * i + 4] != 0.0 || !std::isfinite(red[8 * i]);
+        out[5 * i + 4] = 0.0;
+        if (case_status) case_status[i] = bad ? LB_E_UNSTABLE : LB_OK;
+        unstable |= bad;
+    }
+    if (unstable) return h->fail(LB_E_UNSTABLE, "a case has rho <= 0 or non-finite values");
+    return LB_OK;
+}
+
+lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes)
+{
+    if (!h || !bytes || case_id < 0 || case_id >= (int)h->cases.size()) return LB_E_INVALID;
+    const lb_case& c = h->cases[case_id];
+    const size_t es = h->prec == LB_FP32 ? 4 : 8;
+    *bytes = 16 + (size_t)kQ * c.ny * pitch_of(c.nx) * es;
+    return LB_OK;
+}
+
+lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lb_snapshot_bytes(h, case_id, &need) != LB_OK || !host_buf || bytes < need) {
+        if (h) h->err = "lb_save: bad arguments";
+        return LB_E_INVALID;
+    }
+    if (!h->inited[case_id]) return h->fail(LB_E_STATE, "lb_save: case not initialised");
+    const size_t es = h->prec == LB_FP32 ? 4 : 8;
+    uint8_t* p = (uint8_t*)host_buf;
+    int64_t st = h->steps[case_id];
+    memcpy(p, &st, 8);
+    memcpy(p + 8, &h->rho_ref[case_id], 8);
+    lb_status s = h->cuda(cudaMemcpyAsync(p + 16, (uint8_t*)h->fbuf(h->cur) + h->L.off[case_id] * es, need - 16,
+                                          cudaMemcpyDeviceToHost, h->stream),
+                          "save");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "save sync");
+    return s;
+}
+
+lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lb_snapshot_bytes(h, case_id, &need) != LB_OK || !host_buf || bytes < need) {
+        if (h) h->err = "lb_load: bad arguments";
+        return LB_E_INVALID;
+    }
+    const size_t es = h->prec == LB_FP32 ? 4 : 8;
+    const uint8_t* p = (const uint8_t*)host_buf;
+    int64_t st;
+    double rr;
+    memcpy(&st, p, 8);
+    memcpy(&rr, p + 8, 8);
+    if (st < 0 || !std::isfinite(rr) || rr < 0) return h->fail(LB_E_INVALID, "lb_load: corrupt snapshot header");
+    h->rho_ref[case_id] = h->prec == LB_FP32 ? rr : 0.0;
+    lb_status s = h->upload_case(case_id);
+    if (s == LB_OK)
+        s = h->cuda(cudaMemcpyAsync((uint8_t*)h->fbuf(h->cur) + h->L.off[case_id] * es, p + 16, need - 16,
+                                    cudaMemcpyHostToDevice, h->stream),
+                    "load");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "load sync");
+    if (s != LB_OK) return s;
+    h->steps[case_id] = st;
+    h->inited[case_id] = 1;
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void lb_destroy(lb_handle* h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// Device-side definitions shared by the sm_103a kernels of the free-energy
+// D2Q9 step: per-case parameter records, work items, the equations of state,
+// the lattice stencils and the closed-form moment-space collision.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lbfe {
+
+constexpr int kQ = 9;
+
+// Per-case parameters as the kernels read them (one record per case, in the
+// arithmetic type T of the launch).
+template <typename T>
+struct DevCase {
+    int32_t nx, ny, pitch, pad_;
+    int64_t off;    // element offset of the case inside a population buffer
+    int64_t plane;  // elements between two velocity planes: ny * pitch
+    T RT, a, b, kappa;
+    T c0;           // p_m = (c0 + mu_c)/3 (Eq. 24)
+    T rho_ref;      // populations are stored as f - w rho_ref
+    T lam_e, lam_s, lam_q, lam_v;  // 1/tau of Eq. 8 (all 1/tau_v for BGK)
+    T nu;           // > 0: tau_v from constant kinematic viscosity
+};
+
+// One block of work: output columns [x0, x0 + wv) and rows [y0, y0 + h) of a
+// case. A block computes a halo of columns around the strip itself.
+struct Item {
+    int32_t case_id, x0, wv, y0, h, pad_;
+};
+
+__host__ __device__ __forceinline__ int wrapi(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------- EOS
+// E_f'(rho): van der Waals (Eq. 30 without the kappa term) or
+// Carnahan-Starling, both written as R T h(rho) - 2 a rho.
+template <int EOS, typename T>
+__device__ __forceinline__ T dEf(const DevCase<T>& c, T rho);
+
+template <>
+__device__ __forceinline__ double dEf<0, double>(const DevCase<double>& c, double rho)
+{
+    double r = 1.0 / (1.0 - c.b * rho);
+    return c.RT * (log(rho * r) + r) - 2.0 * c.a * rho;
+}
+template <>
+__device__ __forceinline__ float dEf<0, float>(const DevCase<float>& c, float rho)
+{
+    float r = 1.0f / (1.0f - c.b * rho);
+    return c.RT * (logf(rho * r) + r) - 2.0f * c.a * rho;
+}
+template <>
+__device__ __forceinline__ double dEf<1, double>(const DevCase<double>& c, double rho)
+{
+    double n = 0.25 * c.b * rho;
+    double r = 1.0 / (1.0 - n);
+    double r2 = r * r;
+    return c.RT * (log(rho) + 1.0 + n * (4.0 - 3.0 * n) * r2 + n * (4.0 - 2.0 * n) * r2 * r) -
+           2.0 * c.a * rho;
+}
+template <>
+__device__ __forceinline__ float dEf<1, float>(const DevCase<float>& c, float rho)
+{
+    float n = 0.25f * c.b * rho;
+    float r = 1.0f / (1.0f - n);
+    float r2 = r * r;
+    return c.RT * (logf(rho) + 1.0f + n * (4.0f - 3.0f * n) * r2 + n * (4.0f - 2.0f * n) * r2 * r) -
+           2.0f * c.a * rho;
+}
+
+// ----------------------------------------------------------------- stencils
+// Values of a field around a node: C, E(x+1), W(x-1), N(y+1), S(y-1) and corners.
+// Isotropic Laplacian 6 sum_a w_a (phi(x+e_a) - phi(x)).
+template <typename T>
+__device__ __forceinline__ T lap9(T C, T E, T W, T N, T S, T NE, T NW, T SE, T SW)
+{
+    return (T(4) * ((E + W) + (N + S)) + ((NE + SW) + (NW + SE)) - T(20) * C) * T(1.0 / 6.0);
+}
+// Eq. 17: 3 sum_a w_a phi(x + e_a) e_a.
+template <typename T>
+__device__ __forceinline__ T gradx9(T E, T W, T NE, T NW, T SE, T SW)
+{
+    return (E - W) * T(1.0 / 3.0) + ((NE - SW) + (SE - NW)) * T(1.0 / 12.0);
+}
+template <typename T>
+__device__ __forceinline__ T grady9(T N, T S, T NE, T NW, T SE, T SW)
+{
+    return (N - S) * T(1.0 / 3.0) + ((NE - SW) + (NW - SE)) * T(1.0 / 12.0);
+}
+
+// --------------------------------------------------------------- collision
+// Moment-space collision of Eqs. 9 / 28 in closed form, on populations stored
+// as deviations d_a = f_a - w_a rho_ref (rho_ref = 0 gives plain populations).
+// Inputs: d[9] at the node, drho = sum d, rho = rho_ref + drho, jx, jy of d,
+// the force F, velocity u (Eq. 12), mu_c (for p_m), C1 and C7 (Eq. 29; zero for
+// the standard scheme) and the rates. Output: post-collision deviations.
+template <int SCHEME, typename T>
+__device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T ux, T uy, T Fx, T Fy,
+                                        T mu, T C1, T C7, T rho_ref, T c0, T lam_e, T lam_s,
+                                        T lam_q, T lam_v)
+{
+    // moments of d (rows of M)
+    const T sa = (d[1] + d[3]) + (d[2] + d[4]);
+    const T sd = (d[5] + d[7]) + (d[6] + d[8]);
+    const T m_e = T(2) * sd - sa - T(4) * d[0];
+    const T m_s = sd - T(2) * sa + T(4) * d[0];
+    const T dxd = (d[5] - d[7]) + (d[8] - d[6]);
+    const T dyd = (d[5] - d[7]) + (d[6] - d[8]);
+    const T m_qx = dxd - T(2) * (d[1] - d[3]);
+    const T m_qy = dyd - T(2) * (d[2] - d[4]);
+    const T m_pxx = (d[1] + d[3]) - (d[2] + d[4]);
+    const T m_pxy = (d[5] + d[7]) - (d[6] + d[8]);
+
+    // equilibria (Eq. 11 or Eq. 27) minus the moments of w rho_ref, which are
+    // rho_ref (1, -2, 1, 0, ...)
+    const T uxx = ux * ux, uyy = uy * uy, u2 = uxx + uyy;
+    T eq_e, eq_s, eq_qx, eq_qy;
+    if (SCHEME == 0) {
+        eq_e = T(3) * rho * u2 - T(2) * drho;
+        eq_s = drho - T(3) * rho * u2;
+        eq_qx = -rho * ux;
+        eq_qy = -rho * uy;
+    } else {
+        const T pm3 = c0 + mu;  // 3 p_m
+        eq_e = T(3) * rho * u2 - T(4) * rho + T(2) * pm3 + T(2) * rho_ref;
+        eq_s = T(4) * rho - T(3) * rho * u2 - T(3) * pm3 - rho_ref;
+        const T g2 = pm3 - T(2) * rho;  // rho (gamma - 2)
+        eq_qx = g2 * ux;
+        eq_qy = g2 * uy;
+    }
+    const T eq_pxx = rho * (uxx - uyy);
+    const T eq_pxy = rho * ux * uy;
+
+    // forcing moments S = M G (Eq. 14) and correction C (Eq. 29)
+    const T uF = ux * Fx + uy * Fy;
+    const T S_e = T(6) * uF + T(9) * C1;
+    const T S_s = T(-6) * uF;
+    const T S_pxx = T(2) * (ux * Fx - uy * Fy) + T(3) * C7;
+    const T S_pxy = ux * Fy + uy * Fx;
+
+    const T pe = m_e - lam_e * (m_e - eq_e) + (T(1) - T(0.5) * lam_e) * S_e;
+    const T ps = m_s - lam_s * (m_s - eq_s) + (T(1) - T(0.5) * lam_s) * S_s;
+    const T pqx = m_qx - lam_q * (m_qx - eq_qx) - (T(1) - T(0.5) * lam_q) * Fx;
+    const T pqy = m_qy - lam_q * (m_qy - eq_qy) - (T(1) - T(0.5) * lam_q) * Fy;
+    const T hv = T(1) - T(0.5) * lam_v;
+    const T pxx = m_pxx - lam_v * (m_pxx - eq_pxx) + hv * S_pxx;
+    const T pxy = m_pxy - lam_v * (m_pxy - eq_pxy) + hv * S_pxy;
+    const T pjx = jx + Fx;  // conserved: any rate gives j + F
+    const T pjy = jy + Fy;
+
+    // f* = M^-1 m*, M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const T a0 = drho * T(1.0 / 9.0);
+    const T a1 = pe * T(1.0 / 36.0);
+    const T a2 = ps * T(1.0 / 36.0);
+    const T a3 = pjx * T(1.0 / 6.0);
+    const T a4 = pqx * T(1.0 / 12.0);
+    const T a5 = pjy * T(1.0 / 6.0);
+    const T a6 = pqy * T(1.0 / 12.0);
+    const T a7 = pxx * T(0.25);
+    const T a8 = pxy * T(0.25);
+    const T b_ax = a0 - a1 - T(2) * a2;
+    const T b_dg = a0 + T(2) * a1 + a2;
+    const T ex = a3 - T(2) * a4, ey = a5 - T(2) * a6;
+    const T X = a3 + a4, Y = a5 + a6;
+    d[0] = a0 - T(4) * (a1 - a2);
+    d[1] = b_ax + ex + a7;
+    d[3] = b_ax - ex + a7;
+    d[2] = b_ax + ey - a7;
+    d[4] = b_ax - ey - a7;
+    d[5] = b_dg + (X + Y) + a8;
+    d[7] = b_dg - (X + Y) + a8;
+    d[6] = b_dg + (Y - X) - a8;
+    d[8] = b_dg + (X - Y) - a8;
+}
+
+// Shear rate at a node: constant, or from a constant kinematic viscosity.
+template <int SCHEME, bool NU, typename T>
+__device__ __forceinline__ T shear_rate(const DevCase<T>& c, T rho, T mu)
+{
+    if (!NU) return c.lam_v;
+    if (SCHEME == 1) return T(1) / (T(0.5) + c.nu * rho * T(3) / (c.c0 + mu));
+    return T(1) / (T(0.5) + T(3) * c.nu);
+}
+
+}  // namespace lbfe

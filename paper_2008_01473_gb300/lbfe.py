@@ -1,0 +1,225 @@
+"""Thin Python binding of liblbfe (the C ABI in include/lbfe.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of liblbfe. PyTorch supplies the device workspace and the CUDA stream. The
+library must have been built (``paper_2008_01473_gb300.build.build()``); if it
+is missing, importing the binding's loader raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields as dc_fields
+
+import numpy as np
+
+from .build import LIB
+
+STANDARD, IMPROVED = 0, 1
+BGK, MRT = 0, 1
+VDW, CS = 0, 1
+FP64, FP32 = 0, 1
+
+_STATUS = {0: "LB_OK", 1: "LB_E_INVALID", 2: "LB_E_CUDA", 3: "LB_E_UNSTABLE", 4: "LB_E_TIMEOUT",
+           5: "LB_E_WORKSPACE", 6: "LB_E_STATE"}
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _CCase(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("scheme", C.c_int32), ("collision", C.c_int32),
+                ("eos", C.c_int32), ("reserved", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("R", C.c_double), ("T", C.c_double), ("kappa", C.c_double), ("tau_v", C.c_double),
+                ("tau_e", C.c_double), ("tau_s", C.c_double), ("tau_q", C.c_double),
+                ("pm_c0", C.c_double), ("nu", C.c_double), ("rho_ref", C.c_double)]
+
+
+@dataclass
+class Case:
+    """One periodic case (mirrors ``lb_case``)."""
+    nx: int
+    ny: int
+    scheme: int = IMPROVED
+    collision: int = BGK
+    eos: int = VDW
+    a: float = 9.0 / 392.0
+    b: float = 2.0 / 21.0
+    R: float = 1.0
+    T: float = 0.8 / 14.0
+    kappa: float = 0.02
+    tau_v: float = 1.0
+    tau_e: float = 1.0
+    tau_s: float = 1.0
+    tau_q: float = 1.1
+    pm_c0: float = 1.0
+    nu: float = 0.0
+    rho_ref: float = 0.0
+
+    def cstruct(self) -> _CCase:
+        kw = {f.name: getattr(self, f.name) for f in dc_fields(self)}
+        return _CCase(reserved=0, **kw)
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load liblbfe; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"liblbfe is not built ({LIB} missing); run paper_2008_01473_gb300.build.build()")
+        L = C.CDLL(LIB)
+        vp, i32, i64, dp, sz = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_size_t
+        cp = C.POINTER(_CCase)
+        L.lb_workspace_bytes.argtypes = [cp, i32, i32, C.POINTER(sz)]
+        L.lb_create.argtypes = [cp, i32, i32, vp, sz, vp, C.POINTER(vp)]
+        L.lb_init_fields.argtypes = [vp, i32, vp, vp, vp, i32]
+        L.lb_step.argtypes = [vp, i64]
+        L.lb_moments.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+        L.lb_reductions.argtypes = [vp, dp, C.POINTER(i32)]
+        L.lb_snapshot_bytes.argtypes = [vp, i32, C.POINTER(sz)]
+        L.lb_save.argtypes = [vp, i32, vp, sz]
+        L.lb_load.argtypes = [vp, i32, vp, sz]
+        L.lb_critical.argtypes = [i32, C.c_double, C.c_double, C.c_double, dp, dp]
+        L.lb_maxwell.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
+        L.lb_last_error.argtypes = [vp]
+        L.lb_last_error.restype = C.c_char_p
+        L.lb_destroy.argtypes = [vp]
+        L.lb_destroy.restype = None
+        for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
+                     "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int, h=None, what: str = ""):
+    if st != 0:
+        msg = lib().lb_last_error(h).decode() if h else what
+        raise LBError(st, msg or what)
+
+
+def critical(eos: int, a: float, b: float, R: float = 1.0) -> tuple[float, float]:
+    """(T_c, rho_c) from the host solver of liblbfe."""
+    tc, rc = C.c_double(), C.c_double()
+    _check(lib().lb_critical(eos, a, b, R, C.byref(tc), C.byref(rc)), what="lb_critical")
+    return tc.value, rc.value
+
+
+def maxwell(eos: int, a: float, b: float, R: float, T: float) -> tuple[float, float]:
+    """Maxwell coexistence densities (rho_g, rho_l) from the host solver of liblbfe."""
+    g, l = C.c_double(), C.c_double()
+    _check(lib().lb_maxwell(eos, a, b, R, T, C.byref(g), C.byref(l)), what="lb_maxwell")
+    return g.value, l.value
+
+
+def _host_f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+class Lattice:
+    """A set of independent periodic cases stepped together on one GPU."""
+
+    def __init__(self, cases, precision: int = FP32, device=None, stream=None):
+        import torch
+
+        self.cases = list(cases)
+        self.precision = precision
+        self._torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        arr = (_CCase * len(self.cases))(*[c.cstruct() for c in self.cases])
+        self._carr = arr
+        nb = C.c_size_t()
+        _check(lib().lb_workspace_bytes(arr, len(self.cases), precision, C.byref(nb)),
+               what="lb_workspace_bytes: invalid case parameters")
+        self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        _check(lib().lb_create(arr, len(self.cases), precision, C.c_void_p(self._ws_ptr), nb.value,
+                               C.c_void_p(self.stream.cuda_stream), C.byref(h)), what="lb_create")
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    def _ptr_of(self, a, shape):
+        """(pointer, on_device, keepalive) for a host array or a CUDA tensor of FP64."""
+        torch = self._torch
+        if a is None:
+            return None, 0, None
+        if isinstance(a, torch.Tensor) and a.is_cuda:
+            t = a.detach().to(torch.float64).contiguous()
+            assert tuple(t.shape) == shape, (t.shape, shape)
+            return C.c_void_p(t.data_ptr()), 1, t
+        h = _host_f64(a.cpu().numpy() if isinstance(a, torch.Tensor) else a)
+        assert h.shape == shape, (h.shape, shape)
+        return C.c_void_p(h.ctypes.data), 0, h
+
+    def _shape(self, case_id):
+        c = self.cases[case_id]
+        return (c.ny, c.nx)
+
+    # ---------------------------------------------------------------------- API
+    def init_fields(self, case_id: int, rho0, ux0=None, uy0=None):
+        sh = self._shape(case_id)
+        p, dev, k0 = self._ptr_of(rho0, sh)
+        pu, devu, k1 = self._ptr_of(ux0, sh)
+        pv, devv, k2 = self._ptr_of(uy0, sh)
+        if (ux0 is not None and devu != dev) or (uy0 is not None and devv != dev):
+            raise ValueError("rho0, ux0 and uy0 must all be on the host or all on the device")
+        _check(lib().lb_init_fields(self._h, case_id, p, pu, pv, dev), self._h)
+        del k0, k1, k2
+
+    def step(self, nsteps: int = 1):
+        _check(lib().lb_step(self._h, int(nsteps)), self._h)
+
+    def moments(self, case_id: int, on_device: bool = False):
+        """dict rho, ux, uy, mu of the current state (numpy, or CUDA tensors)."""
+        sh = self._shape(case_id)
+        torch = self._torch
+        if on_device:
+            out = {k: torch.empty(sh, dtype=torch.float64, device=self.device) for k in ("rho", "ux", "uy", "mu")}
+            ptrs = [C.c_void_p(out[k].data_ptr()) for k in ("rho", "ux", "uy", "mu")]
+        else:
+            out = {k: np.empty(sh) for k in ("rho", "ux", "uy", "mu")}
+            ptrs = [C.c_void_p(out[k].ctypes.data) for k in ("rho", "ux", "uy", "mu")]
+        _check(lib().lb_moments(self._h, case_id, *ptrs, 1 if on_device else 0), self._h)
+        return out
+
+    def reductions(self, raise_unstable: bool = False):
+        """(out[ncases, 5] = mass, ke, umax, steps, 0; status[ncases])."""
+        n = len(self.cases)
+        out = np.zeros((n, 5))
+        st = np.zeros(n, dtype=np.int32)
+        rc = lib().lb_reductions(self._h, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                 st.ctypes.data_as(C.POINTER(C.c_int32)))
+        if rc != 0 and (rc != 3 or raise_unstable):
+            _check(rc, self._h)
+        return out, st
+
+    def save(self, case_id: int) -> bytes:
+        nb = C.c_size_t()
+        _check(lib().lb_snapshot_bytes(self._h, case_id, C.byref(nb)), self._h)
+        buf = (C.c_uint8 * nb.value)()
+        _check(lib().lb_save(self._h, case_id, buf, nb.value), self._h)
+        return bytes(buf)
+
+    def load(self, case_id: int, snap: bytes):
+        buf = (C.c_uint8 * len(snap)).from_buffer_copy(snap)
+        _check(lib().lb_load(self._h, case_id, buf, len(snap)), self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

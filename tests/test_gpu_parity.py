@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+FP64 runs must agree to 1e-11 max-abs in rho and u (round-off only: the
+GPU fuses multiply-adds and sums in another order). FP32 runs store
+populations as deviations from w_a rho_ref and compute in FP32; their
+tolerances are stated per test.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import thermo
+from paper_2008_01473_gb300 import inputs, lbfe
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_01473_gb300 import build
+
+    build.build()
+
+
+def _pair(nx, ny, scheme, collision, eos="vdw", t=0.8, tau=0.8, nu=0.0, kappa=0.02, tau_e=1.0,
+          tau_s=1.0, tau_q=1.1):
+    e = thermo.vdw_paper() if eos == "vdw" else thermo.EOS(thermo.CS, 9 / 392, 9 / 98)
+    T, rg, rl = thermo.maxwell_reduced(e, t)
+    kw = dict(nx=nx, ny=ny, scheme=scheme, collision=collision, eos=e.kind, a=e.a, b=e.b, R=1.0, T=T,
+              kappa=kappa, tau_v=tau, tau_e=tau_e, tau_s=tau_s, tau_q=tau_q, nu=nu)
+    return lbfe.Case(**kw), O.Case(**kw), rg, rl
+
+
+def _gpu_run(cases, rho0s, steps, precision, u0s=None):
+    lat = lbfe.Lattice(cases, precision=precision)
+    for i, r in enumerate(rho0s):
+        ux0, uy0 = (u0s[i] if u0s else (None, None))
+        lat.init_fields(i, r, ux0, uy0)
+    lat.step(steps)
+    out = [lat.moments(i) for i in range(len(cases))]
+    return lat, out
+
+
+def _oracle_run(oc, rho0, steps, ux0=None, uy0=None):
+    f = O.init(oc, rho0, ux0, uy0)
+    assert O.step(oc, f, steps) == steps
+    return f, O.fields(oc, f)
+
+
+def _maxerr(m, ref):
+    return max(np.abs(m["rho"] - ref.rho).max(), np.abs(m["ux"] - ref.ux).max(),
+               np.abs(m["uy"] - ref.uy).max())
+
+
+def _gpu_pops(lat, i):
+    """Populations of case i as FP64 f[9, ny, nx] (deviation storage undone)."""
+    c = lat.cases[i]
+    snap = lat.save(i)
+    rho_ref = np.frombuffer(snap[8:16], dtype=np.float64)[0]
+    dt = np.float32 if lat.precision == lbfe.FP32 else np.float64
+    pitch = (c.nx + 31) // 32 * 32
+    raw = np.frombuffer(snap[16:], dtype=dt).reshape(9, c.ny, pitch)[:, :, :c.nx].astype(np.float64)
+    return raw + W[:, None, None] * rho_ref
+
+
+# --------------------------------------------------------------------- FP64
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+def test_fp64_droplet_64_1000_steps(scheme):
+    """64 x 64 droplet of radius 16 (the small droplet set-up), BGK tau = 0.8,
+    1000 FP64 steps: rho and u within 1e-11 of the oracle."""
+    gc, oc, rg, rl = _pair(64, 64, scheme, lbfe.BGK)
+    rho0 = inputs.droplet(64, 64, 16.0, rl, rg, noise=1e-4, seed=0)
+    lat, (m,) = _gpu_run([gc], [rho0], 1000, lbfe.FP64)
+    _, ref = _oracle_run(oc, rho0, 1000)
+    assert _maxerr(m, ref) < 1e-11
+    assert np.abs(m["mu"] - ref.mu).max() < 1e-11
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
+@pytest.mark.parametrize("eos", ["vdw", "cs"])
+@pytest.mark.parametrize("shape", [(530, 37), (7, 300), (3, 3), (5, 4), (257, 9)])
+def test_fp64_ragged_shapes(scheme, collision, eos, shape):
+    """Several strips and row segments, ragged tails, and degenerate lattices
+    (3 x 3 wraps the halo more than once): 12 FP64 steps, element-wise."""
+    nx, ny = shape
+    gc, oc, rg, rl = _pair(nx, ny, scheme, collision, eos=eos, t=0.9)
+    rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=5)
+    ux0 = 0.01 * (2 * inputs.splitmix_uniform(2, 0, nx, ny) - 1)
+    uy0 = 0.01 * (2 * inputs.splitmix_uniform(3, 0, nx, ny) - 1)
+    lat, (m,) = _gpu_run([gc], [rho0], 12, lbfe.FP64, u0s=[(ux0, uy0)])
+    f_ref, ref = _oracle_run(oc, rho0, 12, ux0, uy0)
+    assert _maxerr(m, ref) < 1e-12
+    np.testing.assert_allclose(_gpu_pops(lat, 0), f_ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+def test_fp64_constant_nu(scheme):
+    """Constant kinematic viscosity (tau_v from eta = nu rho per node)."""
+    gc, oc, rg, rl = _pair(48, 40, scheme, lbfe.MRT, nu=0.1)
+    rho0 = inputs.droplet(48, 40, 10.0, rl, rg, noise=1e-3, seed=1)
+    _, (m,) = _gpu_run([gc], [rho0], 200, lbfe.FP64)
+    _, ref = _oracle_run(oc, rho0, 200)
+    assert _maxerr(m, ref) < 1e-11
+
+
+def test_fp64_batched_uneven_cases():
+    """Mixed sizes, schemes, EOS and parameters in one Lattice: each case
+    equals the oracle, and the batched result is bit-identical to the same
+    case run alone."""
+    specs = [(96, 80, lbfe.IMPROVED, lbfe.BGK, "vdw", 0.8, 0.8), (33, 41, lbfe.IMPROVED, lbfe.BGK, "vdw", 0.85, 1.0),
+             (300, 12, lbfe.STANDARD, lbfe.MRT, "cs", 0.9, 0.7), (17, 17, lbfe.IMPROVED, lbfe.MRT, "cs", 0.95, 0.6)]
+    gcs, ocs, rhos = [], [], []
+    for k, (nx, ny, s, co, eos, t, tau) in enumerate(specs):
+        gc, oc, rg, rl = _pair(nx, ny, s, co, eos=eos, t=t, tau=tau)
+        gcs.append(gc)
+        ocs.append(oc)
+        rhos.append(inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=k))
+    lat, ms = _gpu_run(gcs, rhos, 60, lbfe.FP64)
+    for k in range(len(specs)):
+        _, ref = _oracle_run(ocs[k], rhos[k], 60)
+        assert _maxerr(ms[k], ref) < 1e-11
+        _, (alone,) = _gpu_run([gcs[k]], [rhos[k]], 60, lbfe.FP64)
+        for key in ("rho", "ux", "uy", "mu"):
+            assert np.array_equal(alone[key], ms[k][key])
+
+
+def test_fp64_reductions_and_resume():
+    """FP64 reductions (mass, kinetic energy, max |u|) match the oracle, and
+    save/load resumes bit-exactly."""
+    gc, oc, rg, rl = _pair(70, 50, lbfe.IMPROVED, lbfe.MRT)
+    rho0 = inputs.droplet(70, 50, 12.0, rl, rg, noise=1e-3, seed=2)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    lat.init_fields(0, rho0)
+    lat.step(40)
+    snap = lat.save(0)
+    lat.step(30)
+    a = lat.moments(0)
+    out, st = lat.reductions()
+    f, _ = _oracle_run(oc, rho0, 70)
+    red = O.reductions(oc, f)
+    assert st[0] == 0 and out[0, 3] == 70
+    assert abs(out[0, 0] / red["mass"] - 1) < 1e-13
+    assert abs(out[0, 1] - red["ke"]) < 1e-13 * max(1.0, red["ke"]) + 1e-18
+    assert abs(out[0, 2] - red["umax"]) < 1e-12
+    lat.load(0, snap)
+    lat.step(30)
+    b = lat.moments(0)
+    for key in a:
+        assert np.array_equal(a[key], b[key])
+
+
+def test_unstable_case_flagged_others_kept():
+    """A case that blows up (Carnahan-Starling a=1, b=4, kappa=0.02 at
+    0.5 T_c) is reported unstable while a stable case in the same launch
+    stays finite and correct."""
+    e = thermo.cs_unit()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.5)
+    bad = lbfe.Case(nx=64, ny=8, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.CS, a=1.0, b=4.0, T=T,
+                    kappa=0.02, tau_v=1.0)
+    gc, oc, rg2, rl2 = _pair(40, 40, lbfe.IMPROVED, lbfe.BGK)
+    r_bad = inputs.slab(64, 8, rl, rg)
+    r_ok = inputs.droplet(40, 40, 10.0, rl2, rg2)
+    lat = lbfe.Lattice([bad, gc], precision=lbfe.FP64)
+    lat.init_fields(0, r_bad)
+    lat.init_fields(1, r_ok)
+    lat.step(50)
+    out, st = lat.reductions()
+    assert st[0] == 3 and st[1] == 0
+    with pytest.raises(lbfe.LBError):
+        lat.reductions(raise_unstable=True)
+    _, ref = _oracle_run(oc, r_ok, 50)
+    assert _maxerr(lat.moments(1), ref) < 1e-11
+
+
+def test_invalid_inputs_rejected():
+    gc, _, rg, rl = _pair(16, 16, lbfe.IMPROVED, lbfe.BGK)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+    with pytest.raises(lbfe.LBError):
+        lat.step(1)  # before init
+    r = inputs.droplet(16, 16, 4.0, rl, rg)
+    r[3, 3] = np.nan
+    with pytest.raises(lbfe.LBError):
+        lat.init_fields(0, r)
+    r[3, 3] = -1.0
+    with pytest.raises(lbfe.LBError):
+        lat.init_fields(0, r)
+
+
+# --------------------------------------------------------------------- FP32
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
+def test_fp32_one_step_elementwise(scheme, collision):
+    """One FP32 step from the GPU's own state against the oracle step from the
+    same (FP32-representable) populations: post-step populations within
+    3e-6 of max |f| (a few FP32 roundings of O(1) quantities)."""
+    gc, oc, rg, rl = _pair(530, 37, scheme, collision, t=0.85)
+    rho0 = inputs.droplet(530, 37, 12.0, rl, rg, noise=1e-3, seed=9)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+    lat.init_fields(0, rho0)
+    lat.step(5)
+    f0 = _gpu_pops(lat, 0)
+    lat.step(1)
+    f1 = _gpu_pops(lat, 0)
+    g = f0.copy()
+    O.step(oc, g, 1)
+    assert np.abs(f1 - g).max() < 3e-6 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+def test_fp32_droplet_500_steps(scheme):
+    """500 FP32 steps of a 64 x 64 droplet against the FP64 oracle: rho within
+    2e-5 relative to rho_l, u within 2e-6 absolute."""
+    gc, oc, rg, rl = _pair(64, 64, scheme, lbfe.BGK)
+    rho0 = inputs.droplet(64, 64, 16.0, rl, rg, noise=1e-4, seed=0)
+    _, (m,) = _gpu_run([gc], [rho0], 500, lbfe.FP32)
+    _, ref = _oracle_run(oc, rho0, 500)
+    assert np.abs(m["rho"] - ref.rho).max() < 2e-5 * rl
+    assert max(np.abs(m["ux"] - ref.ux).max(), np.abs(m["uy"] - ref.uy).max()) < 2e-6
+
+
+def test_fp32_full_size_sampled_nodes():
+    """The 4096 x 4096 spinodal lattice in the benchmark's launch
+    configuration (improved, MRT, FP32): for 24 sampled nodes the oracle's
+    one-step update of a 13 x 13 patch around the node (whose centre depends
+    on nodes within 4 sites) matches the GPU's post-step populations."""
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    n = 4096
+    gc = lbfe.Case(nx=n, ny=n, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
+                   kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
+    oc = O.Case(nx=13, ny=13, scheme=O.IMPROVED, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02,
+                tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+    lat.init_fields(0, inputs.spinodal(n, n, 0.5 * (rg + rl), 0.01, seed=3))
+    lat.step(20)
+    f0 = _gpu_pops(lat, 0)
+    lat.step(1)
+    f1 = _gpu_pops(lat, 0)
+    rng = np.random.default_rng(0)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (240, 17), (241, 4095)] + \
+          [tuple(rng.integers(0, n, 2)) for _ in range(18)]
+    for (y, x) in pts:
+        ys = (np.arange(y - 6, y + 7)) % n
+        xs = (np.arange(x - 6, x + 7)) % n
+        patch = np.ascontiguousarray(f0[:, ys][:, :, xs])
+        O.step(oc, patch, 1)
+        got = f1[:, y, x]
+        assert np.abs(got - patch[:, 6, 6]).max() < 3e-6 * np.abs(patch[:, 6, 6]).max(), (y, x)
