@@ -126,7 +126,12 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
 lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes);
 
 /* Copy case case_id's populations and step counter to / from host memory
- * (bit-exact resume). host_buf must hold lb_snapshot_bytes bytes. */
+ * (bit-exact resume). host_buf must hold lb_snapshot_bytes bytes. Layout:
+ * int64 step counter, double rho_ref, then the stored populations
+ * [9][ny][pitch] (pitch = nx rounded up to a multiple of 32) in the storage
+ * form of the library: post-collision values before streaming, so that
+ * f_a(x) at the current step is element x - e_a of plane a (periodic);
+ * FP32 planes hold f_a - w_a rho_ref. */
 lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes);
 lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes);
 

@@ -54,9 +54,15 @@ __global__ void init_kernel(DevCase<T> c, DevCase<double> cd, const double* __re
                             cd.c0, 1.0, 1.0, 1.0, 1.0);
     // with d = 0 the moments m_e, m_s, ... of d vanish, so the rates-1 collision
     // leaves exactly the equilibrium; the conserved entries are set from
-    // drho and rho u directly
-    const int64_t o = (int64_t)y * c.pitch + x;
-    for (int a = 0; a < kQ; ++a) f[c.off + a * c.plane + o] = (T)d[a];
+    // drho and rho u directly.
+    // Storage holds post-collision populations before streaming (the step
+    // pulls f_a(x) from x - e_a), so f_a(0) of node x is stored at x - e_a.
+    constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int a = 0; a < kQ; ++a) {
+        const int64_t o = (int64_t)wrapi(y - ey[a], c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
+        f[c.off + a * c.plane + o] = (T)d[a];
+    }
 }
 
 // Pull the populations of the current state into FP64 rho, j_x, j_y fields.

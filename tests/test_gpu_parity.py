@@ -58,15 +58,22 @@ def _maxerr(m, ref):
                np.abs(m["uy"] - ref.uy).max())
 
 
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+
+
 def _gpu_pops(lat, i):
-    """Populations of case i as FP64 f[9, ny, nx] (deviation storage undone)."""
+    """Populations of case i as FP64 f[9, ny, nx] at the nodes, in the oracle's
+    convention: the snapshot holds post-collision values before streaming, so
+    f_a(x) = stored_a(x - e_a); deviation storage is undone."""
     c = lat.cases[i]
     snap = lat.save(i)
     rho_ref = np.frombuffer(snap[8:16], dtype=np.float64)[0]
     dt = np.float32 if lat.precision == lbfe.FP32 else np.float64
     pitch = (c.nx + 31) // 32 * 32
     raw = np.frombuffer(snap[16:], dtype=dt).reshape(9, c.ny, pitch)[:, :, :c.nx].astype(np.float64)
-    return raw + W[:, None, None] * rho_ref
+    f = np.stack([np.roll(raw[a], shift=(EY[a], EX[a]), axis=(0, 1)) for a in range(9)])
+    return f + W[:, None, None] * rho_ref
 
 
 # --------------------------------------------------------------------- FP64
