@@ -105,8 +105,8 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
                          const double* uy0, int32_t on_device);
 
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
- * Eq. 10). Enqueued asynchronously; the last step of the call also records
- * per-case mass, kinetic energy and max|u| for lb_reductions. */
+ * Eq. 10): one fused kernel launch per step and per group of cases that
+ * share scheme, collision, EOS and viscosity mode. Enqueued asynchronously. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of case case_id at the current step: rho and u of
@@ -115,11 +115,12 @@ lb_status lb_step(lb_handle* h, int64_t nsteps);
 lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy,
                      double* mu, int32_t on_device);
 
-/* Per-case results of the last lb_step call, FP64 sums in a fixed order:
+/* Reductions of every case's current state, FP64 sums in a fixed order:
  * out[5*c + {0,1,2,3,4}] = {mass sum rho, kinetic energy sum rho|u|^2/2,
- * max |u|, step count, 0}; case_status[c] = LB_OK or LB_E_UNSTABLE.
- * Host pointers; synchronises the stream. Returns LB_E_UNSTABLE if any case
- * is unstable (the others keep their values). */
+ * max |u|, step count, 0} with rho, u of Eq. 12; case_status[c] = LB_OK or
+ * LB_E_UNSTABLE (rho <= 0 or a non-finite value at some node). Host
+ * pointers (case_status may be NULL); synchronises the stream. Returns
+ * LB_E_UNSTABLE if any case is unstable; every entry is still written. */
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
 
 /* Bytes of one case's snapshot (populations + step counter) for lb_save. */
