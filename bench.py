@@ -96,7 +96,6 @@ class Clocks:
 
 
 def run_gpu(args):
-    import numpy as np
     import torch
 
     from paper_2008_01473_gb300 import build, inputs, lbfe
@@ -111,10 +110,11 @@ def run_gpu(args):
     tc, _ = lbfe.critical(lbfe.VDW, **VDW)
     T = T_RED * tc
     rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], T)
-    case = lbfe.Case(nx=N_SIDE, ny=N_SIDE, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, T=T,
+    n_side = args.side
+    case = lbfe.Case(nx=n_side, ny=n_side, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, T=T,
                      kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW)
-    nodes = N_SIDE * N_SIDE
-    rho0 = inputs.spinodal(N_SIDE, N_SIDE, 0.5 * (rg + rl), 0.01, seed=1 + rank)
+    nodes = n_side * n_side
+    rho0 = inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), 0.01, seed=1 + rank)
     rho0_pin = torch.from_numpy(rho0).pin_memory()
     lat = lbfe.Lattice([case], precision=lbfe.FP32, device=f"cuda:{local}")
     stream = lat.stream
@@ -150,7 +150,7 @@ def run_gpu(args):
     stable = bool(st[0] == 0)
 
     # ------------------------------------------------------------ end to end
-    res = {k: torch.empty((N_SIDE, N_SIDE), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
+    res = {k: torch.empty((n_side, n_side), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
     barrier()
     t0 = time.perf_counter()
     lat.init_fields(0, rho0_pin)
@@ -176,9 +176,10 @@ def run_gpu(args):
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": N_SIDE, "ny": N_SIDE, "nodes_per_gpu": nodes,
+            "config": {"workload": WORKLOAD.replace(f"{N_SIDE}x{N_SIDE}", f"{n_side}x{n_side}"),
+                       "nx": n_side, "ny": n_side, "nodes_per_gpu": nodes,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                       "l2": "populations 1.21 GB per step > 129 MB L2 (no flush needed)",
+                       "l2": f"populations {2 * 36 * nodes / 1e9:.2f} GB per step vs 129 MB L2 (no flush)",
                        "stable": stable},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
@@ -253,6 +254,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=150)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
