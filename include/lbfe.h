@@ -143,6 +143,38 @@ lb_status lb_critical(int32_t eos, double a, double b, double R, double* Tc, dou
 lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double* rho_g,
                      double* rho_l);
 
+/* lb_fields_static: the field-export and reduction pass of lb_moments and
+ * lb_reductions without any device allocation and without a handle. The
+ * paper has no counterpart; this exists for callers that cannot call
+ * cudaMalloc or hand the library a workspace: plug-ins running inside an
+ * application or framework that owns all device memory through its own
+ * pool, and code on paths where an allocation would synchronise the device
+ * or is forbidden (real-time loops, restricted embedding environments).
+ *
+ * Inputs: one case c (nx, ny, scheme, eos, a, b, R, T, kappa, pm_c0 are used)
+ * and d_pops, a device array of its populations in the snapshot layout of
+ * lb_save ([9][ny][pitch], pitch = nx rounded up to 32, storage form of the
+ * library; FP32 planes hold f_a - w_a rho_ref). Outputs (device pointers):
+ * d_rho, d_ux, d_uy, d_mu [ny][nx] as in lb_moments (each may be NULL) and
+ * d_red[5] = {mass, kinetic energy, max |u|, 0, count of nodes with rho <= 0
+ * or non-finite values}. Work is enqueued on cuda_stream; nothing is
+ * synchronised.
+ *
+ * Scratch: a fixed device array inside the library, sized for
+ * nx, ny <= LB_STATIC_MAX_SIDE and nx * ny <= LB_STATIC_MAX_NODES (about
+ * 8.5 MB, held on every GPU that loads the library until the process exits).
+ * Larger cases are rejected with LB_E_INVALID before anything is enqueued.
+ * The first call on a device looks up the array's device address (a CUDA
+ * runtime call); make that first call before any stream capture. Every call
+ * on a device shares the one array: calls whose work may overlap on the GPU
+ * (different streams without ordering, or concurrent host threads) race and
+ * must be serialised by the caller. */
+#define LB_STATIC_MAX_SIDE 4096
+#define LB_STATIC_MAX_NODES 262144
+lb_status lb_fields_static(const lb_case* c, int32_t precision, const void* d_pops, double rho_ref,
+                           double* d_rho, double* d_ux, double* d_uy, double* d_mu, double* d_red,
+                           void* cuda_stream);
+
 const char* lb_last_error(const lb_handle* h);
 void lb_destroy(lb_handle* h);
 

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<double> cd, const
 
 // Fold a case's partials in a fixed order into out[0..4] =
 // {mass, kinetic energy, max |u|, steps, bad-node count}.
-__global__ void finalize_kernel(const Partial* __restrict__ partials, int64_t n, double steps,
+static __global__ void finalize_kernel(const Partial* __restrict__ partials, int64_t n, double steps,
                                 double* __restrict__ out)
 {
     __shared__ double s[4][256];

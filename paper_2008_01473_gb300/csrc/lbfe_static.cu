@@ -1,0 +1,119 @@
+// lb_fields_static: the field-export and reduction pass of lb_moments /
+// lb_reductions for callers that cannot allocate device memory. Its scratch
+// lives in a file-scope device array of fixed size instead of the caller's
+// workspace; see include/lbfe.h for the contract.
+#include <cmath>
+#include <mutex>
+
+#include "../../include/lbfe.h"
+#include "aux_kernels.cuh"
+
+using namespace lbfe;
+
+namespace {
+
+constexpr int64_t kMaxNodes = LB_STATIC_MAX_NODES;
+constexpr int kMaxSide = LB_STATIC_MAX_SIDE;
+// partials of velocity_kernel: ceil(nx / 256) * ny <= nodes / 256 + ny
+constexpr int64_t kMaxParts = kMaxNodes / 256 + kMaxSide;
+constexpr size_t kFieldBytes = kMaxNodes * sizeof(double);
+constexpr size_t kScratchBytes = 4 * kFieldBytes + kMaxParts * sizeof(Partial);
+
+constexpr int kMaxDevices = 256;
+template <typename T>
+DevCase<T> make_case(const lb_case& c, double rho_ref)
+{
+    DevCase<T> d{};
+    d.nx = c.nx;
+    d.ny = c.ny;
+    d.pitch = (c.nx + 31) / 32 * 32;
+    d.off = 0;
+    d.plane = (int64_t)c.ny * d.pitch;
+    d.RT = (T)(c.R * c.T);
+    d.a = (T)c.a;
+    d.b = (T)c.b;
+    d.kappa = (T)c.kappa;
+    d.c0 = (T)c.pm_c0;
+    d.rho_ref = (T)rho_ref;
+    return d;
+}
+
+bool valid_case(const lb_case& c)
+{
+    if (c.nx < 3 || c.ny < 3) return false;
+    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return false;
+    if (c.eos != LB_VDW && c.eos != LB_CS) return false;
+    const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.pm_c0};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return c.a > 0 && c.b > 0 && c.R > 0 && c.T > 0 && c.kappa > 0;
+}
+
+}  // namespace
+
+// Scratch of lb_fields_static: shared by every call on a device and held by
+// every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+namespace {
+std::mutex g_mu;
+void* g_ptr[kMaxDevices] = {};
+
+// Device address of g_scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, not a device address).
+cudaError_t scratch_ptr(void** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_ptr[dev] = p;
+    }
+    *out = g_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const void* d_pops,
+                                      double rho_ref, double* d_rho, double* d_ux, double* d_uy,
+                                      double* d_mu, double* d_red, void* cuda_stream)
+{
+    if (!c || !d_pops || !d_red || !valid_case(*c)) return LB_E_INVALID;
+    if (precision != LB_FP32 && precision != LB_FP64) return LB_E_INVALID;
+    if (!std::isfinite(rho_ref) || rho_ref < 0) return LB_E_INVALID;
+    if (c->nx > kMaxSide || c->ny > kMaxSide || (int64_t)c->nx * c->ny > kMaxNodes) return LB_E_INVALID;
+    void* base = nullptr;
+    if (scratch_ptr(&base) != cudaSuccess) return LB_E_CUDA;
+    unsigned char* p = static_cast<unsigned char*>(base);
+    double* s0 = reinterpret_cast<double*>(p);
+    double* s1 = reinterpret_cast<double*>(p + kFieldBytes);
+    double* s2 = reinterpret_cast<double*>(p + 2 * kFieldBytes);
+    double* s3 = reinterpret_cast<double*>(p + 3 * kFieldBytes);
+    Partial* parts = reinterpret_cast<Partial*>(p + 4 * kFieldBytes);
+    // Every scratch value read below is written earlier in the same call
+    // (all nodes of s0..s3, all partials of the grid), so nothing needs
+    // clearing between calls.
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const double rr = precision == LB_FP32 ? rho_ref : 0.0;
+    const DevCase<double> cd = make_case<double>(*c, rr);
+    const dim3 blk(256), grd((c->nx + 255) / 256, c->ny);
+    if (precision == LB_FP32)
+        pull_moments_kernel<float><<<grd, blk, 0, st>>>(make_case<float>(*c, rr), (const float*)d_pops, s0, s1, s2);
+    else
+        pull_moments_kernel<double><<<grd, blk, 0, st>>>(cd, (const double*)d_pops, s0, s1, s2);
+    if (c->eos == LB_VDW)
+        mu_field_kernel<double, 0><<<grd, blk, 0, st>>>(cd, cd, s0, s3);
+    else
+        mu_field_kernel<double, 1><<<grd, blk, 0, st>>>(cd, cd, s0, s3);
+    if (c->scheme == LB_IMPROVED)
+        velocity_kernel<1><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+    else
+        velocity_kernel<0><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+    finalize_kernel<<<1, 256, 0, st>>>(parts, (int64_t)grd.x * grd.y, 0.0, d_red);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_E_CUDA;
+}

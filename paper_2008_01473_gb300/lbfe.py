@@ -87,12 +87,14 @@ def lib() -> C.CDLL:
         L.lb_load.argtypes = [vp, i32, vp, sz]
         L.lb_critical.argtypes = [i32, C.c_double, C.c_double, C.c_double, dp, dp]
         L.lb_maxwell.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
+        L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
-                     "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell"):
+                     "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
+                     "lb_fields_static"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
