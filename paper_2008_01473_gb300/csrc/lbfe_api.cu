@@ -80,7 +80,8 @@ std::string check_case(const lb_case& c, int i)
         return std::string(buf);
     };
     if (c.nx < 3 || c.ny < 3) return bad("nx and ny must be >= 3");
-    if ((int64_t)c.nx * c.ny > (int64_t)1 << 31) return bad("lattice too large");
+    // the step kernel addresses a case's nine planes with 32-bit offsets
+    if ((int64_t)kQ * c.ny * pitch_of(c.nx) >= (int64_t)1 << 31) return bad("lattice too large");
     if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return bad("unknown scheme");
     if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
     if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");

@@ -11,17 +11,21 @@
 //                 sum e f (Eq. 12)                        -> smem rho rows
 //   B (row r - 1) mu_c = E_f'(rho) - kappa lap(rho)       (Eq. 2; Eq. 30)
 //                                                        -> smem mu rows
+//                 standard only: grad_h rho of row r - 2 (Eq. 17), kept in
+//                 registers
 //   C (row r - 2) improved only: grad_h mu_c (Eq. 17), F (Eq. 24), u (Eq. 12),
 //                 phi u with phi = rho/3 - p_m (Eq. 29)   -> smem phi-u rows
 //   D (row r - 3) improved: C1, C7 (Eq. 29), collision (Eq. 28), store f*
-//     (row r - 2) standard: grad mu_c, grad rho (Eq. 17), F (Eq. 13), u,
-//                 collision (Eq. 9), store f*
+//     (row r - 2) standard: grad mu_c (Eq. 17), F (Eq. 13), u, collision
+//                 (Eq. 9), store f*
 //
-// The populations of a thread's own column stay in a register ring between
-// stage A and the collision. Each population is read from memory once per
-// block; the only re-reads are the halo columns shared with neighbouring
-// strips (L2 hits: neighbouring blocks walk the same rows at the same time)
-// and the pipeline fill rows at the two ends of each row segment.
+// All ring buffers (shared-memory rows, the register ring of the thread's
+// own populations) are four rows deep and indexed by the iteration count
+// modulo 4, which the four-fold unrolled loop makes a compile-time constant.
+// Periodic row indices advance incrementally. Each population is read from
+// memory once per block; the only re-reads are the halo columns shared with
+// neighbouring strips (L2 hits: neighbouring blocks walk the same rows at the
+// same time) and the pipeline fill rows at the two ends of each row segment.
 #pragma once
 
 #include "lbfe_device.cuh"
@@ -30,104 +34,124 @@ namespace lbfe {
 
 template <int SCHEME>
 struct StepGeom {
-    static constexpr int HX = SCHEME == 1 ? 3 : 2;    // column halo of rho
-    static constexpr int LAG = SCHEME == 1 ? 3 : 2;   // rows between stage A and D
-    static constexpr int RING = LAG + 1;              // population register ring depth
-    static constexpr int NRHO = SCHEME == 1 ? 4 : 5;  // smem rows of rho
-    static constexpr int NMU = 4;                     // smem rows of mu
+    static constexpr int HX = SCHEME == 1 ? 3 : 2;   // column halo of rho
+    static constexpr int LAG = SCHEME == 1 ? 3 : 2;  // rows between stage A and D
+    static constexpr int NB = SCHEME == 1 ? 2 : 2;   // first iteration with stage B
+    static constexpr int NC = 4;                     // first iteration with stage C (improved)
+    static constexpr int ND = 2 * LAG;               // first iteration with stage D
 };
 
 template <typename T, int NT, int SCHEME>
 struct StepSmem {
-    T rho[StepGeom<SCHEME>::NRHO][NT];
-    T mu[StepGeom<SCHEME>::NMU][NT];
-    T pux[SCHEME == 1 ? 3 : 1][NT];
-    T puy[SCHEME == 1 ? 3 : 1][NT];
+    T rho[4][NT];
+    T mu[4][NT];
+    T pux[SCHEME == 1 ? 4 : 1][NT];
+    T puy[SCHEME == 1 ? 4 : 1][NT];
 };
 
-template <typename T, int RING>
+template <typename T>
 struct StepRegs {
-    T f[RING][kQ];  // pulled populations (deviation form) of the own column
-    T drho[RING];
-    T jx[RING], jy[RING];
-    T ux[2], uy[2], Fx[2], Fy[2];  // stage C results, two rows (improved)
+    T f[4][kQ];  // pulled populations (deviation form) of the own column
+    T drho[4];
+    T jx[4], jy[4];
+    T ux[2], uy[2], Fx[2], Fy[2];  // stage C results of two rows (improved)
+    T grx, gry;                    // stage B grad rho (standard)
 };
 
 struct StepLane {
-    int t;         // thread index = window column
-    int xc, xm, xp;  // lattice columns x, x-1, x+1 (periodic)
+    int t;            // thread index = window column
+    int xc, xm, xp;   // lattice columns x, x-1, x+1 (periodic)
     bool a, b, c, d;  // active in stages A..D
 };
 
+// Row bookkeeping: the periodic lattice row of stage A and of stage D.
+struct StepRows {
+    int ra;  // lattice row of stage A (wrapped)
+    int rd;  // lattice row of stage D (wrapped)
+};
+
+__device__ __forceinline__ int inc_wrap(int r, int n) { return r + 1 == n ? 0 : r + 1; }
+__device__ __forceinline__ int dec_wrap(int r, int n) { return r == 0 ? n - 1 : r - 1; }
+
+template <typename T>
+__device__ __forceinline__ T rcp_fast(T x);
+template <>
+__device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.0f, x); }
+template <>
+__device__ __forceinline__ double rcp_fast<double>(double x) { return 1.0 / x; }
+
 template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT>
 __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* __restrict__ fout,
-                                          const DevCase<T>& c, int y0, int h, const StepLane& L,
-                                          StepSmem<T, NT, SCHEME>& sm,
-                                          StepRegs<T, StepGeom<SCHEME>::RING>& R)
+                                          const DevCase<T>& c, const StepLane& L, StepRows& rows,
+                                          StepSmem<T, NT, SCHEME>& sm, StepRegs<T>& R)
 {
     using G = StepGeom<SCHEME>;
-    constexpr int RING = G::RING;
-    const int ny = c.ny, pitch = c.pitch, t = L.t;
-    const int64_t P = c.plane;
-    const int ra = y0 - G::HX + it;  // row of stage A
+    constexpr int S0 = SLOT, S1 = (SLOT + 3) & 3, S2 = (SLOT + 2) & 3, S3 = (SLOT + 1) & 3;  // rows ra - k
+    const int ny = c.ny, pitch = c.pitch;
+    const uint32_t P = (uint32_t)c.plane;
+    const int t = L.t;
 
     // ---------------------------------------------------------------- A
     if (L.a) {
-        const int r0 = wrapi(ra, ny) * pitch, rm = wrapi(ra - 1, ny) * pitch,
-                  rp = wrapi(ra + 1, ny) * pitch;
-        T* F = R.f[SLOT];
-        F[0] = __ldg(fin + 0 * P + r0 + L.xc);
-        F[1] = __ldg(fin + 1 * P + r0 + L.xm);
-        F[2] = __ldg(fin + 2 * P + rm + L.xc);
-        F[3] = __ldg(fin + 3 * P + r0 + L.xp);
-        F[4] = __ldg(fin + 4 * P + rp + L.xc);
-        F[5] = __ldg(fin + 5 * P + rm + L.xm);
-        F[6] = __ldg(fin + 6 * P + rm + L.xp);
-        F[7] = __ldg(fin + 7 * P + rp + L.xp);
-        F[8] = __ldg(fin + 8 * P + rp + L.xm);
+        const uint32_t r0 = (uint32_t)rows.ra * pitch;
+        const uint32_t rm = (uint32_t)dec_wrap(rows.ra, ny) * pitch;
+        const uint32_t rp = (uint32_t)inc_wrap(rows.ra, ny) * pitch;
+        T* F = R.f[S0];
+        F[0] = __ldg(fin + (0 * P + r0 + L.xc));
+        F[1] = __ldg(fin + (1 * P + r0 + L.xm));
+        F[2] = __ldg(fin + (2 * P + rm + L.xc));
+        F[3] = __ldg(fin + (3 * P + r0 + L.xp));
+        F[4] = __ldg(fin + (4 * P + rp + L.xc));
+        F[5] = __ldg(fin + (5 * P + rm + L.xm));
+        F[6] = __ldg(fin + (6 * P + rm + L.xp));
+        F[7] = __ldg(fin + (7 * P + rp + L.xp));
+        F[8] = __ldg(fin + (8 * P + rp + L.xm));
         const T dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
-        R.drho[SLOT] = dr;
-        R.jx[SLOT] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
-        R.jy[SLOT] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
-        sm.rho[wrapi(ra, G::NRHO)][t] = c.rho_ref + dr;
+        R.drho[S0] = dr;
+        R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+        R.jy[S0] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+        sm.rho[S0][t] = c.rho_ref + dr;
     }
     __syncthreads();
 
     // ---------------------------------------------------------------- B
-    {
-        const int rb = ra - 1;
-        if (L.b && rb >= y0 - (G::HX - 1) && rb < y0 + h + G::HX - 1) {
-            const T* Sm = sm.rho[wrapi(rb - 1, G::NRHO)];
-            const T* S0 = sm.rho[wrapi(rb, G::NRHO)];
-            const T* Sp = sm.rho[wrapi(rb + 1, G::NRHO)];
-            const T rc = S0[t];
-            const T lap = lap9<T>(rc, S0[t + 1], S0[t - 1], Sp[t], Sm[t], Sp[t + 1], Sp[t - 1],
-                                  Sm[t + 1], Sm[t - 1]);
-            sm.mu[wrapi(rb, G::NMU)][t] = dEf<EOS, T>(c, rc) - c.kappa * lap;
+    if (L.b && it >= G::NB) {
+        const T* Sm = sm.rho[S2];
+        const T* Sc = sm.rho[S1];
+        const T* Sp = sm.rho[S0];
+        const T rc = Sc[t];
+        const T lap = lap9<T>(rc, Sc[t + 1], Sc[t - 1], Sp[t], Sm[t], Sp[t + 1], Sp[t - 1], Sm[t + 1],
+                              Sm[t - 1]);
+        sm.mu[S1][t] = dEf<EOS, T>(c, rc) - c.kappa * lap;
+        if constexpr (SCHEME == 0) {
+            // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
+            if (it >= G::ND) {
+                const T* Qm = sm.rho[S3];
+                R.grx = gradx9<T>(Sm[t + 1], Sm[t - 1], Sc[t + 1], Sc[t - 1], Qm[t + 1], Qm[t - 1]);
+                R.gry = grady9<T>(Sc[t], Qm[t], Sc[t + 1], Sc[t - 1], Qm[t + 1], Qm[t - 1]);
+            }
         }
     }
     __syncthreads();
 
     if constexpr (SCHEME == 1) {
         // ------------------------------------------------------------ C
-        const int rcw = ra - 2;
-        constexpr int S2 = (SLOT + RING - 2) % RING;  // register slot of row ra - 2
-        constexpr int U2 = SLOT & 1;                  // stage C output slot of row ra - 2
-        if (L.c && rcw >= y0 - 1 && rcw < y0 + h + 1) {
-            const T* Mm = sm.mu[wrapi(rcw - 1, G::NMU)];
-            const T* M0 = sm.mu[wrapi(rcw, G::NMU)];
-            const T* Mp = sm.mu[wrapi(rcw + 1, G::NMU)];
-            const T gx = gradx9<T>(M0[t + 1], M0[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+        constexpr int U2 = SLOT & 1;  // stage C output slot of row ra - 2
+        if (L.c && it >= G::NC) {
+            const T* Mm = sm.mu[S3];
+            const T* Mc = sm.mu[S2];
+            const T* Mp = sm.mu[S1];
+            const T gx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
             const T gy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
             const T rho = c.rho_ref + R.drho[S2];
             const T k = T(1.0 / 3.0) - rho;
             const T Fx = k * gx, Fy = k * gy;
-            const T inv = T(1) / rho;
+            const T inv = rcp_fast<T>(rho);
             const T ux = (R.jx[S2] + T(0.5) * Fx) * inv;
             const T uy = (R.jy[S2] + T(0.5) * Fy) * inv;
-            const T phi = (rho - (c.c0 + M0[t])) * T(1.0 / 3.0);
-            sm.pux[wrapi(rcw, 3)][t] = phi * ux;
-            sm.puy[wrapi(rcw, 3)][t] = phi * uy;
+            const T phi = (rho - (c.c0 + Mc[t])) * T(1.0 / 3.0);
+            sm.pux[S2][t] = phi * ux;
+            sm.puy[S2][t] = phi * uy;
             R.ux[U2] = ux;
             R.uy[U2] = uy;
             R.Fx[U2] = Fx;
@@ -135,21 +159,19 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
         }
         __syncthreads();
         // ------------------------------------------------------------ D
-        const int rd = ra - 3;
-        constexpr int S3 = (SLOT + RING - 3) % RING;
         constexpr int U3 = (SLOT + 1) & 1;
-        if (L.d && rd >= y0 && rd < y0 + h) {
-            const T* Am = sm.pux[wrapi(rd - 1, 3)];
-            const T* A0 = sm.pux[wrapi(rd, 3)];
-            const T* Ap = sm.pux[wrapi(rd + 1, 3)];
-            const T* Bm = sm.puy[wrapi(rd - 1, 3)];
-            const T* Bp = sm.puy[wrapi(rd + 1, 3)];
-            const T Ax = gradx9<T>(A0[t + 1], A0[t - 1], Ap[t + 1], Ap[t - 1], Am[t + 1], Am[t - 1]);
+        if (L.d && it >= G::ND) {
+            const T* Am = sm.pux[S0];  // row ra - 4 shares slot S0 with row ra
+            const T* Ac = sm.pux[S3];
+            const T* Ap = sm.pux[S2];
+            const T* Bm = sm.puy[S0];
+            const T* Bp = sm.puy[S2];
+            const T Ax = gradx9<T>(Ac[t + 1], Ac[t - 1], Ap[t + 1], Ap[t - 1], Am[t + 1], Am[t - 1]);
             const T By = grady9<T>(Bp[t], Bm[t], Bp[t + 1], Bp[t - 1], Bm[t + 1], Bm[t - 1]);
             const T C1 = Ax + By, C7 = Ax - By;
             const T drho = R.drho[S3];
             const T rho = c.rho_ref + drho;
-            const T mu = sm.mu[wrapi(rd, G::NMU)][t];
+            const T mu = sm.mu[S3][t];
             T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
             if (NU) {
                 lv = shear_rate<SCHEME, NU, T>(c, rho, mu);
@@ -157,31 +179,24 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
             }
             collide<SCHEME, T>(R.f[S3], drho, rho, R.jx[S3], R.jy[S3], R.ux[U3], R.uy[U3], R.Fx[U3],
                                R.Fy[U3], mu, C1, C7, c.rho_ref, c.c0, le, ls, lq, lv);
-            const int64_t o = (int64_t)wrapi(rd, ny) * pitch + L.xc;
+            const uint32_t o = (uint32_t)rows.rd * pitch + L.xc;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) fout[a * P + o] = R.f[S3][a];
         }
     } else {
         // ------------------------------------------------------- D (standard)
-        const int rd = ra - 2;
-        constexpr int S2 = (SLOT + RING - 2) % RING;
-        if (L.d && rd >= y0 && rd < y0 + h) {
-            const T* Mm = sm.mu[wrapi(rd - 1, G::NMU)];
-            const T* M0 = sm.mu[wrapi(rd, G::NMU)];
-            const T* Mp = sm.mu[wrapi(rd + 1, G::NMU)];
-            const T* Rm = sm.rho[wrapi(rd - 1, G::NRHO)];
-            const T* R0 = sm.rho[wrapi(rd, G::NRHO)];
-            const T* Rp = sm.rho[wrapi(rd + 1, G::NRHO)];
-            const T gmx = gradx9<T>(M0[t + 1], M0[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+        if (L.d && it >= G::ND) {
+            const T* Mm = sm.mu[S3];
+            const T* Mc = sm.mu[S2];
+            const T* Mp = sm.mu[S1];
+            const T gmx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
             const T gmy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
-            const T grx = gradx9<T>(R0[t + 1], R0[t - 1], Rp[t + 1], Rp[t - 1], Rm[t + 1], Rm[t - 1]);
-            const T gry = grady9<T>(Rp[t], Rm[t], Rp[t + 1], Rp[t - 1], Rm[t + 1], Rm[t - 1]);
             const T drho = R.drho[S2];
             const T rho = c.rho_ref + drho;
-            const T mu = M0[t];
-            const T Fx = grx * T(1.0 / 3.0) - rho * gmx;
-            const T Fy = gry * T(1.0 / 3.0) - rho * gmy;
-            const T inv = T(1) / rho;
+            const T mu = Mc[t];
+            const T Fx = R.grx * T(1.0 / 3.0) - rho * gmx;
+            const T Fy = R.gry * T(1.0 / 3.0) - rho * gmy;
+            const T inv = rcp_fast<T>(rho);
             const T ux = (R.jx[S2] + T(0.5) * Fx) * inv;
             const T uy = (R.jy[S2] + T(0.5) * Fy) * inv;
             T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
@@ -191,11 +206,13 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
             }
             collide<SCHEME, T>(R.f[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, T(0), T(0),
                                c.rho_ref, c.c0, le, ls, lq, lv);
-            const int64_t o = (int64_t)wrapi(rd, ny) * pitch + L.xc;
+            const uint32_t o = (uint32_t)rows.rd * pitch + L.xc;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) fout[a * P + o] = R.f[S2][a];
         }
     }
+    rows.ra = inc_wrap(rows.ra, ny);
+    if (it >= G::ND) rows.rd = inc_wrap(rows.rd, ny);
 }
 
 // One launch advances every case listed in the work-list by one time step.
@@ -207,7 +224,6 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
                                                   const Item* __restrict__ items)
 {
     using G = StepGeom<SCHEME>;
-    constexpr int RING = G::RING;
     __shared__ StepSmem<T, NT, SCHEME> sm;
     const Item item = items[blockIdx.x];
     const DevCase<T> c = cases[item.case_id];
@@ -226,18 +242,20 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
     L.c = L.t >= 2 && L.t < span - 2;
     L.d = L.t >= G::HX && L.t < span - G::HX;
 
-    StepRegs<T, RING> R;
+    StepRows rows;
+    rows.ra = wrapi(item.y0 - G::HX, c.ny);
+    rows.rd = item.y0;
+
+    StepRegs<T> R;
     const int niter = item.h + 2 * G::HX;
-    for (int base = 0; base < niter; base += RING) {
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, fin, fout, c, item.y0, item.h, L, sm, R);
+    for (int base = 0; base < niter; base += 4) {
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, fin, fout, c, L, rows, sm, R);
         if (base + 1 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, fin, fout, c, item.y0, item.h, L, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, fin, fout, c, L, rows, sm, R);
         if (base + 2 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, fin, fout, c, item.y0, item.h, L, sm, R);
-        if constexpr (RING > 3) {
-            if (base + 3 >= niter) break;
-            step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, fin, fout, c, item.y0, item.h, L, sm, R);
-        }
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, fin, fout, c, L, rows, sm, R);
+        if (base + 3 >= niter) break;
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, fin, fout, c, L, rows, sm, R);
     }
 }
 
