@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -25,16 +26,20 @@ int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
 
 int halo_of(int scheme) { return scheme == LB_IMPROVED ? 3 : 2; }
 
-int strip_width(int scheme) { return kStepThreads - 2 * halo_of(scheme); }
-
-int64_t max_items_of(const lb_case& c)
+// Widest strip of output columns a block can own. Lattices with nx % 4 == 0
+// get strips of a multiple of 4 columns, at most kStepThreads - 8 wide, as the
+// TMA-staged kernel needs (16-byte aligned runs of [x0 - 4, x0 + wv + 4)).
+int strip_width(const lb_case& c)
 {
-    const int64_t ns = (c.nx + strip_width(c.scheme) - 1) / strip_width(c.scheme);
-    return ns * ((c.ny + kMinRows - 1) / kMinRows);
+    return c.nx % 4 == 0 ? kStepThreads - 8 : kStepThreads - 2 * halo_of(c.scheme);
 }
 
+int strips_of(const lb_case& c) { return (c.nx + strip_width(c) - 1) / strip_width(c); }
+
+int64_t max_items_of(const lb_case& c) { return (int64_t)strips_of(c) * ((c.ny + kMinRows - 1) / kMinRows); }
+
 struct Layout {
-    size_t cases32, cases64, items, f[2], scratch, partials, red, total;
+    size_t cases32, cases64, items, f[2], scratch, partials, red, status, total;
     std::vector<int64_t> off;  // element offset of each case in a population buffer
     int64_t max_items = 0, max_nodes = 0, max_parts = 0;
 };
@@ -68,6 +73,8 @@ Layout layout_of(const lb_case* cs, int n, int prec)
     p = align_up(p + L.max_parts * sizeof(Partial), kAlign);
     L.red = p;
     p = align_up(p + n * 8 * sizeof(double), kAlign);
+    L.status = p;
+    p = align_up(p + sizeof(int), kAlign);
     L.total = p;
     return L;
 }
@@ -124,6 +131,7 @@ DevCase<T> dev_case(const lb_case& c, int64_t off, double rho_ref)
 struct Group {
     int scheme, coll, eos;
     bool nu;
+    bool tma;              // TMA-staged kernel (FP32, every nx % 4 == 0)
     int64_t first, count;  // slice of the item array
 };
 
@@ -141,6 +149,7 @@ struct lb_handle {
     std::vector<char> inited;
     std::vector<Group> groups;
     std::vector<Item> items;
+    int path = 0;  // 0: TMA-staged kernel where eligible, 1: plain-load kernel only
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -153,6 +162,7 @@ struct lb_handle {
                                          k * align_up(L.max_nodes * sizeof(double), kAlign));
     }
     Partial* partials() const { return reinterpret_cast<Partial*>(ws + L.partials); }
+    int* status() const { return reinterpret_cast<int*>(ws + L.status); }
     double* red() const { return reinterpret_cast<double*>(ws + L.red); }
 
     lb_status fail(lb_status s, const std::string& m)
@@ -206,20 +216,22 @@ void build_items(lb_handle* h)
                         }
                     }
                     if (members.empty()) continue;
-                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1)
+                    bool tma = h->prec == LB_FP32 && h->path != 1;
+                    for (int i : members) tma = tma && h->cases[i].nx % 4 == 0;
+                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma)
                                                        : occupancy_step_f64(s, co, e, nu == 1);
                     const double slots = (double)sms * occ;
-                    Group g{s, co, e, nu == 1, (int64_t)h->items.size(), 0};
-                    const int W = strip_width(s);
+                    Group g{s, co, e, nu == 1, tma, (int64_t)h->items.size(), 0};
                     for (int i : members) {
                         const lb_case& c = h->cases[i];
-                        const int ns = (c.nx + W - 1) / W;
+                        const int ns = strips_of(c);
+                        const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
                         const double share = slots * ((double)c.nx * c.ny) / nodes;
                         int nseg = std::max(1, (int)std::floor(share / ns));
                         nseg = std::min(nseg, std::max(1, c.ny / kMinRows));
                         for (int k = 0; k < ns; ++k) {
-                            const int x0 = (int)((int64_t)c.nx * k / ns);
-                            const int x1 = (int)((int64_t)c.nx * (k + 1) / ns);
+                            const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns);
+                            const int x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
                             for (int q = 0; q < nseg; ++q) {
                                 const int y0 = (int)((int64_t)c.ny * q / nseg);
                                 const int y1 = (int)((int64_t)c.ny * (q + 1) / nseg);
@@ -293,10 +305,12 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     for (int i = 0; i < ncases; ++i) h->rho_ref[i] = precision == LB_FP32 ? cases[i].rho_ref : 0.0;
     h->steps.assign(ncases, 0);
     h->inited.assign(ncases, 0);
+    if (const char* p = std::getenv("LBFE_STEP_PATH")) h->path = std::strcmp(p, "ldg") == 0 ? 1 : 0;
     build_items(h);
     lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
                                           cudaMemcpyHostToDevice, h->stream),
                           "upload items");
+    if (s == LB_OK) s = h->cuda(cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream), "clear status");
     for (int i = 0; i < ncases && s == LB_OK; ++i) s = h->upload_case(i);
     if (s != LB_OK) {
         delete h;
@@ -371,13 +385,13 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
         for (const Group& g : h->groups) {
             cudaError_t e;
             if (h->prec == LB_FP32)
-                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, (int)g.count, h->stream,
+                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, (int)g.count, h->stream,
                                     (const float*)h->fbuf(h->cur), (float*)h->fbuf(h->cur ^ 1), h->dc32(),
-                                    h->ditems() + g.first);
+                                    h->ditems() + g.first, h->status());
             else
                 e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, h->stream,
                                     (const double*)h->fbuf(h->cur), (double*)h->fbuf(h->cur ^ 1), h->dc64(),
-                                    h->ditems() + g.first);
+                                    h->ditems() + g.first, h->status());
             if (e != cudaSuccess) return h->cuda(e, "step launch");
         }
         h->cur ^= 1;
@@ -423,9 +437,13 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
         if ((s = h->cuda(cudaGetLastError(), "finalize")) != LB_OK) return s;
     }
     std::vector<double> red((size_t)n * 8);
+    int timeout = 0;
     lb_status s = h->cuda(cudaMemcpyAsync(red.data(), h->red(), red.size() * sizeof(double),
                                           cudaMemcpyDeviceToHost, h->stream),
                           "copy reductions");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemcpyAsync(&timeout, h->status(), sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+                    "copy status");
     if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "reductions sync");
     if (s != LB_OK) return s;
     bool unstable = false;
@@ -435,6 +453,11 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
         out[5 * i + 4] = 0.0;
         if (case_status) case_status[i] = bad ? LB_E_UNSTABLE : LB_OK;
         unstable |= bad;
+    }
+    if (timeout) {
+        cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream);
+        return h->fail(LB_E_TIMEOUT, "a bounded wait for a bulk copy gave up; results since the last "
+                                     "lb_reductions are unreliable");
     }
     if (unstable) return h->fail(LB_E_UNSTABLE, "a case has rho <= 0 or non-finite values");
     return LB_OK;

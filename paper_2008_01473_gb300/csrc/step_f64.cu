@@ -1,4 +1,4 @@
-// Instantiations of the fused step kernel with double populations and arithmetic.
+// Instantiations of the fused step kernel with FP64 populations and arithmetic.
 #include "launch.h"
 #include "step_kernel.cuh"
 
@@ -24,11 +24,12 @@ void* pick(int scheme, int coll, int eos, bool nu)
 }  // namespace
 
 cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks, cudaStream_t s,
-                          const double* fin, double* fout, const DevCase<double>* cases, const Item* items)
+                            const double* fin, double* fout, const DevCase<double>* cases,
+                            const Item* items, int* status)
 {
     void* k = pick(scheme, coll, eos, nu);
     if (!k) return cudaErrorInvalidValue;
-    void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items};
+    void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
     return cudaLaunchKernel(k, dim3(nblocks), dim3(kStepThreads), args, 0, s);
 }
 

@@ -80,8 +80,32 @@ __device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.
 template <>
 __device__ __forceinline__ double rcp_fast<double>(double x) { return 1.0 / x; }
 
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT>
-__device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* __restrict__ fout,
+// Stage A source of the pulled populations: plain read-only global loads.
+template <typename T>
+struct PullGlobal {
+    __device__ __forceinline__ void pull(int, T* F, const T* __restrict__ fin, const DevCase<T>& c,
+                                         const StepLane& L, const StepRows& rows) const
+    {
+        const int ny = c.ny, pitch = c.pitch;
+        const uint32_t P = (uint32_t)c.plane;
+        const uint32_t r0 = (uint32_t)rows.ra * pitch;
+        const uint32_t rm = (uint32_t)dec_wrap(rows.ra, ny) * pitch;
+        const uint32_t rp = (uint32_t)inc_wrap(rows.ra, ny) * pitch;
+        F[0] = __ldg(fin + (0 * P + r0 + L.xc));
+        F[1] = __ldg(fin + (1 * P + r0 + L.xm));
+        F[2] = __ldg(fin + (2 * P + rm + L.xc));
+        F[3] = __ldg(fin + (3 * P + r0 + L.xp));
+        F[4] = __ldg(fin + (4 * P + rp + L.xc));
+        F[5] = __ldg(fin + (5 * P + rm + L.xm));
+        F[6] = __ldg(fin + (6 * P + rm + L.xp));
+        F[7] = __ldg(fin + (7 * P + rp + L.xp));
+        F[8] = __ldg(fin + (8 * P + rp + L.xm));
+    }
+    __device__ __forceinline__ void after_sync(int) const {}
+};
+
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A>
+__device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restrict__ fin, T* __restrict__ fout,
                                           const DevCase<T>& c, const StepLane& L, StepRows& rows,
                                           StepSmem<T, NT, SCHEME>& sm, StepRegs<T>& R)
 {
@@ -93,19 +117,8 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
 
     // ---------------------------------------------------------------- A
     if (L.a) {
-        const uint32_t r0 = (uint32_t)rows.ra * pitch;
-        const uint32_t rm = (uint32_t)dec_wrap(rows.ra, ny) * pitch;
-        const uint32_t rp = (uint32_t)inc_wrap(rows.ra, ny) * pitch;
         T* F = R.f[S0];
-        F[0] = __ldg(fin + (0 * P + r0 + L.xc));
-        F[1] = __ldg(fin + (1 * P + r0 + L.xm));
-        F[2] = __ldg(fin + (2 * P + rm + L.xc));
-        F[3] = __ldg(fin + (3 * P + r0 + L.xp));
-        F[4] = __ldg(fin + (4 * P + rp + L.xc));
-        F[5] = __ldg(fin + (5 * P + rm + L.xm));
-        F[6] = __ldg(fin + (6 * P + rm + L.xp));
-        F[7] = __ldg(fin + (7 * P + rp + L.xp));
-        F[8] = __ldg(fin + (8 * P + rp + L.xm));
+        A_.pull(it, F, fin, c, L, rows);
         const T dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
         R.drho[S0] = dr;
         R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
@@ -113,6 +126,7 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
         sm.rho[S0][t] = c.rho_ref + dr;
     }
     __syncthreads();
+    A_.after_sync(it);  // the TMA source refills the ring slot freed by stage A
 
     // ---------------------------------------------------------------- B
     if (L.b && it >= G::NB) {
@@ -221,8 +235,9 @@ __device__ __forceinline__ void step_iter(int it, const T* __restrict__ fin, T* 
 template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU>
 __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* __restrict__ fout,
                                                   const DevCase<T>* __restrict__ cases,
-                                                  const Item* __restrict__ items)
+                                                  const Item* __restrict__ items, int* __restrict__ status)
 {
+    (void)status;
     using G = StepGeom<SCHEME>;
     __shared__ StepSmem<T, NT, SCHEME> sm;
     const Item item = items[blockIdx.x];
@@ -248,14 +263,15 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
 
     StepRegs<T> R;
     const int niter = item.h + 2 * G::HX;
+    const PullGlobal<T> A;
     for (int base = 0; base < niter; base += 4) {
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, A, fin, fout, c, L, rows, sm, R);
         if (base + 1 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, A, fin, fout, c, L, rows, sm, R);
         if (base + 2 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, A, fin, fout, c, L, rows, sm, R);
         if (base + 3 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
     }
 }
 

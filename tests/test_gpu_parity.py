@@ -203,12 +203,14 @@ def test_invalid_inputs_rejected():
 # --------------------------------------------------------------------- FP32
 @pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
-def test_fp32_one_step_elementwise(scheme, collision):
+@pytest.mark.parametrize("nx", [530, 532])
+def test_fp32_one_step_elementwise(scheme, collision, nx):
     """One FP32 step from the GPU's own state against the oracle step from the
     same (FP32-representable) populations: post-step populations within
-    3e-6 of max |f| (a few FP32 roundings of O(1) quantities)."""
-    gc, oc, rg, rl = _pair(530, 37, scheme, collision, t=0.85)
-    rho0 = inputs.droplet(530, 37, 12.0, rl, rg, noise=1e-3, seed=9)
+    3e-6 of max |f| (a few FP32 roundings of O(1) quantities). nx = 532 runs
+    the TMA-staged kernel, nx = 530 the plain-load one."""
+    gc, oc, rg, rl = _pair(nx, 37, scheme, collision, t=0.85)
+    rho0 = inputs.droplet(nx, 37, 12.0, rl, rg, noise=1e-3, seed=9)
     lat = lbfe.Lattice([gc], precision=lbfe.FP32)
     lat.init_fields(0, rho0)
     lat.step(5)
@@ -260,3 +262,26 @@ def test_fp32_full_size_sampled_nodes():
         O.step(oc, patch, 1)
         got = f1[:, y, x]
         assert np.abs(got - patch[:, 6, 6]).max() < 3e-6 * np.abs(patch[:, 6, 6]).max(), (y, x)
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("shape", [(4, 5), (8, 9), (12, 7), (532, 37), (496, 300), (1000, 16), (2048, 64)])
+def test_fp32_tma_path_bitwise_equals_plain_loads(scheme, shape, monkeypatch):
+    """The TMA-staged kernel (bulk copies of row runs into a shared-memory
+    ring, periodic wrap split into up to three runs) gives bit-identical
+    populations to the plain-load kernel, including lattices narrower than
+    the halo (nx = 4, 8, 12) and several strips and row segments."""
+    nx, ny = shape
+    gc, _, rg, rl = _pair(nx, ny, scheme, lbfe.MRT, t=0.85)
+    rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=6)
+    snaps = {}
+    for path in ("ldg", "tma"):
+        monkeypatch.setenv("LBFE_STEP_PATH", path)
+        lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+        lat.init_fields(0, rho0)
+        lat.step(15)
+        snaps[path] = lat.save(0)
+        _, st = lat.reductions()
+        assert st[0] == 0
+        lat.close()
+    assert snaps["ldg"] == snaps["tma"]
