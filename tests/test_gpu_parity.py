@@ -280,8 +280,8 @@ def test_fp32_tma_path_bitwise_equals_plain_loads(scheme, shape, monkeypatch):
         lat = lbfe.Lattice([gc], precision=lbfe.FP32)
         lat.init_fields(0, rho0)
         lat.step(15)
-        snaps[path] = lat.save(0)
+        snaps[path] = _gpu_pops(lat, 0)  # lattice columns only (row padding is never written)
         _, st = lat.reductions()
         assert st[0] == 0
         lat.close()
-    assert snaps["ldg"] == snaps["tma"]
+    assert np.array_equal(snaps["ldg"], snaps["tma"])
