@@ -46,15 +46,17 @@ cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, in
     void* k = resolve(scheme, coll, eos, nu, tma);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
-    return cudaLaunchKernel(k, dim3(nblocks), dim3(kStepThreads), args, tma ? kTmaSmem : 0, s);
+    // the TMA kernel adds one producer warp to the kStepThreads compute threads
+    return cudaLaunchKernel(k, dim3(nblocks), dim3(tma ? kStepThreads + 32 : kStepThreads), args,
+                            tma ? kTmaSmem : 0, s);
 }
 
 int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma)
 {
     void* k = resolve(scheme, coll, eos, nu, tma);
     int n = 0;
-    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kStepThreads, tma ? kTmaSmem : 0) !=
-                  cudaSuccess)
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tma ? kStepThreads + 32 : kStepThreads,
+                                                            tma ? kTmaSmem : 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }

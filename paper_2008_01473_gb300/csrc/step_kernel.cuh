@@ -102,6 +102,7 @@ struct PullGlobal {
         F[8] = __ldg(fin + (8 * P + rp + L.xm));
     }
     __device__ __forceinline__ void after_sync(int) const {}
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
 template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A>
@@ -125,7 +126,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         R.jy[S0] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
         sm.rho[S0][t] = c.rho_ref + dr;
     }
-    __syncthreads();
+    A_.sync();
     A_.after_sync(it);  // the TMA source refills the ring slot freed by stage A
 
     // ---------------------------------------------------------------- B
@@ -146,7 +147,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             }
         }
     }
-    __syncthreads();
+    A_.sync();
 
     if constexpr (SCHEME == 1) {
         // ------------------------------------------------------------ C
@@ -171,7 +172,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             R.Fx[U2] = Fx;
             R.Fy[U2] = Fy;
         }
-        __syncthreads();
+        A_.sync();
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
         if (L.d && it >= G::ND) {

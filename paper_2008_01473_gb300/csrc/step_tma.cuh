@@ -1,24 +1,28 @@
 // TMA-staged variant of the fused step: the stored rows a block needs are
 // copied from HBM into a shared-memory ring by bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier per ring slot), issued several
-// rows ahead by one thread. Stage A then pulls its nine populations from
-// shared memory, so the warps never wait on HBM latency. Stages B-D are the
-// ones of step_kernel.cuh.
+// (cp.async.bulk), issued ahead of use by a dedicated producer warp. The NT
+// compute threads pull their nine populations from shared memory in stage A,
+// so they never wait on HBM latency; stages B-D are those of step_kernel.cuh,
+// synchronised by a named barrier that the producer warp does not join.
 //
-// Ring: NS slots, each holding the nine planes of one stored row over the
-// block's columns [x0 - 4, x0 + wv + 4) (the rho halo of 3 plus 1 for the
+// Ring: kTmaSlots slots, each holding the nine planes of one stored row over
+// the block's columns [x0 - 4, x0 + wv + 4) (the rho halo of 3 plus 1 for the
 // pull). A row is copied as up to three runs (periodic wrap at the lattice
 // edges); every run starts on a 16-byte boundary because x0, wv and nx are
 // multiples of 4 elements on this path. Stored row s (window coordinates,
-// s0 = y0 - HX - 1 first) lives in slot (s - s0) % NS, phase ((s - s0) / NS) & 1.
-// Stage A of iteration it reads rows s0 + it .. s0 + it + 2; after the block
-// barrier that follows it, row s0 + it is dead and its slot takes row
-// s0 + it + NS.
+// s0 = y0 - HX - 1 first) lives in slot k = (s - s0) % kTmaSlots and is the
+// m-th occupant of that slot, m = (s - s0) / kTmaSlots.
+//
+// Two mbarriers per slot:
+//   full[k]  : producer arrive.expect_tx + bulk-copy completion; the compute
+//              threads wait on phase m & 1 before reading row s.
+//   empty[k] : compute thread 0 arrives once stage A of iteration it = s - s0
+//              (the last reader of row s) is past the block barrier; the
+//              producer waits on phase (m - 1) & 1 before refilling slot k.
 //
 // Every wait is bounded (about one second of SM clock); a wait that gives up
-// sets *status and the block carries on with whatever the slot holds, so no
-// launch can hang. Before exiting, a block that saw a timeout waits (bounded)
-// for its own copies still in flight.
+// sets *status and the thread carries on, so no launch can hang. Before
+// exiting, a block that saw a timeout waits (bounded) for its copies in flight.
 #pragma once
 
 #include "step_kernel.cuh"
@@ -42,6 +46,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
@@ -85,56 +94,33 @@ struct TmaRuns {
 template <typename T, int NT, int SCHEME>
 struct PullTma {
     static constexpr int SW = NT;  // smem columns per plane (>= wv + 8)
-    T* ring;                       // [NS][9][SW]
-    uint64_t* bar;                 // [NS]
+    T* ring;                       // [kTmaSlots][9][SW]
+    uint64_t* full;                // [kTmaSlots]
+    uint64_t* empty;               // [kTmaSlots]
     int* flag;                     // shared: a wait of this block timed out
     int* status;                   // global status word
-    const T* fin;                  // this case's stored populations
     int s0, s_last;                // first / last stored window row of the block
-    int ny, pitch;
-    uint32_t P;
-    uint32_t row_bytes;            // bytes of one stored row over all runs and planes
-    TmaRuns runs;
     int jc;                        // smem column of the thread's own lattice column
 
     __device__ __forceinline__ T* slot(int k) const { return ring + (size_t)k * kQ * SW; }
 
-    // thread 0 only: copy stored window row s into its slot
-    __device__ __forceinline__ void issue(int s) const
+    __device__ __forceinline__ void timed_out() const
     {
-        const int k = (s - s0) % kTmaSlots;
-        uint64_t* b = bar + k;
-        mbar_expect_tx(b, row_bytes);
-        const uint32_t row = (uint32_t)wrapi(s, ny) * pitch;
-        T* dst = slot(k);
-#pragma unroll 1
-        for (int a = 0; a < kQ; ++a) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                if (r < runs.n)
-                    bulk_load(dst + a * SW + runs.j0[r], fin + (a * P + row + (uint32_t)runs.g0[r]),
-                              (uint32_t)runs.len[r] * sizeof(T), b);
-        }
-    }
-
-    __device__ __forceinline__ void wait_row(int s) const
-    {
-        const int i = s - s0;
-        if (!mbar_wait(bar + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u)) {
-            *flag = 1;
-            atomicOr(status, 1);
-        }
+        *flag = 1;
+        atomicOr(status, 1);
     }
 
     __device__ __forceinline__ void pull(int it, T* F, const T* __restrict__, const DevCase<T>&,
                                          const StepLane&, const StepRows&) const
     {
-        const int s = s0 + it;  // stored window row ra - 1
         if (it == 0) {
-            wait_row(s);
-            wait_row(s + 1);
+            if (!mbar_wait(full + 0, 0u)) timed_out();
+            if (!mbar_wait(full + 1, 0u)) timed_out();
         }
-        wait_row(s + 2);
+        {
+            const int i = it + 2;  // stored row s0 + it + 2 = ra + 1
+            if (!mbar_wait(full + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u)) timed_out();
+        }
         const T* Rm = slot(it % kTmaSlots);        // row ra - 1
         const T* R0 = slot((it + 1) % kTmaSlots);  // row ra
         const T* Rp = slot((it + 2) % kTmaSlots);  // row ra + 1
@@ -150,29 +136,57 @@ struct PullTma {
         F[8] = Rp[8 * SW + j - 1];
     }
 
+    // after the barrier that follows stage A: row s0 + it has no reader left
     __device__ __forceinline__ void after_sync(int it) const
     {
-        const int s = s0 + it + kTmaSlots;
-        if (threadIdx.x == 0 && s <= s_last) {
-            // order the generic-proxy reads of the slot before the async-proxy refill
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(s);
-        }
+        if (threadIdx.x == 0) mbar_arrive(empty + it % kTmaSlots);
     }
+
+    // compute threads only (the producer warp never joins)
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory"); }
 };
 
 template <typename T, int NT>
 constexpr size_t tma_dynamic_smem()
 {
-    return (size_t)kTmaSlots * kQ * NT * sizeof(T) + kTmaSlots * sizeof(uint64_t);
+    return (size_t)kTmaSlots * kQ * NT * sizeof(T) + 2 * kTmaSlots * sizeof(uint64_t);
 }
 
-// Same contract as step_kernel; every case of the launch has nx % 4 == 0 and
-// every work item has x0 % 4 == 0 and wv % 4 == 0, wv + 8 <= NT.
+// Producer warp, lane 0: copy stored window rows s0 .. s_last into the ring.
+template <typename T, int NT, int SCHEME>
+__device__ __forceinline__ void tma_produce(const PullTma<T, NT, SCHEME>& A, const T* __restrict__ fin,
+                                            const DevCase<T>& c, const TmaRuns& runs, uint32_t row_bytes)
+{
+    const uint32_t P = (uint32_t)c.plane;
+    for (int s = A.s0; s <= A.s_last; ++s) {
+        const int i = s - A.s0;
+        const int k = i % kTmaSlots, m = i / kTmaSlots;
+        if (m > 0 && !mbar_wait(A.empty + k, (uint32_t)(m - 1) & 1u)) A.timed_out();
+        // order the compute threads' generic reads of the slot before the async refill
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        uint64_t* b = A.full + k;
+        mbar_expect_tx(b, row_bytes);
+        const uint32_t row = (uint32_t)wrapi(s, c.ny) * c.pitch;
+        T* dst = A.slot(k);
+#pragma unroll 1
+        for (int a = 0; a < kQ; ++a) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (r < runs.n)
+                    bulk_load(dst + a * PullTma<T, NT, SCHEME>::SW + runs.j0[r],
+                              fin + (a * P + row + (uint32_t)runs.g0[r]), (uint32_t)runs.len[r] * sizeof(T), b);
+        }
+    }
+}
+
+// Same contract as step_kernel, with blockDim.x == NT + 32 (NT compute
+// threads and one producer warp); every case of the launch has nx % 4 == 0
+// and every work item has x0 % 4 == 0, wv % 4 == 0 and wv + 8 <= NT.
 template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU>
-__global__ void __launch_bounds__(NT) step_kernel_tma(const T* __restrict__ fin, T* __restrict__ fout,
-                                                      const DevCase<T>* __restrict__ cases,
-                                                      const Item* __restrict__ items, int* __restrict__ status)
+__global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__ fin, T* __restrict__ fout,
+                                                           const DevCase<T>* __restrict__ cases,
+                                                           const Item* __restrict__ items,
+                                                           int* __restrict__ status)
 {
     using G = StepGeom<SCHEME>;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -182,6 +196,50 @@ __global__ void __launch_bounds__(NT) step_kernel_tma(const T* __restrict__ fin,
     const DevCase<T> c = cases[item.case_id];
     fin += c.off;
     fout += c.off;
+    const int niter = item.h + 2 * G::HX;
+
+    PullTma<T, NT, SCHEME> A;
+    A.ring = reinterpret_cast<T*>(dsm);
+    A.full = reinterpret_cast<uint64_t*>(dsm + (size_t)kTmaSlots * kQ * NT * sizeof(T));
+    A.empty = A.full + kTmaSlots;
+    A.flag = &flag;
+    A.status = status;
+    A.s0 = item.y0 - G::HX - 1;
+    A.s_last = A.s0 + niter + 1;
+    A.jc = (int)threadIdx.x + 4 - G::HX;
+
+    if (threadIdx.x == 0) {
+        flag = 0;
+        for (int k = 0; k < kTmaSlots; ++k) {
+            mbar_init(A.full + k, 1);
+            mbar_init(A.empty + k, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= NT) {
+        // producer warp
+        if (threadIdx.x == NT) {
+            TmaRuns runs;
+            const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
+            runs.n = 0;
+            int x = start, j = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int g = wrapi(x, c.nx);
+                const int len = min(end - x, c.nx - g);
+                runs.g0[r] = g;
+                runs.j0[r] = j;
+                runs.len[r] = len;
+                if (x < end) runs.n = r + 1;
+                x += len;
+                j += len;
+            }
+            tma_produce<T, NT, SCHEME>(A, fin, c, runs, (uint32_t)(kQ * (end - start) * sizeof(T)));
+        }
+        return;
+    }
 
     StepLane L;
     L.t = threadIdx.x;
@@ -198,46 +256,6 @@ __global__ void __launch_bounds__(NT) step_kernel_tma(const T* __restrict__ fin,
     StepRows rows;
     rows.ra = wrapi(item.y0 - G::HX, c.ny);
     rows.rd = item.y0;
-    const int niter = item.h + 2 * G::HX;
-
-    PullTma<T, NT, SCHEME> A;
-    A.ring = reinterpret_cast<T*>(dsm);
-    A.bar = reinterpret_cast<uint64_t*>(dsm + (size_t)kTmaSlots * kQ * NT * sizeof(T));
-    A.flag = &flag;
-    A.status = status;
-    A.fin = fin;
-    A.s0 = item.y0 - G::HX - 1;
-    A.s_last = A.s0 + niter + 1;
-    A.ny = c.ny;
-    A.pitch = c.pitch;
-    A.P = (uint32_t)c.plane;
-    A.jc = L.t + 4 - G::HX;
-    {
-        // runs of [x0 - 4, x0 + wv + 4) split at the periodic edges
-        const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
-        A.runs.n = 0;
-        int x = start, j = 0;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int g = wrapi(x, c.nx);
-            const int len = min(end - x, c.nx - g);
-            A.runs.g0[r] = g;
-            A.runs.j0[r] = j;
-            A.runs.len[r] = len;
-            if (x < end) A.runs.n = r + 1;
-            x += len;
-            j += len;
-        }
-        A.row_bytes = (uint32_t)(kQ * (end - start) * sizeof(T));
-    }
-    if (L.t == 0) {
-        flag = 0;
-        for (int k = 0; k < kTmaSlots; ++k) mbar_init(A.bar + k, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    if (L.t == 0)
-        for (int s = A.s0; s < A.s0 + kTmaSlots && s <= A.s_last; ++s) A.issue(s);
 
     StepRegs<T> R;
     for (int base = 0; base < niter; base += 4) {
@@ -250,11 +268,11 @@ __global__ void __launch_bounds__(NT) step_kernel_tma(const T* __restrict__ fin,
         step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
-    __syncthreads();
+    A.sync();
     if (L.t == 0 && flag) {
         for (int s = max(A.s0, A.s_last - kTmaSlots + 1); s <= A.s_last; ++s) {
             const int i = s - A.s0;
-            mbar_wait(A.bar + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u);
+            mbar_wait(A.full + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u);
         }
     }
 }
