@@ -93,7 +93,12 @@ lb_status lb_workspace_bytes(const lb_case* cases, int32_t ncases, int32_t preci
 /* Validate the cases, lay the workspace out and build the launch work-lists.
  * d_workspace: device memory of at least lb_workspace_bytes bytes, owned by
  * the caller and not touched by anyone else until lb_destroy. cuda_stream:
- * cudaStream_t (void*). On LB_OK *out holds a new handle. */
+ * cudaStream_t (void*). On LB_OK *out holds a new handle.
+ * Kernel selection (results are bit-identical either way): FP32 groups whose
+ * lattices all have nx % 4 == 0 use the TMA-staged step kernel, others the
+ * plain-load one. Environment overrides read here, for tuning:
+ * LBFE_STEP_PATH=ldg forces the plain-load kernel; LBFE_STEP_THREADS=128|256
+ * sets the compute threads per block of the TMA kernel (default 128). */
 lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, void* d_workspace,
                     size_t ws_bytes, void* cuda_stream, lb_handle** out);
 

@@ -12,13 +12,15 @@ constexpr int kStepThreads = 256;
 // tma: use the TMA-staged kernel (FP32 only; every case of the launch has
 // nx % 4 == 0 and every item x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kStepThreads).
 // status: device word that a bounded wait which gave up sets to nonzero.
-cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nblocks, cudaStream_t s,
-                            const float* fin, float* fout, const DevCase<float>* cases, const Item* items,
-                            int* status);
+// nt: compute threads per block of the TMA kernel (128 or 256; the plain-load
+// kernel always uses kStepThreads).
+cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, int nblocks,
+                            cudaStream_t s, const float* fin, float* fout, const DevCase<float>* cases,
+                            const Item* items, int* status);
 cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks, cudaStream_t s,
                             const double* fin, double* fout, const DevCase<double>* cases,
                             const Item* items, int* status);
-int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma);
+int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt);
 int occupancy_step_f64(int scheme, int coll, int eos, bool nu);
 
 }  // namespace lbfe

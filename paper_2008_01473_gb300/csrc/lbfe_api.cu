@@ -26,17 +26,19 @@ int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
 
 int halo_of(int scheme) { return scheme == LB_IMPROVED ? 3 : 2; }
 
-// Widest strip of output columns a block can own. Lattices with nx % 4 == 0
-// get strips of a multiple of 4 columns, at most kStepThreads - 8 wide, as the
-// TMA-staged kernel needs (16-byte aligned runs of [x0 - 4, x0 + wv + 4)).
-int strip_width(const lb_case& c)
+// Widest strip of output columns a block of nt threads can own. Lattices with
+// nx % 4 == 0 get strips of a multiple of 4 columns, at most nt - 8 wide, as
+// the TMA-staged kernel needs (16-byte aligned runs of [x0 - 4, x0 + wv + 4)).
+int strip_width(const lb_case& c, int nt) { return c.nx % 4 == 0 ? nt - 8 : nt - 2 * halo_of(c.scheme); }
+
+int strips_of(const lb_case& c, int nt) { return (c.nx + strip_width(c, nt) - 1) / strip_width(c, nt); }
+
+constexpr int kMinBlockThreads = 128;  // narrowest block any path uses
+
+int64_t max_items_of(const lb_case& c)
 {
-    return c.nx % 4 == 0 ? kStepThreads - 8 : kStepThreads - 2 * halo_of(c.scheme);
+    return (int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinRows - 1) / kMinRows);
 }
-
-int strips_of(const lb_case& c) { return (c.nx + strip_width(c) - 1) / strip_width(c); }
-
-int64_t max_items_of(const lb_case& c) { return (int64_t)strips_of(c) * ((c.ny + kMinRows - 1) / kMinRows); }
 
 struct Layout {
     size_t cases32, cases64, items, f[2], scratch, partials, red, status, total;
@@ -132,6 +134,7 @@ struct Group {
     int scheme, coll, eos;
     bool nu;
     bool tma;              // TMA-staged kernel (FP32, every nx % 4 == 0)
+    int nt;                // compute threads per block
     int64_t first, count;  // slice of the item array
 };
 
@@ -149,7 +152,8 @@ struct lb_handle {
     std::vector<char> inited;
     std::vector<Group> groups;
     std::vector<Item> items;
-    int path = 0;  // 0: TMA-staged kernel where eligible, 1: plain-load kernel only
+    int path = 0;           // 0: TMA-staged kernel where eligible, 1: plain-load kernel only
+    int tma_threads = 128;  // compute threads per block of the TMA kernel (128 or 256)
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -218,13 +222,14 @@ void build_items(lb_handle* h)
                     if (members.empty()) continue;
                     bool tma = h->prec == LB_FP32 && h->path != 1;
                     for (int i : members) tma = tma && h->cases[i].nx % 4 == 0;
-                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma)
+                    const int nt = tma ? h->tma_threads : kStepThreads;
+                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
                                                        : occupancy_step_f64(s, co, e, nu == 1);
                     const double slots = (double)sms * occ;
-                    Group g{s, co, e, nu == 1, tma, (int64_t)h->items.size(), 0};
+                    Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
                     for (int i : members) {
                         const lb_case& c = h->cases[i];
-                        const int ns = strips_of(c);
+                        const int ns = strips_of(c, nt);
                         const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
                         const double share = slots * ((double)c.nx * c.ny) / nodes;
                         int nseg = std::max(1, (int)std::floor(share / ns));
@@ -306,6 +311,7 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     h->steps.assign(ncases, 0);
     h->inited.assign(ncases, 0);
     if (const char* p = std::getenv("LBFE_STEP_PATH")) h->path = std::strcmp(p, "ldg") == 0 ? 1 : 0;
+    if (const char* p = std::getenv("LBFE_STEP_THREADS")) h->tma_threads = std::atoi(p) == 256 ? 256 : 128;
     build_items(h);
     lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
                                           cudaMemcpyHostToDevice, h->stream),
@@ -385,7 +391,7 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
         for (const Group& g : h->groups) {
             cudaError_t e;
             if (h->prec == LB_FP32)
-                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, (int)g.count, h->stream,
+                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, h->stream,
                                     (const float*)h->fbuf(h->cur), (float*)h->fbuf(h->cur ^ 1), h->dc32(),
                                     h->ditems() + g.first, h->status());
             else
