@@ -12,8 +12,9 @@ constexpr int kStepThreads = 256;
 // tma: use the TMA-staged kernel (FP32 only; every case of the launch has
 // nx % 4 == 0 and every item x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kStepThreads).
 // status: device word that a bounded wait which gave up sets to nonzero.
-// nt: compute threads per block of the TMA kernel (128 or 256; the plain-load
-// kernel always uses kStepThreads).
+// nt: kernel shape on the TMA path: 0 = two columns per thread with packed
+// FP32 arithmetic (256 columns per block), 128 or 256 = one column per
+// thread. The plain-load kernel always uses kStepThreads.
 cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, int nblocks,
                             cudaStream_t s, const float* fin, float* fout, const DevCase<float>* cases,
                             const Item* items, int* status);

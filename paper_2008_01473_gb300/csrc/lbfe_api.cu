@@ -153,7 +153,7 @@ struct lb_handle {
     std::vector<Group> groups;
     std::vector<Item> items;
     int path = 0;           // 0: TMA-staged kernel where eligible, 1: plain-load kernel only
-    int tma_threads = 128;  // compute threads per block of the TMA kernel (128 or 256)
+    int tma_threads = 0;    // TMA kernel shape: 0 packed two-column, 128 or 256 one-column
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -222,14 +222,15 @@ void build_items(lb_handle* h)
                     if (members.empty()) continue;
                     bool tma = h->prec == LB_FP32 && h->path != 1;
                     for (int i : members) tma = tma && h->cases[i].nx % 4 == 0;
-                    const int nt = tma ? h->tma_threads : kStepThreads;
+                    const int nt = tma ? h->tma_threads : kStepThreads;  // 0: packed two-column kernel
+                    const int width = nt == 0 ? 256 : nt;                   // columns per block
                     const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
                                                        : occupancy_step_f64(s, co, e, nu == 1);
                     const double slots = (double)sms * occ;
                     Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
                     for (int i : members) {
                         const lb_case& c = h->cases[i];
-                        const int ns = strips_of(c, nt);
+                        const int ns = strips_of(c, width);
                         const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
                         const double share = slots * ((double)c.nx * c.ny) / nodes;
                         int nseg = std::max(1, (int)std::floor(share / ns));
@@ -311,7 +312,10 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     h->steps.assign(ncases, 0);
     h->inited.assign(ncases, 0);
     if (const char* p = std::getenv("LBFE_STEP_PATH")) h->path = std::strcmp(p, "ldg") == 0 ? 1 : 0;
-    if (const char* p = std::getenv("LBFE_STEP_THREADS")) h->tma_threads = std::atoi(p) == 256 ? 256 : 128;
+    if (const char* p = std::getenv("LBFE_STEP_THREADS")) {
+        const int v = std::atoi(p);
+        h->tma_threads = (v == 128 || v == 256) ? v : 0;
+    }
     build_items(h);
     lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
                                           cudaMemcpyHostToDevice, h->stream),

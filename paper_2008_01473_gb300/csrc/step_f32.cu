@@ -1,14 +1,17 @@
 // Instantiations of the fused step kernels with FP32 populations and arithmetic.
 #include "launch.h"
-#include "step_tma.cuh"
+#include "step_pair.cuh"
 
 namespace lbfe {
 
 namespace {
+// NT = 0 selects the two-columns-per-thread packed kernel
 template <int S, int C, int E, bool NU, bool TMA, int NT>
 void* kernel_ptr()
 {
-    if constexpr (TMA)
+    if constexpr (TMA && NT == 0)
+        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU>);
+    else if constexpr (TMA)
         return reinterpret_cast<void*>(&step_kernel_tma<float, NT, S, C, E, NU>);
     else
         return reinterpret_cast<void*>(&step_kernel<float, kStepThreads, S, C, E, NU>);
@@ -28,12 +31,16 @@ void* pick(int scheme, int coll, int eos, bool nu)
 
 size_t tma_smem(int nt)
 {
-    return nt == 128 ? tma_dynamic_smem<float, 128>() : tma_dynamic_smem<float, 256>();
+    return nt == 0 ? pair_dynamic_smem<float>()
+                   : (nt == 128 ? tma_dynamic_smem<float, 128>() : tma_dynamic_smem<float, 256>());
 }
+
+int block_threads(bool tma, int nt) { return !tma ? kStepThreads : (nt == 0 ? kPairThreads + 32 : nt + 32); }
 
 void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 {
     void* k = !tma           ? pick<false, kStepThreads>(scheme, coll, eos, nu)
+              : nt == 0      ? pick<true, 0>(scheme, coll, eos, nu)
               : nt == 128    ? pick<true, 128>(scheme, coll, eos, nu)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;
@@ -52,15 +59,15 @@ cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, in
     void* k = resolve(scheme, coll, eos, nu, tma, nt);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
-    // the TMA kernel adds one producer warp to its nt compute threads
-    return cudaLaunchKernel(k, dim3(nblocks), dim3(tma ? nt + 32 : kStepThreads), args, tma ? tma_smem(nt) : 0, s);
+    // the TMA kernels add one producer warp to their compute threads
+    return cudaLaunchKernel(k, dim3(nblocks), dim3(block_threads(tma, nt)), args, tma ? tma_smem(nt) : 0, s);
 }
 
 int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 {
     void* k = resolve(scheme, coll, eos, nu, tma, nt);
     int n = 0;
-    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, tma ? nt + 32 : kStepThreads,
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block_threads(tma, nt),
                                                             tma ? tma_smem(nt) : 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;

@@ -1,0 +1,488 @@
+// FP32 fused step with two lattice columns per thread and packed FP32
+// arithmetic (FADD2 / FMUL2 / FFMA2 of sm_100+), fed by the TMA row ring of
+// step_tma.cuh.
+//
+// Same method and stage plan as step_kernel.cuh (A: pull, rho, j; B: mu_c;
+// C: grad mu_c, F, u, phi u; D: correction C1/C7, collision, store), but
+// thread p of the kPairThreads compute threads owns the two adjacent ring
+// columns j = 2p and 2p + 1, i.e. lattice columns x0 - 4 + j and x0 - 3 + j.
+// Every per-node quantity is a float2 (.x = column j, .y = column j + 1), so
+// one packed instruction advances two nodes. In the five-point neighbourhoods
+// of the stencils the pair's own values come from registers; only the columns
+// j - 1 and j + 2 are read from the shared-memory field rows. Populations
+// are stored with 64-bit stores (x0 and wv are multiples of 4).
+//
+// Column coverage per stage (ring columns; wv = strip width, halo HX):
+//   A: all pairs (columns the ring does not hold give unused values)
+//   B: pairs 1 .. (wv + 6)/2 - 1   -> columns [2, wv + 6)
+//   C: same pairs (improved)       -> columns [2, wv + 6)
+//   D: pairs 2 .. (wv + 4)/2 - 1   -> columns [4, wv + 4) = the strip
+// The improved scheme needs rho on [1, wv + 7), mu_c on [2, wv + 6) and phi u
+// on [3, wv + 5); the standard one rho on [2, wv + 6) and mu_c on [3, wv + 5).
+#pragma once
+
+#include "step_tma.cuh"
+
+namespace lbfe {
+
+constexpr int kPairThreads = 128;             // compute threads per block
+constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block
+constexpr int kPairSlots = 8;                 // TMA ring slots
+
+// ------------------------------------------------------------ packed FP32
+__device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __ffma2_rn(b, v2(-1.0f), a); }
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+// Row of a field around the pair: own (x = col j, y = col j + 1) plus the
+// neighbours at j - 1 (l) and j + 2 (r).
+struct Row2 {
+    float2 c;
+    float l, r;
+    __device__ __forceinline__ float2 E() const { return make_float2(c.y, r); }
+    __device__ __forceinline__ float2 W() const { return make_float2(l, c.x); }
+};
+
+__device__ __forceinline__ Row2 row2(const float* row, int j, float2 own)
+{
+    Row2 q;
+    q.c = own;
+    q.l = row[j - 1];
+    q.r = row[j + 2];
+    return q;
+}
+
+// 6 sum_a w_a (phi(x + e_a) - phi(x)) with rows S (y-1), C (y), N (y+1)
+__device__ __forceinline__ float2 lap2(const Row2& S, const Row2& C, const Row2& N)
+{
+    const float2 edges = (C.E() + C.W()) + (N.c + S.c);
+    const float2 corners = (N.E() + S.W()) + (N.W() + S.E());
+    return fma2(edges, v2(4.0f / 6.0f), fma2(corners, v2(1.0f / 6.0f), C.c * v2(-20.0f / 6.0f)));
+}
+
+// Eq. 17 components
+__device__ __forceinline__ float2 gx2(const Row2& S, const Row2& C, const Row2& N)
+{
+    return fma2(C.E() - C.W(), v2(1.0f / 3.0f), ((N.E() - S.W()) + (S.E() - N.W())) * v2(1.0f / 12.0f));
+}
+__device__ __forceinline__ float2 gy2(const Row2& S, const Row2& N)
+{
+    return fma2(N.c - S.c, v2(1.0f / 3.0f), ((N.E() - S.W()) + (N.W() - S.E())) * v2(1.0f / 12.0f));
+}
+
+template <int EOS>
+__device__ __forceinline__ float2 dEf2(const DevCase<float>& c, float2 rho)
+{
+    float2 out;
+    if (EOS == 0) {
+        const float2 r = make_float2(__fdividef(1.0f, fmaf(-c.b, rho.x, 1.0f)),
+                                     __fdividef(1.0f, fmaf(-c.b, rho.y, 1.0f)));
+        const float2 lg = make_float2(__logf(rho.x * r.x), __logf(rho.y * r.y));
+        out = fma2(v2(c.RT), lg + r, rho * v2(-2.0f * c.a));
+    } else {
+        const float2 n = rho * v2(0.25f * c.b);
+        const float2 r = make_float2(__fdividef(1.0f, 1.0f - n.x), __fdividef(1.0f, 1.0f - n.y));
+        const float2 r2 = r * r;
+        const float2 lg = make_float2(__logf(rho.x), __logf(rho.y));
+        const float2 t1 = n * (v2(4.0f) - v2(3.0f) * n) * r2;
+        const float2 t2 = n * (v2(4.0f) - v2(2.0f) * n) * r2 * r;
+        out = fma2(v2(c.RT), lg + v2(1.0f) + t1 + t2, rho * v2(-2.0f * c.a));
+    }
+    return out;
+}
+
+// Moment-space collision (Eqs. 9 / 28) on deviation populations, packed.
+// Same algebra as collide() in lbfe_device.cuh.
+template <int SCHEME>
+__device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rho, float2 jx, float2 jy,
+                                         float2 ux, float2 uy, float2 Fx, float2 Fy, float2 mu, float2 C1,
+                                         float2 C7, const DevCase<float>& c, float2 le, float2 ls, float2 lq,
+                                         float2 lv)
+{
+    const float2 sa = (d[1] + d[3]) + (d[2] + d[4]);
+    const float2 sd = (d[5] + d[7]) + (d[6] + d[8]);
+    const float2 m_e = fma2(v2(2.0f), sd, fma2(v2(-4.0f), d[0], v2(0.0f) - sa));
+    const float2 m_s = fma2(v2(-2.0f), sa, fma2(v2(4.0f), d[0], sd));
+    const float2 d57 = d[5] - d[7];
+    const float2 dxd = d57 + (d[8] - d[6]);
+    const float2 dyd = d57 + (d[6] - d[8]);
+    const float2 m_qx = fma2(v2(-2.0f), d[1] - d[3], dxd);
+    const float2 m_qy = fma2(v2(-2.0f), d[2] - d[4], dyd);
+    const float2 m_pxx = (d[1] + d[3]) - (d[2] + d[4]);
+    const float2 m_pxy = (d[5] + d[7]) - (d[6] + d[8]);
+
+    const float2 uxx = ux * ux, uyy = uy * uy;
+    const float2 ru2 = rho * (uxx + uyy);
+    float2 eq_e, eq_s, eq_qx, eq_qy;
+    if (SCHEME == 0) {
+        eq_e = fma2(v2(3.0f), ru2, v2(-2.0f) * drho);
+        eq_s = fma2(v2(-3.0f), ru2, drho);
+        eq_qx = v2(0.0f) - rho * ux;
+        eq_qy = v2(0.0f) - rho * uy;
+    } else {
+        const float2 pm3 = v2(c.c0) + mu;  // 3 p_m
+        eq_e = fma2(v2(3.0f), ru2, fma2(v2(-4.0f), rho, fma2(v2(2.0f), pm3, v2(2.0f * c.rho_ref))));
+        eq_s = fma2(v2(-3.0f), ru2, fma2(v2(4.0f), rho, fma2(v2(-3.0f), pm3, v2(-c.rho_ref))));
+        const float2 g2 = fma2(v2(-2.0f), rho, pm3);  // rho (gamma - 2)
+        eq_qx = g2 * ux;
+        eq_qy = g2 * uy;
+    }
+    const float2 eq_pxx = rho * (uxx - uyy);
+    const float2 eq_pxy = rho * ux * uy;
+
+    const float2 uF = fma2(ux, Fx, uy * Fy);
+    const float2 S_e = fma2(v2(6.0f), uF, v2(9.0f) * C1);
+    const float2 S_pxx = fma2(v2(2.0f), fma2(ux, Fx, v2(0.0f) - uy * Fy), v2(3.0f) * C7);
+    const float2 S_pxy = fma2(ux, Fy, uy * Fx);
+
+    // m* = m - lam (m - eq) + (1 - lam/2) S
+    const float2 he = fma2(v2(-0.5f), le, v2(1.0f)), hs = fma2(v2(-0.5f), ls, v2(1.0f));
+    const float2 hq = fma2(v2(-0.5f), lq, v2(1.0f)), hv = fma2(v2(-0.5f), lv, v2(1.0f));
+    const float2 pe = fma2(he, S_e, fma2(le, eq_e - m_e, m_e));
+    const float2 ps = fma2(hs, v2(-6.0f) * uF, fma2(ls, eq_s - m_s, m_s));
+    const float2 pqx = fma2(v2(0.0f) - hq, Fx, fma2(lq, eq_qx - m_qx, m_qx));
+    const float2 pqy = fma2(v2(0.0f) - hq, Fy, fma2(lq, eq_qy - m_qy, m_qy));
+    const float2 pxx = fma2(hv, S_pxx, fma2(lv, eq_pxx - m_pxx, m_pxx));
+    const float2 pxy = fma2(hv, S_pxy, fma2(lv, eq_pxy - m_pxy, m_pxy));
+
+    // f* = M^-1 m*
+    const float2 a0 = drho * v2(1.0f / 9.0f);
+    const float2 a1 = pe * v2(1.0f / 36.0f);
+    const float2 a2 = ps * v2(1.0f / 36.0f);
+    const float2 a3 = (jx + Fx) * v2(1.0f / 6.0f);
+    const float2 a4 = pqx * v2(1.0f / 12.0f);
+    const float2 a5 = (jy + Fy) * v2(1.0f / 6.0f);
+    const float2 a6 = pqy * v2(1.0f / 12.0f);
+    const float2 a7 = pxx * v2(0.25f);
+    const float2 a8 = pxy * v2(0.25f);
+    const float2 b_ax = fma2(v2(-2.0f), a2, a0 - a1);
+    const float2 b_dg = fma2(v2(2.0f), a1, a0 + a2);
+    const float2 ex = fma2(v2(-2.0f), a4, a3), ey = fma2(v2(-2.0f), a6, a5);
+    const float2 X = a3 + a4, Y = a5 + a6;
+    d[0] = fma2(v2(-4.0f), a1 - a2, a0);
+    d[1] = (b_ax + ex) + a7;
+    d[3] = (b_ax - ex) + a7;
+    d[2] = (b_ax + ey) - a7;
+    d[4] = (b_ax - ey) - a7;
+    d[5] = (b_dg + (X + Y)) + a8;
+    d[7] = (b_dg - (X + Y)) + a8;
+    d[6] = (b_dg + (Y - X)) - a8;
+    d[8] = (b_dg + (X - Y)) - a8;
+}
+
+template <int SCHEME>
+struct PairSmem {
+    float rho[4][kPairCols];
+    float mu[4][kPairCols];
+    float pux[SCHEME == 1 ? 4 : 1][kPairCols];
+    float puy[SCHEME == 1 ? 4 : 1][kPairCols];
+};
+
+struct PairRegs {
+    float2 f[4][kQ];  // pulled populations (deviation form) of the pair
+    float2 drho[4], jx[4], jy[4];
+    float2 mu[4];
+    float2 ux[2], uy[2], Fx[2], Fy[2];  // stage C results of two rows (improved)
+    float2 grx, gry;                    // stage B grad rho (standard)
+};
+
+struct PairCtx {
+    const float* ring;  // [kPairSlots][9][kPairCols]
+    uint64_t* full;
+    uint64_t* empty;
+    int* flag;
+    int* status;
+    int j;              // ring column of the pair's first node
+    bool b, c, d;       // pair active in stages B/C, D
+    int ks;             // ring slot of stored row ra - 1 (= s0 + it)
+    int rd;             // lattice row of stage D
+    float* out;         // fout + column of the pair's first node (stage D pairs)
+};
+
+__device__ __forceinline__ void pair_timeout(const PairCtx& X)
+{
+    *X.flag = 1;
+    atomicOr(X.status, 1);
+}
+
+template <int SCHEME, int COLL, int EOS, bool NU, int SLOT>
+__device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME>& sm,
+                                          PairRegs& R)
+{
+    using G = StepGeom<SCHEME>;
+    constexpr int S0 = SLOT, S1 = (SLOT + 3) & 3, S2 = (SLOT + 2) & 3, S3 = (SLOT + 1) & 3;
+    constexpr int SW = kPairCols;
+    const int j = X.j;
+
+    // ---------------------------------------------------------------- A
+    {
+        const int i2 = it + 2;  // stored row ra + 1
+        const int k2 = X.ks + 2 >= kPairSlots ? X.ks + 2 - kPairSlots : X.ks + 2;
+        if (it == 0) {
+            if (!mbar_wait(X.full + 0, 0u)) pair_timeout(X);
+            if (!mbar_wait(X.full + 1, 0u)) pair_timeout(X);
+        }
+        if (!mbar_wait(X.full + k2, (uint32_t)(i2 / kPairSlots) & 1u)) pair_timeout(X);
+        const int k1 = X.ks + 1 >= kPairSlots ? X.ks + 1 - kPairSlots : X.ks + 1;
+        const float* Rm = X.ring + (size_t)X.ks * kQ * SW;
+        const float* R0 = X.ring + (size_t)k1 * kQ * SW;
+        const float* Rp = X.ring + (size_t)k2 * kQ * SW;
+        const int jl = j > 0 ? j - 1 : 0;
+        const int jr = j + 2 < SW ? j + 2 : SW - 1;
+        float2* F = R.f[S0];
+        F[0] = ld2(R0 + 0 * SW + j);
+        F[1] = make_float2(R0[1 * SW + jl], R0[1 * SW + j]);
+        F[2] = ld2(Rm + 2 * SW + j);
+        F[3] = make_float2(R0[3 * SW + j + 1], R0[3 * SW + jr]);
+        F[4] = ld2(Rp + 4 * SW + j);
+        F[5] = make_float2(Rm[5 * SW + jl], Rm[5 * SW + j]);
+        F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jr]);
+        F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jr]);
+        F[8] = make_float2(Rp[8 * SW + jl], Rp[8 * SW + j]);
+        const float2 dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+        R.drho[S0] = dr;
+        R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+        R.jy[S0] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+        st2(sm.rho[S0] + j, v2(c.rho_ref) + dr);
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+    if (threadIdx.x == 0) mbar_arrive(X.empty + X.ks);  // stored row ra - 1 has no reader left
+
+    // ---------------------------------------------------------------- B
+    if (X.b && it >= G::NB) {
+        const float2 rr = v2(c.rho_ref);
+        const Row2 Sm = row2(sm.rho[S2], j, rr + R.drho[S2]);
+        const Row2 Sc = row2(sm.rho[S1], j, rr + R.drho[S1]);
+        const Row2 Sp = row2(sm.rho[S0], j, rr + R.drho[S0]);
+        const float2 mu = fma2(v2(-c.kappa), lap2(Sm, Sc, Sp), dEf2<EOS>(c, Sc.c));
+        R.mu[S1] = mu;
+        st2(sm.mu[S1] + j, mu);
+        if constexpr (SCHEME == 0) {
+            if (it >= G::ND) {  // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
+                const Row2 Qm = row2(sm.rho[S3], j, rr + R.drho[S3]);
+                R.grx = gx2(Qm, Sm, Sc);
+                R.gry = gy2(Qm, Sc);
+            }
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+
+    if constexpr (SCHEME == 1) {
+        // ------------------------------------------------------------ C
+        constexpr int U2 = SLOT & 1;
+        if (X.b && it >= G::NC) {
+            const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
+            const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
+            const Row2 Mp = row2(sm.mu[S1], j, R.mu[S1]);
+            const float2 gx = gx2(Mm, Mc, Mp), gy = gy2(Mm, Mp);
+            const float2 rho = v2(c.rho_ref) + R.drho[S2];
+            const float2 k = v2(1.0f / 3.0f) - rho;
+            const float2 Fx = k * gx, Fy = k * gy;
+            const float2 inv = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+            const float2 ux = fma2(v2(0.5f), Fx, R.jx[S2]) * inv;
+            const float2 uy = fma2(v2(0.5f), Fy, R.jy[S2]) * inv;
+            const float2 phi = (rho - (v2(c.c0) + Mc.c)) * v2(1.0f / 3.0f);
+            st2(sm.pux[S2] + j, phi * ux);
+            st2(sm.puy[S2] + j, phi * uy);
+            R.ux[U2] = ux;
+            R.uy[U2] = uy;
+            R.Fx[U2] = Fx;
+            R.Fy[U2] = Fy;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+        // ------------------------------------------------------------ D
+        constexpr int U3 = (SLOT + 1) & 1;
+        if (X.d && it >= G::ND) {
+            const Row2 Am = row2(sm.pux[S0], j, ld2(sm.pux[S0] + j));  // row ra - 4
+            const Row2 Ac = row2(sm.pux[S3], j, ld2(sm.pux[S3] + j));  // row ra - 3
+            const Row2 Ap = row2(sm.pux[S2], j, ld2(sm.pux[S2] + j));  // row ra - 2
+            const Row2 Bm = row2(sm.puy[S0], j, ld2(sm.puy[S0] + j));
+            const Row2 Bp = row2(sm.puy[S2], j, ld2(sm.puy[S2] + j));
+            const float2 Ax = gx2(Am, Ac, Ap), By = gy2(Bm, Bp);
+            const float2 C1 = Ax + By, C7 = Ax - By;
+            const float2 drho = R.drho[S3];
+            const float2 rho = v2(c.rho_ref) + drho;
+            const float2 mu = R.mu[S3];
+            float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
+            if (NU) {
+                lv = make_float2(shear_rate<SCHEME, NU, float>(c, rho.x, mu.x),
+                                 shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
+                if (COLL == 0) le = ls = lq = lv;
+            }
+            collide2<SCHEME>(R.f[S3], drho, rho, R.jx[S3], R.jy[S3], R.ux[U3], R.uy[U3], R.Fx[U3], R.Fy[U3], mu,
+                             C1, C7, c, le, ls, lq, lv);
+            float* o = X.out + (uint32_t)X.rd * c.pitch;
+            const uint32_t P = (uint32_t)c.plane;
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S3][a]);
+        }
+    } else {
+        // ------------------------------------------------------- D (standard)
+        if (X.d && it >= G::ND) {
+            const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
+            const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
+            const Row2 Mp = row2(sm.mu[S1], j, R.mu[S1]);
+            const float2 gmx = gx2(Mm, Mc, Mp), gmy = gy2(Mm, Mp);
+            const float2 drho = R.drho[S2];
+            const float2 rho = v2(c.rho_ref) + drho;
+            const float2 mu = Mc.c;
+            const float2 Fx = fma2(R.grx, v2(1.0f / 3.0f), v2(0.0f) - rho * gmx);
+            const float2 Fy = fma2(R.gry, v2(1.0f / 3.0f), v2(0.0f) - rho * gmy);
+            const float2 inv = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
+            const float2 ux = fma2(v2(0.5f), Fx, R.jx[S2]) * inv;
+            const float2 uy = fma2(v2(0.5f), Fy, R.jy[S2]) * inv;
+            float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
+            if (NU) {
+                lv = make_float2(shear_rate<SCHEME, NU, float>(c, rho.x, mu.x),
+                                 shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
+                if (COLL == 0) le = ls = lq = lv;
+            }
+            collide2<SCHEME>(R.f[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, v2(0.0f), v2(0.0f), c, le,
+                             ls, lq, lv);
+            float* o = X.out + (uint32_t)X.rd * c.pitch;
+            const uint32_t P = (uint32_t)c.plane;
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S2][a]);
+        }
+    }
+    X.ks = X.ks + 1 == kPairSlots ? 0 : X.ks + 1;
+    if (it >= G::ND) X.rd = X.rd + 1 == c.ny ? 0 : X.rd + 1;
+}
+
+template <typename T>
+constexpr size_t pair_dynamic_smem()
+{
+    return (size_t)kPairSlots * kQ * kPairCols * sizeof(T) + 2 * kPairSlots * sizeof(uint64_t);
+}
+
+// Producer warp, lane 0: copy stored window rows s0 .. s_last into the ring.
+// Row i = s - s0 goes to slot i % kPairSlots; its previous occupant i - kPairSlots
+// is released by stage A of iteration i - kPairSlots.
+__device__ __forceinline__ void pair_produce(float* ring, uint64_t* full, uint64_t* empty, int* flag, int* status,
+                                             int s0, int s_last, const float* __restrict__ fin,
+                                             const DevCase<float>& c, const TmaRuns& runs, uint32_t row_bytes)
+{
+    const uint32_t P = (uint32_t)c.plane;
+    int k = 0, m = 0;
+    for (int s = s0; s <= s_last; ++s) {
+        if (m > 0 && !mbar_wait(empty + k, (uint32_t)(m - 1) & 1u)) {
+            *flag = 1;
+            atomicOr(status, 1);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        uint64_t* b = full + k;
+        mbar_expect_tx(b, row_bytes);
+        const uint32_t row = (uint32_t)wrapi(s, c.ny) * c.pitch;
+        float* dst = ring + (size_t)k * kQ * kPairCols;
+#pragma unroll 1
+        for (int a = 0; a < kQ; ++a) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                if (r < runs.n)
+                    bulk_load(dst + a * kPairCols + runs.j0[r], fin + (a * P + row + (uint32_t)runs.g0[r]),
+                              (uint32_t)runs.len[r] * sizeof(float), b);
+        }
+        if (++k == kPairSlots) {
+            k = 0;
+            ++m;
+        }
+    }
+}
+
+// FP32 step with kPairThreads compute threads (two columns each) and one
+// producer warp: blockDim.x == kPairThreads + 32. Every case of the launch
+// has nx % 4 == 0; every item x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kPairCols.
+template <int SCHEME, int COLL, int EOS, bool NU>
+__global__ void __launch_bounds__(kPairThreads + 32) step_kernel_pair(const float* __restrict__ fin,
+                                                                      float* __restrict__ fout,
+                                                                      const DevCase<float>* __restrict__ cases,
+                                                                      const Item* __restrict__ items,
+                                                                      int* __restrict__ status)
+{
+    using G = StepGeom<SCHEME>;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(16) PairSmem<SCHEME> sm;
+    __shared__ int flag;
+    const Item item = items[blockIdx.x];
+    const DevCase<float> c = cases[item.case_id];
+    fin += c.off;
+    fout += c.off;
+    const int niter = item.h + 2 * G::HX;
+    const int s0 = item.y0 - G::HX - 1, s_last = s0 + niter + 1;
+
+    float* ring = reinterpret_cast<float*>(dsm);
+    uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * kPairCols * sizeof(float));
+    uint64_t* empty = full + kPairSlots;
+    if (threadIdx.x == 0) {
+        flag = 0;
+        for (int k = 0; k < kPairSlots; ++k) {
+            mbar_init(full + k, 1);
+            mbar_init(empty + k, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= kPairThreads) {
+        if (threadIdx.x == kPairThreads) {
+            TmaRuns runs;
+            const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
+            runs.n = 0;
+            int x = start, jj = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int g = wrapi(x, c.nx);
+                const int len = min(end - x, c.nx - g);
+                runs.g0[r] = g;
+                runs.j0[r] = jj;
+                runs.len[r] = len;
+                if (x < end) runs.n = r + 1;
+                x += len;
+                jj += len;
+            }
+            pair_produce(ring, full, empty, &flag, status, s0, s_last, fin, c, runs,
+                         (uint32_t)(kQ * (end - start) * sizeof(float)));
+        }
+        return;
+    }
+
+    PairCtx X;
+    X.ring = ring;
+    X.full = full;
+    X.empty = empty;
+    X.flag = &flag;
+    X.status = status;
+    const int p = threadIdx.x;
+    X.j = 2 * p;
+    X.b = p >= 1 && 2 * p < item.wv + 6;
+    X.d = p >= 2 && 2 * p < item.wv + 4;
+    X.c = X.b;
+    X.ks = 0;
+    X.rd = item.y0;
+    X.out = fout + (item.x0 - 4 + 2 * p);  // valid for stage D pairs only
+
+    PairRegs R;
+    for (int base = 0; base < niter; base += 4) {
+        pair_iter<SCHEME, COLL, EOS, NU, 0>(base, X, c, sm, R);
+        if (base + 1 >= niter) break;
+        pair_iter<SCHEME, COLL, EOS, NU, 1>(base + 1, X, c, sm, R);
+        if (base + 2 >= niter) break;
+        pair_iter<SCHEME, COLL, EOS, NU, 2>(base + 2, X, c, sm, R);
+        if (base + 3 >= niter) break;
+        pair_iter<SCHEME, COLL, EOS, NU, 3>(base + 3, X, c, sm, R);
+    }
+    // every issued row was waited on by stage A; after a timeout, drain (bounded)
+    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+    if (threadIdx.x == 0 && flag) {
+        for (int s = max(s0, s_last - kPairSlots + 1); s <= s_last; ++s) {
+            const int i = s - s0;
+            mbar_wait(full + i % kPairSlots, (uint32_t)(i / kPairSlots) & 1u);
+        }
+    }
+}
+
+}  // namespace lbfe

@@ -266,22 +266,28 @@ def test_fp32_full_size_sampled_nodes():
 
 @pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
 @pytest.mark.parametrize("shape", [(4, 5), (8, 9), (12, 7), (532, 37), (496, 300), (1000, 16), (2048, 64)])
-def test_fp32_tma_path_bitwise_equals_plain_loads(scheme, shape, monkeypatch):
-    """The TMA-staged kernel (bulk copies of row runs into a shared-memory
-    ring, periodic wrap split into up to three runs) gives bit-identical
-    populations to the plain-load kernel, including lattices narrower than
-    the halo (nx = 4, 8, 12) and several strips and row segments."""
+def test_fp32_kernel_shapes_agree(scheme, shape, monkeypatch):
+    """The one-column TMA-staged kernels (bulk copies of row runs into a
+    shared-memory ring, periodic wrap split into up to three runs; 128 and 256
+    threads) give bit-identical populations to the plain-load kernel, and the
+    packed two-column kernel agrees to FP32 rounding, including lattices
+    narrower than the halo (nx = 4, 8, 12) and several strips and segments."""
     nx, ny = shape
     gc, _, rg, rl = _pair(nx, ny, scheme, lbfe.MRT, t=0.85)
     rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=6)
     snaps = {}
-    for path in ("ldg", "tma"):
+    for path, threads in (("ldg", "128"), ("tma", "128"), ("tma", "256"), ("tma", "0")):
         monkeypatch.setenv("LBFE_STEP_PATH", path)
+        monkeypatch.setenv("LBFE_STEP_THREADS", threads)
         lat = lbfe.Lattice([gc], precision=lbfe.FP32)
         lat.init_fields(0, rho0)
         lat.step(15)
-        snaps[path] = _gpu_pops(lat, 0)  # lattice columns only (row padding is never written)
+        snaps[(path, threads)] = _gpu_pops(lat, 0)  # lattice columns only (row padding is never written)
         _, st = lat.reductions()
         assert st[0] == 0
         lat.close()
-    assert np.array_equal(snaps["ldg"], snaps["tma"])
+    ref = snaps[("ldg", "128")]
+    assert np.array_equal(ref, snaps[("tma", "128")])
+    assert np.array_equal(ref, snaps[("tma", "256")])
+    # the packed two-column kernel rounds its fused multiply-adds differently
+    assert np.abs(snaps[("tma", "0")] - ref).max() < 2e-6 * np.abs(ref).max()
