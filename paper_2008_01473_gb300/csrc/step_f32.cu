@@ -45,8 +45,10 @@ void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;
     if (k && tma) {
-        // idempotent; needed once per kernel for more than 48 KB of dynamic smem
+        // idempotent; needed once per kernel for more than 48 KB of dynamic smem,
+        // and the largest shared-memory carveout so that two blocks fit per SM
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(nt));
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     return k;
 }

@@ -47,12 +47,14 @@ struct Row2 {
     __device__ __forceinline__ float2 W() const { return make_float2(l, c.x); }
 };
 
+// neighbours through aligned 64-bit loads (a stride-2 scalar pattern would
+// hit each shared-memory bank twice); needs 2 <= j <= kPairCols - 4
 __device__ __forceinline__ Row2 row2(const float* row, int j, float2 own)
 {
     Row2 q;
     q.c = own;
-    q.l = row[j - 1];
-    q.r = row[j + 2];
+    q.l = ld2(row + j - 2).y;
+    q.r = ld2(row + j + 2).x;
     return q;
 }
 
@@ -231,18 +233,20 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         const float* Rm = X.ring + (size_t)X.ks * kQ * SW;
         const float* R0 = X.ring + (size_t)k1 * kQ * SW;
         const float* Rp = X.ring + (size_t)k2 * kQ * SW;
-        const int jl = j > 0 ? j - 1 : 0;
-        const int jr = j + 2 < SW ? j + 2 : SW - 1;
+        // aligned pairs (j-2, j-1), (j, j+1), (j+2, j+3); the outermost pairs
+        // of the block read a clamped pair and produce unused values
+        const int jl = j >= 2 ? j - 2 : 0;
+        const int jr = j + 2 <= SW - 2 ? j + 2 : SW - 2;
         float2* F = R.f[S0];
         F[0] = ld2(R0 + 0 * SW + j);
-        F[1] = make_float2(R0[1 * SW + jl], R0[1 * SW + j]);
+        F[1] = make_float2(ld2(R0 + 1 * SW + jl).y, ld2(R0 + 1 * SW + j).x);
         F[2] = ld2(Rm + 2 * SW + j);
-        F[3] = make_float2(R0[3 * SW + j + 1], R0[3 * SW + jr]);
+        F[3] = make_float2(ld2(R0 + 3 * SW + j).y, ld2(R0 + 3 * SW + jr).x);
         F[4] = ld2(Rp + 4 * SW + j);
-        F[5] = make_float2(Rm[5 * SW + jl], Rm[5 * SW + j]);
-        F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jr]);
-        F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jr]);
-        F[8] = make_float2(Rp[8 * SW + jl], Rp[8 * SW + j]);
+        F[5] = make_float2(ld2(Rm + 5 * SW + jl).y, ld2(Rm + 5 * SW + j).x);
+        F[6] = make_float2(ld2(Rm + 6 * SW + j).y, ld2(Rm + 6 * SW + jr).x);
+        F[7] = make_float2(ld2(Rp + 7 * SW + j).y, ld2(Rp + 7 * SW + jr).x);
+        F[8] = make_float2(ld2(Rp + 8 * SW + jl).y, ld2(Rp + 8 * SW + j).x);
         const float2 dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
         R.drho[S0] = dr;
         R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
@@ -397,7 +401,7 @@ __device__ __forceinline__ void pair_produce(float* ring, uint64_t* full, uint64
 // producer warp: blockDim.x == kPairThreads + 32. Every case of the launch
 // has nx % 4 == 0; every item x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kPairCols.
 template <int SCHEME, int COLL, int EOS, bool NU>
-__global__ void __launch_bounds__(kPairThreads + 32) step_kernel_pair(const float* __restrict__ fin,
+__global__ void __launch_bounds__(kPairThreads + 32, 2) step_kernel_pair(const float* __restrict__ fin,
                                                                       float* __restrict__ fout,
                                                                       const DevCase<float>* __restrict__ cases,
                                                                       const Item* __restrict__ items,
