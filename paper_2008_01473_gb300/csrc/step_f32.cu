@@ -35,7 +35,7 @@ size_t tma_smem(int nt)
                    : (nt == 128 ? tma_dynamic_smem<float, 128>() : tma_dynamic_smem<float, 256>());
 }
 
-int block_threads(bool tma, int nt) { return !tma ? kStepThreads : (nt == 0 ? kPairThreads + 32 : nt + 32); }
+int block_threads(bool tma, int nt) { return !tma ? kStepThreads : (nt == 0 ? kPairThreads : nt + 32); }
 
 void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 {
@@ -46,7 +46,7 @@ void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
                              : nullptr;
     if (k && tma) {
         // idempotent; needed once per kernel for more than 48 KB of dynamic smem,
-        // and the largest shared-memory carveout so that two blocks fit per SM
+        // and the largest shared-memory carveout so that several blocks fit per SM
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(nt));
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }

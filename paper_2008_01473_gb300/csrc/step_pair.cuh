@@ -1,6 +1,7 @@
 // FP32 fused step with two lattice columns per thread and packed FP32
-// arithmetic (FADD2 / FMUL2 / FFMA2 of sm_100+), fed by the TMA row ring of
-// step_tma.cuh.
+// arithmetic (FADD2 / FMUL2 / FFMA2 of sm_100+), fed by a ring of stored rows
+// that bulk asynchronous copies (cp.async.bulk, the TMA helpers of
+// step_tma.cuh) fill two rows ahead of use.
 //
 // Same method and stage plan as step_kernel.cuh (A: pull, rho, j; B: mu_c;
 // C: grad mu_c, F, u, phi u; D: correction C1/C7, collision, store), but
@@ -11,6 +12,14 @@
 // of the stencils the pair's own values come from registers; only the columns
 // j - 1 and j + 2 are read from the shared-memory field rows. Populations
 // are stored with 64-bit stores (x0 and wv are multiples of 4).
+//
+// Ring: kPairSlots slots of one stored row (nine planes over the block's
+// columns [x0 - 4, x0 + wv + 4)), one full-mbarrier each. Stored row i = s - s0
+// lives in slot i % kPairSlots, phase (i / kPairSlots) & 1. Stage A of
+// iteration it reads rows it .. it + 2; after the block barrier that follows
+// it, row it is dead and lanes of warp 0 refill its slot with row
+// it + kPairSlots (one lane per plane and run), so no producer warp is needed
+// and three blocks fit on an SM.
 //
 // Column coverage per stage (ring columns; wv = strip width, halo HX):
 //   A: all pairs (columns the ring does not hold give unused values)
@@ -27,7 +36,7 @@ namespace lbfe {
 
 constexpr int kPairThreads = 128;             // compute threads per block
 constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block
-constexpr int kPairSlots = 8;                 // TMA ring slots
+constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight
 
 // ------------------------------------------------------------ packed FP32
 __device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
@@ -193,11 +202,14 @@ struct PairRegs {
 };
 
 struct PairCtx {
-    const float* ring;  // [kPairSlots][9][kPairCols]
+    float* ring;        // [kPairSlots][9][kPairCols]
     uint64_t* full;
-    uint64_t* empty;
     int* flag;
     int* status;
+    const float* fin;   // this case's stored populations
+    int s0, s_last;     // first / last stored window row of the block
+    TmaRuns runs;       // column runs of one stored row (periodic split)
+    uint32_t row_bytes;
     int j;              // ring column of the pair's first node
     bool b, c, d;       // pair active in stages B/C, D
     int ks;             // ring slot of stored row ra - 1 (= s0 + it)
@@ -209,6 +221,28 @@ __device__ __forceinline__ void pair_timeout(const PairCtx& X)
 {
     *X.flag = 1;
     atomicOr(X.status, 1);
+}
+
+// Warp 0 only: copy stored row i = s - s0 into slot k. Lane 0 arms the
+// slot's mbarrier with the byte count, then lane q < 9 * runs issues the copy
+// of plane q % 9, run q / 9.
+__device__ __forceinline__ void pair_issue(const PairCtx& X, const DevCase<float>& c, int i, int k)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t* b = X.full + k;
+    if (lane == 0) mbar_expect_tx(b, X.row_bytes);
+    __syncwarp();
+    if (lane < kQ * X.runs.n) {
+        const int a = lane % kQ, r = lane / kQ;
+        const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
+        const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
+        const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
+        const uint32_t row = (uint32_t)wrapi(X.s0 + i, c.ny) * c.pitch;
+        // order earlier generic-proxy reads of the slot before the async refill
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_load(X.ring + ((size_t)k * kQ + a) * kPairCols + j0,
+                  X.fin + ((uint32_t)a * (uint32_t)c.plane + row + (uint32_t)g0), (uint32_t)len * sizeof(float), b);
+    }
 }
 
 template <int SCHEME, int COLL, int EOS, bool NU, int SLOT>
@@ -253,8 +287,9 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         R.jy[S0] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
         st2(sm.rho[S0] + j, v2(c.rho_ref) + dr);
     }
-    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
-    if (threadIdx.x == 0) mbar_arrive(X.empty + X.ks);  // stored row ra - 1 has no reader left
+    __syncthreads();
+    // stored row it (ra - 1) has no reader left: refill its slot
+    if (threadIdx.x < 32 && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, c, it + kPairSlots, X.ks);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -273,7 +308,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             }
         }
     }
-    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+    __syncthreads();
 
     if constexpr (SCHEME == 1) {
         // ------------------------------------------------------------ C
@@ -297,7 +332,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             R.Fx[U2] = Fx;
             R.Fy[U2] = Fy;
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+        __syncthreads();
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
         if (X.d && it >= G::ND) {
@@ -360,52 +395,18 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
 template <typename T>
 constexpr size_t pair_dynamic_smem()
 {
-    return (size_t)kPairSlots * kQ * kPairCols * sizeof(T) + 2 * kPairSlots * sizeof(uint64_t);
+    return (size_t)kPairSlots * kQ * kPairCols * sizeof(T) + kPairSlots * sizeof(uint64_t);
 }
 
-// Producer warp, lane 0: copy stored window rows s0 .. s_last into the ring.
-// Row i = s - s0 goes to slot i % kPairSlots; its previous occupant i - kPairSlots
-// is released by stage A of iteration i - kPairSlots.
-__device__ __forceinline__ void pair_produce(float* ring, uint64_t* full, uint64_t* empty, int* flag, int* status,
-                                             int s0, int s_last, const float* __restrict__ fin,
-                                             const DevCase<float>& c, const TmaRuns& runs, uint32_t row_bytes)
-{
-    const uint32_t P = (uint32_t)c.plane;
-    int k = 0, m = 0;
-    for (int s = s0; s <= s_last; ++s) {
-        if (m > 0 && !mbar_wait(empty + k, (uint32_t)(m - 1) & 1u)) {
-            *flag = 1;
-            atomicOr(status, 1);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        uint64_t* b = full + k;
-        mbar_expect_tx(b, row_bytes);
-        const uint32_t row = (uint32_t)wrapi(s, c.ny) * c.pitch;
-        float* dst = ring + (size_t)k * kQ * kPairCols;
-#pragma unroll 1
-        for (int a = 0; a < kQ; ++a) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                if (r < runs.n)
-                    bulk_load(dst + a * kPairCols + runs.j0[r], fin + (a * P + row + (uint32_t)runs.g0[r]),
-                              (uint32_t)runs.len[r] * sizeof(float), b);
-        }
-        if (++k == kPairSlots) {
-            k = 0;
-            ++m;
-        }
-    }
-}
-
-// FP32 step with kPairThreads compute threads (two columns each) and one
-// producer warp: blockDim.x == kPairThreads + 32. Every case of the launch
-// has nx % 4 == 0; every item x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kPairCols.
+// FP32 step with kPairThreads threads of two columns each: blockDim.x ==
+// kPairThreads. Every case of the launch has nx % 4 == 0; every item
+// x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kPairCols.
 template <int SCHEME, int COLL, int EOS, bool NU>
-__global__ void __launch_bounds__(kPairThreads + 32, 2) step_kernel_pair(const float* __restrict__ fin,
-                                                                      float* __restrict__ fout,
-                                                                      const DevCase<float>* __restrict__ cases,
-                                                                      const Item* __restrict__ items,
-                                                                      int* __restrict__ status)
+__global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float* __restrict__ fin,
+                                                                    float* __restrict__ fout,
+                                                                    const DevCase<float>* __restrict__ cases,
+                                                                    const Item* __restrict__ items,
+                                                                    int* __restrict__ status)
 {
     using G = StepGeom<SCHEME>;
     extern __shared__ __align__(128) unsigned char dsm[];
@@ -416,50 +417,42 @@ __global__ void __launch_bounds__(kPairThreads + 32, 2) step_kernel_pair(const f
     fin += c.off;
     fout += c.off;
     const int niter = item.h + 2 * G::HX;
-    const int s0 = item.y0 - G::HX - 1, s_last = s0 + niter + 1;
 
-    float* ring = reinterpret_cast<float*>(dsm);
-    uint64_t* full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * kPairCols * sizeof(float));
-    uint64_t* empty = full + kPairSlots;
+    PairCtx X;
+    X.ring = reinterpret_cast<float*>(dsm);
+    X.full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * kPairCols * sizeof(float));
+    X.flag = &flag;
+    X.status = status;
+    X.fin = fin;
+    X.s0 = item.y0 - G::HX - 1;
+    X.s_last = X.s0 + niter + 1;
+    {
+        // runs of [x0 - 4, x0 + wv + 4) split at the periodic edges
+        const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
+        X.runs.n = 0;
+        int x = start, jj = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int g = wrapi(x, c.nx);
+            const int len = min(end - x, c.nx - g);
+            X.runs.g0[r] = g;
+            X.runs.j0[r] = jj;
+            X.runs.len[r] = len;
+            if (x < end) X.runs.n = r + 1;
+            x += len;
+            jj += len;
+        }
+        X.row_bytes = (uint32_t)(kQ * (end - start) * sizeof(float));
+    }
     if (threadIdx.x == 0) {
         flag = 0;
-        for (int k = 0; k < kPairSlots; ++k) {
-            mbar_init(full + k, 1);
-            mbar_init(empty + k, 1);
-        }
+        for (int k = 0; k < kPairSlots; ++k) mbar_init(X.full + k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    if (threadIdx.x < 32)
+        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) pair_issue(X, c, i, i);
 
-    if (threadIdx.x >= kPairThreads) {
-        if (threadIdx.x == kPairThreads) {
-            TmaRuns runs;
-            const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
-            runs.n = 0;
-            int x = start, jj = 0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const int g = wrapi(x, c.nx);
-                const int len = min(end - x, c.nx - g);
-                runs.g0[r] = g;
-                runs.j0[r] = jj;
-                runs.len[r] = len;
-                if (x < end) runs.n = r + 1;
-                x += len;
-                jj += len;
-            }
-            pair_produce(ring, full, empty, &flag, status, s0, s_last, fin, c, runs,
-                         (uint32_t)(kQ * (end - start) * sizeof(float)));
-        }
-        return;
-    }
-
-    PairCtx X;
-    X.ring = ring;
-    X.full = full;
-    X.empty = empty;
-    X.flag = &flag;
-    X.status = status;
     const int p = threadIdx.x;
     X.j = 2 * p;
     X.b = p >= 1 && 2 * p < item.wv + 6;
@@ -467,7 +460,7 @@ __global__ void __launch_bounds__(kPairThreads + 32, 2) step_kernel_pair(const f
     X.c = X.b;
     X.ks = 0;
     X.rd = item.y0;
-    X.out = fout + (item.x0 - 4 + 2 * p);  // valid for stage D pairs only
+    X.out = fout + (X.d ? item.x0 - 4 + 2 * p : 0);
 
     PairRegs R;
     for (int base = 0; base < niter; base += 4) {
@@ -480,11 +473,11 @@ __global__ void __launch_bounds__(kPairThreads + 32, 2) step_kernel_pair(const f
         pair_iter<SCHEME, COLL, EOS, NU, 3>(base + 3, X, c, sm, R);
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
-    asm volatile("bar.sync 1, %0;" ::"r"(kPairThreads) : "memory");
+    __syncthreads();
     if (threadIdx.x == 0 && flag) {
-        for (int s = max(s0, s_last - kPairSlots + 1); s <= s_last; ++s) {
-            const int i = s - s0;
-            mbar_wait(full + i % kPairSlots, (uint32_t)(i / kPairSlots) & 1u);
+        for (int s = max(X.s0, X.s_last - kPairSlots + 1); s <= X.s_last; ++s) {
+            const int i = s - X.s0;
+            mbar_wait(X.full + i % kPairSlots, (uint32_t)(i / kPairSlots) & 1u);
         }
     }
 }
