@@ -152,7 +152,9 @@ def run_gpu(args):
     nodes = n_side * n_side
     rho0 = inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), 0.01, seed=1 + rank)
     rho0_pin = torch.from_numpy(rho0).pin_memory()
-    lat = lbfe.Lattice([case], precision=lbfe.FP32, device=f"cuda:{local}")
+    prec = lbfe.FP64 if args.precision == "fp64" else lbfe.FP32
+    dtype = "f64" if prec == lbfe.FP64 else "f32"
+    lat = lbfe.Lattice([case], precision=prec, device=f"cuda:{local}")
     stream = lat.stream
 
     def barrier():
@@ -206,26 +208,29 @@ def run_gpu(args):
     if rank == 0:
         peak, src = _peaks()
         mean_ms = sum(per) / len(per)
-        achieved = BYTES_PER_NODE["f32"] * nodes / (mean_ms * 1e-3) / 1e9
+        achieved = BYTES_PER_NODE[dtype] * nodes / (mean_ms * 1e-3) / 1e9
         value = ws * nodes * args.steps / (total_ms * 1e-3) / 1e6
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace(f"{N_SIDE}x{N_SIDE}", f"{n_side}x{n_side}"),
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace(f"{N_SIDE}x{N_SIDE}", f"{n_side}x{n_side}").replace(
+                           "FP32 deviation storage", "FP32 deviation storage" if dtype == "f32" else "FP64"),
                        "nx": n_side, "ny": n_side, "nodes_per_gpu": nodes,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                       "l2": f"populations {2 * 36 * nodes / 1e9:.2f} GB per step vs 129 MB L2 (no flush)",
+                       "l2": f"populations {BYTES_PER_NODE[dtype] * nodes / 1e9:.2f} GB per step vs 129 MB L2 "
+                             "(no flush)",
                        "stable": stable},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(n_side),
-                         "peak_source": src, "bytes_per_node": BYTES_PER_NODE["f32"],
+                         "frac": round(achieved / peak, 4),
+                         "traffic": _profiled_traffic(n_side) if dtype == "f32" else None,
+                         "peak_source": src, "bytes_per_node": BYTES_PER_NODE[dtype],
                          "kernel_ms_mean": round(mean_ms, 4), "kernel_ms_min": round(min(per), 4)},
             "clocks": clk,
             "e2e": {"value": round(ws * nodes * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
                     "h2d_bytes_per_step": int(8 * nodes / args.steps),
-                    "d2h_bytes_per_step": int((8 + 3 * 8) * nodes / args.steps),
-                    "includes": "lb_init_fields from pinned host rho0 (with its validation read-back), "
+                    "d2h_bytes_per_step": int((3 * 8 * nodes + 40) / args.steps),
+                    "includes": "lb_init_fields from pinned host rho0 (validated on the device), "
                                 "K lb_step calls, lb_moments of rho, ux, uy to pinned host"},
             "gpu_launches": args.steps,
         }
@@ -291,6 +296,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=150)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

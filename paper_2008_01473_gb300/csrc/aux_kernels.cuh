@@ -1,157 +1,25 @@
 // Kernels around the time step: initial populations, macroscopic-field
 // export and the per-case FP64 reductions. They run once per call, not per
-// step, and work through FP64 scratch fields in the workspace.
+// step, through scratch fields of type C in the workspace: C is the storage
+// precision of the populations (per-node arithmetic in C; every sum over the
+// lattice in FP64).
 #pragma once
 
 #include "lbfe_device.cuh"
 
 namespace lbfe {
 
-// Scratch layout (FP64, one case at a time): four [ny][nx] fields.
-struct Scratch {
-    double* s0;  // rho
-    double* s1;  // j_x (moments) / u_x0 (init)
-    double* s2;  // j_y (moments) / u_y0 (init)
-    double* s3;  // mu_c
-};
-
-// mu_c = E_f'(rho) - kappa lap(rho) on the FP64 field s0 (Eq. 2).
-template <typename T, int EOS>
-__global__ void mu_field_kernel(DevCase<T> c, DevCase<double> cd, const double* __restrict__ rho,
-                                double* __restrict__ mu)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= c.nx) return;
-    const int nx = c.nx, ny = c.ny;
-    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    const int ym = wrapi(y - 1, ny) * nx, y0 = y * nx, yp = wrapi(y + 1, ny) * nx;
-    const double C = rho[y0 + x];
-    const double lap = lap9<double>(C, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x],
-                                    rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
-    mu[y0 + x] = dEf<EOS, double>(cd, C) - cd.kappa * lap;
-}
-
-// f(0) = M^-1 m_eq(rho0, u0) with mu_c of rho0, stored as f - w rho_ref in T.
-template <typename T, int SCHEME>
-__global__ void init_kernel(DevCase<T> c, DevCase<double> cd, const double* __restrict__ rho0,
-                            const double* __restrict__ ux0, const double* __restrict__ uy0,
-                            const double* __restrict__ mu0, T* __restrict__ f)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= c.nx) return;
-    const int i = y * c.nx + x;
-    const double rho = rho0[i];
-    const double ux = ux0 ? ux0[i] : 0.0, uy = uy0 ? uy0[i] : 0.0;
-    const double rr = cd.rho_ref;
-    // deviation moments of the equilibrium, then M^-1 (the collision with
-    // all rates 1 and no force returns exactly M^-1 m_eq)
-    double d[kQ];
-    for (int a = 0; a < kQ; ++a) d[a] = 0.0;
-    const double drho = rho - rr;
-    collide<SCHEME, double>(d, drho, rho, rho * ux, rho * uy, ux, uy, 0.0, 0.0, mu0[i], 0.0, 0.0, rr,
-                            cd.c0, 1.0, 1.0, 1.0, 1.0);
-    // with d = 0 the moments m_e, m_s, ... of d vanish, so the rates-1 collision
-    // leaves exactly the equilibrium; the conserved entries are set from
-    // drho and rho u directly.
-    // Storage holds post-collision populations before streaming (the step
-    // pulls f_a(x) from x - e_a), so f_a(0) of node x is stored at x - e_a.
-    constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-    for (int a = 0; a < kQ; ++a) {
-        const int64_t o = (int64_t)wrapi(y - ey[a], c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
-        f[c.off + a * c.plane + o] = (T)d[a];
-    }
-}
-
-// Pull the populations of the current state into FP64 rho, j_x, j_y fields.
-template <typename T>
-__global__ void pull_moments_kernel(DevCase<T> c, const T* __restrict__ f, double* __restrict__ rho,
-                                    double* __restrict__ jx, double* __restrict__ jy)
-{
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= c.nx) return;
-    const int nx = c.nx, ny = c.ny, pitch = c.pitch;
-    const int64_t P = c.plane;
-    f += c.off;
-    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    const int rm = wrapi(y - 1, ny) * pitch, r0 = y * pitch, rp = wrapi(y + 1, ny) * pitch;
-    double F[kQ];
-    F[0] = (double)f[0 * P + r0 + x];
-    F[1] = (double)f[1 * P + r0 + xm];
-    F[2] = (double)f[2 * P + rm + x];
-    F[3] = (double)f[3 * P + r0 + xp];
-    F[4] = (double)f[4 * P + rp + x];
-    F[5] = (double)f[5 * P + rm + xm];
-    F[6] = (double)f[6 * P + rm + xp];
-    F[7] = (double)f[7 * P + rp + xp];
-    F[8] = (double)f[8 * P + rp + xm];
-    const double dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
-    const int i = y * nx + x;
-    rho[i] = (double)c.rho_ref + dr;
-    jx[i] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
-    jy[i] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
-}
-
-// Per-block partial sums of a case's state: mass, kinetic energy, max |u|^2
-// and a count of non-physical nodes.
+// Per-block partial sums: mass (or any sum), kinetic energy, max |u|^2 and a
+// count of non-physical nodes.
 struct Partial {
     double mass, ke, umax2, bad;
 };
 
-// Velocity of Eq. 12 from rho, j and the force of the case's scheme; writes
-// the requested outputs and one Partial per block (blockDim.x == 256).
-template <int SCHEME>
-__global__ void __launch_bounds__(256) velocity_kernel(DevCase<double> cd, const double* __restrict__ rho,
-                                                       const double* __restrict__ jx,
-                                                       const double* __restrict__ jy,
-                                                       const double* __restrict__ mu,
-                                                       double* __restrict__ out_rho,
-                                                       double* __restrict__ out_ux,
-                                                       double* __restrict__ out_uy,
-                                                       double* __restrict__ out_mu,
-                                                       Partial* __restrict__ partials)
+// Block reduction of one Partial per thread (blockDim.x == 256) into
+// partials[block index].
+__device__ __forceinline__ void block_partial(double mass, double ke, double um, double bad,
+                                              Partial* __restrict__ partials)
 {
-    const int nx = cd.nx, ny = cd.ny;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
-    if (x < nx) {
-        const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-        const int ym = wrapi(y - 1, ny) * nx, y0 = y * nx, yp = wrapi(y + 1, ny) * nx;
-        const int i = y0 + x;
-        const double r = rho[i];
-        const double gmx = gradx9<double>(mu[y0 + xp], mu[y0 + xm], mu[yp + xp], mu[yp + xm], mu[ym + xp],
-                                          mu[ym + xm]);
-        const double gmy = grady9<double>(mu[yp + x], mu[ym + x], mu[yp + xp], mu[yp + xm], mu[ym + xp],
-                                          mu[ym + xm]);
-        double Fx, Fy;
-        if (SCHEME == 1) {
-            Fx = (1.0 / 3.0 - r) * gmx;
-            Fy = (1.0 / 3.0 - r) * gmy;
-        } else {
-            const double grx = gradx9<double>(rho[y0 + xp], rho[y0 + xm], rho[yp + xp], rho[yp + xm],
-                                              rho[ym + xp], rho[ym + xm]);
-            const double gry = grady9<double>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
-                                              rho[ym + xp], rho[ym + xm]);
-            Fx = grx * (1.0 / 3.0) - r * gmx;
-            Fy = gry * (1.0 / 3.0) - r * gmy;
-        }
-        const double ux = (jx[i] + 0.5 * Fx) / r;
-        const double uy = (jy[i] + 0.5 * Fy) / r;
-        if (out_rho) out_rho[i] = r;
-        if (out_ux) out_ux[i] = ux;
-        if (out_uy) out_uy[i] = uy;
-        if (out_mu) out_mu[i] = mu[i];
-        const double u2 = ux * ux + uy * uy;
-        mass = r;
-        ke = 0.5 * r * u2;
-        um = u2;
-        bad = (r > 0.0 && isfinite(u2) && isfinite(mu[i])) ? 0.0 : 1.0;
-    }
-    // block reduction: warp shuffles, then one value per warp through smem
     __shared__ double s[4][8];
     for (int o = 16; o > 0; o >>= 1) {
         mass += __shfl_xor_sync(0xffffffffu, mass, o);
@@ -179,10 +47,157 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<double> cd, const
     }
 }
 
+// Copy the FP64 initial density into C scratch and check it: one Partial per
+// block with the sum of rho0 and the count of values that are not finite,
+// not > 0, or outside the EOS domain (b rho < 1 for vdW, b rho / 4 < 1 for CS).
+template <typename C>
+__global__ void __launch_bounds__(256) rho0_kernel(int nx, int eos, double b, const double* __restrict__ rho0,
+                                                   C* __restrict__ out, Partial* __restrict__ partials)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    double sum = 0.0, bad = 0.0;
+    if (x < nx) {
+        const int64_t i = (int64_t)y * nx + x;
+        const double r = rho0[i];
+        const double lim = eos == 0 ? b * r : 0.25 * b * r;
+        const bool ok = r > 0.0 && isfinite(r) && lim < 1.0;
+        sum = ok ? r : 0.0;
+        bad = ok ? 0.0 : 1.0;
+        out[i] = (C)r;
+    }
+    block_partial(sum, 0.0, 0.0, bad, partials);
+}
+
+// mu_c = E_f'(rho) - kappa lap(rho) on a C field (Eq. 2).
+template <typename C, int EOS>
+__global__ void mu_field_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ mu)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= c.nx) return;
+    const int nx = c.nx, ny = c.ny;
+    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+    const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx, yp = (int64_t)wrapi(y + 1, ny) * nx;
+    const C Cc = rho[y0 + x];
+    const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
+                          rho[ym + xp], rho[ym + xm]);
+    mu[y0 + x] = dEf<EOS, C>(c, Cc) - c.kappa * lap;
+}
+
+// f(0) = M^-1 m_eq(rho0, u0) with mu_c of rho0, stored as f - w rho_ref in T.
+template <typename T, int SCHEME, typename C>
+__global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ rho0,
+                            const double* __restrict__ ux0, const double* __restrict__ uy0,
+                            const C* __restrict__ mu0, T* __restrict__ f)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= c.nx) return;
+    const int64_t i = (int64_t)y * c.nx + x;
+    const C rho = rho0[i];
+    const C ux = ux0 ? (C)ux0[i] : C(0), uy = uy0 ? (C)uy0[i] : C(0);
+    const C rr = cc.rho_ref;
+    // with all deviation moments zero, the collision with rates 1 and no
+    // force returns exactly M^-1 of the equilibrium (minus w rho_ref); the
+    // conserved entries come from drho and rho u directly
+    C d[kQ];
+    for (int a = 0; a < kQ; ++a) d[a] = C(0);
+    collide<SCHEME, C>(d, rho - rr, rho, rho * ux, rho * uy, ux, uy, C(0), C(0), mu0[i], C(0), C(0), rr, cc.c0,
+                       C(1), C(1), C(1), C(1));
+    // Storage holds post-collision populations before streaming (the step
+    // pulls f_a(x) from x - e_a), so f_a(0) of node x is stored at x - e_a.
+    constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    for (int a = 0; a < kQ; ++a) {
+        const int64_t o = (int64_t)wrapi(y - ey[a], c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
+        f[c.off + a * c.plane + o] = (T)d[a];
+    }
+}
+
+// Pull the populations of the current state into C fields rho, j_x, j_y.
+template <typename T, typename C>
+__global__ void pull_moments_kernel(DevCase<T> c, const T* __restrict__ f, C* __restrict__ rho,
+                                    C* __restrict__ jx, C* __restrict__ jy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= c.nx) return;
+    const int nx = c.nx, ny = c.ny, pitch = c.pitch;
+    const int64_t P = c.plane;
+    f += c.off;
+    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+    const int64_t rm = (int64_t)wrapi(y - 1, ny) * pitch, r0 = (int64_t)y * pitch,
+                  rp = (int64_t)wrapi(y + 1, ny) * pitch;
+    C F[kQ];
+    F[0] = (C)f[0 * P + r0 + x];
+    F[1] = (C)f[1 * P + r0 + xm];
+    F[2] = (C)f[2 * P + rm + x];
+    F[3] = (C)f[3 * P + r0 + xp];
+    F[4] = (C)f[4 * P + rp + x];
+    F[5] = (C)f[5 * P + rm + xm];
+    F[6] = (C)f[6 * P + rm + xp];
+    F[7] = (C)f[7 * P + rp + xp];
+    F[8] = (C)f[8 * P + rp + xm];
+    const C dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+    const int64_t i = (int64_t)y * nx + x;
+    rho[i] = (C)c.rho_ref + dr;
+    jx[i] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+    jy[i] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+}
+
+// Velocity of Eq. 12 from rho, j and the force of the case's scheme; writes
+// the requested FP64 outputs and one Partial per block (blockDim.x == 256).
+template <int SCHEME, typename C>
+__global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* __restrict__ rho,
+                                                       const C* __restrict__ jx, const C* __restrict__ jy,
+                                                       const C* __restrict__ mu, double* __restrict__ out_rho,
+                                                       double* __restrict__ out_ux, double* __restrict__ out_uy,
+                                                       double* __restrict__ out_mu, Partial* __restrict__ partials)
+{
+    const int nx = cc.nx, ny = cc.ny;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
+    if (x < nx) {
+        const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+        const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx,
+                      yp = (int64_t)wrapi(y + 1, ny) * nx;
+        const int64_t i = y0 + x;
+        const C r = rho[i];
+        const C gmx = gradx9<C>(mu[y0 + xp], mu[y0 + xm], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
+        const C gmy = grady9<C>(mu[yp + x], mu[ym + x], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
+        C Fx, Fy;
+        if (SCHEME == 1) {
+            Fx = (C(1.0 / 3.0) - r) * gmx;
+            Fy = (C(1.0 / 3.0) - r) * gmy;
+        } else {
+            const C grx = gradx9<C>(rho[y0 + xp], rho[y0 + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp],
+                                    rho[ym + xm]);
+            const C gry = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp],
+                                    rho[ym + xm]);
+            Fx = grx * C(1.0 / 3.0) - r * gmx;
+            Fy = gry * C(1.0 / 3.0) - r * gmy;
+        }
+        const C ux = (jx[i] + C(0.5) * Fx) / r;
+        const C uy = (jy[i] + C(0.5) * Fy) / r;
+        if (out_rho) out_rho[i] = (double)r;
+        if (out_ux) out_ux[i] = (double)ux;
+        if (out_uy) out_uy[i] = (double)uy;
+        if (out_mu) out_mu[i] = (double)mu[i];
+        const double u2 = (double)ux * (double)ux + (double)uy * (double)uy;
+        mass = (double)r;
+        ke = 0.5 * (double)r * u2;
+        um = u2;
+        bad = (r > C(0) && isfinite(u2) && isfinite((double)mu[i])) ? 0.0 : 1.0;
+    }
+    block_partial(mass, ke, um, bad, partials);
+}
+
 // Fold a case's partials in a fixed order into out[0..4] =
 // {mass, kinetic energy, max |u|, steps, bad-node count}.
 static __global__ void finalize_kernel(const Partial* __restrict__ partials, int64_t n, double steps,
-                                double* __restrict__ out)
+                                       double* __restrict__ out)
 {
     __shared__ double s[4][256];
     double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;

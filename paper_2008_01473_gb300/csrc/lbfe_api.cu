@@ -252,29 +252,70 @@ void build_items(lb_handle* h)
 
 lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
 
-// Pull-moment, chemical-potential and velocity passes for one case; outputs
-// may be device pointers or NULL. Partials of the case land in h->partials().
-lb_status fields_pass(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
+// Pull-moment, chemical-potential and velocity passes for one case, in the
+// storage precision C per node (FP64 sums); outputs may be device pointers
+// or NULL. Partials of the case land in h->partials().
+template <typename T, typename C>
+lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
 {
     const lb_case& c = h->cases[i];
-    const DevCase<double> cd = dev_case<double>(c, h->L.off[i], h->rho_ref[i]);
+    const DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
+    const DevCase<C> cc = dev_case<C>(c, h->L.off[i], h->rho_ref[i]);
     const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
-    double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2), *s3 = h->scratch(3);
-    if (h->prec == LB_FP32) {
-        const DevCase<float> cf = dev_case<float>(c, h->L.off[i], h->rho_ref[i]);
-        pull_moments_kernel<float><<<grd, blk, 0, h->stream>>>(cf, (const float*)h->fbuf(h->cur), s0, s1, s2);
-    } else {
-        pull_moments_kernel<double><<<grd, blk, 0, h->stream>>>(cd, (const double*)h->fbuf(h->cur), s0, s1, s2);
-    }
+    C* s0 = reinterpret_cast<C*>(h->scratch(0));
+    C* s1 = reinterpret_cast<C*>(h->scratch(1));
+    C* s2 = reinterpret_cast<C*>(h->scratch(2));
+    C* s3 = reinterpret_cast<C*>(h->scratch(3));
+    pull_moments_kernel<T, C><<<grd, blk, 0, h->stream>>>(ct, (const T*)h->fbuf(h->cur), s0, s1, s2);
     if (c.eos == LB_VDW)
-        mu_field_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+        mu_field_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
     else
-        mu_field_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
+        mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
     if (c.scheme == LB_IMPROVED)
-        velocity_kernel<1><<<grd, blk, 0, h->stream>>>(cd, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
+        velocity_kernel<1, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
     else
-        velocity_kernel<0><<<grd, blk, 0, h->stream>>>(cd, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
+        velocity_kernel<0, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
     return h->cuda(cudaGetLastError(), "fields pass");
+}
+
+lb_status fields_pass(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
+{
+    return h->prec == LB_FP32 ? fields_pass_t<float, float>(h, i, o_rho, o_ux, o_uy, o_mu)
+                              : fields_pass_t<double, double>(h, i, o_rho, o_ux, o_uy, o_mu);
+}
+
+// Initial populations of case i from the FP64 fields already in scratch
+// (u0 in scratch 1, 2 when given): rho0 -> C scratch 0 with a device-side
+// check, mu_c of rho0, then the equilibrium.
+template <typename T, typename C>
+lb_status init_pass_t(lb_handle* h, int i, const double* d_rho0, const double* pux, const double* puy)
+{
+    const lb_case& c = h->cases[i];
+    const int64_t N = (int64_t)c.nx * c.ny;
+    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    C* r0 = reinterpret_cast<C*>(h->scratch(4));
+    C* mu = reinterpret_cast<C*>(h->scratch(5));
+    rho0_kernel<C><<<grd, blk, 0, h->stream>>>(c.nx, c.eos, c.b, d_rho0, r0, h->partials());
+    finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), (int64_t)grd.x * grd.y, 0.0, h->red() + 8 * i);
+    double chk[5];
+    lb_status s = h->cuda(cudaMemcpyAsync(chk, h->red() + 8 * i, sizeof chk, cudaMemcpyDeviceToHost, h->stream),
+                          "check rho0");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "check rho0");
+    if (s != LB_OK) return s;
+    if (chk[4] != 0.0) return h->fail(LB_E_INVALID, "rho0 must be finite, > 0 and inside the EOS domain");
+    if (h->prec == LB_FP32) h->rho_ref[i] = c.rho_ref > 0 ? c.rho_ref : chk[0] / (double)N;
+    if ((s = h->upload_case(i)) != LB_OK) return s;
+    const DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
+    const DevCase<C> cc = dev_case<C>(c, h->L.off[i], h->rho_ref[i]);
+    if (c.eos == LB_VDW)
+        mu_field_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, r0, mu);
+    else
+        mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, r0, mu);
+    if (c.scheme == LB_IMPROVED)
+        init_kernel<T, 1, C><<<grd, blk, 0, h->stream>>>(ct, cc, r0, pux, puy, mu, (T*)h->fbuf(h->cur));
+    else
+        init_kernel<T, 0, C><<<grd, blk, 0, h->stream>>>(ct, cc, r0, pux, puy, mu, (T*)h->fbuf(h->cur));
+    return h->cuda(cudaGetLastError(), "init kernels");
 }
 
 }  // namespace
@@ -340,46 +381,27 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     const int64_t N = (int64_t)c.nx * c.ny;
     const size_t bytes = N * sizeof(double);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2), *s3 = h->scratch(3);
-    lb_status s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
-    if (s == LB_OK && ux0) s = h->cuda(cudaMemcpyAsync(s1, ux0, bytes, kind, h->stream), "copy ux0");
-    if (s == LB_OK && uy0) s = h->cuda(cudaMemcpyAsync(s2, uy0, bytes, kind, h->stream), "copy uy0");
-    if (s != LB_OK) return s;
-    // validate on the host (init is a one-off)
-    std::vector<double> r(N);
-    s = h->cuda(cudaMemcpyAsync(r.data(), s0, bytes, cudaMemcpyDeviceToHost, h->stream), "check rho0");
-    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "check rho0");
-    if (s != LB_OK) return s;
-    double sum = 0.0;
-    for (double v : r) {
-        if (!(v > 0.0) || !std::isfinite(v)) return h->fail(LB_E_INVALID, "rho0 must be finite and > 0");
-        if (c.eos == LB_VDW && !(c.b * v < 1.0)) return h->fail(LB_E_INVALID, "rho0 outside 0 < b rho < 1");
-        if (c.eos == LB_CS && !(0.25 * c.b * v < 1.0)) return h->fail(LB_E_INVALID, "rho0 outside b rho/4 < 1");
-        sum += v;
+    double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2);
+    lb_status s = LB_OK;
+    const double* d_rho0 = rho0;
+    if (!on_device) {
+        s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
+        d_rho0 = s0;
     }
-    if (h->prec == LB_FP32) h->rho_ref[case_id] = c.rho_ref > 0 ? c.rho_ref : sum / (double)N;
-    if ((s = h->upload_case(case_id)) != LB_OK) return s;
-    const DevCase<double> cd = dev_case<double>(c, h->L.off[case_id], h->rho_ref[case_id]);
-    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
-    if (c.eos == LB_VDW)
-        mu_field_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
-    else
-        mu_field_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, s3);
-    const double* pux = ux0 ? s1 : nullptr;
-    const double* puy = uy0 ? s2 : nullptr;
-    if (h->prec == LB_FP32) {
-        const DevCase<float> cf = dev_case<float>(c, h->L.off[case_id], h->rho_ref[case_id]);
-        if (c.scheme == LB_IMPROVED)
-            init_kernel<float, 1><<<grd, blk, 0, h->stream>>>(cf, cd, s0, pux, puy, s3, (float*)h->fbuf(h->cur));
-        else
-            init_kernel<float, 0><<<grd, blk, 0, h->stream>>>(cf, cd, s0, pux, puy, s3, (float*)h->fbuf(h->cur));
-    } else {
-        if (c.scheme == LB_IMPROVED)
-            init_kernel<double, 1><<<grd, blk, 0, h->stream>>>(cd, cd, s0, pux, puy, s3, (double*)h->fbuf(h->cur));
-        else
-            init_kernel<double, 0><<<grd, blk, 0, h->stream>>>(cd, cd, s0, pux, puy, s3, (double*)h->fbuf(h->cur));
+    const double* pux = nullptr;
+    const double* puy = nullptr;
+    if (s == LB_OK && ux0) {
+        s = h->cuda(cudaMemcpyAsync(s1, ux0, bytes, kind, h->stream), "copy ux0");
+        pux = s1;
     }
-    if ((s = h->cuda(cudaGetLastError(), "init kernels")) != LB_OK) return s;
+    if (s == LB_OK && uy0) {
+        s = h->cuda(cudaMemcpyAsync(s2, uy0, bytes, kind, h->stream), "copy uy0");
+        puy = s2;
+    }
+    if (s != LB_OK) return s;
+    s = h->prec == LB_FP32 ? init_pass_t<float, float>(h, case_id, d_rho0, pux, puy)
+                           : init_pass_t<double, double>(h, case_id, d_rho0, pux, puy);
+    if (s != LB_OK) return s;
     h->steps[case_id] = 0;
     h->inited[case_id] = 1;
     return LB_OK;

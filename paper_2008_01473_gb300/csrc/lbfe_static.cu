@@ -103,17 +103,18 @@ extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const
     const DevCase<double> cd = make_case<double>(*c, rr);
     const dim3 blk(256), grd((c->nx + 255) / 256, c->ny);
     if (precision == LB_FP32)
-        pull_moments_kernel<float><<<grd, blk, 0, st>>>(make_case<float>(*c, rr), (const float*)d_pops, s0, s1, s2);
+        pull_moments_kernel<float, double>
+            <<<grd, blk, 0, st>>>(make_case<float>(*c, rr), (const float*)d_pops, s0, s1, s2);
     else
-        pull_moments_kernel<double><<<grd, blk, 0, st>>>(cd, (const double*)d_pops, s0, s1, s2);
+        pull_moments_kernel<double, double><<<grd, blk, 0, st>>>(cd, (const double*)d_pops, s0, s1, s2);
     if (c->eos == LB_VDW)
-        mu_field_kernel<double, 0><<<grd, blk, 0, st>>>(cd, cd, s0, s3);
+        mu_field_kernel<double, 0><<<grd, blk, 0, st>>>(cd, s0, s3);
     else
-        mu_field_kernel<double, 1><<<grd, blk, 0, st>>>(cd, cd, s0, s3);
+        mu_field_kernel<double, 1><<<grd, blk, 0, st>>>(cd, s0, s3);
     if (c->scheme == LB_IMPROVED)
-        velocity_kernel<1><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+        velocity_kernel<1, double><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
     else
-        velocity_kernel<0><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+        velocity_kernel<0, double><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
     finalize_kernel<<<1, 256, 0, st>>>(parts, (int64_t)grd.x * grd.y, 0.0, d_red);
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_E_CUDA;
 }
