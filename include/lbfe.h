@@ -115,8 +115,9 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 lb_status lb_step(lb_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of case case_id at the current step: rho and u of
- * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2; any output may be
- * NULL. Device outputs if on_device, else host (stream synchronised). */
+ * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2, computed per node in
+ * the storage precision and returned as FP64; any output may be NULL.
+ * Device outputs if on_device, else host (stream synchronised). */
 lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy,
                      double* mu, int32_t on_device);
 

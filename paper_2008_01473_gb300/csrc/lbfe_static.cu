@@ -79,6 +79,28 @@ cudaError_t scratch_ptr(void** out)
 }
 }  // namespace
 
+// The pass of lb_moments / lb_reductions in the storage precision T of the
+// populations (per-node arithmetic in T, sums in FP64), on the static scratch.
+template <typename T>
+void fields_static(const lb_case& c, double rho_ref, const T* d_pops, unsigned char* p, Partial* parts,
+                   double* d_rho, double* d_ux, double* d_uy, double* d_mu, dim3 grd, dim3 blk, cudaStream_t st)
+{
+    T* s0 = reinterpret_cast<T*>(p);
+    T* s1 = reinterpret_cast<T*>(p + kFieldBytes);
+    T* s2 = reinterpret_cast<T*>(p + 2 * kFieldBytes);
+    T* s3 = reinterpret_cast<T*>(p + 3 * kFieldBytes);
+    const DevCase<T> ct = make_case<T>(c, rho_ref);
+    pull_moments_kernel<T, T><<<grd, blk, 0, st>>>(ct, d_pops, s0, s1, s2);
+    if (c.eos == LB_VDW)
+        mu_field_kernel<T, 0><<<grd, blk, 0, st>>>(ct, s0, s3);
+    else
+        mu_field_kernel<T, 1><<<grd, blk, 0, st>>>(ct, s0, s3);
+    if (c.scheme == LB_IMPROVED)
+        velocity_kernel<1, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+    else
+        velocity_kernel<0, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+}
+
 extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const void* d_pops,
                                       double rho_ref, double* d_rho, double* d_ux, double* d_uy,
                                       double* d_mu, double* d_red, void* cuda_stream)
@@ -90,31 +112,16 @@ extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const
     void* base = nullptr;
     if (scratch_ptr(&base) != cudaSuccess) return LB_E_CUDA;
     unsigned char* p = static_cast<unsigned char*>(base);
-    double* s0 = reinterpret_cast<double*>(p);
-    double* s1 = reinterpret_cast<double*>(p + kFieldBytes);
-    double* s2 = reinterpret_cast<double*>(p + 2 * kFieldBytes);
-    double* s3 = reinterpret_cast<double*>(p + 3 * kFieldBytes);
     Partial* parts = reinterpret_cast<Partial*>(p + 4 * kFieldBytes);
     // Every scratch value read below is written earlier in the same call
-    // (all nodes of s0..s3, all partials of the grid), so nothing needs
-    // clearing between calls.
+    // (all nodes of the four fields, all partials of the grid), so nothing
+    // needs clearing between calls.
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const double rr = precision == LB_FP32 ? rho_ref : 0.0;
-    const DevCase<double> cd = make_case<double>(*c, rr);
     const dim3 blk(256), grd((c->nx + 255) / 256, c->ny);
     if (precision == LB_FP32)
-        pull_moments_kernel<float, double>
-            <<<grd, blk, 0, st>>>(make_case<float>(*c, rr), (const float*)d_pops, s0, s1, s2);
+        fields_static<float>(*c, rho_ref, (const float*)d_pops, p, parts, d_rho, d_ux, d_uy, d_mu, grd, blk, st);
     else
-        pull_moments_kernel<double, double><<<grd, blk, 0, st>>>(cd, (const double*)d_pops, s0, s1, s2);
-    if (c->eos == LB_VDW)
-        mu_field_kernel<double, 0><<<grd, blk, 0, st>>>(cd, s0, s3);
-    else
-        mu_field_kernel<double, 1><<<grd, blk, 0, st>>>(cd, s0, s3);
-    if (c->scheme == LB_IMPROVED)
-        velocity_kernel<1, double><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
-    else
-        velocity_kernel<0, double><<<grd, blk, 0, st>>>(cd, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+        fields_static<double>(*c, 0.0, (const double*)d_pops, p, parts, d_rho, d_ux, d_uy, d_mu, grd, blk, st);
     finalize_kernel<<<1, 256, 0, st>>>(parts, (int64_t)grd.x * grd.y, 0.0, d_red);
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_E_CUDA;
 }
