@@ -45,6 +45,8 @@ def _dist():
 
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_pair_spinodal4096.md")
+# files that define the FP32 step kernel and its launch
+STEP_SOURCES = ("launch.h", "lbfe_device.cuh", "step_f32.cu", "step_kernel.cuh", "step_pair.cuh", "step_tma.cuh")
 
 
 def _kernel_source_sha256() -> str:
@@ -52,11 +54,10 @@ def _kernel_source_sha256() -> str:
 
     d = os.path.join(ROOT, "paper_2008_01473_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in STEP_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
