@@ -242,6 +242,83 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def batched_cases(lbfe, n_cases: int = 256, seed: int = 7):
+    """The uneven batch: square periodic droplets, side uniform over the
+    multiples of 4 in [32, 512], T/T_c ~ U[0.8, 0.9], kappa ~ U[0.01, 0.03],
+    tau ~ U[0.8, 1.0], radius ~ U[0.15, 0.3] x side; improved scheme, BGK, vdW."""
+    import numpy as np
+
+    from paper_2008_01473_gb300 import inputs
+
+    rng = np.random.default_rng(seed)
+    tc, _ = lbfe.critical(lbfe.VDW, **VDW)
+    cases, rhos = [], []
+    for i in range(n_cases):
+        side = 4 * int(rng.integers(8, 129))
+        t = rng.uniform(0.8, 0.9)
+        kappa = rng.uniform(0.01, 0.03)
+        tau = rng.uniform(0.8, 1.0)
+        frac = rng.uniform(0.15, 0.3)
+        T = t * tc
+        rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], T)
+        cases.append(lbfe.Case(nx=side, ny=side, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, T=T,
+                               kappa=kappa, tau_v=tau, **VDW))
+        rhos.append(inputs.droplet(side, side, frac * side, rl, rg, seed=seed, case=i))
+    return cases, rhos
+
+
+def run_batched(args):
+    """Throughput of the uneven batch in one handle (one launch per step)
+    against one handle per case (one launch per case per step)."""
+    import torch
+
+    from paper_2008_01473_gb300 import build, lbfe
+
+    build.build()
+    torch.cuda.set_device(0)
+    cases, rhos = batched_cases(lbfe)
+    nodes = sum(c.nx * c.ny for c in cases)
+    lat = lbfe.Lattice(cases, precision=lbfe.FP32)
+    for i, r in enumerate(rhos):
+        lat.init_fields(i, r)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(args.steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    _, st = lat.reductions()
+    lat.close()
+    lats = []
+    for c, r in zip(cases, rhos):
+        l1 = lbfe.Lattice([c], precision=lbfe.FP32)
+        l1.init_fields(0, r)
+        l1.step(args.warmup)
+        lats.append(l1)
+    torch.cuda.synchronize()
+    e0.record(lats[0].stream)
+    for l1 in lats:
+        l1.step(args.steps)
+    e1.record(lats[0].stream)
+    torch.cuda.synchronize()
+    per_case_ms = e0.elapsed_time(e1)
+    for l1 in lats:
+        l1.close()
+    v = nodes * args.steps / (batched_ms * 1e-3) / 1e6
+    line = {"metric": METRIC, "value": round(v, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(batched_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched uneven droplets: " + (batched_cases.__doc__ or "").split(":")[1].strip(),
+                       "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum())},
+            "per_case_launches": {"value": round(nodes * args.steps / (per_case_ms * 1e-3) / 1e6, 1),
+                                  "unit": "MLUPS", "ms_per_step": round(per_case_ms / args.steps, 4)},
+            "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / args.steps * 1e-3) / 1e9, 1),
+                         "peak": _peaks()[0], "unit": "GB/s"}}
+    print(json.dumps(line), flush=True)
+
+
 def _oracle_sample():
     import oracle as O
     from oracle import thermo
@@ -298,11 +375,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched"],
+                    help="spinodal: the 4096^2 lattice (default); batched: 256 uneven droplets")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

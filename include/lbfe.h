@@ -111,7 +111,10 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
  * Eq. 10): one fused kernel launch per step and per group of cases that
- * share scheme, collision, EOS and viscosity mode. Enqueued asynchronously. */
+ * share scheme, collision, EOS, viscosity mode and nx % 4 == 0. Runs of 8
+ * steps replay a CUDA graph captured on the first such call (on a private
+ * stream, then launched on the handle's stream; set LBFE_GRAPH=0 before
+ * lb_create to launch every step directly). Enqueued asynchronously. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of case case_id at the current step: rho and u of

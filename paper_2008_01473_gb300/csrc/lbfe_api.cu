@@ -153,6 +153,9 @@ struct lb_handle {
     std::vector<Group> groups;
     std::vector<Item> items;
     int path = 0;           // 0: TMA-staged kernel where eligible, 1: plain-load kernel only
+    bool use_graph = true;  // replay lb_step through captured CUDA graphs
+    cudaStream_t cap_stream = nullptr;              // private stream used only for graph capture
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer 0 / 1
     int tma_threads = 0;    // TMA kernel shape: 0 packed two-column, 128 or 256 one-column
     std::string err;
 
@@ -195,6 +198,8 @@ struct lb_handle {
 
 namespace {
 
+constexpr int kGraphSteps = 8;  // steps per captured graph (even: buffer parity returns)
+
 // Split every case into column strips and row segments so that one launch
 // fills the GPU about once: each case gets a share of the resident block
 // slots proportional to its node count.
@@ -209,19 +214,21 @@ void build_items(lb_handle* h)
     for (int s = 0; s < 2; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
-                for (int nu = 0; nu < 2; ++nu) {
+                for (int nu = 0; nu < 2; ++nu)
+                    for (int al = 0; al < 2; ++al) {
+                    // al: lattices with nx % 4 == 0 (TMA-eligible) or not
                     std::vector<int> members;
                     double nodes = 0;
                     for (int i = 0; i < n; ++i) {
                         const lb_case& c = h->cases[i];
-                        if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1)) {
+                        if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
+                            (c.nx % 4 == 0) == (al == 1)) {
                             members.push_back(i);
                             nodes += (double)c.nx * c.ny;
                         }
                     }
                     if (members.empty()) continue;
-                    bool tma = h->prec == LB_FP32 && h->path != 1;
-                    for (int i : members) tma = tma && h->cases[i].nx % 4 == 0;
+                    const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
                     const int nt = tma ? h->tma_threads : kStepThreads;  // 0: packed two-column kernel
                     const int width = nt == 0 ? 256 : nt;                   // columns per block
                     const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
@@ -353,6 +360,7 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     h->steps.assign(ncases, 0);
     h->inited.assign(ncases, 0);
     if (const char* p = std::getenv("LBFE_STEP_PATH")) h->path = std::strcmp(p, "ldg") == 0 ? 1 : 0;
+    if (const char* p = std::getenv("LBFE_GRAPH")) h->use_graph = std::strcmp(p, "0") != 0;
     if (const char* p = std::getenv("LBFE_STEP_THREADS")) {
         const int v = std::atoi(p);
         h->tma_threads = (v == 128 || v == 256) ? v : 0;
@@ -407,28 +415,68 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     return LB_OK;
 }
 
+// Enqueue one time step (every group) on stream st, reading buffer cur.
+static lb_status enqueue_step(lb_handle* h, int cur, cudaStream_t st)
+{
+    for (const Group& g : h->groups) {
+        cudaError_t e;
+        if (h->prec == LB_FP32)
+            e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, st,
+                                (const float*)h->fbuf(cur), (float*)h->fbuf(cur ^ 1), h->dc32(),
+                                h->ditems() + g.first, h->status());
+        else
+            e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, st, (const double*)h->fbuf(cur),
+                                (double*)h->fbuf(cur ^ 1), h->dc64(), h->ditems() + g.first, h->status());
+        if (e != cudaSuccess) return h->cuda(e, "step launch");
+    }
+    return LB_OK;
+}
+
+// Capture kGraphSteps steps starting from buffer cur into h->graph[cur].
+static lb_status capture_graph(lb_handle* h, int cur)
+{
+    if (!h->cap_stream) {
+        lb_status s = h->cuda(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "capture stream");
+        if (s != LB_OK) return s;
+    }
+    lb_status s = h->cuda(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (s != LB_OK) return s;
+    lb_status ls = LB_OK;
+    for (int k = 0; k < kGraphSteps && ls == LB_OK; ++k) ls = enqueue_step(h, cur ^ (k & 1), h->cap_stream);
+    cudaGraph_t g = nullptr;
+    s = h->cuda(cudaStreamEndCapture(h->cap_stream, &g), "end capture");
+    if (ls != LB_OK || s != LB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return ls != LB_OK ? ls : s;
+    }
+    s = h->cuda(cudaGraphInstantiate(&h->graph[cur], g, 0), "instantiate graph");
+    cudaGraphDestroy(g);
+    return s;
+}
+
 lb_status lb_step(lb_handle* h, int64_t nsteps)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (nsteps < 0) return h->fail(LB_E_INVALID, "lb_step: nsteps < 0");
     for (size_t i = 0; i < h->cases.size(); ++i)
         if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_step: every case needs lb_init_fields first");
-    for (int64_t n = 0; n < nsteps; ++n) {
-        for (const Group& g : h->groups) {
-            cudaError_t e;
-            if (h->prec == LB_FP32)
-                e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, h->stream,
-                                    (const float*)h->fbuf(h->cur), (float*)h->fbuf(h->cur ^ 1), h->dc32(),
-                                    h->ditems() + g.first, h->status());
-            else
-                e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, h->stream,
-                                    (const double*)h->fbuf(h->cur), (double*)h->fbuf(h->cur ^ 1), h->dc64(),
-                                    h->ditems() + g.first, h->status());
-            if (e != cudaSuccess) return h->cuda(e, "step launch");
+    int64_t n = nsteps;
+    if (h->use_graph && n >= kGraphSteps) {
+        if (!h->graph[h->cur]) {
+            lb_status s = capture_graph(h, h->cur);
+            if (s != LB_OK) return s;
         }
+        for (; n >= kGraphSteps; n -= kGraphSteps) {
+            lb_status s = h->cuda(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
+            if (s != LB_OK) return s;
+        }
+    }
+    for (; n > 0; --n) {
+        lb_status s = enqueue_step(h, h->cur, h->stream);
+        if (s != LB_OK) return s;
         h->cur ^= 1;
     }
-    for (auto& s : h->steps) s += nsteps;
+    for (auto& st : h->steps) st += nsteps;
     return LB_OK;
 }
 
@@ -553,6 +601,13 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
 
 const char* lb_last_error(const lb_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
-void lb_destroy(lb_handle* h) { delete h; }
+void lb_destroy(lb_handle* h)
+{
+    if (!h) return;
+    for (cudaGraphExec_t& g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
 
 }  // extern "C"
