@@ -32,6 +32,7 @@ VDW, CS = thermo.VDW, thermo.CS
 # planted-mistake hooks (pin tests only)
 FLAG_DROP_C = 1
 FLAG_FLIP_HALF_FORCE = 2
+FLAG_ADJOINT_DROP_C = 4
 
 
 class _CCase(C.Structure):
@@ -106,6 +107,7 @@ def lib() -> C.CDLL:
         _lib.orc_fields.argtypes = [cp, dp] + [dp] * 8; _lib.orc_fields.restype = C.c_int
         _lib.orc_step.argtypes = [cp, dp, i64]; _lib.orc_step.restype = i64
         _lib.orc_init.argtypes = [cp, dp, dp, dp, dp]; _lib.orc_init.restype = C.c_int
+        _lib.orc_adjoint.argtypes = [cp, dp, i64, i64, dp, dp, dp, dp, dp]; _lib.orc_adjoint.restype = C.c_int
         del i32
     return _lib
 
@@ -231,3 +233,34 @@ def reductions(case: Case, f: np.ndarray) -> dict:
     u2 = fl.ux**2 + fl.uy**2
     return {"mass": float(fl.rho.sum()), "ke": float(0.5 * (fl.rho * u2).sum()),
             "umax": float(np.sqrt(u2.max()))}
+
+
+def adjoint(case: Case, rho0: np.ndarray, nsteps: int, u_from: int, s_final=None):
+    """Loss L = sum_{n=u_from}^{nsteps} sum_x |u^n|^2 + sum_x s_final rho^N and its
+    gradients (dL/drho0, dL/dkappa, dL/dT) by the oracle's reverse sweep."""
+    rho0 = _f64(rho0)
+    assert rho0.shape == (case.ny, case.nx)
+    sf = None if s_final is None else _f64(s_final)
+    g = np.empty_like(rho0)
+    L, gk, gT = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().orc_adjoint(C.byref(case.cstruct()), _ptr(rho0), int(nsteps), int(u_from), _ptr(sf), C.byref(L),
+                           _ptr(g), C.byref(gk), C.byref(gT))
+    if rc != 0:
+        raise ValueError("oracle adjoint failed (non-physical state or nu > 0)")
+    return L.value, g, gk.value, gT.value
+
+
+def loss(case: Case, rho0: np.ndarray, nsteps: int, u_from: int, s_final=None) -> float:
+    """The loss of adjoint() from a plain forward run."""
+    f = init(case, rho0)
+    L = 0.0
+    for n in range(nsteps + 1):
+        if n >= u_from or n == nsteps:
+            fl = fields(case, f)
+            if n >= u_from:
+                L += float((fl.ux ** 2 + fl.uy ** 2).sum())
+            if n == nsteps and s_final is not None:
+                L += float((np.asarray(s_final) * fl.rho).sum())
+        if n < nsteps:
+            assert step(case, f, 1) == 1
+    return L

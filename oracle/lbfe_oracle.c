@@ -71,7 +71,8 @@ typedef struct {
     int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
                           bit 0: drop the correction term C of Eq. 28
-                          bit 1: flip the sign of the F/2 shift in Eq. 12 */
+                          bit 1: flip the sign of the F/2 shift in Eq. 12
+                          bit 2: the adjoint ignores C (forward unchanged) */
     double a, b, R, T, kappa;
     double tau_v, tau_e, tau_s, tau_q; /* MRT rates of Eq. 8; tau_c = 1 */
     double pm_c0;                      /* p_m = (c0 + mu_c)/3; the paper's c0 is 1 */
@@ -433,4 +434,417 @@ int orc_init(const orc_case* c, const double* rho0, const double* ux0, const dou
     }
     free(lap);
     return bad ? -1 : 0;
+}
+
+/* ====================================================================== */
+/* Adjoint (reverse-mode derivative) of the literal step above.            */
+/*                                                                         */
+/* Loss: L = sum_{n = u_from}^{N} sum_x |u^n(x)|^2 + sum_x s(x) rho^N(x),   */
+/* with u^n, rho^n the fields (Eq. 12) of the state after n steps from      */
+/* f(0) = init(rho0, u0 = 0). Every stage of orc_step is transposed in      */
+/* reverse order, following the forward's own intermediate quantities;     */
+/* stencil transposes are written as their own gathers (x - e_a). The       */
+/* trajectory is rebuilt from checkpoints every K steps. Constant tau only. */
+/* ====================================================================== */
+
+/* d E_f'(rho) / d rho */
+static double d2Ef(const orc_case* c, double rho)
+{
+    if (c->eos == 0) {
+        double q = 1.0 / (1.0 - c->b * rho);
+        return c->R * c->T * (1.0 / rho + c->b * q + c->b * q * q) - 2.0 * c->a;
+    }
+    double n = c->b * rho / 4.0, q = 1.0 / (1.0 - n);
+    return c->R * c->T * (1.0 / rho + 0.25 * c->b * (8.0 - 2.0 * n) * q * q * q * q) - 2.0 * c->a;
+}
+
+/* d E_f'(rho) / d T */
+static double dEf_dT(const orc_case* c, double rho)
+{
+    orc_case u = *c;
+    u.T = 1.0;
+    u.a = 0.0;
+    return orc_dEf(&u, rho); /* R h(rho) */
+}
+
+/* transpose of the Eq. 17 stencil component: (G^T v)(y) = 3 sum_a w_a e_a v(y - e_a) */
+static void gradT(int nx, int ny, const double* vx, const double* vy, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a) {
+                int i = wrap(y - EY[a], ny) * nx + wrap(x - EX[a], nx);
+                if (vx) s += 3.0 * WA[a] * EX[a] * vx[i];
+                if (vy) s += 3.0 * WA[a] * EY[a] * vy[i];
+            }
+            out[y * nx + x] = s;
+        }
+}
+
+/* transpose of the Laplacian: (L^T v)(y) = 6 sum_a w_a (v(y - e_a) - v(y)) */
+static void lapT(int nx, int ny, const double* v, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a) s += WA[a] * (v[wrap(y - EY[a], ny) * nx + wrap(x - EX[a], nx)] - v[y * nx + x]);
+            out[y * nx + x] = 6.0 * s;
+        }
+}
+
+typedef struct {
+    double *rho, *lap, *mu, *gmx, *gmy, *Fx, *Fy, *jx, *jy, *ux, *uy, *phi, *C1, *C7;
+} orc_fwd;
+
+static void fwd_alloc(orc_fwd* w, int N)
+{
+    double** p = (double**)w;
+    for (int k = 0; k < (int)(sizeof(orc_fwd) / sizeof(double*)); ++k) p[k] = calloc(N, sizeof(double));
+}
+static void fwd_free(orc_fwd* w)
+{
+    double** p = (double**)w;
+    for (int k = 0; k < (int)(sizeof(orc_fwd) / sizeof(double*)); ++k) free(p[k]);
+}
+
+/* the intermediate fields of stages 1-7 at state f (same arithmetic as orc_fields) */
+static void fwd_fields(const orc_case* c, const double* f, orc_fwd* w)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double* r3 = calloc(N, sizeof(double));
+    double* grx = calloc(N, sizeof(double));
+    double* gry = calloc(N, sizeof(double));
+    double* Ax = calloc(N, sizeof(double));
+    double* Ay = calloc(N, sizeof(double));
+    double* Bx = calloc(N, sizeof(double));
+    double* By = calloc(N, sizeof(double));
+    double* A = calloc(N, sizeof(double));
+    double* B = calloc(N, sizeof(double));
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0, jx = 0.0, jy = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            s += f[a * N + i];
+            jx += EX[a] * f[a * N + i];
+            jy += EY[a] * f[a * N + i];
+        }
+        w->rho[i] = s;
+        w->jx[i] = jx;
+        w->jy[i] = jy;
+    }
+    orc_laplacian(nx, ny, w->rho, w->lap);
+    for (int i = 0; i < N; ++i) w->mu[i] = orc_dEf(c, w->rho[i]) - c->kappa * w->lap[i];
+    orc_grad(nx, ny, w->mu, w->gmx, w->gmy);
+    if (c->scheme == 0) {
+        for (int i = 0; i < N; ++i) r3[i] = w->rho[i] * CS2;
+        orc_grad(nx, ny, r3, grx, gry);
+    }
+    for (int i = 0; i < N; ++i) {
+        if (c->scheme == 0) {
+            w->Fx[i] = grx[i] - w->rho[i] * w->gmx[i];
+            w->Fy[i] = gry[i] - w->rho[i] * w->gmy[i];
+        } else {
+            w->Fx[i] = (CS2 - w->rho[i]) * w->gmx[i];
+            w->Fy[i] = (CS2 - w->rho[i]) * w->gmy[i];
+        }
+        w->ux[i] = (w->jx[i] + 0.5 * w->Fx[i]) / w->rho[i];
+        w->uy[i] = (w->jy[i] + 0.5 * w->Fy[i]) / w->rho[i];
+    }
+    if (c->scheme == 1) {
+        for (int i = 0; i < N; ++i) {
+            double pm = (c->pm_c0 + w->mu[i]) / 3.0;
+            w->phi[i] = w->rho[i] * CS2 - pm;
+            A[i] = w->phi[i] * w->ux[i];
+            B[i] = w->phi[i] * w->uy[i];
+        }
+        orc_grad(nx, ny, A, Ax, Ay);
+        orc_grad(nx, ny, B, Bx, By);
+        for (int i = 0; i < N; ++i) {
+            w->C1[i] = Ax[i] + By[i];
+            w->C7[i] = Ax[i] - By[i];
+        }
+    }
+    free(r3); free(grx); free(gry); free(Ax); free(Ay); free(Bx); free(By); free(A); free(B);
+}
+
+/* Transpose of stages 1-7 at state w: given the adjoints of the node-level
+ * quantities (rb = rho, jxb, jyb, uxb, uyb, Fxb, Fyb, mub, C1b, C7b; all are
+ * consumed), add to lam_f[a][i] and to the parameter gradients. */
+static void fields_vjp(const orc_case* c, const orc_fwd* w, double* rb, double* jxb, double* jyb, double* uxb,
+                       double* uyb, double* Fxb, double* Fyb, double* mub, double* C1b, double* C7b,
+                       double* lam_f, double* g_kappa, double* g_T)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double* t1 = calloc(N, sizeof(double));
+    double* t2 = calloc(N, sizeof(double));
+    double* gmxb = calloc(N, sizeof(double));
+    double* gmyb = calloc(N, sizeof(double));
+    /* 7': C1 = Ax + By, C7 = Ax - By; A = phi ux, B = phi uy; phi = rho/3 - (c0 + mu)/3 */
+    if (c->scheme == 1) {
+        double* Axb = calloc(N, sizeof(double));
+        double* Byb = calloc(N, sizeof(double));
+        for (int i = 0; i < N; ++i) {
+            Axb[i] = C1b[i] + C7b[i];
+            Byb[i] = C1b[i] - C7b[i];
+        }
+        gradT(nx, ny, Axb, NULL, t1); /* A-bar */
+        gradT(nx, ny, NULL, Byb, t2); /* B-bar */
+        for (int i = 0; i < N; ++i) {
+            double phib = t1[i] * w->ux[i] + t2[i] * w->uy[i];
+            uxb[i] += w->phi[i] * t1[i];
+            uyb[i] += w->phi[i] * t2[i];
+            rb[i] += phib * CS2;
+            mub[i] -= phib / 3.0;
+        }
+        free(Axb); free(Byb);
+    }
+    /* 6': u = (j + F/2) / rho */
+    double half = (c->flags & 2) ? -0.5 : 0.5;
+    for (int i = 0; i < N; ++i) {
+        double r = w->rho[i];
+        jxb[i] += uxb[i] / r;
+        jyb[i] += uyb[i] / r;
+        Fxb[i] += half * uxb[i] / r;
+        Fyb[i] += half * uyb[i] / r;
+        rb[i] -= (uxb[i] * w->ux[i] + uyb[i] * w->uy[i]) / r;
+    }
+    /* 5': force */
+    for (int i = 0; i < N; ++i) {
+        if (c->scheme == 0) {
+            gmxb[i] = -w->rho[i] * Fxb[i];
+            gmyb[i] = -w->rho[i] * Fyb[i];
+        } else {
+            gmxb[i] = (CS2 - w->rho[i]) * Fxb[i];
+            gmyb[i] = (CS2 - w->rho[i]) * Fyb[i];
+        }
+        rb[i] -= w->gmx[i] * Fxb[i] + w->gmy[i] * Fyb[i];
+    }
+    if (c->scheme == 0) { /* F includes grad(rho/3) */
+        gradT(nx, ny, Fxb, Fyb, t1);
+        for (int i = 0; i < N; ++i) rb[i] += t1[i] * CS2;
+    }
+    /* 4': g = grad mu */
+    gradT(nx, ny, gmxb, gmyb, t1);
+    for (int i = 0; i < N; ++i) mub[i] += t1[i];
+    /* 3': mu = E_f'(rho) - kappa lap */
+    for (int i = 0; i < N; ++i) {
+        rb[i] += d2Ef(c, w->rho[i]) * mub[i];
+        *g_kappa -= mub[i] * w->lap[i];
+        *g_T += mub[i] * dEf_dT(c, w->rho[i]);
+        t2[i] = -c->kappa * mub[i];
+    }
+    /* 2': lap */
+    lapT(nx, ny, t2, t1);
+    for (int i = 0; i < N; ++i) rb[i] += t1[i];
+    /* 1': rho = sum f, j = sum e f */
+    for (int i = 0; i < N; ++i)
+        for (int a = 0; a < Q; ++a) lam_f[a * N + i] += rb[i] + EX[a] * jxb[i] + EY[a] * jyb[i];
+    free(t1); free(t2); free(gmxb); free(gmyb);
+}
+
+/* d meq / d (rho, ux, uy, mu): rows k, columns (rho, ux, uy, mu) */
+static void meq_jac(const orc_case* c, double rho, double ux, double uy, double mu, double J[Q][4])
+{
+    double u2 = ux * ux + uy * uy;
+    for (int k = 0; k < Q; ++k) J[k][0] = J[k][1] = J[k][2] = J[k][3] = 0.0;
+    J[0][0] = 1.0;
+    if (c->scheme == 0) {
+        J[1][0] = -2.0 + 3.0 * u2; J[1][1] = 6.0 * rho * ux; J[1][2] = 6.0 * rho * uy;
+        J[2][0] = 1.0 - 3.0 * u2;  J[2][1] = -6.0 * rho * ux; J[2][2] = -6.0 * rho * uy;
+        J[4][0] = -ux; J[4][1] = -rho;
+        J[6][0] = -uy; J[6][2] = -rho;
+    } else {
+        double s = c->pm_c0 + mu; /* rho * gamma */
+        J[1][0] = -4.0 + 3.0 * u2; J[1][1] = 6.0 * rho * ux; J[1][2] = 6.0 * rho * uy; J[1][3] = 2.0;
+        J[2][0] = 4.0 - 3.0 * u2;  J[2][1] = -6.0 * rho * ux; J[2][2] = -6.0 * rho * uy; J[2][3] = -3.0;
+        J[4][0] = -2.0 * ux; J[4][1] = s - 2.0 * rho; J[4][3] = ux;
+        J[6][0] = -2.0 * uy; J[6][2] = s - 2.0 * rho; J[6][3] = uy;
+    }
+    J[3][0] = ux; J[3][1] = rho;
+    J[5][0] = uy; J[5][2] = rho;
+    J[7][0] = ux * ux - uy * uy; J[7][1] = 2.0 * rho * ux; J[7][2] = -2.0 * rho * uy;
+    J[8][0] = ux * uy; J[8][1] = rho * uy; J[8][2] = rho * ux;
+}
+
+/* One reverse step: lam (in: adjoint of the state after the step, node
+ * convention; out: adjoint of the state f before it, plus the u seeds at f).
+ * u_seed != 0 adds the derivative of sum |u|^2 at state f. */
+static void step_vjp(const orc_case* c, const double* f, double* lam, int u_seed, double* g_kappa, double* g_T)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double Mi[Q * Q], lamr[Q];
+    orc_Minv(Mi);
+    relax_rates(c, c->tau_v, lamr);
+    orc_fwd w;
+    fwd_alloc(&w, N);
+    fwd_fields(c, f, &w);
+    double* ls = malloc((size_t)Q * N * sizeof(double));
+    double* lf = calloc((size_t)Q * N, sizeof(double));
+    double *rb = calloc(N, sizeof(double)), *jxb = calloc(N, sizeof(double)), *jyb = calloc(N, sizeof(double));
+    double *uxb = calloc(N, sizeof(double)), *uyb = calloc(N, sizeof(double));
+    double *Fxb = calloc(N, sizeof(double)), *Fyb = calloc(N, sizeof(double));
+    double *mub = calloc(N, sizeof(double)), *C1b = calloc(N, sizeof(double)), *C7b = calloc(N, sizeof(double));
+    /* 11': transpose of push streaming */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            for (int a = 0; a < Q; ++a)
+                ls[a * N + y * nx + x] = lam[a * N + wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)];
+    for (int i = 0; i < N; ++i) {
+        double msb[Q], mb[Q], meqb[Q], Sb[Q], Gb[Q], J[Q][4];
+        /* 10': fs = Minv ms */
+        for (int k = 0; k < Q; ++k) {
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a) s += Mi[a * Q + k] * ls[a * N + i];
+            msb[k] = s;
+        }
+        /* 9': ms = m - L (m - meq) + (1 - L/2)(S + C) */
+        for (int k = 0; k < Q; ++k) {
+            mb[k] = (1.0 - lamr[k]) * msb[k];
+            meqb[k] = lamr[k] * msb[k];
+            Sb[k] = (1.0 - 0.5 * lamr[k]) * msb[k];
+        }
+        if (c->scheme == 1 && !(c->flags & 1) && !(c->flags & 4)) {
+            C1b[i] += 9.0 * Sb[1];
+            C7b[i] += 3.0 * Sb[7];
+        }
+        /* 8': m = M f, S = M G, meq(rho, u, mu), G(u, F) */
+        for (int a = 0; a < Q; ++a) {
+            double s = 0.0, g = 0.0;
+            for (int k = 0; k < Q; ++k) {
+                s += MM[k][a] * mb[k];
+                g += MM[k][a] * Sb[k];
+            }
+            lf[a * N + i] += s;
+            Gb[a] = g;
+        }
+        meq_jac(c, w.rho[i], w.ux[i], w.uy[i], w.mu[i], J);
+        for (int k = 0; k < Q; ++k) {
+            rb[i] += J[k][0] * meqb[k];
+            uxb[i] += J[k][1] * meqb[k];
+            uyb[i] += J[k][2] * meqb[k];
+            mub[i] += J[k][3] * meqb[k];
+        }
+        {
+            double ux = w.ux[i], uy = w.uy[i], Fx = w.Fx[i], Fy = w.Fy[i];
+            for (int a = 0; a < Q; ++a) {
+                double eu = EX[a] * ux + EY[a] * uy, eF = EX[a] * Fx + EY[a] * Fy;
+                double vx = (EX[a] - ux) / CS2 + eu * EX[a] / (CS2 * CS2);
+                double vy = (EY[a] - uy) / CS2 + eu * EY[a] / (CS2 * CS2);
+                Fxb[i] += Gb[a] * WA[a] * vx;
+                Fyb[i] += Gb[a] * WA[a] * vy;
+                uxb[i] += Gb[a] * WA[a] * (-Fx / CS2 + EX[a] * eF / (CS2 * CS2));
+                uyb[i] += Gb[a] * WA[a] * (-Fy / CS2 + EY[a] * eF / (CS2 * CS2));
+            }
+        }
+        if (u_seed) {
+            uxb[i] += 2.0 * w.ux[i];
+            uyb[i] += 2.0 * w.uy[i];
+        }
+    }
+    fields_vjp(c, &w, rb, jxb, jyb, uxb, uyb, Fxb, Fyb, mub, C1b, C7b, lf, g_kappa, g_T);
+    memcpy(lam, lf, (size_t)Q * N * sizeof(double));
+    free(ls); free(lf); free(rb); free(jxb); free(jyb); free(uxb); free(uyb); free(Fxb); free(Fyb);
+    free(mub); free(C1b); free(C7b);
+    fwd_free(&w);
+}
+
+/* Adjoint of the initial populations f(0) = M^-1 m_eq(rho0, 0, mu(rho0)). */
+static void init_vjp(const orc_case* c, const double* rho0, const double* lam0, double* g_rho0, double* g_kappa,
+                     double* g_T)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double Mi[Q * Q];
+    orc_Minv(Mi);
+    double* lap = calloc(N, sizeof(double));
+    double* mub = calloc(N, sizeof(double));
+    double* t = calloc(N, sizeof(double));
+    orc_laplacian(nx, ny, rho0, lap);
+    for (int i = 0; i < N; ++i) {
+        double mu = orc_dEf(c, rho0[i]) - c->kappa * lap[i];
+        double J[Q][4], meqb[Q];
+        for (int k = 0; k < Q; ++k) {
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a) s += Mi[a * Q + k] * lam0[a * N + i];
+            meqb[k] = s;
+        }
+        meq_jac(c, rho0[i], 0.0, 0.0, mu, J);
+        double rb = 0.0, mb = 0.0;
+        for (int k = 0; k < Q; ++k) {
+            rb += J[k][0] * meqb[k];
+            mb += J[k][3] * meqb[k];
+        }
+        g_rho0[i] = rb + d2Ef(c, rho0[i]) * mb;
+        mub[i] = mb;
+        *g_kappa -= mb * lap[i];
+        *g_T += mb * dEf_dT(c, rho0[i]);
+        t[i] = -c->kappa * mb;
+    }
+    double* lt = calloc(N, sizeof(double));
+    lapT(nx, ny, t, lt);
+    for (int i = 0; i < N; ++i) g_rho0[i] += lt[i];
+    free(lap); free(mub); free(t); free(lt);
+}
+
+/* Loss and gradients with respect to rho0, kappa and T (see the block
+ * comment above). Returns 0, or -1 on a non-physical state or nu > 0. */
+int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u_from, const double* s_final,
+                double* loss, double* g_rho0, double* g_kappa, double* g_T)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    if (c->nu > 0.0 || nsteps < 0) return -1;
+    int64_t K = 1;
+    while (K * K < nsteps) ++K;
+    const int64_t ncp = nsteps / K + 1;
+    double* cp = malloc((size_t)ncp * Q * N * sizeof(double));
+    double* f = malloc((size_t)Q * N * sizeof(double));
+    if (orc_init(c, rho0, NULL, NULL, f) != 0) return -1;
+    /* forward: loss and checkpoints of the states 0, K, 2K, ... */
+    double L = 0.0;
+    orc_fwd w;
+    fwd_alloc(&w, N);
+    for (int64_t n = 0; n <= nsteps; ++n) {
+        if (n % K == 0) memcpy(cp + (size_t)(n / K) * Q * N, f, (size_t)Q * N * sizeof(double));
+        if (n >= u_from || n == nsteps) {
+            fwd_fields(c, f, &w);
+            for (int i = 0; i < N; ++i) {
+                if (n >= u_from) L += w.ux[i] * w.ux[i] + w.uy[i] * w.uy[i];
+                if (n == nsteps && s_final) L += s_final[i] * w.rho[i];
+            }
+        }
+        if (n < nsteps && orc_step(c, f, 1) != 1) {
+            fwd_free(&w); free(cp); free(f);
+            return -1;
+        }
+    }
+    fwd_free(&w);
+    *loss = L;
+    *g_kappa = 0.0;
+    *g_T = 0.0;
+    /* reverse sweep over segments [s, e] of at most K + 1 states, rebuilt
+     * from the checkpoint at s; lam holds the adjoint of the state after n */
+    double* lam = calloc((size_t)Q * N, sizeof(double));
+    double* seg = malloc((size_t)(K + 1) * Q * N * sizeof(double));
+    for (int64_t s = (nsteps / K) * K, e = nsteps; s >= 0; e = s - 1, s -= K) {
+        memcpy(seg, cp + (size_t)(s / K) * Q * N, (size_t)Q * N * sizeof(double));
+        for (int64_t n = s + 1; n <= e; ++n) {
+            memcpy(seg + (size_t)(n - s) * Q * N, seg + (size_t)(n - s - 1) * Q * N, (size_t)Q * N * sizeof(double));
+            orc_step(c, seg + (size_t)(n - s) * Q * N, 1);
+        }
+        for (int64_t n = e; n >= s; --n) {
+            const double* fn = seg + (size_t)(n - s) * Q * N;
+            if (n == nsteps) {
+                /* final state: no later step; its u terms and the density term */
+                memset(lam, 0, (size_t)Q * N * sizeof(double));
+                if (nsteps >= u_from) step_vjp(c, fn, lam, 1, g_kappa, g_T);
+                if (s_final)
+                    for (int i = 0; i < N; ++i)
+                        for (int a = 0; a < Q; ++a) lam[a * N + i] += s_final[i];
+            } else {
+                step_vjp(c, fn, lam, n >= u_from, g_kappa, g_T);
+            }
+        }
+    }
+    init_vjp(c, rho0, lam, g_rho0, g_kappa, g_T);
+    free(lam); free(seg); free(cp); free(f);
+    return 0;
 }
