@@ -145,6 +145,24 @@ lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes);
 lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes);
 lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes);
 
+/* Reverse-mode gradient of a trajectory of case case_id (LB_FP64 handles,
+ * constant relaxation times), the discrete adjoint of the step above:
+ *   f(0) = M^-1 m_eq(rho0, 0) as lb_init_fields, then nsteps steps;
+ *   L = sum_{n = u_from}^{nsteps} sum_x |u^n(x)|^2 + sum_x s_final(x) rho^N(x)
+ * (u^n, rho^n of Eq. 12 after n steps; s_final may be NULL). Outputs the loss,
+ * dL/drho0 [ny][nx] (may be NULL), dL/dkappa and dL/dT (T absolute). The
+ * forward trajectory is recomputed from checkpoints taken every ckpt_every
+ * steps (0: about sqrt(nsteps)). d_ws: caller-owned device memory of at least
+ * lb_adjoint_workspace_bytes, 256-byte aligned. rho0, s_final and grad_rho0
+ * are device pointers if on_device, else host. Runs on the handle's stream,
+ * synchronises it, and leaves the handle's own state untouched. The
+ * north-star's lb_adjoint_step is this call over the whole horizon. */
+lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_t nsteps, int32_t ckpt_every,
+                                     size_t* bytes);
+lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
+                     const double* s_final, int32_t on_device, int32_t ckpt_every, void* d_ws, size_t ws_bytes,
+                     double* loss, double* grad_rho0, double* grad_kappa, double* grad_T);
+
 /* Host thermodynamics for set-up (FP64, Newton): critical point and the
  * Maxwell equal-area coexistence densities rho_g < rho_l (Sec. IV A; Table II
  * lists the vdW values). eos = LB_VDW or LB_CS. */

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/lbfe.h"
+#include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "launch.h"
 
@@ -596,6 +597,227 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
     if (s != LB_OK) return s;
     h->steps[case_id] = st;
     h->inited[case_id] = 1;
+    return LB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ adjoint
+namespace {
+
+struct AdjLayout {
+    size_t cases, items, ckpt, seg, lam, lamd, fields, partials, acc, rho0, sfin, grad, total;
+    int64_t K, ncp, state, nitems, N, parts;
+};
+
+constexpr int kAdjFields = 29;
+
+AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K)
+{
+    AdjLayout L;
+    L.K = K;
+    L.ncp = nsteps / K + 1;
+    L.N = (int64_t)c.nx * c.ny;
+    L.state = (int64_t)kQ * c.ny * pitch_of(c.nx);
+    L.nitems = max_items_of(c);
+    L.parts = (int64_t)((c.nx + 255) / 256) * c.ny;
+    size_t p = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = p;
+        p = align_up(p + bytes, kAlign);
+        return at;
+    };
+    L.cases = take(sizeof(DevCase<double>));
+    L.items = take(L.nitems * sizeof(Item));
+    L.ckpt = take((size_t)L.ncp * L.state * sizeof(double));
+    L.seg = take((size_t)(K + 1) * L.state * sizeof(double));
+    L.lam = take((size_t)kQ * L.N * sizeof(double));
+    L.lamd = take((size_t)kQ * L.N * sizeof(double));
+    L.fields = take((size_t)kAdjFields * align_up(L.N * sizeof(double), kAlign));
+    L.partials = take(L.parts * sizeof(Partial));
+    L.acc = take(8 * sizeof(double));
+    L.rho0 = take(L.N * sizeof(double));
+    L.sfin = take(L.N * sizeof(double));
+    L.grad = take(L.N * sizeof(double));
+    L.total = p;
+    return L;
+}
+
+int64_t adj_default_K(int64_t nsteps)
+{
+    int64_t K = 1;
+    while (K * K < nsteps) ++K;
+    return K;
+}
+
+template <int SCHEME, int EOS>
+lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_t* ws, const double* s_fin,
+                      int64_t nsteps, int64_t u_from)
+{
+    cudaStream_t st = h->stream;
+    const DevCase<double> cd = dev_case<double>(c, 0, 0.0);
+    const DevCase<double>* dcase = reinterpret_cast<const DevCase<double>*>(ws + L.cases);
+    const Item* items = reinterpret_cast<const Item*>(ws + L.items);
+    double* ckpt = reinterpret_cast<double*>(ws + L.ckpt);
+    double* seg = reinterpret_cast<double*>(ws + L.seg);
+    double* lam = reinterpret_cast<double*>(ws + L.lam);
+    double* lamd = reinterpret_cast<double*>(ws + L.lamd);
+    Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
+    double* acc = reinterpret_cast<double*>(ws + L.acc);
+    const double* rho0 = reinterpret_cast<const double*>(ws + L.rho0);
+    double* grad = reinterpret_cast<double*>(ws + L.grad);
+    AdjFields F;
+    double** fp = reinterpret_cast<double**>(&F);
+    for (int k = 0; k < kAdjFields; ++k)
+        fp[k] = reinterpret_cast<double*>(ws + L.fields + k * align_up(L.N * sizeof(double), kAlign));
+    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    const int nitems = (int)L.nitems;
+    auto state = [&](int64_t k) { return ckpt + k * L.state; };
+    auto step = [&](const double* in, double* out) {
+        return launch_step_f64(SCHEME, c.collision, EOS, false, nitems, st, in, out, dcase, items, h->status());
+    };
+    // forward: f(0), then the checkpoints every K steps
+    cudaMemcpyAsync(F.rho, rho0, L.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    mu_field_kernel<double, EOS><<<grd, blk, 0, st>>>(cd, F.rho, F.mu);
+    init_kernel<double, SCHEME, double><<<grd, blk, 0, st>>>(cd, cd, F.rho, nullptr, nullptr, F.mu, state(0));
+    const double* cur = state(0);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        double* out = ((n + 1) % L.K == 0) ? state((n + 1) / L.K) : (cur == seg ? seg + L.state : seg);
+        if (step(cur, out) != cudaSuccess) return h->cuda(cudaGetLastError(), "adjoint forward");
+        cur = out;
+    }
+    cudaMemsetAsync(acc, 0, 4 * sizeof(double), st);
+    cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(double), st);
+    // reverse sweep over segments [s, e], states s+1..e rebuilt into seg
+    for (int64_t s = (nsteps / L.K) * L.K, e = nsteps; s >= 0; e = s - 1, s -= L.K) {
+        for (int64_t n = s + 1; n <= e; ++n) {
+            const double* in = n - 1 == s ? state(s / L.K) : seg + (n - 1 - s) * L.state;
+            if (step(in, seg + (n - s) * L.state) != cudaSuccess)
+                return h->cuda(cudaGetLastError(), "adjoint recompute");
+        }
+        for (int64_t n = e; n >= s; --n) {
+            const double* fn = n == s ? state(s / L.K) : seg + (n - s) * L.state;
+            pull_moments_kernel<double, double><<<grd, blk, 0, st>>>(cd, fn, F.rho, F.jx, F.jy);
+            adj_fwd_mu<EOS><<<grd, blk, 0, st>>>(cd, F);
+            adj_fwd_force<SCHEME><<<grd, blk, 0, st>>>(cd, F, n >= u_from ? 1.0 : 0.0, n == nsteps ? s_fin : nullptr,
+                                                       parts);
+            adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 0, nullptr);
+            if (SCHEME == 1) adj_fwd_corr<<<grd, blk, 0, st>>>(cd, F);
+            adj_collide<SCHEME><<<grd, blk, 0, st>>>(cd, F, lam, n < nsteps, n >= u_from, lamd);
+            adj_force<SCHEME><<<grd, blk, 0, st>>>(cd, F);
+            adj_mu<SCHEME, EOS><<<grd, blk, 0, st>>>(cd, c.R, F, parts);
+            adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
+            adj_lambda<<<grd, blk, 0, st>>>(cd, F, lamd, n == nsteps ? s_fin : nullptr, lam);
+        }
+        if (s == 0) break;
+    }
+    // initial populations
+    cudaMemcpyAsync(F.rho, rho0, L.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    adj_fwd_mu<EOS><<<grd, blk, 0, st>>>(cd, F);
+    adj_init<SCHEME, EOS><<<grd, blk, 0, st>>>(cd, c.R, F, lam, parts);
+    adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
+    adj_init_out<<<grd, blk, 0, st>>>(cd, F, grad);
+    return h->cuda(cudaGetLastError(), "adjoint kernels");
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_t nsteps, int32_t ckpt_every,
+                                     size_t* bytes)
+{
+    if (!h || !bytes || case_id < 0 || case_id >= (int)h->cases.size() || nsteps < 0 || ckpt_every < 0)
+        return LB_E_INVALID;
+    const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
+    *bytes = adj_layout(h->cases[case_id], nsteps, K).total;
+    return LB_OK;
+}
+
+lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
+                     const double* s_final, int32_t on_device, int32_t ckpt_every, void* d_ws, size_t ws_bytes,
+                     double* loss, double* grad_rho0, double* grad_kappa, double* grad_T)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size() || !rho0 || nsteps < 0 || u_from < 0 || ckpt_every < 0 ||
+        !loss || !grad_kappa || !grad_T)
+        return h->fail(LB_E_INVALID, "lb_adjoint: bad arguments");
+    if (h->prec != LB_FP64) return h->fail(LB_E_INVALID, "lb_adjoint: needs an LB_FP64 handle");
+    const lb_case& c = h->cases[case_id];
+    if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint: constant relaxation times only (nu = 0)");
+    const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
+    const AdjLayout L = adj_layout(c, nsteps, K);
+    if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || ws_bytes < L.total)
+        return h->fail(LB_E_WORKSPACE, "lb_adjoint: workspace misaligned or smaller than lb_adjoint_workspace_bytes");
+    uint8_t* ws = static_cast<uint8_t*>(d_ws);
+    cudaStream_t st = h->stream;
+    // one-case step tables at offset 0 of the workspace's state buffers
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const DevCase<double> cd = dev_case<double>(c, 0, 0.0);
+    std::vector<Item> items;
+    {
+        const int ns = strips_of(c, kStepThreads);
+        int nseg = std::max(1, std::min(c.ny / kMinRows, (2 * sms) / ns));
+        for (int k = 0; k < ns; ++k) {
+            const int q = c.nx % 4 == 0 ? 4 : 1;
+            const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns), x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
+            for (int g = 0; g < nseg; ++g) {
+                const int y0 = (int)((int64_t)c.ny * g / nseg), y1 = (int)((int64_t)c.ny * (g + 1) / nseg);
+                items.push_back(Item{0, x0, x1 - x0, y0, y1 - y0, 0});
+            }
+        }
+    }
+    AdjLayout Lr = L;
+    Lr.nitems = (int64_t)items.size();
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    lb_status s = h->cuda(cudaMemcpyAsync(ws + L.cases, &cd, sizeof cd, cudaMemcpyHostToDevice, st), "adjoint case");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemcpyAsync(ws + L.items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, st),
+                    "adjoint items");
+    if (s == LB_OK) s = h->cuda(cudaMemcpyAsync(ws + L.rho0, rho0, L.N * sizeof(double), kind, st), "adjoint rho0");
+    const double* sfin = nullptr;
+    if (s == LB_OK && s_final) {
+        s = h->cuda(cudaMemcpyAsync(ws + L.sfin, s_final, L.N * sizeof(double), kind, st), "adjoint s_final");
+        sfin = reinterpret_cast<const double*>(ws + L.sfin);
+    }
+    if (s != LB_OK) return s;
+    // validate rho0 on the device
+    {
+        Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
+        double* acc = reinterpret_cast<double*>(ws + L.acc);
+        double* scratch = reinterpret_cast<double*>(ws + L.grad);
+        const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+        rho0_kernel<double><<<grd, blk, 0, st>>>(c.nx, c.eos, c.b, reinterpret_cast<const double*>(ws + L.rho0),
+                                                 scratch, parts);
+        finalize_kernel<<<1, 256, 0, st>>>(parts, L.parts, 0.0, acc);
+        double chk[5];
+        s = h->cuda(cudaMemcpyAsync(chk, acc, sizeof chk, cudaMemcpyDeviceToHost, st), "adjoint check");
+        if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(st), "adjoint check");
+        if (s != LB_OK) return s;
+        if (chk[4] != 0.0) return h->fail(LB_E_INVALID, "lb_adjoint: rho0 must be finite, > 0 and inside the EOS domain");
+    }
+    if (c.scheme == LB_IMPROVED)
+        s = c.eos == LB_VDW ? adjoint_run<1, 0>(h, c, Lr, ws, sfin, nsteps, u_from)
+                            : adjoint_run<1, 1>(h, c, Lr, ws, sfin, nsteps, u_from);
+    else
+        s = c.eos == LB_VDW ? adjoint_run<0, 0>(h, c, Lr, ws, sfin, nsteps, u_from)
+                            : adjoint_run<0, 1>(h, c, Lr, ws, sfin, nsteps, u_from);
+    if (s != LB_OK) return s;
+    double acc[4];
+    s = h->cuda(cudaMemcpyAsync(acc, ws + L.acc, sizeof acc, cudaMemcpyDeviceToHost, st), "adjoint results");
+    if (s == LB_OK && grad_rho0)
+        s = h->cuda(cudaMemcpyAsync(grad_rho0, ws + L.grad, L.N * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+                    "adjoint grad");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(st), "adjoint sync");
+    if (s != LB_OK) return s;
+    *loss = acc[0];
+    *grad_kappa = acc[1];
+    *grad_T = acc[2];
+    if (!std::isfinite(acc[0]) || !std::isfinite(acc[1]) || !std::isfinite(acc[2]))
+        return h->fail(LB_E_UNSTABLE, "lb_adjoint: non-finite loss or gradient");
     return LB_OK;
 }
 

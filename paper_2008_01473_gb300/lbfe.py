@@ -88,13 +88,15 @@ def lib() -> C.CDLL:
         L.lb_critical.argtypes = [i32, C.c_double, C.c_double, C.c_double, dp, dp]
         L.lb_maxwell.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
         L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
+        L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
+        L.lb_adjoint.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -203,6 +205,33 @@ class Lattice:
         if rc != 0 and (rc != 3 or raise_unstable):
             _check(rc, self._h)
         return out, st
+
+    def adjoint(self, case_id: int, rho0, nsteps: int, u_from: int, s_final=None, ckpt_every: int = 0):
+        """Loss L = sum_{n >= u_from} sum |u^n|^2 + sum s_final rho^N of a run from
+        rho0, and (L, dL/drho0, dL/dkappa, dL/dT) by the library's adjoint
+        (LB_FP64 handles). Arrays on the host or CUDA tensors (results follow rho0)."""
+        torch = self._torch
+        sh = self._shape(case_id)
+        nb = C.c_size_t()
+        _check(lib().lb_adjoint_workspace_bytes(self._h, case_id, int(nsteps), int(ckpt_every), C.byref(nb)),
+               self._h, "lb_adjoint_workspace_bytes")
+        ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+        wsp = (ws.data_ptr() + 255) // 256 * 256
+        p, dev, k0 = self._ptr_of(rho0, sh)
+        ps, devs, k1 = self._ptr_of(s_final, sh)
+        if s_final is not None and devs != dev:
+            raise ValueError("rho0 and s_final must both be on the host or both on the device")
+        if dev:
+            grad = torch.empty(sh, dtype=torch.float64, device=self.device)
+            gp = C.c_void_p(grad.data_ptr())
+        else:
+            grad = np.empty(sh)
+            gp = C.c_void_p(grad.ctypes.data)
+        L, gk, gT = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().lb_adjoint(self._h, case_id, p, int(nsteps), int(u_from), ps, dev, int(ckpt_every),
+                                C.c_void_p(wsp), nb.value, C.byref(L), gp, C.byref(gk), C.byref(gT)), self._h)
+        del k0, k1, ws
+        return L.value, grad, gk.value, gT.value
 
     def save(self, case_id: int) -> bytes:
         nb = C.c_size_t()

@@ -1,0 +1,106 @@
+"""GPU adjoint (lb_adjoint, FP64) against the oracle's adjoint and against
+central finite differences of the GPU's own loss; the autograd wrapper."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import thermo
+from paper_2008_01473_gb300 import inputs, lbfe
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_01473_gb300 import build
+
+    build.build()
+
+
+def _setup(nx, ny, scheme, collision, eos="vdw", t=0.8):
+    e = thermo.vdw_paper() if eos == "vdw" else thermo.EOS(thermo.CS, 9 / 392, 9 / 98)
+    T, rg, rl = thermo.maxwell_reduced(e, t)
+    kw = dict(nx=nx, ny=ny, scheme=scheme, collision=collision, eos=e.kind, a=e.a, b=e.b, R=1.0, T=T,
+              kappa=0.02, tau_v=0.8)
+    rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=1)
+    sf = 1e-3 * (2 * inputs.splitmix_uniform(5, 0, nx, ny) - 1)
+    return lbfe.Case(**kw), O.Case(**kw), rho0, sf
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
+@pytest.mark.parametrize("eos", ["vdw", "cs"])
+@pytest.mark.parametrize("shape,ckpt", [((12, 10), 0), ((33, 21), 7), ((257, 9), 1)])
+def test_gpu_adjoint_matches_oracle(scheme, collision, eos, shape, ckpt):
+    """Loss, dL/dkappa, dL/dT and dL/drho0 agree with the oracle's reverse sweep
+    to 1e-10 relative (FP64 rounding order only), over checkpoint intervals
+    that do and do not divide the horizon."""
+    nx, ny = shape
+    gc, oc, rho0, sf = _setup(nx, ny, scheme, collision, eos, t=0.9 if eos == "cs" else 0.8)
+    N, uf = 27, 15
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    L, g, gk, gT = lat.adjoint(0, rho0, N, uf, sf, ckpt)
+    Lo, go, gko, gTo = O.adjoint(oc, rho0, N, uf, sf)
+    assert abs(L / Lo - 1) < 1e-10
+    assert abs(gk / gko - 1) < 1e-10 and abs(gT / gTo - 1) < 1e-10
+    np.testing.assert_allclose(g, go, rtol=0, atol=1e-10 * np.abs(go).max())
+
+
+def test_gpu_adjoint_central_differences():
+    """dL/dkappa, dL/dT and a directional dL/drho0 of the GPU adjoint equal
+    central differences (FP64) of the GPU's own loss to 1e-6 relative."""
+    gc, _, rho0, sf = _setup(48, 40, lbfe.IMPROVED, lbfe.MRT)
+    N, uf = 120, 100
+
+    def loss(c, r):
+        lat = lbfe.Lattice([c], precision=lbfe.FP64)
+        out = lat.adjoint(0, r, N, uf, sf)[0]
+        lat.close()
+        return out
+
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    L, g, gk, gT = lat.adjoint(0, rho0, N, uf, sf, 10)
+    hk, hT = 1e-6, 1e-6 * gc.T
+    fdk = (loss(dataclasses.replace(gc, kappa=gc.kappa + hk), rho0) - loss(dataclasses.replace(gc, kappa=gc.kappa - hk), rho0)) / (2 * hk)
+    fdT = (loss(dataclasses.replace(gc, T=gc.T + hT), rho0) - loss(dataclasses.replace(gc, T=gc.T - hT), rho0)) / (2 * hT)
+    v = 2 * inputs.splitmix_uniform(3, 0, 48, 40) - 1
+    fdr = (loss(gc, rho0 + 1e-5 * v) - loss(gc, rho0 - 1e-5 * v)) / 2e-5
+    assert abs(gk / fdk - 1) < 1e-6
+    assert abs(gT / fdT - 1) < 1e-6
+    assert abs((g * v).sum() / fdr - 1) < 1e-6
+
+
+def test_autograd_function():
+    """LBLoss backpropagates the adjoint's gradients through torch."""
+    import torch
+
+    from paper_2008_01473_gb300.autograd import LBLoss
+
+    gc, _, rho0, sf = _setup(24, 20, lbfe.IMPROVED, lbfe.BGK)
+    kappa = torch.tensor(gc.kappa, dtype=torch.float64, requires_grad=True)
+    T = torch.tensor(gc.T, dtype=torch.float64, requires_grad=True)
+    r0 = torch.tensor(rho0, dtype=torch.float64, device="cuda", requires_grad=True)
+    L = LBLoss.apply(kappa, T, r0, gc, 30, 20, torch.tensor(sf, device="cuda"), 0)
+    (3.0 * L).backward()
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    Lr, g, gk, gT = lat.adjoint(0, rho0, 30, 20, sf)
+    assert abs(float(L) - Lr) < 1e-12 * abs(Lr)
+    assert abs(float(kappa.grad) - 3 * gk) < 1e-12 * abs(gk)
+    assert abs(float(T.grad) - 3 * gT) < 1e-12 * abs(gT)
+    np.testing.assert_allclose(r0.grad.cpu().numpy(), 3 * g, rtol=1e-12, atol=0)
+
+
+def test_adjoint_rejects_fp32_and_bad_rho0():
+    gc, _, rho0, sf = _setup(12, 10, lbfe.IMPROVED, lbfe.BGK)
+    with pytest.raises(lbfe.LBError):
+        lbfe.Lattice([gc], precision=lbfe.FP32).adjoint(0, rho0, 5, 0)
+    bad = rho0.copy()
+    bad[2, 3] = -1.0
+    with pytest.raises(lbfe.LBError):
+        lbfe.Lattice([gc], precision=lbfe.FP64).adjoint(0, bad, 5, 0)
