@@ -319,6 +319,76 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """Differentiation workload: 256^2 periodic droplet of radius 64 (vdW, T =
+    0.8 T_c, kappa 0.02, BGK tau 0.8, FP64), 2000 steps checkpointed every 100;
+    L = sum of |u|^2 over the last 100 steps + (rho_g - rho_g^Maxwell(T))^2 with
+    rho_g the mean density over the four corner squares of side L/8. Times the
+    gradient (forward + reverse sweep) and checks dL/dkappa and dL/d(T/T_c)
+    against central differences (h = 1e-4 relative) of the GPU forward loss."""
+    import numpy as np
+    import torch
+
+    from paper_2008_01473_gb300 import build, inputs, lbfe
+
+    build.build()
+    n, steps, window, ckpt = 256, 2000, 100, 100
+    tc, _ = lbfe.critical(lbfe.VDW, **VDW)
+    t_red = 0.8
+    rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc)
+    rho0 = inputs.droplet(n, n, 64.0, rl, rg)
+    m = n // 8
+    w = np.zeros((n, n))
+    for ys in (slice(0, m), slice(n - m, n)):
+        for xs in (slice(0, m), slice(n - m, n)):
+            w[ys, xs] = 1.0
+    w /= w.sum()
+
+    def case(kappa, t):
+        return lbfe.Case(nx=n, ny=n, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, T=t * tc, kappa=kappa,
+                         tau_v=0.8, **VDW)
+
+    def forward_loss(kappa, t):
+        lat = lbfe.Lattice([case(kappa, t)], precision=lbfe.FP64)
+        lat.init_fields(0, rho0)
+        lat.step(steps - window)
+        lu = 0.0
+        for k in range(window + 1):
+            mo = lat.moments(0)
+            lu += float((mo["ux"] ** 2 + mo["uy"] ** 2).sum())
+            if k < window:
+                lat.step(1)
+        g_m = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t * tc)[0]
+        rho_g = float((w * mo["rho"]).sum())
+        lat.close()
+        return lu + (rho_g - g_m) ** 2, rho_g, g_m
+
+    kappa = 0.02
+    L0, rho_g, gm = forward_loss(kappa, t_red)
+    s_final = 2.0 * (rho_g - gm) * w
+    lat = lbfe.Lattice([case(kappa, t_red)], precision=lbfe.FP64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    La, g_rho0, gk, gT = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt)
+    t_adj = time.perf_counter() - t0
+    lat.close()
+    # dL/dT: trajectory term from the adjoint, plus the explicit -2 (rho_g - rho_g^M) d rho_g^M / dT
+    hT = 1e-6 * tc
+    dgm = (lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc + hT)[0]
+           - lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc - hT)[0]) / (2 * hT)
+    dL_dt = tc * (gT - 2.0 * (rho_g - gm) * dgm)
+    hk, ht = 1e-4 * kappa, 1e-4 * t_red
+    fd_k = (forward_loss(kappa + hk, t_red)[0] - forward_loss(kappa - hk, t_red)[0]) / (2 * hk)
+    fd_t = (forward_loss(kappa, t_red + ht)[0] - forward_loss(kappa, t_red - ht)[0]) / (2 * ht)
+    line = {"metric": "adjoint gradient (lb_adjoint) vs central differences", "workload": run_adjoint.__doc__.split(".")[0],
+            "loss": L0, "adjoint_seconds": round(t_adj, 3),
+            "adjoint_node_steps_per_s": round(n * n * steps / t_adj, 1),
+            "dL_dkappa": {"adjoint": gk, "fd": fd_k, "rel_err": abs(gk - fd_k) / abs(fd_k)},
+            "dL_dT_over_Tc": {"adjoint": dL_dt, "fd": fd_t, "rel_err": abs(dL_dt - fd_t) / abs(fd_t)},
+            "dL_drho0_norm": float(np.sqrt((g_rho0 ** 2).sum())), "rho_g": rho_g, "rho_g_maxwell": gm}
+    print(json.dumps(line), flush=True)
+
+
 def _oracle_sample():
     import oracle as O
     from oracle import thermo
@@ -375,8 +445,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched"],
-                    help="spinodal: the 4096^2 lattice (default); batched: 256 uneven droplets")
+    ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "adjoint"],
+                    help="spinodal: the 4096^2 lattice (default); batched: 256 uneven droplets; "
+                         "adjoint: gradient of the 256^2 droplet loss with a finite-difference check")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -384,6 +455,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_gpu(args)
 

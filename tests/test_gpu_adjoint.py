@@ -104,3 +104,21 @@ def test_adjoint_rejects_fp32_and_bad_rho0():
     bad[2, 3] = -1.0
     with pytest.raises(lbfe.LBError):
         lbfe.Lattice([gc], precision=lbfe.FP64).adjoint(0, bad, 5, 0)
+
+
+def test_gpu_adjoint_matches_oracle_droplet_64():
+    """A longer horizon on the droplet shape of the differentiation workload
+    (64^2, radius 16, 200 steps, u window of 20, checkpoints every 20) against
+    the oracle's reverse sweep."""
+    gc, oc, _, _ = _setup(64, 64, lbfe.IMPROVED, lbfe.BGK)
+    e = thermo.vdw_paper()
+    _, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    rho0 = inputs.droplet(64, 64, 16.0, rl, rg)
+    sf = np.zeros((64, 64))
+    sf[:8, :8] = sf[:8, -8:] = sf[-8:, :8] = sf[-8:, -8:] = 1e-2 / 256
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    L, g, gk, gT = lat.adjoint(0, rho0, 200, 180, sf, 20)
+    Lo, go, gko, gTo = O.adjoint(oc, rho0, 200, 180, sf)
+    assert abs(L / Lo - 1) < 1e-9
+    assert abs(gk / gko - 1) < 1e-8 and abs(gT / gTo - 1) < 1e-8
+    np.testing.assert_allclose(g, go, rtol=0, atol=1e-8 * np.abs(go).max())
