@@ -17,7 +17,7 @@
 // columns [x0 - 4, x0 + wv + 4)), one full-mbarrier each. Stored row i = s - s0
 // lives in slot i % kPairSlots, phase (i / kPairSlots) & 1. Stage A of
 // iteration it reads rows it .. it + 2; after the block barrier that follows
-// it, row it is dead and lanes of warp 0 refill its slot with row
+// it, row it is dead and lanes of warps 0..2 refill its slot with row
 // it + kPairSlots (one lane per plane and run), so no producer warp is needed
 // and three blocks fit on an SM.
 //
@@ -223,17 +223,18 @@ __device__ __forceinline__ void pair_timeout(const PairCtx& X)
     atomicOr(X.status, 1);
 }
 
-// Warp 0 only: copy stored row i = s - s0 into slot k. Lane 0 arms the
-// slot's mbarrier with the byte count, then lane q < 9 * runs issues the copy
-// of plane q % 9, run q / 9.
+// Copy stored row i = s - s0 into slot k, spread over warps 0..2: thread 0
+// arms the slot's mbarrier with the byte count, and lane q < 3 * runs of warp
+// w issues the copy of plane 3 w + q % 3, run q / 3. (A copy may complete
+// before the arming arrive; the phase cannot complete before it, since that
+// arrive is the phase's only one.) Called by warps 0..2 only.
 __device__ __forceinline__ void pair_issue(const PairCtx& X, const DevCase<float>& c, int i, int k)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t* b = X.full + k;
-    if (lane == 0) mbar_expect_tx(b, X.row_bytes);
-    __syncwarp();
-    if (lane < kQ * X.runs.n) {
-        const int a = lane % kQ, r = lane / kQ;
+    if (threadIdx.x == 0) mbar_expect_tx(b, X.row_bytes);
+    if (lane < 3 * X.runs.n) {
+        const int a = 3 * w + lane % 3, r = lane / 3;
         const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
         const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
         const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
@@ -289,7 +290,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
     __syncthreads();
     // stored row it (ra - 1) has no reader left: refill its slot
-    if (threadIdx.x < 32 && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, c, it + kPairSlots, X.ks);
+    if (threadIdx.x < 96 && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, c, it + kPairSlots, X.ks);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float*
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x < 32)
+    if (threadIdx.x < 96)
         for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) pair_issue(X, c, i, i);
 
     const int p = threadIdx.x;
