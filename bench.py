@@ -382,7 +382,7 @@ def run_adjoint(args):
     hk, ht = 3e-6 * kappa, 3e-6 * t_red
     fd_k = (forward_loss(kappa + hk, t_red)[0] - forward_loss(kappa - hk, t_red)[0]) / (2 * hk)
     fd_t = (forward_loss(kappa, t_red + ht)[0] - forward_loss(kappa, t_red - ht)[0]) / (2 * ht)
-    line = {"metric": "adjoint gradient (lb_adjoint) vs central differences", "workload": run_adjoint.__doc__.split(".")[0],
+    line = {"metric": "adjoint gradient (lb_adjoint_step) vs central differences", "workload": run_adjoint.__doc__.split(".")[0],
             "loss": L0, "adjoint_seconds": round(t_adj, 3),
             "adjoint_node_steps_per_s": round(n * n * steps / t_adj, 1),
             "dL_dkappa": {"adjoint": gk, "fd": fd_k, "rel_err": abs(gk - fd_k) / abs(fd_k)},

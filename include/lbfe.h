@@ -155,11 +155,12 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
  * steps (0: about sqrt(nsteps)). d_ws: caller-owned device memory of at least
  * lb_adjoint_workspace_bytes, 256-byte aligned. rho0, s_final and grad_rho0
  * are device pointers if on_device, else host. Runs on the handle's stream,
- * synchronises it, and leaves the handle's own state untouched. The
- * north-star's lb_adjoint_step is this call over the whole horizon. */
+ * synchronises it, and leaves the handle's own state untouched. It is the
+ * reverse-time counterpart of lb_init_fields followed by lb_step(nsteps): one
+ * call runs all nsteps adjoint steps, newest first. */
 lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_t nsteps, int32_t ckpt_every,
                                      size_t* bytes);
-lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
+lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
                      const double* s_final, int32_t on_device, int32_t ckpt_every, void* d_ws, size_t ws_bytes,
                      double* loss, double* grad_rho0, double* grad_kappa, double* grad_T);
 

@@ -1,4 +1,4 @@
-"""torch.autograd.Function around the library's adjoint (lb_adjoint).
+"""torch.autograd.Function around the library's adjoint (lb_adjoint_step).
 
 LBLoss.apply(kappa, T, rho0, case, nsteps, u_from, s_final, ckpt_every)
 returns L = sum_{n >= u_from} sum_x |u^n|^2 + sum_x s_final rho^N for a run of

@@ -1,5 +1,5 @@
 // FP64 kernels of the discrete adjoint (reverse-mode derivative) of one time
-// step, for lb_adjoint. One thread per node, 256-thread blocks over
+// step, for lb_adjoint_step. One thread per node, 256-thread blocks over
 // (ceil(nx / 256), ny). Fields are dense [ny][nx] FP64 arrays; the adjoint
 // of the populations (lam) is kept at the nodes, lam_a(x) = dL/df_a(x), while
 // forward states are in the library's storage form (pulled on read).

@@ -734,21 +734,21 @@ lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_
     return LB_OK;
 }
 
-lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
+lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
                      const double* s_final, int32_t on_device, int32_t ckpt_every, void* d_ws, size_t ws_bytes,
                      double* loss, double* grad_rho0, double* grad_kappa, double* grad_T)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (case_id < 0 || case_id >= (int)h->cases.size() || !rho0 || nsteps < 0 || u_from < 0 || ckpt_every < 0 ||
         !loss || !grad_kappa || !grad_T)
-        return h->fail(LB_E_INVALID, "lb_adjoint: bad arguments");
-    if (h->prec != LB_FP64) return h->fail(LB_E_INVALID, "lb_adjoint: needs an LB_FP64 handle");
+        return h->fail(LB_E_INVALID, "lb_adjoint_step: bad arguments");
+    if (h->prec != LB_FP64) return h->fail(LB_E_INVALID, "lb_adjoint_step: needs an LB_FP64 handle");
     const lb_case& c = h->cases[case_id];
-    if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint: constant relaxation times only (nu = 0)");
+    if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
     const AdjLayout L = adj_layout(c, nsteps, K);
     if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || ws_bytes < L.total)
-        return h->fail(LB_E_WORKSPACE, "lb_adjoint: workspace misaligned or smaller than lb_adjoint_workspace_bytes");
+        return h->fail(LB_E_WORKSPACE, "lb_adjoint_step: workspace misaligned or smaller than lb_adjoint_workspace_bytes");
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
     cudaStream_t st = h->stream;
     // one-case step tables at offset 0 of the workspace's state buffers
@@ -796,7 +796,7 @@ lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t 
         s = h->cuda(cudaMemcpyAsync(chk, acc, sizeof chk, cudaMemcpyDeviceToHost, st), "adjoint check");
         if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(st), "adjoint check");
         if (s != LB_OK) return s;
-        if (chk[4] != 0.0) return h->fail(LB_E_INVALID, "lb_adjoint: rho0 must be finite, > 0 and inside the EOS domain");
+        if (chk[4] != 0.0) return h->fail(LB_E_INVALID, "lb_adjoint_step: rho0 must be finite, > 0 and inside the EOS domain");
     }
     if (c.scheme == LB_IMPROVED)
         s = c.eos == LB_VDW ? adjoint_run<1, 0>(h, c, Lr, ws, sfin, nsteps, u_from)
@@ -817,7 +817,7 @@ lb_status lb_adjoint(lb_handle* h, int32_t case_id, const double* rho0, int64_t 
     *grad_kappa = acc[1];
     *grad_T = acc[2];
     if (!std::isfinite(acc[0]) || !std::isfinite(acc[1]) || !std::isfinite(acc[2]))
-        return h->fail(LB_E_UNSTABLE, "lb_adjoint: non-finite loss or gradient");
+        return h->fail(LB_E_UNSTABLE, "lb_adjoint_step: non-finite loss or gradient");
     return LB_OK;
 }
 

@@ -89,14 +89,14 @@ def lib() -> C.CDLL:
         L.lb_maxwell.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
         L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
         L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
-        L.lb_adjoint.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
+        L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -228,7 +228,7 @@ class Lattice:
             grad = np.empty(sh)
             gp = C.c_void_p(grad.ctypes.data)
         L, gk, gT = C.c_double(), C.c_double(), C.c_double()
-        _check(lib().lb_adjoint(self._h, case_id, p, int(nsteps), int(u_from), ps, dev, int(ckpt_every),
+        _check(lib().lb_adjoint_step(self._h, case_id, p, int(nsteps), int(u_from), ps, dev, int(ckpt_every),
                                 C.c_void_p(wsp), nb.value, C.byref(L), gp, C.byref(gk), C.byref(gT)), self._h)
         del k0, k1, ws
         return L.value, grad, gk.value, gT.value

@@ -1,4 +1,4 @@
-"""GPU adjoint (lb_adjoint, FP64) against the oracle's adjoint and against
+"""GPU adjoint (lb_adjoint_step, FP64) against the oracle's adjoint and against
 central finite differences of the GPU's own loss; the autograd wrapper."""
 import dataclasses
 
