@@ -414,6 +414,44 @@ def test_standard_flat_interface_drifts():
     assert fl.mu.max() - fl.mu.min() > 1e-3
 
 
+def _square_gradient_tension(e, T, rg, rl, kappa):
+    """Surface tension of a flat interface in square-gradient theory (the
+    free energy int E_f + kappa/2 |grad rho|^2 of Eq. 2): sigma = int from
+    rho_g to rho_l of sqrt(2 kappa (E_f - mu rho + p)) drho at coexistence."""
+    from scipy.integrate import quad
+
+    mu, p = e.mu(rg, T), e.p(rg, T)
+    return quad(lambda r: np.sqrt(max(2.0 * kappa * (e.Ef(r, T) - mu * r + p), 0.0)), rg, rl, limit=200)[0]
+
+
+def test_laplace_law_droplets():
+    """Laplace's law (Sec. IV B, Eq. 32 rests on it): improved-scheme droplets
+    at 0.8 T_c reach a pressure jump p_EOS(rho_in) - p_EOS(rho_out) = sigma / r
+    with sigma the square-gradient tension of the EOS and kappa, computed here
+    by quadrature, not by the scheme; r is the equimolar radius. Centre disc of
+    radius r0/4 and corner squares of side L/8 give rho_in and rho_out."""
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    sigma = _square_gradient_tension(e, T, rg, rl, 0.02)
+    out = []
+    for r0, L, n in ((12, 48, 2000), (16, 56, 3000)):
+        c = O.Case(nx=L, ny=L, scheme=O.IMPROVED, eos=O.VDW, a=e.a, b=e.b, R=1.0, T=T, kappa=0.02, tau_v=1.0)
+        f = O.init(c, inputs.droplet(L, L, float(r0), rl, rg))
+        assert O.step(c, f, n) == n
+        rho = O.fields(c, f).rho
+        y, x = np.mgrid[0:L, 0:L]
+        rin = rho[np.hypot(x - L / 2, y - L / 2) < r0 / 4].mean()
+        s = L // 8
+        rout = np.concatenate([rho[:s, :s].ravel(), rho[:s, -s:].ravel(), rho[-s:, :s].ravel(),
+                               rho[-s:, -s:].ravel()]).mean()
+        r = np.sqrt((rho.sum() - rout * L * L) / (np.pi * (rin - rout)))
+        out.append((r, e.p(rin, T) - e.p(rout, T)))
+    for r, dp in out:
+        assert abs(dp * r / sigma - 1) < 0.02
+    # dp proportional to 1/r between the two radii
+    assert abs((out[0][1] * out[0][0]) / (out[1][1] * out[1][0]) - 1) < 0.01
+
+
 def test_spurious_currents_table1():
     """Table I: at T = 0.8 Tc the improved scheme's spurious currents fall to
     round-off (1e-15..1e-14) while the standard scheme keeps ~5e-4; a 32 x 32
