@@ -267,6 +267,62 @@ def batched_cases(lbfe, n_cases: int = 256, seed: int = 7):
     return cases, rhos
 
 
+def _vdw_p(rho, T):
+    """van der Waals pressure of Eq. 30's free energy, for the diagnostics."""
+    return rho * VDW["R"] * T / (1.0 - VDW["b"] * rho) - VDW["a"] * rho * rho
+
+
+def _batched_accuracy(lbfe, cases, rhos, steps):
+    """Droplet diagnostics of a sub-batch run in FP32 against the same cases
+    run in FP64 (whose step is checked against the FP64 oracle by the GPU
+    tests) for the same number of steps: pressure jump p(rho_in) -
+    p(rho_out) (centre disc of radius r0/4, corner squares of side L/8),
+    equimolar radius and max |u|. Returns the worst relative errors and the
+    largest spurious currents of both runs."""
+    import numpy as np
+
+    lats = {}
+    for prec in (lbfe.FP32, lbfe.FP64):
+        lat = lbfe.Lattice(cases, precision=prec)
+        for i, r in enumerate(rhos):
+            lat.init_fields(i, r)
+        lat.step(steps)
+        lats[prec] = lat
+    err_dp, err_r, u = 0.0, 0.0, {lbfe.FP32: 0.0, lbfe.FP64: 0.0}
+    for i, c in enumerate(cases):
+        L = c.nx
+        y, x = np.mgrid[0:L, 0:L]
+        disc = np.hypot(x - L / 2, y - L / 2) < 0.25 * _batched_r0(rhos[i])
+        s = L // 8
+        dp, req = {}, {}
+        for prec, lat in lats.items():
+            m = lat.moments(i)
+            rho = m["rho"]
+            rout = np.concatenate([rho[:s, :s].ravel(), rho[:s, -s:].ravel(), rho[-s:, :s].ravel(),
+                                   rho[-s:, -s:].ravel()]).mean()
+            rin = rho[disc].mean()
+            dp[prec] = _vdw_p(rin, c.T) - _vdw_p(rout, c.T)
+            req[prec] = np.sqrt((rho.sum() - rout * L * L) / (np.pi * (rin - rout)))
+            u[prec] = max(u[prec], float(np.hypot(m["ux"], m["uy"]).max()))
+        err_dp = max(err_dp, abs(dp[lbfe.FP32] / dp[lbfe.FP64] - 1))
+        err_r = max(err_r, abs(req[lbfe.FP32] / req[lbfe.FP64] - 1))
+    for lat in lats.values():
+        lat.close()
+    return {"cases": len(cases), "steps": steps, "max_rel_err_pressure_jump": err_dp,
+            "max_rel_err_equimolar_radius": err_r, "max_u_fp32": u[lbfe.FP32], "max_u_fp64": u[lbfe.FP64]}
+
+
+def _batched_r0(rho0):
+    """Initial droplet radius from the tanh profile: the half-density
+    crossing along the centre row."""
+    import numpy as np
+
+    L = rho0.shape[0]
+    row = rho0[L // 2, L // 2:]
+    mid = 0.5 * (row.max() + row.min())
+    return float(np.argmax(row < mid))
+
+
 def run_batched(args):
     """Throughput of the uneven batch in one handle (one launch per step)
     against one handle per case (one launch per case per step)."""
@@ -290,7 +346,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1)
     _, st = lat.reductions()
+    seg_rows, n_items = lat.worklist()
     lat.close()
+    acc = _batched_accuracy(lbfe, cases[::8], rhos[::8], args.accuracy_steps) if args.accuracy_steps else None
     lats = []
     for c, r in zip(cases, rhos):
         l1 = lbfe.Lattice([c], precision=lbfe.FP32)
@@ -311,7 +369,9 @@ def run_batched(args):
             "warmup": args.warmup, "ms_per_step": round(batched_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched uneven droplets: " + (batched_cases.__doc__ or "").split(":")[1].strip(),
-                       "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum())},
+                       "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum()),
+                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items}},
+            "fp32_vs_fp64": acc,  # every 8th case of the batch
             "per_case_launches": {"value": round(nodes * args.steps / (per_case_ms * 1e-3) / 1e6, 1),
                                   "unit": "MLUPS", "ms_per_step": round(per_case_ms / args.steps, 4)},
             "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / args.steps * 1e-3) / 1e9, 1),
@@ -499,6 +559,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=150)
+    ap.add_argument("--accuracy-steps", type=int, default=10000,
+                    help="batched workload: steps of the FP32-vs-FP64 droplet check (0 skips it)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])

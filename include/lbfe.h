@@ -111,11 +111,23 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
  * Eq. 10): one fused kernel launch per step and per group of cases that
- * share scheme, collision, EOS, viscosity mode and nx % 4 == 0. Runs of 8
+ * share scheme, collision, EOS, viscosity mode and nx % 4 == 0; each launch
+ * runs a work-list of (case, column strip, row segment) items. The first
+ * call with nsteps > 0 autotunes the work-list: it times one step under
+ * several row-segment sizes and keeps the fastest (these trial launches read
+ * the current populations and write only the buffer the next step
+ * overwrites, so the state and every result are unchanged; the choice
+ * affects speed only). LBFE_SEG_ROWS=n before lb_create fixes the segment
+ * size instead (0: a share of the GPU's block slots per case). Runs of 8
  * steps replay a CUDA graph captured on the first such call (on a private
  * stream, then launched on the handle's stream; set LBFE_GRAPH=0 before
- * lb_create to launch every step directly). Enqueued asynchronously. */
+ * lb_create to launch every step directly). Enqueued asynchronously, except
+ * that the autotuning call synchronises the stream. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
+
+/* The work-list in use: rows per segment (0: slot-share rule) and item
+ * count. Before the first lb_step it is the untuned default. */
+lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items);
 
 /* Macroscopic fields of case case_id at the current step: rho and u of
  * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2, computed per node in

@@ -158,6 +158,9 @@ struct lb_handle {
     cudaStream_t cap_stream = nullptr;              // private stream used only for graph capture
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer 0 / 1
     int tma_threads = 0;    // TMA kernel shape: 0 packed two-column, 128 or 256 one-column
+    int seg_rows = 0;       // work-list rows per segment, 0: share of the block slots
+    bool autotune = true;   // pick seg_rows by timing on the first lb_step
+    bool tuned = false;
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -201,11 +204,16 @@ namespace {
 
 constexpr int kGraphSteps = 8;  // steps per captured graph (even: buffer parity returns)
 
-// Split every case into column strips and row segments so that one launch
-// fills the GPU about once: each case gets a share of the resident block
-// slots proportional to its node count.
+// Split every case into column strips and row segments. seg_rows == 0: each
+// case gets a share of the resident block slots proportional to its node
+// count, so that one launch fills the GPU about once; seg_rows > 0: segments
+// of about seg_rows rows (at least kMinRows). Within a group the items run
+// longest first, so the block scheduler hands the short ones to the slots
+// that free up last. The decomposition changes no result: every node's
+// update is the same arithmetic on the same inputs whichever item owns it.
 void build_items(lb_handle* h)
 {
+    const int seg_rows = h->seg_rows;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -241,8 +249,9 @@ void build_items(lb_handle* h)
                         const int ns = strips_of(c, width);
                         const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
                         const double share = slots * ((double)c.nx * c.ny) / nodes;
-                        int nseg = std::max(1, (int)std::floor(share / ns));
-                        nseg = std::min(nseg, std::max(1, c.ny / kMinRows));
+                        int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows
+                                                : (int)std::floor(share / ns);
+                        nseg = std::min(std::max(1, nseg), std::max(1, c.ny / kMinRows));
                         for (int k = 0; k < ns; ++k) {
                             const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns);
                             const int x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
@@ -254,8 +263,17 @@ void build_items(lb_handle* h)
                         }
                     }
                     g.count = (int64_t)h->items.size() - g.first;
+                    std::stable_sort(h->items.begin() + g.first, h->items.end(),
+                                     [](const Item& a, const Item& b) { return a.h > b.h; });
                     h->groups.push_back(g);
                 }
+}
+
+lb_status upload_items(lb_handle* h)
+{
+    return h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
+                                   cudaMemcpyHostToDevice, h->stream),
+                   "upload items");
 }
 
 lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
@@ -366,10 +384,12 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
         const int v = std::atoi(p);
         h->tma_threads = (v == 128 || v == 256) ? v : 0;
     }
+    if (const char* p = std::getenv("LBFE_SEG_ROWS")) {
+        h->seg_rows = std::max(0, std::atoi(p));
+        h->autotune = false;
+    }
     build_items(h);
-    lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
-                                          cudaMemcpyHostToDevice, h->stream),
-                          "upload items");
+    lb_status s = upload_items(h);
     if (s == LB_OK) s = h->cuda(cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream), "clear status");
     for (int i = 0; i < ncases && s == LB_OK; ++i) s = h->upload_case(i);
     if (s != LB_OK) {
@@ -455,12 +475,55 @@ static lb_status capture_graph(lb_handle* h, int cur)
     return s;
 }
 
+// Time one step under each candidate work-list and keep the fastest. Every
+// trial launch reads the current buffer and writes the other one, which the
+// next real step overwrites, so the state is untouched.
+static lb_status autotune(lb_handle* h)
+{
+    static const int cands[] = {0, 256, 128, 64, 32, 16};
+    constexpr int kReps = 3;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    lb_status s = h->cuda(cudaEventCreate(&e0), "tune event");
+    if (s == LB_OK) s = h->cuda(cudaEventCreate(&e1), "tune event");
+    int best = 0;
+    float best_ms = 0.f;
+    for (int k = 0; k < (int)(sizeof cands / sizeof cands[0]) && s == LB_OK; ++k) {
+        h->seg_rows = cands[k];
+        build_items(h);
+        if ((int64_t)h->items.size() > h->L.max_items) continue;
+        if ((s = upload_items(h)) != LB_OK) break;
+        if ((s = enqueue_step(h, h->cur, h->stream)) != LB_OK) break;
+        if ((s = h->cuda(cudaEventRecord(e0, h->stream), "tune record")) != LB_OK) break;
+        for (int r = 0; r < kReps && s == LB_OK; ++r) s = enqueue_step(h, h->cur, h->stream);
+        if (s != LB_OK) break;
+        if ((s = h->cuda(cudaEventRecord(e1, h->stream), "tune record")) != LB_OK) break;
+        if ((s = h->cuda(cudaEventSynchronize(e1), "tune sync")) != LB_OK) break;
+        float ms = 0.f;
+        if ((s = h->cuda(cudaEventElapsedTime(&ms, e0, e1), "tune time")) != LB_OK) break;
+        if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = cands[k];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->seg_rows = best;
+    build_items(h);
+    lb_status u = upload_items(h);
+    h->tuned = true;
+    return s != LB_OK ? s : u;
+}
+
 lb_status lb_step(lb_handle* h, int64_t nsteps)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (nsteps < 0) return h->fail(LB_E_INVALID, "lb_step: nsteps < 0");
     for (size_t i = 0; i < h->cases.size(); ++i)
         if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_step: every case needs lb_init_fields first");
+    if (h->autotune && !h->tuned && nsteps > 0) {
+        lb_status s = autotune(h);
+        if (s != LB_OK) return s;
+    }
     int64_t n = nsteps;
     if (h->use_graph && n >= kGraphSteps) {
         if (!h->graph[h->cur]) {
@@ -478,6 +541,14 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
         h->cur ^= 1;
     }
     for (auto& st : h->steps) st += nsteps;
+    return LB_OK;
+}
+
+lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items)
+{
+    if (!h) return LB_E_INVALID;
+    if (seg_rows) *seg_rows = h->seg_rows;
+    if (n_items) *n_items = (int64_t)h->items.size();
     return LB_OK;
 }
 

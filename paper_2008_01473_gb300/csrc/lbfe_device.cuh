@@ -167,7 +167,6 @@ __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T
     const T b_dg = a0 + T(2) * a1 + a2;
     const T ex = a3 - T(2) * a4, ey = a5 - T(2) * a6;
     const T X = a3 + a4, Y = a5 + a6;
-    d[0] = a0 - T(4) * (a1 - a2);
     d[1] = b_ax + ex + a7;
     d[3] = b_ax - ex + a7;
     d[2] = b_ax + ey - a7;
@@ -176,6 +175,10 @@ __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T
     d[7] = b_dg - (X + Y) + a8;
     d[6] = b_dg + (Y - X) - a8;
     d[8] = b_dg + (X - Y) - a8;
+    // rest population from the conserved density: equal to the M^-1 row
+    // a0 - 4 (a1 - a2) in exact arithmetic, and in finite precision keeps
+    // the stored density equal to the pulled one up to two rounded sums
+    d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 
 // Shear rate at a node: constant, or from a constant kinematic viscosity.

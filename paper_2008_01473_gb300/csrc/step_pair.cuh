@@ -174,7 +174,6 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     const float2 b_dg = fma2(v2(2.0f), a1, a0 + a2);
     const float2 ex = fma2(v2(-2.0f), a4, a3), ey = fma2(v2(-2.0f), a6, a5);
     const float2 X = a3 + a4, Y = a5 + a6;
-    d[0] = fma2(v2(-4.0f), a1 - a2, a0);
     d[1] = (b_ax + ex) + a7;
     d[3] = (b_ax - ex) + a7;
     d[2] = (b_ax + ey) - a7;
@@ -183,6 +182,13 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     d[7] = (b_dg - (X + Y)) + a8;
     d[6] = (b_dg + (Y - X)) - a8;
     d[8] = (b_dg + (X - Y)) - a8;
+    // Rest population last, from the conserved density (m*_rho = drho):
+    // d0 = drho - the sum of the eight moving ones. In exact arithmetic this
+    // is the M^-1 row a0 - 4 (a1 - a2); in FP32 it keeps the stored density
+    // equal to the pulled one up to the rounding of two sums, where nine
+    // independently rounded rows of magnitude |drho| drift the mass
+    // systematically once the flow is steady (the same rounding every step).
+    d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 
 template <int SCHEME>

@@ -90,13 +90,14 @@ def lib() -> C.CDLL:
         L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
         L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
+        L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64)]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -181,6 +182,13 @@ class Lattice:
 
     def step(self, nsteps: int = 1):
         _check(lib().lb_step(self._h, int(nsteps)), self._h)
+
+    def worklist(self):
+        """(rows per segment, item count) of the work-list in use; 0 rows is
+        the slot-share rule."""
+        r, n = C.c_int32(), C.c_int64()
+        _check(lib().lb_worklist(self._h, C.byref(r), C.byref(n)), self._h)
+        return r.value, n.value
 
     def moments(self, case_id: int, on_device: bool = False):
         """dict rho, ux, uy, mu of the current state (numpy, or CUDA tensors)."""

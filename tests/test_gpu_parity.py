@@ -339,3 +339,82 @@ def test_improved_flat_interface_reaches_maxwell_on_gpu(precision):
         rho = lat.moments(i)["rho"][0]
         assert abs(rho[:6].mean() / rg - 1) < 1e-4
         assert abs(rho[44:56].mean() / rl - 1) < 1e-4
+
+
+def _droplet_diag(e, T, rho, ux, uy, r0):
+    """Pressure jump p_EOS(rho_in) - p_EOS(rho_out) (centre disc of radius
+    r0/4, corner squares of side L/8), equimolar radius, max |u|."""
+    L = rho.shape[0]
+    y, x = np.mgrid[0:L, 0:L]
+    rin = rho[np.hypot(x - L / 2, y - L / 2) < r0 / 4].mean()
+    s = L // 8
+    rout = np.concatenate([rho[:s, :s].ravel(), rho[:s, -s:].ravel(), rho[-s:, :s].ravel(),
+                           rho[-s:, -s:].ravel()]).mean()
+    r = np.sqrt((rho.sum() - rout * L * L) / (np.pi * (rin - rout)))
+    return e.p(rin, T) - e.p(rout, T), r, float(np.hypot(ux, uy).max())
+
+
+def test_fp32_batched_droplets_vs_oracle():
+    """Uneven batch in one FP32 handle (four droplets, sides 32..48, their own
+    T, kappa, tau and radius; improved, BGK, vdW) against the FP64 oracle run
+    case by case: after 3000 steps the pressure jump agrees to 2e-3 relative,
+    the equimolar radius to 1e-3, and the FP32 spurious current stays below
+    2e-5 (the oracle's, still decaying, below 1e-8)."""
+    rng = np.random.default_rng(3)
+    e = thermo.vdw_paper()
+    cases, ocs, rhos, meta = [], [], [], []
+    for side in (32, 36, 40, 48):
+        t, kappa, tau, frac = rng.uniform(0.8, 0.9), rng.uniform(0.01, 0.03), rng.uniform(0.8, 1.0), \
+            rng.uniform(0.2, 0.3)
+        T, rg, rl = thermo.maxwell_reduced(e, t)
+        kw = dict(nx=side, ny=side, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, a=e.a, b=e.b, R=1.0,
+                  T=T, kappa=kappa, tau_v=tau)
+        cases.append(lbfe.Case(**kw))
+        ocs.append(O.Case(**kw))
+        rhos.append(inputs.droplet(side, side, frac * side, rl, rg))
+        meta.append((T, frac * side))
+    lat, outs = _gpu_run(cases, rhos, 3000, lbfe.FP32)
+    lat.close()
+    for i, oc in enumerate(ocs):
+        _, ref = _oracle_run(oc, rhos[i], 3000)
+        T, r0 = meta[i]
+        dp_o, r_o, u_o = _droplet_diag(e, T, ref.rho, ref.ux, ref.uy, r0)
+        m = outs[i]
+        dp_g, r_g, u_g = _droplet_diag(e, T, m["rho"], m["ux"], m["uy"], r0)
+        assert abs(dp_g / dp_o - 1) < 2e-3, (i, dp_g, dp_o)
+        assert abs(r_g / r_o - 1) < 1e-3
+        assert u_o < 1e-8 and u_g < 2e-5, (u_o, u_g)
+
+
+def test_autotuned_worklist_changes_no_result(monkeypatch):
+    """The work-list autotuner picks a row-segment size by timing; every
+    choice gives bit-identical populations (FP32 batch of uneven cases)."""
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.85)
+    cases, rhos = [], []
+    for side in (64, 100, 260, 36):
+        cases.append(lbfe.Case(nx=side, ny=side + 8, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW,
+                               a=e.a, b=e.b, T=T, kappa=0.02, tau_v=0.9))
+        rhos.append(inputs.droplet(side, side + 8, 0.25 * side, rl, rg, noise=1e-3, case=side))
+    snaps = {}
+    for seg in ("0", "16", "64", None):
+        if seg is None:
+            monkeypatch.delenv("LBFE_SEG_ROWS", raising=False)
+        else:
+            monkeypatch.setenv("LBFE_SEG_ROWS", seg)
+        lat = lbfe.Lattice(cases, precision=lbfe.FP32)
+        for i, r in enumerate(rhos):
+            lat.init_fields(i, r)
+        lat.step(21)
+        rows, n_items = lat.worklist()
+        if seg is not None:
+            assert rows == int(seg)
+        assert n_items >= len(cases)
+        snaps[seg] = [lat.save(i) for i in range(len(cases))]
+        lat.close()
+    for seg in ("16", "64", None):
+        for i, c in enumerate(cases):
+            pitch = (c.nx + 31) // 32 * 32
+            a = np.frombuffer(snaps["0"][i][16:], dtype=np.float32).reshape(9, c.ny, pitch)[:, :, :c.nx]
+            b = np.frombuffer(snaps[seg][i][16:], dtype=np.float32).reshape(9, c.ny, pitch)[:, :, :c.nx]
+            assert np.array_equal(a, b), (seg, i)
