@@ -200,6 +200,7 @@ def run_gpu(args):
                                C.c_void_p(res["uy"].data_ptr()), None, 0)
     lbfe._check(rc, lat._h)
     e2e_s = time.perf_counter() - t0
+    seg_rows, n_items = lat.worklist()
     if ws > 1:
         t = torch.tensor([e2e_s], device=f"cuda:{local}")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -221,7 +222,8 @@ def run_gpu(args):
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": f"populations {BYTES_PER_NODE[dtype] * nodes / 1e9:.2f} GB per step vs 129 MB L2 "
                              "(no flush)",
-                       "stable": stable},
+                       "stable": stable,
+                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": _profiled_traffic(n_side) if dtype == "f32" else None,

@@ -477,37 +477,56 @@ static lb_status capture_graph(lb_handle* h, int cur)
 
 // Time one step under each candidate work-list and keep the fastest. Every
 // trial launch reads the current buffer and writes the other one, which the
-// next real step overwrites, so the state is untouched.
+// next real step overwrites, so the state is untouched. Each candidate runs
+// for about 1 ms per pass (3 to 64 launches) in two interleaved passes, its
+// time is the better pass, and a candidate replaces the slot-share rule only
+// if it is at least 2 % faster.
+static lb_status tune_time(lb_handle* h, cudaEvent_t e0, cudaEvent_t e1, int reps, float* ms)
+{
+    lb_status s = h->cuda(cudaEventRecord(e0, h->stream), "tune record");
+    for (int r = 0; r < reps && s == LB_OK; ++r) s = enqueue_step(h, h->cur, h->stream);
+    if (s == LB_OK) s = h->cuda(cudaEventRecord(e1, h->stream), "tune record");
+    if (s == LB_OK) s = h->cuda(cudaEventSynchronize(e1), "tune sync");
+    if (s == LB_OK) s = h->cuda(cudaEventElapsedTime(ms, e0, e1), "tune time");
+    if (s == LB_OK) *ms /= (float)reps;
+    return s;
+}
+
 static lb_status autotune(lb_handle* h)
 {
     static const int cands[] = {0, 256, 128, 64, 32, 16};
-    constexpr int kReps = 3;
+    constexpr int kCands = (int)(sizeof cands / sizeof cands[0]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     lb_status s = h->cuda(cudaEventCreate(&e0), "tune event");
     if (s == LB_OK) s = h->cuda(cudaEventCreate(&e1), "tune event");
-    int best = 0;
-    float best_ms = 0.f;
-    for (int k = 0; k < (int)(sizeof cands / sizeof cands[0]) && s == LB_OK; ++k) {
-        h->seg_rows = cands[k];
-        build_items(h);
-        if ((int64_t)h->items.size() > h->L.max_items) continue;
-        if ((s = upload_items(h)) != LB_OK) break;
-        if ((s = enqueue_step(h, h->cur, h->stream)) != LB_OK) break;
-        if ((s = h->cuda(cudaEventRecord(e0, h->stream), "tune record")) != LB_OK) break;
-        for (int r = 0; r < kReps && s == LB_OK; ++r) s = enqueue_step(h, h->cur, h->stream);
-        if (s != LB_OK) break;
-        if ((s = h->cuda(cudaEventRecord(e1, h->stream), "tune record")) != LB_OK) break;
-        if ((s = h->cuda(cudaEventSynchronize(e1), "tune sync")) != LB_OK) break;
-        float ms = 0.f;
-        if ((s = h->cuda(cudaEventElapsedTime(&ms, e0, e1), "tune time")) != LB_OK) break;
-        if (k == 0 || ms < best_ms) {
-            best_ms = ms;
-            best = cands[k];
-        }
+    float best_ms[kCands];
+    for (float& b : best_ms) b = 1e30f;
+    int reps = 3;
+    // candidate 0 (the current list) sets the launch count: two warm-up
+    // launches, then one timed
+    if (s == LB_OK) {
+        float t1 = 0.f;
+        for (int r = 0; r < 2 && s == LB_OK; ++r) s = enqueue_step(h, h->cur, h->stream);
+        if (s == LB_OK) s = tune_time(h, e0, e1, 1, &t1);
+        if (s == LB_OK) reps = std::max(3, std::min(64, (int)(1.0f / std::max(t1, 1e-3f))));
     }
+    for (int pass = 0; pass < 2 && s == LB_OK; ++pass)
+        for (int k = 0; k < kCands && s == LB_OK; ++k) {
+            h->seg_rows = cands[k];
+            build_items(h);
+            if ((int64_t)h->items.size() > h->L.max_items) continue;
+            if ((s = upload_items(h)) != LB_OK) break;
+            if ((s = enqueue_step(h, h->cur, h->stream)) != LB_OK) break;
+            float ms = 0.f;
+            if ((s = tune_time(h, e0, e1, reps, &ms)) != LB_OK) break;
+            best_ms[k] = std::min(best_ms[k], ms);
+        }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    h->seg_rows = best;
+    int best = 0;
+    for (int k = 1; k < kCands; ++k)
+        if (best_ms[k] < 0.98f * best_ms[0] && best_ms[k] < best_ms[best]) best = k;
+    h->seg_rows = cands[best];
     build_items(h);
     lb_status u = upload_items(h);
     h->tuned = true;
