@@ -98,6 +98,29 @@ def _profiled_traffic(n_side: int):
     return int(vals["traffic_bytes_per_launch:"])
 
 
+# FP64 step (one column per thread): FP64 instructions executed per node update,
+# halo recomputation included, from ncu's per-opcode thread counts at 2048^2
+# (DADD 111.4, DFMA 88.5, DMUL 30.6); FLOPs count 2 per DFMA.
+FP64_INST_PER_NODE = 230.5
+FP64_FLOP_PER_NODE = 2 * 88.5 + 111.4 + 30.6
+# GB300 FP64 rate: 2 FP64 thread-instructions per clock per SM (1.25 TFLOP/s
+# of DFMA over 152 SMs at 2.07 GHz)
+FP64_PER_CLK_SM, N_SMS, SM_MAX_GHZ = 2, 152, 2.07
+
+
+def _fp64_roofline(nodes: int, mean_ms: float, hbm_frac: float) -> dict:
+    """The FP64 step is bound by the FP64 pipe, not by HBM."""
+    rate = nodes / (mean_ms * 1e-3)
+    peak = N_SMS * FP64_PER_CLK_SM * 2 * SM_MAX_GHZ * 1e9
+    achieved = rate * FP64_FLOP_PER_NODE
+    return {"bound": "alu", "achieved": round(achieved / 1e12, 4), "peak": round(peak / 1e12, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz",
+            "fp64_pipe_frac": round(rate * FP64_INST_PER_NODE / (N_SMS * FP64_PER_CLK_SM * SM_MAX_GHZ * 1e9), 4),
+            "fp64_inst_per_node": FP64_INST_PER_NODE, "hbm_frac": round(hbm_frac, 4),
+            "kernel_ms_mean": round(mean_ms, 4)}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -237,7 +260,8 @@ def run_gpu(args):
                          "frac": round(achieved / peak, 4),
                          "traffic": _profiled_traffic(n_side) if dtype == "f32" else None,
                          "peak_source": src, "bytes_per_node": BYTES_PER_NODE[dtype],
-                         "kernel_ms_mean": round(mean_ms, 4), "kernel_ms_min": round(min(per), 4)},
+                         "kernel_ms_mean": round(mean_ms, 4), "kernel_ms_min": round(min(per), 4)}
+            if dtype == "f32" else _fp64_roofline(nodes, mean_ms, achieved / peak),
             "clocks": clk,
             "e2e": {"value": round(_job_mlups(ws, nodes, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
                     "h2d_bytes_per_step": int(8 * nodes / args.steps),
