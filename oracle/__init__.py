@@ -25,7 +25,7 @@ _SRC = os.path.join(_HERE, "lbfe_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liblbfe_oracle.so")
 _lib = None
 
-STANDARD, IMPROVED = 0, 1
+STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
 BGK, MRT = 0, 1
 VDW, CS = thermo.VDW, thermo.CS
 

@@ -66,7 +66,8 @@ static const double MM[Q][Q] = {
 
 typedef struct {
     int32_t nx, ny;
-    int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28) */
+    int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28),
+                          2 = standard with the pressure-tensor force (Eq. 13 left) */
     int32_t collision; /* 0 = BGK (all rates 1/tau_v), 1 = MRT (Eq. 8) */
     int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
@@ -194,7 +195,7 @@ static void matvec(const double* A, const double* v, double* out)
 void orc_meq(const orc_case* c, double rho, double ux, double uy, double mu, double* meq)
 {
     double u2 = ux * ux + uy * uy;
-    if (c->scheme == 0) {
+    if (c->scheme != 1) {
         meq[0] = rho;
         meq[1] = rho * (-2.0 + 3.0 * u2);
         meq[2] = rho * (1.0 - 3.0 * u2);
@@ -314,6 +315,37 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
             Fx[i] = grx[i] - rho[i] * gmx[i];
             Fy[i] = gry[i] - rho[i] * gmy[i];
         }
+    } else if (c->scheme == 2) {
+        /* pressure-tensor form: F = grad(rho c_s^2) - div P, with the non-local
+         * pressure of Eq. 4 and the tensor of Eq. 5 built at every node from the
+         * Eq. 17 gradient and the Laplacian of rho, then div P by Eq. 17 applied
+         * to each component */
+        double* r3 = calloc(N, sizeof(double));
+        double* drx = calloc(N, sizeof(double));
+        double* dry = calloc(N, sizeof(double));
+        double* Pxx = calloc(N, sizeof(double));
+        double* Pxy = calloc(N, sizeof(double));
+        double* Pyy = calloc(N, sizeof(double));
+        double* gx = calloc(N, sizeof(double));
+        double* gy = calloc(N, sizeof(double));
+        for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
+        orc_grad(nx, ny, r3, grx, gry);
+        orc_grad(nx, ny, rho, drx, dry);
+        for (int i = 0; i < N; ++i) {
+            double p = orc_pEOS(c, rho[i]) - c->kappa * rho[i] * lap[i] -
+                       0.5 * c->kappa * (drx[i] * drx[i] + dry[i] * dry[i]);
+            Pxx[i] = p + c->kappa * drx[i] * drx[i];
+            Pyy[i] = p + c->kappa * dry[i] * dry[i];
+            Pxy[i] = c->kappa * drx[i] * dry[i];
+        }
+        for (int i = 0; i < N; ++i) Fx[i] = grx[i], Fy[i] = gry[i];
+        orc_grad(nx, ny, Pxx, gx, gy);
+        for (int i = 0; i < N; ++i) Fx[i] -= gx[i];
+        orc_grad(nx, ny, Pxy, gx, gy);
+        for (int i = 0; i < N; ++i) Fx[i] -= gy[i], Fy[i] -= gx[i];
+        orc_grad(nx, ny, Pyy, gx, gy);
+        for (int i = 0; i < N; ++i) Fy[i] -= gy[i];
+        free(r3); free(drx); free(dry); free(Pxx); free(Pxy); free(Pyy); free(gx); free(gy);
     } else {
         for (int i = 0; i < N; ++i) {
             Fx[i] = (CS2 - rho[i]) * gmx[i];
@@ -791,7 +823,7 @@ int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u
                 double* loss, double* g_rho0, double* g_kappa, double* g_T)
 {
     const int nx = c->nx, ny = c->ny, N = nx * ny;
-    if (c->nu > 0.0 || nsteps < 0) return -1;
+    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2) return -1; /* no pressure-tensor adjoint */
     int64_t K = 1;
     while (K * K < nsteps) ++K;
     const int64_t ncp = nsteps / K + 1;

@@ -326,7 +326,7 @@ def test_mrt_equal_rates_is_bgk():
 
 
 # ------------------------------------------------------------------ invariants
-@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED])
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.STANDARD_PT])
 @pytest.mark.parametrize("collision", [O.BGK, O.MRT])
 def test_mass_conservation(scheme, collision):
     """sum G = 0 (Eq. 14), zero mass entries of S and C (Eq. 28) and periodic
@@ -338,7 +338,7 @@ def test_mass_conservation(scheme, collision):
     assert abs(f.sum() / m0 - 1) < 1e-13
 
 
-@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED])
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.STANDARD_PT])
 def test_quiescent_uniform_state(scheme):
     """A uniform fluid at rest stays exactly uniform with u = 0."""
     c, rg, rl = vdw_case(0.8, scheme=scheme, nx=8, ny=8, collision=O.MRT, tau_v=0.8)
@@ -450,6 +450,43 @@ def test_laplace_law_droplets():
         assert abs(dp * r / sigma - 1) < 0.02
     # dp proportional to 1/r between the two radii
     assert abs((out[0][1] * out[0][0]) / (out[1][1] * out[1][0]) - 1) < 0.01
+
+
+def test_pressure_tensor_force_matches_chemical_potential_form():
+    """Eq. 6: div P = rho grad mu_c in the continuum, so the pressure-tensor
+    force (Eq. 13 left, P from Eqs. 4-5) and the chemical-potential force
+    (Eq. 13 right) differ only by discretisation error: on a smooth periodic
+    density field the relative difference falls at second order or faster
+    with the grid step, although with kappa = 1 the gradient terms of P carry
+    a share of the force of order one on the coarse grid (a wrong
+    coefficient or sign there would leave an O(1) difference)."""
+    e = thermo.vdw_paper()
+    T = 0.8 * e.critical()[0]
+    rel = []
+    for n in (32, 64, 128):
+        x = np.arange(n)
+        X, Y = np.meshgrid(x, x)
+        k = 2 * np.pi / n
+        rho = 1.0 + 0.3 * np.sin(k * X) * np.cos(2 * k * Y) + 0.2 * np.cos(k * Y)
+        F = {}
+        for s in (O.STANDARD, O.STANDARD_PT):
+            c = O.Case(nx=n, ny=n, scheme=s, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=1.0, tau_v=1.0)
+            fl = O.fields(c, O.init(c, rho))
+            F[s] = np.stack([fl.Fx, fl.Fy])
+        rel.append(np.abs(F[O.STANDARD] - F[O.STANDARD_PT]).max() / np.abs(F[O.STANDARD]).max())
+    assert rel[0] < 2e-2 and rel[1] < 2e-3 and rel[2] < 4e-4
+    assert rel[0] / rel[1] > 4 and rel[1] / rel[2] > 4
+
+
+def test_pressure_tensor_form_also_drifts():
+    """Sec. I: the force balance fails at the lattice level in the
+    pressure-tensor form as in the chemical-potential form, so the standard
+    scheme's flat-interface gas density drifts from Maxwell in both."""
+    for scheme in (O.STANDARD, O.STANDARD_PT):
+        c, rg, rl = vdw_case(0.8, scheme=scheme, tau_v=1.0)
+        f = O.init(c, inputs.slab(100, 4, rl, rg))
+        assert O.step(c, f, 6000) == 6000
+        assert abs(O.fields(c, f).rho[0, :6].mean() / rg - 1) > 0.1
 
 
 def test_spurious_currents_table1():
