@@ -492,8 +492,8 @@ def run_sweep(args):
     middle half (tanh edges of width 5), T/T_c evenly spaced from 0.95 down to
     0.75, vdW (a = 9/392, b = 2/21, kappa = 0.02), BGK tau = 1.0, all 16 in one
     handle; 50,000 steps; rho_g and rho_l (means over x < L/16 and |x - L/2| <
-    L/16) against the Maxwell construction, for the improved and the standard
-    scheme."""
+    L/16) against the Maxwell construction, for the improved scheme and the
+    standard one with either force form."""
     import numpy as np
     import torch
 
@@ -505,7 +505,8 @@ def run_sweep(args):
     ts = np.linspace(0.95, 0.75, 16)
     nx, ny, steps = 1024, 8, args.steps if args.steps > 1000 else 50000
     out = {}
-    for scheme, name in ((lbfe.IMPROVED, "improved"), (lbfe.STANDARD, "standard")):
+    for scheme, name in ((lbfe.IMPROVED, "improved"), (lbfe.STANDARD, "standard"),
+                         (lbfe.STANDARD_PT, "standard_pressure_tensor")):
         cases, rhos, mx = [], [], []
         for t in ts:
             rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t * tc)

@@ -53,7 +53,12 @@ typedef enum {
     LB_E_STATE = 6      /* call out of order (e.g. step before init) */
 } lb_status;
 
-enum { LB_STANDARD = 0, LB_IMPROVED = 1 };  /* Eq. 13 right / Eqs. 24-29 */
+/* LB_STANDARD: standard scheme, chemical-potential force (Eq. 13 right);
+ * LB_IMPROVED: the improved scheme (Eqs. 24-29); LB_STANDARD_PT: standard
+ * scheme with the pressure-tensor force F = grad(rho c_s^2) - div P (Eq. 13
+ * left), P of Eqs. 4-5 built from the Eq. 17 gradient and the isotropic
+ * Laplacian of rho, div P by Eq. 17 on each component. */
+enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2 };
 enum { LB_BGK = 0, LB_MRT = 1 };            /* single rate 1/tau_v / Eq. 8 */
 enum { LB_VDW = 0, LB_CS = 1 };             /* Eq. 30 / Carnahan-Starling */
 enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic */
@@ -71,7 +76,7 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * rho_ref = 0 asks lb_init_fields to use the mean of the initial density. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
-    int32_t scheme;      /* LB_STANDARD or LB_IMPROVED */
+    int32_t scheme;      /* LB_STANDARD, LB_IMPROVED or LB_STANDARD_PT */
     int32_t collision;   /* LB_BGK or LB_MRT */
     int32_t eos;         /* LB_VDW or LB_CS */
     int32_t reserved;    /* must be 0 */
@@ -158,7 +163,8 @@ lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes);
 lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes);
 
 /* Reverse-mode gradient of a trajectory of case case_id (LB_FP64 handles,
- * constant relaxation times), the discrete adjoint of the step above:
+ * constant relaxation times, LB_STANDARD or LB_IMPROVED), the discrete
+ * adjoint of the step above:
  *   f(0) = M^-1 m_eq(rho0, 0) as lb_init_fields, then nsteps steps;
  *   L = sum_{n = u_from}^{nsteps} sum_x |u^n(x)|^2 + sum_x s_final(x) rho^N(x)
  * (u^n, rho^n of Eq. 12 after n steps; s_final may be NULL). Outputs the loss,
@@ -195,7 +201,9 @@ lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double
  * and d_pops, a device array of its populations in the snapshot layout of
  * lb_save ([9][ny][pitch], pitch = nx rounded up to 32, storage form of the
  * library; FP32 planes hold f_a - w_a rho_ref). Outputs (device pointers):
- * d_rho, d_ux, d_uy, d_mu [ny][nx] as in lb_moments (each may be NULL) and
+ * (LB_STANDARD or LB_IMPROVED cases; LB_STANDARD_PT is rejected with
+ * LB_E_INVALID) d_rho, d_ux, d_uy, d_mu [ny][nx] as in lb_moments (each may
+ * be NULL) and
  * d_red[5] = {mass, kinetic energy, max |u|, 0, count of nodes with rho <= 0
  * or non-finite values}. Work is enqueued on cuda_stream; nothing is
  * synchronised.

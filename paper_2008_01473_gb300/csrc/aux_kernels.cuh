@@ -85,6 +85,29 @@ __global__ void mu_field_kernel(DevCase<C> c, const C* __restrict__ rho, C* __re
     mu[y0 + x] = dEf<EOS, C>(c, Cc) - c.kappa * lap;
 }
 
+// Pressure tensor P of Eqs. 4-5 on C fields (pressure-tensor force form).
+template <typename C, int EOS>
+__global__ void ptensor_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ pxx,
+                               C* __restrict__ pxy, C* __restrict__ pyy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= c.nx) return;
+    const int nx = c.nx, ny = c.ny;
+    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
+    const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx, yp = (int64_t)wrapi(y + 1, ny) * nx;
+    const C Cc = rho[y0 + x];
+    const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
+                          rho[ym + xp], rho[ym + xm]);
+    const C gx = gradx9<C>(rho[y0 + xp], rho[y0 + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+    const C gy = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+    C a, b, d;
+    pressure_tensor<C>(pEOS<EOS, C>(c, Cc), Cc, gx, gy, lap, c.kappa, a, b, d);
+    pxx[y0 + x] = a;
+    pxy[y0 + x] = b;
+    pyy[y0 + x] = d;
+}
+
 // f(0) = M^-1 m_eq(rho0, u0) with mu_c of rho0, stored as f - w rho_ref in T.
 template <typename T, int SCHEME, typename C>
 __global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ rho0,
@@ -148,10 +171,13 @@ __global__ void pull_moments_kernel(DevCase<T> c, const T* __restrict__ f, C* __
 
 // Velocity of Eq. 12 from rho, j and the force of the case's scheme; writes
 // the requested FP64 outputs and one Partial per block (blockDim.x == 256).
+// SCHEME 2 takes its force from the pressure tensor P (pxx, pxy, pyy).
 template <int SCHEME, typename C>
 __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* __restrict__ rho,
                                                        const C* __restrict__ jx, const C* __restrict__ jy,
-                                                       const C* __restrict__ mu, double* __restrict__ out_rho,
+                                                       const C* __restrict__ mu, const C* __restrict__ pxx,
+                                                       const C* __restrict__ pxy, const C* __restrict__ pyy,
+                                                       double* __restrict__ out_rho,
                                                        double* __restrict__ out_ux, double* __restrict__ out_uy,
                                                        double* __restrict__ out_mu, Partial* __restrict__ partials)
 {
@@ -176,8 +202,21 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
                                     rho[ym + xm]);
             const C gry = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp],
                                     rho[ym + xm]);
-            Fx = grx * C(1.0 / 3.0) - r * gmx;
-            Fy = gry * C(1.0 / 3.0) - r * gmy;
+            if (SCHEME == 2) {
+                const C divx = gradx9<C>(pxx[y0 + xp], pxx[y0 + xm], pxx[yp + xp], pxx[yp + xm], pxx[ym + xp],
+                                         pxx[ym + xm]) +
+                               grady9<C>(pxy[yp + x], pxy[ym + x], pxy[yp + xp], pxy[yp + xm], pxy[ym + xp],
+                                         pxy[ym + xm]);
+                const C divy = gradx9<C>(pxy[y0 + xp], pxy[y0 + xm], pxy[yp + xp], pxy[yp + xm], pxy[ym + xp],
+                                         pxy[ym + xm]) +
+                               grady9<C>(pyy[yp + x], pyy[ym + x], pyy[yp + xp], pyy[yp + xm], pyy[ym + xp],
+                                         pyy[ym + xm]);
+                Fx = grx * C(1.0 / 3.0) - divx;
+                Fy = gry * C(1.0 / 3.0) - divy;
+            } else {
+                Fx = grx * C(1.0 / 3.0) - r * gmx;
+                Fy = gry * C(1.0 / 3.0) - r * gmy;
+            }
         }
         const C ux = (jx[i] + C(0.5) * Fx) / r;
         const C uy = (jy[i] + C(0.5) * Fy) / r;

@@ -20,6 +20,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kMinRows = 8;  // smallest row segment of a work item
+// scratch fields: rho, j_x, j_y, mu (0-3), host staging of outputs / init
+// inputs (4-7), pressure tensor P_xx, P_xy, P_yy (8-10)
+constexpr int kScratchFields = 11;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -70,8 +73,8 @@ Layout layout_of(const lb_case* cs, int n, int prec)
         L.f[b] = p;
         p = align_up(p + elems * es, kAlign);
     }
-    L.scratch = p;  // eight FP64 fields of the largest case
-    p = align_up(p + 8 * align_up(L.max_nodes * sizeof(double), kAlign), kAlign);
+    L.scratch = p;  // kScratchFields FP64 fields of the largest case
+    p = align_up(p + kScratchFields * align_up(L.max_nodes * sizeof(double), kAlign), kAlign);
     L.partials = p;
     p = align_up(p + L.max_parts * sizeof(Partial), kAlign);
     L.red = p;
@@ -92,7 +95,8 @@ std::string check_case(const lb_case& c, int i)
     if (c.nx < 3 || c.ny < 3) return bad("nx and ny must be >= 3");
     // the step kernel addresses a case's nine planes with 32-bit offsets
     if ((int64_t)kQ * c.ny * pitch_of(c.nx) >= (int64_t)1 << 31) return bad("lattice too large");
-    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return bad("unknown scheme");
+    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED && c.scheme != LB_STANDARD_PT)
+        return bad("unknown scheme");
     if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
     if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");
     if (c.reserved != 0) return bad("reserved must be 0");
@@ -220,7 +224,7 @@ void build_items(lb_handle* h)
     const int n = (int)h->cases.size();
     h->items.clear();
     h->groups.clear();
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 3; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
@@ -297,10 +301,23 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
         mu_field_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
     else
         mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
-    if (c.scheme == LB_IMPROVED)
-        velocity_kernel<1, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
-    else
-        velocity_kernel<0, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, o_rho, o_ux, o_uy, o_mu, h->partials());
+    if (c.scheme == LB_IMPROVED) {
+        velocity_kernel<1, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+                                                          o_uy, o_mu, h->partials());
+    } else if (c.scheme == LB_STANDARD_PT) {
+        C* p0 = reinterpret_cast<C*>(h->scratch(8));
+        C* p1 = reinterpret_cast<C*>(h->scratch(9));
+        C* p2 = reinterpret_cast<C*>(h->scratch(10));
+        if (c.eos == LB_VDW)
+            ptensor_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, s0, p0, p1, p2);
+        else
+            ptensor_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, p0, p1, p2);
+        velocity_kernel<2, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, p0, p1, p2, o_rho, o_ux, o_uy, o_mu,
+                                                          h->partials());
+    } else {
+        velocity_kernel<0, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+                                                          o_uy, o_mu, h->partials());
+    }
     return h->cuda(cudaGetLastError(), "fields pass");
 }
 
@@ -835,6 +852,8 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     if (h->prec != LB_FP64) return h->fail(LB_E_INVALID, "lb_adjoint_step: needs an LB_FP64 handle");
     const lb_case& c = h->cases[case_id];
     if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
+    if (c.scheme == LB_STANDARD_PT)
+        return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of the pressure-tensor force form");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
     const AdjLayout L = adj_layout(c, nsteps, K);
     if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || ws_bytes < L.total)

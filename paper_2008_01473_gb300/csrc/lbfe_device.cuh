@@ -73,6 +73,30 @@ __device__ __forceinline__ float dEf<1, float>(const DevCase<float>& c, float rh
            2.0f * c.a * rho;
 }
 
+// p_EOS = rho E_f' - E_f (below Eq. 4) in closed form: van der Waals
+// rho R T / (1 - b rho) - a rho^2; Carnahan-Starling
+// rho R T (1 + n + n^2 - n^3) / (1 - n)^3 - a rho^2 with n = b rho / 4.
+template <int EOS, typename T>
+__device__ __forceinline__ T pEOS(const DevCase<T>& c, T rho)
+{
+    if (EOS == 0) return rho * c.RT / (T(1) - c.b * rho) - c.a * rho * rho;
+    const T n = T(0.25) * c.b * rho;
+    const T r = T(1) / (T(1) - n);
+    return rho * c.RT * (T(1) + n + n * n - n * n * n) * (r * r * r) - c.a * rho * rho;
+}
+
+// Thermodynamic pressure tensor at a node (Eqs. 4-5) from p_EOS, rho, the
+// Eq. 17 gradient (gx, gy) and the Laplacian of rho.
+template <typename T>
+__device__ __forceinline__ void pressure_tensor(T p_eos, T rho, T gx, T gy, T lap, T kappa, T& Pxx, T& Pxy,
+                                                T& Pyy)
+{
+    const T p = p_eos - kappa * (rho * lap + T(0.5) * (gx * gx + gy * gy));
+    Pxx = p + kappa * gx * gx;
+    Pyy = p + kappa * gy * gy;
+    Pxy = kappa * gx * gy;
+}
+
 // ----------------------------------------------------------------- stencils
 // Values of a field around a node: C, E(x+1), W(x-1), N(y+1), S(y-1) and corners.
 // Isotropic Laplacian 6 sum_a w_a (phi(x+e_a) - phi(x)).
@@ -99,6 +123,8 @@ __device__ __forceinline__ T grady9(T N, T S, T NE, T NW, T SE, T SW)
 // Inputs: d[9] at the node, drho = sum d, rho = rho_ref + drho, jx, jy of d,
 // the force F, velocity u (Eq. 12), mu_c (for p_m), C1 and C7 (Eq. 29; zero for
 // the standard scheme) and the rates. Output: post-collision deviations.
+// SCHEME: 0 standard, 1 improved, 2 standard with the pressure-tensor force
+// (the same collision as 0).
 template <int SCHEME, typename T>
 __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T ux, T uy, T Fx, T Fy,
                                         T mu, T C1, T C7, T rho_ref, T c0, T lam_e, T lam_s,
@@ -120,7 +146,7 @@ __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T
     // rho_ref (1, -2, 1, 0, ...)
     const T uxx = ux * ux, uyy = uy * uy, u2 = uxx + uyy;
     T eq_e, eq_s, eq_qx, eq_qy;
-    if (SCHEME == 0) {
+    if (SCHEME != 1) {  // standard scheme, either force form: Eq. 11
         eq_e = T(3) * rho * u2 - T(2) * drho;
         eq_s = drho - T(3) * rho * u2;
         eq_qx = -rho * ux;

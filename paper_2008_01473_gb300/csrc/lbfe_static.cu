@@ -96,9 +96,11 @@ void fields_static(const lb_case& c, double rho_ref, const T* d_pops, unsigned c
     else
         mu_field_kernel<T, 1><<<grd, blk, 0, st>>>(ct, s0, s3);
     if (c.scheme == LB_IMPROVED)
-        velocity_kernel<1, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+        velocity_kernel<1, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, nullptr, nullptr, nullptr, d_rho, d_ux, d_uy,
+                                                   d_mu, parts);
     else
-        velocity_kernel<0, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, d_rho, d_ux, d_uy, d_mu, parts);
+        velocity_kernel<0, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, nullptr, nullptr, nullptr, d_rho, d_ux, d_uy,
+                                                   d_mu, parts);
 }
 
 extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const void* d_pops,

@@ -25,6 +25,7 @@ void* pick(int scheme, int coll, int eos, bool nu)
         return nu ? kernel_ptr<S, C, E, true, TMA, NT>() : kernel_ptr<S, C, E, false, TMA, NT>();
     LBFE_PICK(0, 0, 0) LBFE_PICK(0, 0, 1) LBFE_PICK(0, 1, 0) LBFE_PICK(0, 1, 1)
     LBFE_PICK(1, 0, 0) LBFE_PICK(1, 0, 1) LBFE_PICK(1, 1, 0) LBFE_PICK(1, 1, 1)
+    LBFE_PICK(2, 0, 0) LBFE_PICK(2, 0, 1) LBFE_PICK(2, 1, 0) LBFE_PICK(2, 1, 1)
 #undef LBFE_PICK
     return nullptr;
 }

@@ -19,6 +19,11 @@
 //     (row r - 2) standard: grad mu_c (Eq. 17), F (Eq. 13), u, collision
 //                 (Eq. 9), store f*
 //
+// Pressure-tensor form of the standard force (SCHEME 2, Eq. 13 left): stage
+// B computes the tensor P of Eqs. 4-5 at row r - 1 instead of mu_c (its three
+// components take the mu and phi-u rows) and stage D takes div P by Eq. 17
+// applied to each component in place of rho grad mu_c.
+//
 // All ring buffers (shared-memory rows, the register ring of the thread's
 // own populations) are four rows deep and indexed by the iteration count
 // modulo 4, which the four-fold unrolled loop makes a compile-time constant.
@@ -45,8 +50,8 @@ template <typename T, int NT, int SCHEME>
 struct StepSmem {
     T rho[4][NT];
     T mu[4][NT];
-    T pux[SCHEME == 1 ? 4 : 1][NT];
-    T puy[SCHEME == 1 ? 4 : 1][NT];
+    T pux[SCHEME == 0 ? 1 : 4][NT];  // phi u_x (improved) or P_xy (pressure tensor)
+    T puy[SCHEME == 0 ? 1 : 4][NT];  // phi u_y (improved) or P_yy (pressure tensor)
 };
 
 template <typename T>
@@ -137,8 +142,19 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         const T rc = Sc[t];
         const T lap = lap9<T>(rc, Sc[t + 1], Sc[t - 1], Sp[t], Sm[t], Sp[t + 1], Sp[t - 1], Sm[t + 1],
                               Sm[t - 1]);
-        sm.mu[S1][t] = dEf<EOS, T>(c, rc) - c.kappa * lap;
-        if constexpr (SCHEME == 0) {
+        if constexpr (SCHEME == 2) {
+            // pressure tensor of row ra - 1 (P_xx in the mu rows)
+            const T gx = gradx9<T>(Sc[t + 1], Sc[t - 1], Sp[t + 1], Sp[t - 1], Sm[t + 1], Sm[t - 1]);
+            const T gy = grady9<T>(Sp[t], Sm[t], Sp[t + 1], Sp[t - 1], Sm[t + 1], Sm[t - 1]);
+            T Pxx, Pxy, Pyy;
+            pressure_tensor<T>(pEOS<EOS, T>(c, rc), rc, gx, gy, lap, c.kappa, Pxx, Pxy, Pyy);
+            sm.mu[S1][t] = Pxx;
+            sm.pux[S1][t] = Pxy;
+            sm.puy[S1][t] = Pyy;
+        } else {
+            sm.mu[S1][t] = dEf<EOS, T>(c, rc) - c.kappa * lap;
+        }
+        if constexpr (SCHEME != 1) {
             // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
             if (it >= G::ND) {
                 const T* Qm = sm.rho[S3];
@@ -204,13 +220,30 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T* Mm = sm.mu[S3];
             const T* Mc = sm.mu[S2];
             const T* Mp = sm.mu[S1];
-            const T gmx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
-            const T gmy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
             const T drho = R.drho[S2];
             const T rho = c.rho_ref + drho;
-            const T mu = Mc[t];
-            const T Fx = R.grx * T(1.0 / 3.0) - rho * gmx;
-            const T Fy = R.gry * T(1.0 / 3.0) - rho * gmy;
+            T mu, Fx, Fy;
+            if constexpr (SCHEME == 2) {
+                // F = grad(rho/3) - div P, each component of P through Eq. 17
+                const T* Xm = sm.pux[S3];
+                const T* Xc = sm.pux[S2];
+                const T* Xp = sm.pux[S1];
+                const T* Ym = sm.puy[S3];
+                const T* Yp = sm.puy[S1];
+                const T divx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]) +
+                               grady9<T>(Xp[t], Xm[t], Xp[t + 1], Xp[t - 1], Xm[t + 1], Xm[t - 1]);
+                const T divy = gradx9<T>(Xc[t + 1], Xc[t - 1], Xp[t + 1], Xp[t - 1], Xm[t + 1], Xm[t - 1]) +
+                               grady9<T>(Yp[t], Ym[t], Yp[t + 1], Yp[t - 1], Ym[t + 1], Ym[t - 1]);
+                mu = T(0);  // the standard collision does not use mu_c
+                Fx = R.grx * T(1.0 / 3.0) - divx;
+                Fy = R.gry * T(1.0 / 3.0) - divy;
+            } else {
+                const T gmx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+                const T gmy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+                mu = Mc[t];
+                Fx = R.grx * T(1.0 / 3.0) - rho * gmx;
+                Fy = R.gry * T(1.0 / 3.0) - rho * gmy;
+            }
             const T inv = rcp_fast<T>(rho);
             const T ux = (R.jx[S2] + T(0.5) * Fx) * inv;
             const T uy = (R.jy[S2] + T(0.5) * Fy) * inv;

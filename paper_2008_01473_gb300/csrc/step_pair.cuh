@@ -129,7 +129,7 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     const float2 uxx = ux * ux, uyy = uy * uy;
     const float2 ru2 = rho * (uxx + uyy);
     float2 eq_e, eq_s, eq_qx, eq_qy;
-    if (SCHEME == 0) {
+    if (SCHEME != 1) {  // standard equilibrium (Eq. 11), either force form
         eq_e = fma2(v2(3.0f), ru2, v2(-2.0f) * drho);
         eq_s = fma2(v2(-3.0f), ru2, drho);
         eq_qx = v2(0.0f) - rho * ux;
@@ -195,8 +195,8 @@ template <int SCHEME>
 struct PairSmem {
     float rho[4][kPairCols];
     float mu[4][kPairCols];
-    float pux[SCHEME == 1 ? 4 : 1][kPairCols];
-    float puy[SCHEME == 1 ? 4 : 1][kPairCols];
+    float pux[SCHEME == 0 ? 1 : 4][kPairCols];  // phi u_x (improved) or P_xy (pressure tensor)
+    float puy[SCHEME == 0 ? 1 : 4][kPairCols];  // phi u_y (improved) or P_yy (pressure tensor)
 };
 
 struct PairRegs {
@@ -304,10 +304,22 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         const Row2 Sm = row2(sm.rho[S2], j, rr + R.drho[S2]);
         const Row2 Sc = row2(sm.rho[S1], j, rr + R.drho[S1]);
         const Row2 Sp = row2(sm.rho[S0], j, rr + R.drho[S0]);
-        const float2 mu = fma2(v2(-c.kappa), lap2(Sm, Sc, Sp), dEf2<EOS>(c, Sc.c));
-        R.mu[S1] = mu;
-        st2(sm.mu[S1] + j, mu);
-        if constexpr (SCHEME == 0) {
+        if constexpr (SCHEME == 2) {
+            // pressure tensor of row ra - 1 (Eqs. 4-5; P_xx in the mu rows)
+            const float2 gx = gx2(Sm, Sc, Sp), gy = gy2(Sm, Sp);
+            const float2 lap = lap2(Sm, Sc, Sp);
+            const float2 r = Sc.c;
+            const float2 pe = make_float2(pEOS<EOS, float>(c, r.x), pEOS<EOS, float>(c, r.y));
+            const float2 p = pe - v2(c.kappa) * fma2(r, lap, v2(0.5f) * fma2(gx, gx, gy * gy));
+            st2(sm.mu[S1] + j, fma2(v2(c.kappa) * gx, gx, p));
+            st2(sm.pux[S1] + j, v2(c.kappa) * gx * gy);
+            st2(sm.puy[S1] + j, fma2(v2(c.kappa) * gy, gy, p));
+        } else {
+            const float2 mu = fma2(v2(-c.kappa), lap2(Sm, Sc, Sp), dEf2<EOS>(c, Sc.c));
+            R.mu[S1] = mu;
+            st2(sm.mu[S1] + j, mu);
+        }
+        if constexpr (SCHEME != 1) {
             if (it >= G::ND) {  // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
                 const Row2 Qm = row2(sm.rho[S3], j, rr + R.drho[S3]);
                 R.grx = gx2(Qm, Sm, Sc);
@@ -369,15 +381,33 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     } else {
         // ------------------------------------------------------- D (standard)
         if (X.d && it >= G::ND) {
-            const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
-            const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
-            const Row2 Mp = row2(sm.mu[S1], j, R.mu[S1]);
-            const float2 gmx = gx2(Mm, Mc, Mp), gmy = gy2(Mm, Mp);
             const float2 drho = R.drho[S2];
             const float2 rho = v2(c.rho_ref) + drho;
-            const float2 mu = Mc.c;
-            const float2 Fx = fma2(R.grx, v2(1.0f / 3.0f), v2(0.0f) - rho * gmx);
-            const float2 Fy = fma2(R.gry, v2(1.0f / 3.0f), v2(0.0f) - rho * gmy);
+            float2 mu, Fx, Fy;
+            if constexpr (SCHEME == 2) {
+                // F = grad(rho/3) - div P, each component of P through Eq. 17
+                const Row2 Pm = row2(sm.mu[S3], j, ld2(sm.mu[S3] + j));
+                const Row2 Pc = row2(sm.mu[S2], j, ld2(sm.mu[S2] + j));
+                const Row2 Pp = row2(sm.mu[S1], j, ld2(sm.mu[S1] + j));
+                const Row2 Xm = row2(sm.pux[S3], j, ld2(sm.pux[S3] + j));
+                const Row2 Xc = row2(sm.pux[S2], j, ld2(sm.pux[S2] + j));
+                const Row2 Xp = row2(sm.pux[S1], j, ld2(sm.pux[S1] + j));
+                const Row2 Ym = row2(sm.puy[S3], j, ld2(sm.puy[S3] + j));
+                const Row2 Yp = row2(sm.puy[S1], j, ld2(sm.puy[S1] + j));
+                const float2 divx = gx2(Pm, Pc, Pp) + gy2(Xm, Xp);
+                const float2 divy = gx2(Xm, Xc, Xp) + gy2(Ym, Yp);
+                mu = v2(0.0f);  // the standard collision does not use mu_c
+                Fx = fma2(R.grx, v2(1.0f / 3.0f), v2(0.0f) - divx);
+                Fy = fma2(R.gry, v2(1.0f / 3.0f), v2(0.0f) - divy);
+            } else {
+                const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
+                const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
+                const Row2 Mp = row2(sm.mu[S1], j, R.mu[S1]);
+                const float2 gmx = gx2(Mm, Mc, Mp), gmy = gy2(Mm, Mp);
+                mu = Mc.c;
+                Fx = fma2(R.grx, v2(1.0f / 3.0f), v2(0.0f) - rho * gmx);
+                Fy = fma2(R.gry, v2(1.0f / 3.0f), v2(0.0f) - rho * gmy);
+            }
             const float2 inv = make_float2(__fdividef(1.0f, rho.x), __fdividef(1.0f, rho.y));
             const float2 ux = fma2(v2(0.5f), Fx, R.jx[S2]) * inv;
             const float2 uy = fma2(v2(0.5f), Fy, R.jy[S2]) * inv;

@@ -15,7 +15,7 @@ import numpy as np
 
 from .build import LIB
 
-STANDARD, IMPROVED = 0, 1
+STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
 BGK, MRT = 0, 1
 VDW, CS = 0, 1
 FP64, FP32 = 0, 1

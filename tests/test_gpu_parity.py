@@ -77,7 +77,7 @@ def _gpu_pops(lat, i):
 
 
 # --------------------------------------------------------------------- FP64
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 def test_fp64_droplet_64_1000_steps(scheme):
     """64 x 64 droplet of radius 16 (the small droplet set-up), BGK tau = 0.8,
     1000 FP64 steps: rho and u within 1e-11 of the oracle."""
@@ -89,7 +89,7 @@ def test_fp64_droplet_64_1000_steps(scheme):
     assert np.abs(m["mu"] - ref.mu).max() < 1e-11
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("eos", ["vdw", "cs"])
 @pytest.mark.parametrize("shape", [(530, 37), (7, 300), (3, 3), (5, 4), (257, 9)])
@@ -107,7 +107,7 @@ def test_fp64_ragged_shapes(scheme, collision, eos, shape):
     np.testing.assert_allclose(_gpu_pops(lat, 0), f_ref, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 def test_fp64_constant_nu(scheme):
     """Constant kinematic viscosity (tau_v from eta = nu rho per node)."""
     gc, oc, rg, rl = _pair(48, 40, scheme, lbfe.MRT, nu=0.1)
@@ -201,7 +201,7 @@ def test_invalid_inputs_rejected():
 
 
 # --------------------------------------------------------------------- FP32
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("nx", [530, 532])
 def test_fp32_one_step_elementwise(scheme, collision, nx):
@@ -222,7 +222,7 @@ def test_fp32_one_step_elementwise(scheme, collision, nx):
     assert np.abs(f1 - g).max() < 3e-6 * np.abs(g).max()
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 def test_fp32_droplet_500_steps(scheme):
     """500 FP32 steps of a 64 x 64 droplet against the FP64 oracle: rho within
     2e-5 relative to rho_l, u within 2e-6 absolute."""
@@ -264,7 +264,7 @@ def test_fp32_full_size_sampled_nodes():
         assert np.abs(got - patch[:, 6, 6]).max() < 3e-6 * np.abs(patch[:, 6, 6]).max(), (y, x)
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
 @pytest.mark.parametrize("shape", [(4, 5), (8, 9), (12, 7), (532, 37), (496, 300), (1000, 16), (2048, 64)])
 def test_fp32_kernel_shapes_agree(scheme, shape, monkeypatch):
     """The one-column TMA-staged kernels (bulk copies of row runs into a
