@@ -236,7 +236,7 @@ def run_gpu(args):
                                C.c_void_p(res["uy"].data_ptr()), None, 0)
     lbfe._check(rc, lat._h)
     e2e_s = _max_over_ranks(time.perf_counter() - t0, ws, f"cuda:{local}")
-    seg_rows, n_items = lat.worklist()
+    seg_rows, n_items, narrow = lat.worklist()
     lat.close()
 
     if rank == 0:
@@ -255,7 +255,8 @@ def run_gpu(args):
                        "l2": f"populations {BYTES_PER_NODE[dtype] * nodes / 1e9:.2f} GB per step vs 129 MB L2 "
                              "(no flush)",
                        "stable": stable,
-                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items}},
+                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items,
+                                    "narrow_blocks": narrow}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "traffic": _profiled_traffic(n_side) if dtype == "f32" else None,
@@ -381,7 +382,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1)
     _, st = lat.reductions()
-    seg_rows, n_items = lat.worklist()
+    seg_rows, n_items, narrow = lat.worklist()
     lat.close()
     acc = _batched_accuracy(lbfe, cases[::8], rhos[::8], args.accuracy_steps) if args.accuracy_steps else None
     lats = []
@@ -405,7 +406,8 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched uneven droplets: " + (batched_cases.__doc__ or "").split(":")[1].strip(),
                        "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum()),
-                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items}},
+                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items,
+                                    "narrow_blocks": narrow}},
             "fp32_vs_fp64": acc,  # every 8th case of the batch
             "per_case_launches": {"value": round(nodes * args.steps / (per_case_ms * 1e-3) / 1e6, 1),
                                   "unit": "MLUPS", "ms_per_step": round(per_case_ms / args.steps, 4)},

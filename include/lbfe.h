@@ -119,20 +119,25 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
  * share scheme, collision, EOS, viscosity mode and nx % 4 == 0; each launch
  * runs a work-list of (case, column strip, row segment) items. The first
  * call with nsteps > 0 autotunes the work-list: it times one step under
- * several row-segment sizes and keeps the fastest (these trial launches read
+ * several row-segment sizes, with and without narrow blocks for the lattices
+ * that fit them better, and keeps the fastest (these trial launches read
  * the current populations and write only the buffer the next step
  * overwrites, so the state and every result are unchanged; the choice
  * affects speed only). LBFE_SEG_ROWS=n before lb_create fixes the segment
- * size instead (0: a share of the GPU's block slots per case). Runs of 8
+ * size instead (0: a share of the GPU's block slots per case), and
+ * LBFE_PAIR_NARROW=0|1 the narrow-block choice. Groups run as parallel
+ * branches that fork from and join the handle's stream. Runs of 8
  * steps replay a CUDA graph captured on the first such call (on a private
  * stream, then launched on the handle's stream; set LBFE_GRAPH=0 before
  * lb_create to launch every step directly). Enqueued asynchronously, except
  * that the autotuning call synchronises the stream. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
 
-/* The work-list in use: rows per segment (0: slot-share rule) and item
- * count. Before the first lb_step it is the untuned default. */
-lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items);
+/* The work-list in use: rows per segment (0: slot-share rule), item count,
+ * and whether narrow blocks (64 threads, 128 columns) run the lattices that
+ * fit them with fewer idle lanes. Before the first lb_step it is the untuned
+ * default. Any pointer may be NULL. */
+lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, int32_t* narrow);
 
 /* Macroscopic fields of case case_id at the current step: rho and u of
  * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2, computed per node in

@@ -23,6 +23,7 @@ constexpr int kMinRows = 8;  // smallest row segment of a work item
 // scratch fields: rho, j_x, j_y, mu (0-3), host staging of outputs / init
 // inputs (4-7), pressure tensor P_xx, P_xy, P_yy (8-10)
 constexpr int kScratchFields = 11;
+constexpr int kPairCols256 = 256, kPairCols128 = 128;  // ring columns of the wide / narrow packed blocks
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -163,7 +164,11 @@ struct lb_handle {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // kGraphSteps steps starting from buffer 0 / 1
     int tma_threads = 0;    // TMA kernel shape: 0 packed two-column, 128 or 256 one-column
     int seg_rows = 0;       // work-list rows per segment, 0: share of the block slots
-    bool autotune = true;   // pick seg_rows by timing on the first lb_step
+    bool autotune = true;   // pick seg_rows (and narrow) by timing on the first lb_step
+    bool narrow = false;    // narrow packed blocks for the lattices that prefer them
+    bool narrow_fixed = false;  // narrow set by LBFE_PAIR_NARROW, not tuned
+    std::vector<cudaStream_t> aux;       // capture branches for groups after the first
+    std::vector<cudaEvent_t> fork_join;  // [2 * branch]: fork, join
     bool tuned = false;
     std::string err;
 
@@ -215,6 +220,16 @@ constexpr int kGraphSteps = 8;  // steps per captured graph (even: buffer parity
 // longest first, so the block scheduler hands the short ones to the slots
 // that free up last. The decomposition changes no result: every node's
 // update is the same arithmetic on the same inputs whichever item owns it.
+// Packed-kernel shape of an FP32 lattice with nx % 4 == 0: the narrow
+// (64-thread, 128-column) blocks when they cover the lattice's columns with
+// fewer idle lanes than the wide (128-thread, 256-column) ones.
+bool prefers_narrow(const lb_case& c)
+{
+    const int wide = (c.nx + kPairCols256 - 9) / (kPairCols256 - 8) * kPairCols256;
+    const int narrow = (c.nx + kPairCols128 - 9) / (kPairCols128 - 8) * kPairCols128;
+    return narrow < wide;
+}
+
 void build_items(lb_handle* h)
 {
     const int seg_rows = h->seg_rows;
@@ -224,53 +239,59 @@ void build_items(lb_handle* h)
     const int n = (int)h->cases.size();
     h->items.clear();
     h->groups.clear();
+    // one group (one launch per step) per kernel variant and block shape
+    auto emit = [&](const std::vector<int>& members, int s, int co, int e, int nu, bool tma, int nt) {
+        if (members.empty()) return;
+        double nodes = 0;
+        for (int i : members) nodes += (double)h->cases[i].nx * h->cases[i].ny;
+        const int width = !tma ? kStepThreads
+                          : nt == kPairWide   ? kPairCols256
+                          : nt == kPairNarrow ? kPairCols128
+                                              : nt;  // columns per block
+        const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
+                                           : occupancy_step_f64(s, co, e, nu == 1);
+        const double slots = (double)sms * occ;
+        Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
+        for (int i : members) {
+            const lb_case& c = h->cases[i];
+            const int ns = strips_of(c, width);
+            const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
+            const double share = slots * ((double)c.nx * c.ny) / nodes;
+            int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows : (int)std::floor(share / ns);
+            nseg = std::min(std::max(1, nseg), std::max(1, c.ny / kMinRows));
+            for (int k = 0; k < ns; ++k) {
+                const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns);
+                const int x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
+                for (int r = 0; r < nseg; ++r) {
+                    const int y0 = (int)((int64_t)c.ny * r / nseg);
+                    const int y1 = (int)((int64_t)c.ny * (r + 1) / nseg);
+                    h->items.push_back(Item{i, x0, x1 - x0, y0, y1 - y0, 0});
+                }
+            }
+        }
+        g.count = (int64_t)h->items.size() - g.first;
+        std::stable_sort(h->items.begin() + g.first, h->items.end(),
+                         [](const Item& a, const Item& b) { return a.h > b.h; });
+        h->groups.push_back(g);
+    };
     for (int s = 0; s < 3; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
                     for (int al = 0; al < 2; ++al) {
-                    // al: lattices with nx % 4 == 0 (TMA-eligible) or not
-                    std::vector<int> members;
-                    double nodes = 0;
-                    for (int i = 0; i < n; ++i) {
-                        const lb_case& c = h->cases[i];
-                        if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
-                            (c.nx % 4 == 0) == (al == 1)) {
-                            members.push_back(i);
-                            nodes += (double)c.nx * c.ny;
+                        // al: lattices with nx % 4 == 0 (TMA-eligible) or not
+                        const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
+                        const bool pair = tma && h->tma_threads == 0;
+                        std::vector<int> members, narrow;
+                        for (int i = 0; i < n; ++i) {
+                            const lb_case& c = h->cases[i];
+                            if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
+                                (c.nx % 4 == 0) == (al == 1))
+                                (pair && h->narrow && prefers_narrow(c) ? narrow : members).push_back(i);
                         }
+                        emit(members, s, co, e, nu, tma, !tma ? kStepThreads : pair ? kPairWide : h->tma_threads);
+                        emit(narrow, s, co, e, nu, tma, kPairNarrow);
                     }
-                    if (members.empty()) continue;
-                    const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
-                    const int nt = tma ? h->tma_threads : kStepThreads;  // 0: packed two-column kernel
-                    const int width = nt == 0 ? 256 : nt;                   // columns per block
-                    const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
-                                                       : occupancy_step_f64(s, co, e, nu == 1);
-                    const double slots = (double)sms * occ;
-                    Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
-                    for (int i : members) {
-                        const lb_case& c = h->cases[i];
-                        const int ns = strips_of(c, width);
-                        const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
-                        const double share = slots * ((double)c.nx * c.ny) / nodes;
-                        int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows
-                                                : (int)std::floor(share / ns);
-                        nseg = std::min(std::max(1, nseg), std::max(1, c.ny / kMinRows));
-                        for (int k = 0; k < ns; ++k) {
-                            const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns);
-                            const int x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
-                            for (int q = 0; q < nseg; ++q) {
-                                const int y0 = (int)((int64_t)c.ny * q / nseg);
-                                const int y1 = (int)((int64_t)c.ny * (q + 1) / nseg);
-                                h->items.push_back(Item{i, x0, x1 - x0, y0, y1 - y0, 0});
-                            }
-                        }
-                    }
-                    g.count = (int64_t)h->items.size() - g.first;
-                    std::stable_sort(h->items.begin() + g.first, h->items.end(),
-                                     [](const Item& a, const Item& b) { return a.h > b.h; });
-                    h->groups.push_back(g);
-                }
 }
 
 lb_status upload_items(lb_handle* h)
@@ -405,6 +426,10 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
         h->seg_rows = std::max(0, std::atoi(p));
         h->autotune = false;
     }
+    if (const char* p = std::getenv("LBFE_PAIR_NARROW")) {
+        h->narrow = std::strcmp(p, "0") != 0;
+        h->narrow_fixed = true;
+    }
     build_items(h);
     lb_status s = upload_items(h);
     if (s == LB_OK) s = h->cuda(cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream), "clear status");
@@ -454,20 +479,48 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 }
 
 // Enqueue one time step (every group) on stream st, reading buffer cur.
+// With several groups, the groups after the first run on branch streams that
+// fork from st and join it again, so their launches can overlap on the GPU
+// (they write disjoint cases); inside a capture this makes them parallel
+// graph nodes.
 static lb_status enqueue_step(lb_handle* h, int cur, cudaStream_t st)
 {
-    for (const Group& g : h->groups) {
+    const int nb = (int)h->groups.size() - 1;
+    lb_status s = LB_OK;
+    while ((int)h->aux.size() < nb && s == LB_OK) {
+        cudaStream_t a = nullptr;
+        cudaEvent_t f = nullptr, j = nullptr;
+        s = h->cuda(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking), "branch stream");
+        if (s == LB_OK) s = h->cuda(cudaEventCreateWithFlags(&f, cudaEventDisableTiming), "branch event");
+        if (s == LB_OK) s = h->cuda(cudaEventCreateWithFlags(&j, cudaEventDisableTiming), "branch event");
+        if (a) h->aux.push_back(a);
+        if (f) h->fork_join.push_back(f);
+        if (j) h->fork_join.push_back(j);
+    }
+    if (s != LB_OK) return s;
+    for (int b = 0; b < nb && s == LB_OK; ++b) {
+        s = h->cuda(cudaEventRecord(h->fork_join[2 * b], st), "fork");
+        if (s == LB_OK) s = h->cuda(cudaStreamWaitEvent(h->aux[b], h->fork_join[2 * b], 0), "fork");
+    }
+    for (int k = 0; k <= nb && s == LB_OK; ++k) {
+        const Group& g = h->groups[k];
+        const cudaStream_t gs = k == 0 ? st : h->aux[k - 1];
         cudaError_t e;
         if (h->prec == LB_FP32)
-            e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, st,
+            e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, gs,
                                 (const float*)h->fbuf(cur), (float*)h->fbuf(cur ^ 1), h->dc32(),
                                 h->ditems() + g.first, h->status());
         else
-            e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, st, (const double*)h->fbuf(cur),
+            e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, gs, (const double*)h->fbuf(cur),
                                 (double*)h->fbuf(cur ^ 1), h->dc64(), h->ditems() + g.first, h->status());
-        if (e != cudaSuccess) return h->cuda(e, "step launch");
+        if (e != cudaSuccess) s = h->cuda(e, "step launch");
     }
-    return LB_OK;
+    for (int b = 0; b < nb; ++b) {  // join every branch, even after a failed launch
+        lb_status t = h->cuda(cudaEventRecord(h->fork_join[2 * b + 1], h->aux[b]), "join");
+        if (t == LB_OK) t = h->cuda(cudaStreamWaitEvent(st, h->fork_join[2 * b + 1], 0), "join");
+        if (s == LB_OK) s = t;
+    }
+    return s;
 }
 
 // Capture kGraphSteps steps starting from buffer cur into h->graph[cur].
@@ -511,12 +564,23 @@ static lb_status tune_time(lb_handle* h, cudaEvent_t e0, cudaEvent_t e1, int rep
 
 static lb_status autotune(lb_handle* h)
 {
-    static const int cands[] = {0, 256, 128, 64, 32, 16};
-    constexpr int kCands = (int)(sizeof cands / sizeof cands[0]);
+    // candidates: row-segment rule x (narrow packed blocks off, on); the
+    // second half only when some lattice prefers narrow blocks
+    static const int segs[] = {0, 256, 128, 64, 32, 16};
+    constexpr int kSegs = (int)(sizeof segs / sizeof segs[0]);
+    bool any_narrow = false;
+    if (h->prec == LB_FP32 && h->path != 1 && h->tma_threads == 0 && !h->narrow_fixed)
+        for (const lb_case& c : h->cases) any_narrow = any_narrow || (c.nx % 4 == 0 && prefers_narrow(c));
+    const bool narrow0 = h->narrow;
+    const int kCands = any_narrow ? 2 * kSegs : kSegs;
+    auto apply = [&](int k) {
+        h->seg_rows = segs[k % kSegs];
+        h->narrow = any_narrow ? k >= kSegs : narrow0;
+    };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     lb_status s = h->cuda(cudaEventCreate(&e0), "tune event");
     if (s == LB_OK) s = h->cuda(cudaEventCreate(&e1), "tune event");
-    float best_ms[kCands];
+    float best_ms[2 * kSegs];
     for (float& b : best_ms) b = 1e30f;
     int reps = 3;
     // candidate 0 (the current list) sets the launch count: two warm-up
@@ -529,7 +593,7 @@ static lb_status autotune(lb_handle* h)
     }
     for (int pass = 0; pass < 2 && s == LB_OK; ++pass)
         for (int k = 0; k < kCands && s == LB_OK; ++k) {
-            h->seg_rows = cands[k];
+            apply(k);
             build_items(h);
             if ((int64_t)h->items.size() > h->L.max_items) continue;
             if ((s = upload_items(h)) != LB_OK) break;
@@ -543,7 +607,7 @@ static lb_status autotune(lb_handle* h)
     int best = 0;
     for (int k = 1; k < kCands; ++k)
         if (best_ms[k] < 0.98f * best_ms[0] && best_ms[k] < best_ms[best]) best = k;
-    h->seg_rows = cands[best];
+    apply(best);
     build_items(h);
     lb_status u = upload_items(h);
     h->tuned = true;
@@ -580,11 +644,15 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
     return LB_OK;
 }
 
-lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items)
+lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, int32_t* narrow)
 {
     if (!h) return LB_E_INVALID;
     if (seg_rows) *seg_rows = h->seg_rows;
     if (n_items) *n_items = (int64_t)h->items.size();
+    if (narrow) {
+        *narrow = 0;
+        for (const Group& g : h->groups) *narrow |= g.tma && g.nt == kPairNarrow;
+    }
     return LB_OK;
 }
 
@@ -938,6 +1006,8 @@ void lb_destroy(lb_handle* h)
     for (cudaGraphExec_t& g : h->graph)
         if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (cudaStream_t a : h->aux) cudaStreamDestroy(a);
+    for (cudaEvent_t e : h->fork_join) cudaEventDestroy(e);
     delete h;
 }
 

@@ -5,12 +5,15 @@
 namespace lbfe {
 
 namespace {
-// NT = 0 selects the two-columns-per-thread packed kernel
+// NT = kPairWide / kPairNarrow select the two-columns-per-thread packed
+// kernel with 128 / 64 threads
 template <int S, int C, int E, bool NU, bool TMA, int NT>
 void* kernel_ptr()
 {
-    if constexpr (TMA && NT == 0)
-        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU>);
+    if constexpr (TMA && NT == kPairWide)
+        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads>);
+    else if constexpr (TMA && NT == kPairNarrow)
+        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow>);
     else if constexpr (TMA)
         return reinterpret_cast<void*>(&step_kernel_tma<float, NT, S, C, E, NU>);
     else
@@ -32,16 +35,22 @@ void* pick(int scheme, int coll, int eos, bool nu)
 
 size_t tma_smem(int nt)
 {
-    return nt == 0 ? pair_dynamic_smem<float>()
-                   : (nt == 128 ? tma_dynamic_smem<float, 128>() : tma_dynamic_smem<float, 256>());
+    return nt == kPairWide     ? pair_dynamic_smem<float, kPairThreads>()
+           : nt == kPairNarrow ? pair_dynamic_smem<float, kPairThreadsNarrow>()
+           : nt == 128         ? tma_dynamic_smem<float, 128>()
+                               : tma_dynamic_smem<float, 256>();
 }
 
-int block_threads(bool tma, int nt) { return !tma ? kStepThreads : (nt == 0 ? kPairThreads : nt + 32); }
+int block_threads(bool tma, int nt)
+{
+    return !tma ? kStepThreads : nt == kPairWide ? kPairThreads : nt == kPairNarrow ? kPairThreadsNarrow : nt + 32;
+}
 
 void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 {
     void* k = !tma           ? pick<false, kStepThreads>(scheme, coll, eos, nu)
-              : nt == 0      ? pick<true, 0>(scheme, coll, eos, nu)
+              : nt == kPairWide   ? pick<true, kPairWide>(scheme, coll, eos, nu)
+              : nt == kPairNarrow ? pick<true, kPairNarrow>(scheme, coll, eos, nu)
               : nt == 128    ? pick<true, 128>(scheme, coll, eos, nu)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;

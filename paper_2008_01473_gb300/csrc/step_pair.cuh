@@ -5,7 +5,7 @@
 //
 // Same method and stage plan as step_kernel.cuh (A: pull, rho, j; B: mu_c;
 // C: grad mu_c, F, u, phi u; D: correction C1/C7, collision, store), but
-// thread p of the kPairThreads compute threads owns the two adjacent ring
+// thread p of the NP compute threads owns the two adjacent ring
 // columns j = 2p and 2p + 1, i.e. lattice columns x0 - 4 + j and x0 - 3 + j.
 // Every per-node quantity is a float2 (.x = column j, .y = column j + 1), so
 // one packed instruction advances two nodes. In the five-point neighbourhoods
@@ -21,6 +21,12 @@
 // it + kPairSlots (one lane per plane and run), so no producer warp is needed
 // and three blocks fit on an SM.
 //
+// Two block shapes share the code: NP = 128 threads (256 ring columns,
+// strips of up to 248 outputs; copies issued by warps 0-2, three planes
+// each) for wide lattices, and NP = 64 (128 columns, strips of up to 120;
+// warps 0-1 issue five and four planes) for narrow ones. A node's arithmetic
+// does not depend on the shape, so both give the same bits.
+//
 // Column coverage per stage (ring columns; wv = strip width, halo HX):
 //   A: all pairs (columns the ring does not hold give unused values)
 //   B: pairs 1 .. (wv + 6)/2 - 1   -> columns [2, wv + 6)
@@ -34,9 +40,13 @@
 
 namespace lbfe {
 
-constexpr int kPairThreads = 128;             // compute threads per block
-constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block
+constexpr int kPairThreads = 128;             // compute threads per block, wide shape
+constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block, wide shape
+constexpr int kPairThreadsNarrow = 64;        // the narrow shape
 constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight
+
+// threads that issue a stored row's bulk copies: three warps (wide), two (narrow)
+__host__ __device__ constexpr int pair_issuers(int np) { return np == kPairThreads ? 96 : 64; }
 
 // ------------------------------------------------------------ packed FP32
 __device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
@@ -57,7 +67,7 @@ struct Row2 {
 };
 
 // neighbours through aligned 64-bit loads (a stride-2 scalar pattern would
-// hit each shared-memory bank twice); needs 2 <= j <= kPairCols - 4
+// hit each shared-memory bank twice); needs 2 <= j <= (ring columns) - 4
 __device__ __forceinline__ Row2 row2(const float* row, int j, float2 own)
 {
     Row2 q;
@@ -191,12 +201,12 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 
-template <int SCHEME>
+template <int SCHEME, int COLS>
 struct PairSmem {
-    float rho[4][kPairCols];
-    float mu[4][kPairCols];
-    float pux[SCHEME == 0 ? 1 : 4][kPairCols];  // phi u_x (improved) or P_xy (pressure tensor)
-    float puy[SCHEME == 0 ? 1 : 4][kPairCols];  // phi u_y (improved) or P_yy (pressure tensor)
+    float rho[4][COLS];
+    float mu[4][COLS];
+    float pux[SCHEME == 0 ? 1 : 4][COLS];  // phi u_x (improved) or P_xy (pressure tensor)
+    float puy[SCHEME == 0 ? 1 : 4][COLS];  // phi u_y (improved) or P_yy (pressure tensor)
 };
 
 struct PairRegs {
@@ -208,7 +218,7 @@ struct PairRegs {
 };
 
 struct PairCtx {
-    float* ring;        // [kPairSlots][9][kPairCols]
+    float* ring;        // [kPairSlots][9][ring columns]
     uint64_t* full;
     int* flag;
     int* status;
@@ -229,36 +239,42 @@ __device__ __forceinline__ void pair_timeout(const PairCtx& X)
     atomicOr(X.status, 1);
 }
 
-// Copy stored row i = s - s0 into slot k, spread over warps 0..2: thread 0
-// arms the slot's mbarrier with the byte count, and lane q < 3 * runs of warp
-// w issues the copy of plane 3 w + q % 3, run q / 3. (A copy may complete
-// before the arming arrive; the phase cannot complete before it, since that
-// arrive is the phase's only one.) Called by warps 0..2 only.
+// Copy stored row i = s - s0 into slot k, spread over the issuing warps:
+// thread 0 arms the slot's mbarrier with the byte count, and each lane of
+// an issuing warp copies one (plane, run) pair: wide shape, warp w < 3
+// takes planes 3w .. 3w + 2; narrow shape, warp 0 planes 0-4, warp 1 planes
+// 5-8. (A copy may complete before the arming arrive; the phase cannot
+// complete before it, since that arrive is the phase's only one.) Called by
+// the first pair_issuers(NP) threads only.
+template <int NP>
 __device__ __forceinline__ void pair_issue(const PairCtx& X, const DevCase<float>& c, int i, int k)
 {
+    constexpr int COLS = 2 * NP;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t* b = X.full + k;
     if (threadIdx.x == 0) mbar_expect_tx(b, X.row_bytes);
-    if (lane < 3 * X.runs.n) {
-        const int a = 3 * w + lane % 3, r = lane / 3;
+    const int pw = NP == kPairThreads ? 3 : (w == 0 ? 5 : 4);  // planes of this warp
+    const int a0 = NP == kPairThreads ? 3 * w : (w == 0 ? 0 : 5);
+    if (lane < pw * X.runs.n) {
+        const int a = a0 + lane % pw, r = lane / pw;
         const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
         const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
         const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
         const uint32_t row = (uint32_t)wrapi(X.s0 + i, c.ny) * c.pitch;
         // order earlier generic-proxy reads of the slot before the async refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(X.ring + ((size_t)k * kQ + a) * kPairCols + j0,
+        bulk_load(X.ring + ((size_t)k * kQ + a) * COLS + j0,
                   X.fin + ((uint32_t)a * (uint32_t)c.plane + row + (uint32_t)g0), (uint32_t)len * sizeof(float), b);
     }
 }
 
-template <int SCHEME, int COLL, int EOS, bool NU, int SLOT>
-__device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME>& sm,
+template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT>
+__device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME, 2 * NP>& sm,
                                           PairRegs& R)
 {
     using G = StepGeom<SCHEME>;
     constexpr int S0 = SLOT, S1 = (SLOT + 3) & 3, S2 = (SLOT + 2) & 3, S3 = (SLOT + 1) & 3;
-    constexpr int SW = kPairCols;
+    constexpr int SW = 2 * NP;
     const int j = X.j;
 
     // ---------------------------------------------------------------- A
@@ -296,7 +312,8 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
     __syncthreads();
     // stored row it (ra - 1) has no reader left: refill its slot
-    if (threadIdx.x < 96 && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, c, it + kPairSlots, X.ks);
+    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last)
+        pair_issue<NP>(X, c, it + kPairSlots, X.ks);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -429,17 +446,17 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     if (it >= G::ND) X.rd = X.rd + 1 == c.ny ? 0 : X.rd + 1;
 }
 
-template <typename T>
+template <typename T, int NP>
 constexpr size_t pair_dynamic_smem()
 {
-    return (size_t)kPairSlots * kQ * kPairCols * sizeof(T) + kPairSlots * sizeof(uint64_t);
+    return (size_t)kPairSlots * kQ * (2 * NP) * sizeof(T) + kPairSlots * sizeof(uint64_t);
 }
 
-// FP32 step with kPairThreads threads of two columns each: blockDim.x ==
-// kPairThreads. Every case of the launch has nx % 4 == 0; every item
-// x0 % 4 == 0, wv % 4 == 0, wv + 8 <= kPairCols.
-template <int SCHEME, int COLL, int EOS, bool NU>
-__global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float* __restrict__ fin,
+// FP32 step with NP threads of two columns each: blockDim.x == NP (128 or
+// 64). Every case of the launch has nx % 4 == 0; every item x0 % 4 == 0,
+// wv % 4 == 0, wv + 8 <= 2 NP.
+template <int SCHEME, int COLL, int EOS, bool NU, int NP>
+__global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pair(const float* __restrict__ fin,
                                                                     float* __restrict__ fout,
                                                                     const DevCase<float>* __restrict__ cases,
                                                                     const Item* __restrict__ items,
@@ -447,7 +464,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float*
 {
     using G = StepGeom<SCHEME>;
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ __align__(16) PairSmem<SCHEME> sm;
+    __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
     __shared__ int flag;
     const Item item = items[blockIdx.x];
     const DevCase<float> c = cases[item.case_id];
@@ -457,7 +474,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float*
 
     PairCtx X;
     X.ring = reinterpret_cast<float*>(dsm);
-    X.full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * kPairCols * sizeof(float));
+    X.full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * (2 * NP) * sizeof(float));
     X.flag = &flag;
     X.status = status;
     X.fin = fin;
@@ -487,8 +504,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float*
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x < 96)
-        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) pair_issue(X, c, i, i);
+    if (threadIdx.x < pair_issuers(NP))
+        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) pair_issue<NP>(X, c, i, i);
 
     const int p = threadIdx.x;
     X.j = 2 * p;
@@ -501,13 +518,13 @@ __global__ void __launch_bounds__(kPairThreads, 3) step_kernel_pair(const float*
 
     PairRegs R;
     for (int base = 0; base < niter; base += 4) {
-        pair_iter<SCHEME, COLL, EOS, NU, 0>(base, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 0>(base, X, c, sm, R);
         if (base + 1 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, 1>(base + 1, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 1>(base + 1, X, c, sm, R);
         if (base + 2 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, 2>(base + 2, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 2>(base + 2, X, c, sm, R);
         if (base + 3 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, 3>(base + 3, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 3>(base + 3, X, c, sm, R);
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
     __syncthreads();

@@ -90,7 +90,7 @@ def lib() -> C.CDLL:
         L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
         L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
-        L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64)]
+        L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
@@ -184,11 +184,11 @@ class Lattice:
         _check(lib().lb_step(self._h, int(nsteps)), self._h)
 
     def worklist(self):
-        """(rows per segment, item count) of the work-list in use; 0 rows is
-        the slot-share rule."""
-        r, n = C.c_int32(), C.c_int64()
-        _check(lib().lb_worklist(self._h, C.byref(r), C.byref(n)), self._h)
-        return r.value, n.value
+        """(rows per segment, item count, narrow blocks used) of the work-list
+        in use; 0 rows is the slot-share rule."""
+        r, n, w = C.c_int32(), C.c_int64(), C.c_int32()
+        _check(lib().lb_worklist(self._h, C.byref(r), C.byref(n), C.byref(w)), self._h)
+        return r.value, n.value, bool(w.value)
 
     def moments(self, case_id: int, on_device: bool = False):
         """dict rho, ux, uy, mu of the current state (numpy, or CUDA tensors)."""

@@ -406,7 +406,7 @@ def test_autotuned_worklist_changes_no_result(monkeypatch):
         for i, r in enumerate(rhos):
             lat.init_fields(i, r)
         lat.step(21)
-        rows, n_items = lat.worklist()
+        rows, n_items, _ = lat.worklist()
         if seg is not None:
             assert rows == int(seg)
         assert n_items >= len(cases)
@@ -418,3 +418,75 @@ def test_autotuned_worklist_changes_no_result(monkeypatch):
             a = np.frombuffer(snaps["0"][i][16:], dtype=np.float32).reshape(9, c.ny, pitch)[:, :, :c.nx]
             b = np.frombuffer(snaps[seg][i][16:], dtype=np.float32).reshape(9, c.ny, pitch)[:, :, :c.nx]
             assert np.array_equal(a, b), (seg, i)
+
+
+def test_fp32_batched_workload_full_size_sampled():
+    """The benchmark's uneven batch at full size (256 droplet cases, 24.5 M
+    nodes, improved scheme, BGK, FP32) in the launch configuration the
+    benchmark times (one handle, autotuned work-list, graph replay): after 24
+    steps, one step of 24 sampled nodes in 8 cases (the smallest, the largest
+    and six seeded others) matches the oracle's step of a 13 x 13 patch."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    cases, rhos = bench.batched_cases(lbfe)
+    lat = lbfe.Lattice(cases, precision=lbfe.FP32)
+    for i, r in enumerate(rhos):
+        lat.init_fields(i, r)
+    lat.step(24)
+    sides = [c.nx for c in cases]
+    rng = np.random.default_rng(4)
+    picks = {int(np.argmin(sides)), int(np.argmax(sides))} | set(int(i) for i in rng.choice(len(cases), 6, False))
+    before = {i: _gpu_pops(lat, i) for i in picks}
+    lat.step(1)
+    after = {i: _gpu_pops(lat, i) for i in picks}
+    _, st = lat.reductions()
+    assert (st == 0).all()
+    lat.close()
+    for i in sorted(picks):
+        c = cases[i]
+        oc = O.Case(nx=13, ny=13, scheme=O.IMPROVED, collision=O.BGK, eos=O.VDW, a=c.a, b=c.b, R=c.R, T=c.T,
+                    kappa=c.kappa, tau_v=c.tau_v)
+        n = c.nx
+        pts = [(0, 0), (n - 1, n - 1)] + [tuple(rng.integers(0, n, 2)) for _ in range(1)]
+        for (y, x) in pts:
+            ys = np.arange(y - 6, y + 7) % n
+            xs = np.arange(x - 6, x + 7) % n
+            patch = np.ascontiguousarray(before[i][:, ys][:, :, xs])
+            O.step(oc, patch, 1)
+            ref = patch[:, 6, 6]
+            assert np.abs(after[i][:, y, x] - ref).max() < 3e-6 * np.abs(ref).max(), (i, y, x)
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
+def test_narrow_packed_blocks_bit_identical(scheme, monkeypatch):
+    """Narrow packed blocks (64 threads, 128 columns, copies issued by two
+    warps) for the lattices they fit better, running as a parallel branch of
+    the wide group: populations bit-identical to wide blocks only, graph
+    replay and direct launches alike (nx = 8 .. 376, one handle, FP32)."""
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.85)
+    cases, rhos = [], []
+    for nx, ny in ((8, 20), (36, 36), (100, 52), (120, 33), (124, 40), (248, 24), (260, 30), (376, 18)):
+        cases.append(lbfe.Case(nx=nx, ny=ny, scheme=scheme, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
+                               kappa=0.02, tau_v=0.9))
+        rhos.append(inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, case=nx))
+    snaps = {}
+    for narrow, graph in (("0", "1"), ("1", "1"), ("1", "0")):
+        monkeypatch.setenv("LBFE_PAIR_NARROW", narrow)
+        monkeypatch.setenv("LBFE_GRAPH", graph)
+        lat = lbfe.Lattice(cases, precision=lbfe.FP32)
+        for i, r in enumerate(rhos):
+            lat.init_fields(i, r)
+        lat.step(21)
+        assert lat.worklist()[2] == (narrow == "1")
+        _, st = lat.reductions()
+        assert (st == 0).all()
+        snaps[(narrow, graph)] = [_gpu_pops(lat, i) for i in range(len(cases))]
+        lat.close()
+    for key in (("1", "1"), ("1", "0")):
+        for i in range(len(cases)):
+            assert np.array_equal(snaps[("0", "1")][i], snaps[key][i]), (key, i)
