@@ -48,7 +48,7 @@ typedef enum {
     LB_E_INVALID = 1,   /* bad argument or parameter set (nothing was enqueued) */
     LB_E_CUDA = 2,      /* a CUDA runtime call failed; see lb_last_error */
     LB_E_UNSTABLE = 3,  /* a case produced rho <= 0 or a non-finite value */
-    LB_E_TIMEOUT = 4,   /* reserved: a bounded device-side wait gave up */
+    LB_E_TIMEOUT = 4,   /* a bounded device-side wait gave up (see lb_wait_selftest) */
     LB_E_WORKSPACE = 5, /* workspace pointer misaligned or too small */
     LB_E_STATE = 6      /* call out of order (e.g. step before init) */
 } lb_status;
@@ -153,6 +153,15 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
  * pointers (case_status may be NULL); synchronises the stream. Returns
  * LB_E_UNSTABLE if any case is unstable; every entry is still written. */
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
+
+/* Failure-detection self-test (the paper has no counterpart): enqueues on the
+ * handle's stream one kernel whose single thread waits, with the bound of the
+ * step kernels' waits (about one second of SM clock), on an mbarrier phase
+ * that nothing completes, and then records the give-up in the handle's
+ * status word as a step kernel would. The next lb_reductions returns
+ * LB_E_TIMEOUT and clears the word. Nothing else is written; the GPU context
+ * stays usable. */
+lb_status lb_wait_selftest(lb_handle* h);
 
 /* Bytes of one case's snapshot (populations + step counter) for lb_save. */
 lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes);

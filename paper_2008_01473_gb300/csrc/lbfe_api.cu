@@ -13,6 +13,7 @@
 #include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "launch.h"
+#include "step_tma.cuh"
 
 using namespace lbfe;
 
@@ -302,6 +303,19 @@ lb_status upload_items(lb_handle* h)
 }
 
 lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
+
+// Failure-detection self-test: one thread waits, bounded like every wait of
+// the step kernels, on an mbarrier phase that nothing completes (no copy is
+// issued, no other thread arrives), then records the give-up in the status
+// word the way the step kernels do.
+__global__ void wait_selftest_kernel(int* status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0u)) atomicOr(status, 1);
+}
 
 // Pull-moment, chemical-potential and velocity passes for one case, in the
 // storage precision C per node (FP64 sums); outputs may be device pointers
@@ -717,6 +731,13 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
     }
     if (unstable) return h->fail(LB_E_UNSTABLE, "a case has rho <= 0 or non-finite values");
     return LB_OK;
+}
+
+lb_status lb_wait_selftest(lb_handle* h)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    wait_selftest_kernel<<<1, 32, 0, h->stream>>>(h->status());
+    return h->cuda(cudaGetLastError(), "wait self-test");
 }
 
 lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes)

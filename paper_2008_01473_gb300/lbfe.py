@@ -91,13 +91,14 @@ def lib() -> C.CDLL:
         L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
         L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
+        L.lb_wait_selftest.argtypes = [vp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -182,6 +183,11 @@ class Lattice:
 
     def step(self, nsteps: int = 1):
         _check(lib().lb_step(self._h, int(nsteps)), self._h)
+
+    def wait_selftest(self):
+        """Enqueue the failure-detection self-test (a bounded wait that gives
+        up); the next reductions() call reports LB_E_TIMEOUT."""
+        _check(lib().lb_wait_selftest(self._h), self._h)
 
     def worklist(self):
         """(rows per segment, item count, narrow blocks used) of the work-list

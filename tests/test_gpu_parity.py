@@ -490,3 +490,40 @@ def test_narrow_packed_blocks_bit_identical(scheme, monkeypatch):
     for key in (("1", "1"), ("1", "0")):
         for i in range(len(cases)):
             assert np.array_equal(snaps[("0", "1")][i], snaps[key][i]), (key, i)
+
+
+def test_bounded_wait_gives_up_and_is_reported():
+    """Failure detection without a GPU fault: a device wait on an mbarrier
+    phase that nothing completes gives up after its bound (about a second)
+    and the next reductions report LB_E_TIMEOUT; the context stays usable,
+    the handle steps on and the following reductions are clean."""
+    import time
+
+    gc, _, rg, rl = _pair(64, 40, lbfe.IMPROVED, lbfe.BGK)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+    lat.init_fields(0, inputs.droplet(64, 40, 12.0, rl, rg))
+    lat.step(10)
+    out0, st0 = lat.reductions()
+    assert (st0 == 0).all()
+    t0 = time.time()
+    lat.wait_selftest()
+    with pytest.raises(lbfe.LBError) as err:
+        lat.reductions()
+    assert err.value.status == 4
+    assert 0.2 < time.time() - t0 < 30
+    lat.step(10)
+    out1, st1 = lat.reductions()
+    assert (st1 == 0).all() and out1[0, 3] == 20
+    lat.close()
+
+
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
+def test_fp64_droplet_64_5000_steps(scheme):
+    """The small-droplet set-up over its full 5000 steps (both schemes, FP64):
+    rho and u within 5e-11 of the oracle (1e-11 is the bar at 1000 steps;
+    rounding differences grow slowly with the step count)."""
+    gc, oc, rg, rl = _pair(64, 64, scheme, lbfe.BGK)
+    rho0 = inputs.droplet(64, 64, 16.0, rl, rg, noise=1e-4, seed=0)
+    _, (m,) = _gpu_run([gc], [rho0], 5000, lbfe.FP64)
+    _, ref = _oracle_run(oc, rho0, 5000)
+    assert _maxerr(m, ref) < 5e-11
