@@ -324,22 +324,20 @@ def _batched_accuracy(lbfe, cases, rhos, steps):
             lat.init_fields(i, r)
         lat.step(steps)
         lats[prec] = lat
-    err_dp, err_r, u = 0.0, 0.0, {lbfe.FP32: 0.0, lbfe.FP64: 0.0}
+    err_dp, err_r, u = 0.0, 0.0, {}
+    for prec, lat in lats.items():  # max |u| of every case, reduced on the GPU
+        u[prec] = float(lat.reductions()[0][:, 2].max())
     for i, c in enumerate(cases):
         L = c.nx
-        y, x = np.mgrid[0:L, 0:L]
-        disc = np.hypot(x - L / 2, y - L / 2) < 0.25 * _batched_r0(rhos[i])
         s = L // 8
         dp, req = {}, {}
         for prec, lat in lats.items():
-            m = lat.moments(i)
-            rho = m["rho"]
-            rout = np.concatenate([rho[:s, :s].ravel(), rho[:s, -s:].ravel(), rho[-s:, :s].ravel(),
-                                   rho[-s:, -s:].ravel()]).mean()
-            rin = rho[disc].mean()
+            # GPU FP64 window means: centre disc, the four corner squares (one
+            # periodic square of side 2s around the corner node), whole lattice
+            rin, rout, rbar = lat.window_means(i, [("disc", L / 2, L / 2, 0.25 * _batched_r0(rhos[i])),
+                                                   ("rect", L - s, L - s, 2 * s, 2 * s), ("rect", 0, 0, L, L)])
             dp[prec] = _vdw_p(rin, c.T) - _vdw_p(rout, c.T)
-            req[prec] = np.sqrt((rho.sum() - rout * L * L) / (np.pi * (rin - rout)))
-            u[prec] = max(u[prec], float(np.hypot(m["ux"], m["uy"]).max()))
+            req[prec] = np.sqrt((rbar - rout) * L * L / (np.pi * (rin - rout)))
         err_dp = max(err_dp, abs(dp[lbfe.FP32] / dp[lbfe.FP64] - 1))
         err_r = max(err_r, abs(req[lbfe.FP32] / req[lbfe.FP64] - 1))
     for lat in lats.values():
@@ -529,9 +527,8 @@ def run_sweep(args):
         _, st = lat.reductions()
         errs = []
         for i, (rg, rl) in enumerate(mx):
-            rho = lat.moments(i)["rho"][0]
-            g = rho[: nx // 16].mean()
-            l = rho[nx // 2 - nx // 16: nx // 2 + nx // 16].mean()
+            # gas window x < L/16, liquid window |x - L/2| < L/16: GPU FP64 means
+            g, l = lat.window_means(i, [("rect", 0, 0, nx // 16, ny), ("rect", nx // 2 - nx // 16, 0, nx // 8, ny)])
             errs.append((float(ts[i]), float(g / rg - 1), float(l / rl - 1)))
         lat.close()
         out[name] = {"mlups": round(len(cases) * nx * ny * steps / (ms * 1e-3) / 1e6, 1),

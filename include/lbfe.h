@@ -154,6 +154,24 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
  * LB_E_UNSTABLE if any case is unstable; every entry is still written. */
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
 
+/* Coexistence-density averages (the rho_g / rho_l measurements of Sec. IV):
+ * the mean of rho (Eq. 12) at the current step over each of nwin windows of
+ * case case_id, with the node values in the storage precision and the sums
+ * in FP64 on the GPU, in a fixed order. A window is
+ *   kind LB_WIN_RECT: nodes x0 <= x < x0 + w, y0 <= y < y0 + h, indices
+ *     taken modulo nx, ny (a = x0, b = y0, c = w, d = h; 1 <= w <= nx,
+ *     1 <= h <= ny), or
+ *   kind LB_WIN_DISC: nodes whose periodic distance to (a, b) is below c
+ *     (0 < c <= min(nx, ny) / 2; d unused).
+ * mean[k] = (sum of rho over window k) / (its node count), NaN for a disc
+ * that holds no node. Host outputs; synchronises the handle's stream. */
+enum { LB_WIN_RECT = 0, LB_WIN_DISC = 1 };
+typedef struct {
+    int32_t kind, reserved;
+    double a, b, c, d;
+} lb_window;
+lb_status lb_window_means(lb_handle* h, int32_t case_id, int32_t nwin, const lb_window* win, double* mean);
+
 /* Failure-detection self-test (the paper has no counterpart): enqueues on the
  * handle's stream one kernel whose single thread waits, with the bound of the
  * step kernels' waits (about one second of SM clock), on an mbarrier phase

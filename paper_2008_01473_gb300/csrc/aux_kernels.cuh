@@ -233,6 +233,34 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
     block_partial(mass, ke, um, bad, partials);
 }
 
+// Sum and node count of a window of a C density field [ny][nx]: the grid
+// covers the window's bounding box (bw x bh nodes from (bx0, by0), indices
+// periodic); disc windows keep the nodes whose periodic distance to
+// (cx, cy) is below r. One Partial per block (mass = sum, bad = count).
+template <typename C>
+__global__ void __launch_bounds__(256) window_sum_kernel(const C* __restrict__ rho, int nx, int ny, int bx0,
+                                                         int by0, int bw, int disc, double cx, double cy,
+                                                         double r, Partial* __restrict__ partials)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double sum = 0.0, cnt = 0.0;
+    if (i < bw) {
+        const int x = wrapi(bx0 + i, nx), y = wrapi(by0 + (int)blockIdx.y, ny);
+        bool in = true;
+        if (disc) {
+            double dx = fabs((double)x - cx), dy = fabs((double)y - cy);
+            dx = fmin(dx, (double)nx - dx);
+            dy = fmin(dy, (double)ny - dy);
+            in = dx * dx + dy * dy < r * r;
+        }
+        if (in) {
+            sum = (double)rho[(int64_t)y * nx + x];
+            cnt = 1.0;
+        }
+    }
+    block_partial(sum, 0.0, 0.0, cnt, partials);
+}
+
 // Fold a case's partials in a fixed order into out[0..4] =
 // {mass, kinetic energy, max |u|, steps, bad-node count}.
 static __global__ void finalize_kernel(const Partial* __restrict__ partials, int64_t n, double steps,

@@ -733,6 +733,68 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
     return LB_OK;
 }
 
+lb_status lb_window_means(lb_handle* h, int32_t case_id, int32_t nwin, const lb_window* win, double* mean)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size() || nwin < 0 || (nwin > 0 && (!win || !mean)))
+        return h->fail(LB_E_INVALID, "lb_window_means: bad arguments");
+    if (!h->inited[case_id]) return h->fail(LB_E_STATE, "lb_window_means: case not initialised");
+    const lb_case& c = h->cases[case_id];
+    // bounding boxes first, so that nothing is enqueued for a bad window
+    std::vector<int> bx(nwin), by(nwin), bw(nwin), bh(nwin);
+    for (int k = 0; k < nwin; ++k) {
+        const lb_window& w = win[k];
+        const double v[] = {w.a, w.b, w.c, w.d};
+        for (double x : v)
+            if (!std::isfinite(x)) return h->fail(LB_E_INVALID, "lb_window_means: non-finite window");
+        if (w.kind == LB_WIN_RECT) {
+            if (!(w.c >= 1 && w.c <= c.nx && w.d >= 1 && w.d <= c.ny))
+                return h->fail(LB_E_INVALID, "lb_window_means: rectangle larger than the lattice or empty");
+            bx[k] = (int)std::floor(w.a);
+            by[k] = (int)std::floor(w.b);
+            bw[k] = (int)w.c;
+            bh[k] = (int)w.d;
+        } else if (w.kind == LB_WIN_DISC) {
+            if (!(w.c > 0 && 2 * w.c <= std::min(c.nx, c.ny)))
+                return h->fail(LB_E_INVALID, "lb_window_means: disc radius outside (0, min(nx, ny) / 2]");
+            bx[k] = (int)std::floor(w.a - w.c);
+            by[k] = (int)std::floor(w.b - w.c);
+            bw[k] = std::min(c.nx, (int)std::ceil(2 * w.c) + 2);
+            bh[k] = std::min(c.ny, (int)std::ceil(2 * w.c) + 2);
+        } else {
+            return h->fail(LB_E_INVALID, "lb_window_means: unknown window kind");
+        }
+        bx[k] = ((bx[k] % c.nx) + c.nx) % c.nx;
+        by[k] = ((by[k] % c.ny) + c.ny) % c.ny;
+    }
+    lb_status s = fields_pass(h, case_id, nullptr, nullptr, nullptr, nullptr);  // rho -> scratch 0
+    if (s != LB_OK) return s;
+    double* res = h->red() + 8 * case_id;  // the case's reduction slot, rewritten by lb_reductions
+    std::vector<double> out(5);
+    for (int k = 0; k < nwin && s == LB_OK; ++k) {
+        const dim3 blk(256), grd((bw[k] + 255) / 256, bh[k]);
+        const bool disc = win[k].kind == LB_WIN_DISC;
+        // disc centre in [0, nx) x [0, ny), so that periodic distances are min(d, n - d)
+        const double cx = win[k].a - c.nx * std::floor(win[k].a / c.nx);
+        const double cy = win[k].b - c.ny * std::floor(win[k].b / c.ny);
+        if (h->prec == LB_FP32)
+            window_sum_kernel<float><<<grd, blk, 0, h->stream>>>(reinterpret_cast<const float*>(h->scratch(0)), c.nx,
+                                                                c.ny, bx[k], by[k], bw[k], disc, cx, cy, win[k].c,
+                                                                h->partials());
+        else
+            window_sum_kernel<double><<<grd, blk, 0, h->stream>>>(h->scratch(0), c.nx, c.ny, bx[k], by[k], bw[k],
+                                                                 disc, cx, cy, win[k].c, h->partials());
+        finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), (int64_t)grd.x * grd.y, 0.0, res);
+        s = h->cuda(cudaGetLastError(), "window sums");
+        if (s == LB_OK)
+            s = h->cuda(cudaMemcpyAsync(out.data(), res, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                        "copy window sums");
+        if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "window sync");
+        if (s == LB_OK) mean[k] = out[4] > 0 ? out[0] / out[4] : std::nan("");
+    }
+    return s;
+}
+
 lb_status lb_wait_selftest(lb_handle* h)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;

@@ -30,6 +30,14 @@ class LBError(RuntimeError):
         self.status = status
 
 
+class _CWindow(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("c", C.c_double), ("d", C.c_double)]
+
+
+WIN_RECT, WIN_DISC = 0, 1
+
+
 class _CCase(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("scheme", C.c_int32), ("collision", C.c_int32),
                 ("eos", C.c_int32), ("reserved", C.c_int32), ("a", C.c_double), ("b", C.c_double),
@@ -92,13 +100,14 @@ def lib() -> C.CDLL:
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
         L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
         L.lb_wait_selftest.argtypes = [vp]
+        L.lb_window_means.argtypes = [vp, i32, i32, C.POINTER(_CWindow), dp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -183,6 +192,22 @@ class Lattice:
 
     def step(self, nsteps: int = 1):
         _check(lib().lb_step(self._h, int(nsteps)), self._h)
+
+    def window_means(self, case_id: int, windows):
+        """Mean of rho over each window, summed on the GPU in FP64: windows
+        are ("rect", x0, y0, w, h) (periodic) or ("disc", cx, cy, r)."""
+        arr = (_CWindow * max(1, len(windows)))()
+        for k, w in enumerate(windows):
+            if w[0] == "rect":
+                arr[k] = _CWindow(WIN_RECT, 0, float(w[1]), float(w[2]), float(w[3]), float(w[4]))
+            elif w[0] == "disc":
+                arr[k] = _CWindow(WIN_DISC, 0, float(w[1]), float(w[2]), float(w[3]), 0.0)
+            else:
+                raise ValueError(f"unknown window {w[0]!r}")
+        out = np.empty(max(1, len(windows)))
+        _check(lib().lb_window_means(self._h, case_id, len(windows), arr,
+                                     out.ctypes.data_as(C.POINTER(C.c_double))), self._h)
+        return out[:len(windows)]
 
     def wait_selftest(self):
         """Enqueue the failure-detection self-test (a bounded wait that gives

@@ -527,3 +527,32 @@ def test_fp64_droplet_64_5000_steps(scheme):
     _, (m,) = _gpu_run([gc], [rho0], 5000, lbfe.FP64)
     _, ref = _oracle_run(oc, rho0, 5000)
     assert _maxerr(m, ref) < 5e-11
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP64, lbfe.FP32])
+def test_window_means_match_exported_fields(precision):
+    """lb_window_means (FP64 sums on the GPU) against numpy means of the
+    exported density: rectangles that wrap both edges, the flat-interface
+    windows, discs near and across the periodic edges."""
+    gc, _, rg, rl = _pair(100, 60, lbfe.IMPROVED, lbfe.MRT)
+    lat = lbfe.Lattice([gc], precision=precision)
+    lat.init_fields(0, inputs.droplet(100, 60, 14.0, rl, rg, noise=1e-3))
+    lat.step(30)
+    rho = lat.moments(0)["rho"]
+    wins = [("rect", 0, 0, 100 // 16, 60), ("rect", 44, 0, 12, 60), ("rect", 95, 57, 10, 7), ("rect", 0, 0, 100, 60),
+            ("disc", 50, 30, 3.5), ("disc", 1.25, 58.5, 6.0), ("disc", -3.0, 70.0, 10.0)]
+    got = lat.window_means(0, wins)
+    y, x = np.mgrid[0:60, 0:100]
+    for (kind, *p), g in zip(wins, got):
+        if kind == "rect":
+            x0, y0, w, h = p
+            m = ((x - x0) % 100 < w) & ((y - y0) % 60 < h)
+        else:
+            cx, cy, r = p
+            dx = np.abs(x - cx % 100)
+            dy = np.abs(y - cy % 60)
+            m = np.minimum(dx, 100 - dx) ** 2 + np.minimum(dy, 60 - dy) ** 2 < r * r
+        assert abs(g - rho[m].mean()) < 1e-13 * abs(g)
+    with pytest.raises(lbfe.LBError):
+        lat.window_means(0, [("disc", 10, 10, 31.0)])
+    lat.close()
