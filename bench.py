@@ -411,6 +411,14 @@ def run_batched(args):
                                   "unit": "MLUPS", "ms_per_step": round(per_case_ms / args.steps, 4)},
             "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / args.steps * 1e-3) / 1e9, 1),
                          "peak": _peaks()[0], "unit": "GB/s"}}
+    if not args.no_cpu:
+        import numpy as np
+
+        # 16 seeded cases spanning the size range (evenly spaced ranks by side)
+        order = np.argsort([c.nx for c in cases], kind="stable")
+        pick = [int(order[k]) for k in np.linspace(0, len(cases) - 1, 16).round().astype(int)]
+        line["cpu_baseline"] = _oracle_pool_baseline([cases[i] for i in pick], [rhos[i] for i in pick], 100,
+                                                     "16 cases of the batch spanning its sizes")
     print(json.dumps(line), flush=True)
 
 
@@ -505,6 +513,7 @@ def run_sweep(args):
     ts = np.linspace(0.95, 0.75, 16)
     nx, ny, steps = 1024, 8, args.steps if args.steps > 1000 else 50000
     out = {}
+    first = None
     for scheme, name in ((lbfe.IMPROVED, "improved"), (lbfe.STANDARD, "standard"),
                          (lbfe.STANDARD_PT, "standard_pressure_tensor")):
         cases, rhos, mx = [], [], []
@@ -514,6 +523,7 @@ def run_sweep(args):
                                    kappa=0.02, tau_v=1.0, **VDW))
             rhos.append(inputs.slab(nx, ny, rl, rg))
             mx.append((rg, rl))
+        first = first or (cases, rhos)
         lat = lbfe.Lattice(cases, precision=prec)
         for i, r in enumerate(rhos):
             lat.init_fields(i, r)
@@ -538,7 +548,41 @@ def run_sweep(args):
                      "per_T": [[round(t, 4), f"{eg:.2e}", f"{el:.2e}"] for t, eg, el in errs]}
     line = {"metric": "coexistence sweep vs Maxwell", "workload": run_sweep.__doc__.split(";")[0].strip(),
             "dtype": "f64" if prec == lbfe.FP64 else "f32", "steps": steps, **out}
+    if not args.no_cpu:
+        line["cpu_baseline"] = _oracle_pool_baseline(*first, 2000, "the 16 improved-scheme strips")
     print(json.dumps(line), flush=True)
+
+
+def _oracle_case_steps(args):
+    """One oracle run (pool worker): a case given as keyword fields and its
+    initial density, stepped `steps` times; returns (node updates, seconds)."""
+    kw, rho0, steps = args
+    import oracle as O
+
+    oc = O.Case(**kw)
+    f = O.init(oc, rho0)
+    t0 = time.perf_counter()
+    done = O.step(oc, f, steps)
+    return oc.nx * oc.ny * done, time.perf_counter() - t0
+
+
+def _oracle_pool_baseline(cases, rhos, steps, what):
+    """The FP64 oracle, as it stands, on a bounded sample of a batched
+    workload, one case per process over the host's cores (a spawn pool):
+    whole-sample node updates over the longest case's stepping time (process
+    start-up excluded; with more cases than cores the sum would be needed)."""
+    import multiprocessing as mp
+
+    keys = ("nx", "ny", "scheme", "collision", "eos", "a", "b", "R", "T", "kappa", "tau_v", "tau_e", "tau_s",
+            "tau_q", "nu")
+    jobs = [({k: getattr(c, k) for k in keys}, r, steps) for c, r in zip(cases, rhos)]
+    cores = min(len(jobs), os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_case_steps, jobs, chunksize=1)
+    span = max(r[1] for r in res)  # the cases run side by side: the longest sets the time
+    nodes = sum(r[0] for r in res)
+    return {"value": round(nodes / span / 1e6, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{what}, {steps} steps each, one case per process, longest {span:.1f} s"}
 
 
 def _oracle_sample():
