@@ -470,11 +470,23 @@ def run_adjoint(args):
     L0, rho_g, gm = forward_loss(kappa, t_red)
     s_final = 2.0 * (rho_g - gm) * w
     lat = lbfe.Lattice([case(kappa, t_red)], precision=lbfe.FP64)
+    lat.adjoint(0, rho0, 8, 0, None, 0)  # warm-up: module load, first launches
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     La, g_rho0, gk, gT = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt)
     t_adj = time.perf_counter() - t0
     lat.close()
+    # the same gradient from an FP32 handle (FP32 forward, recompute and reverse sweep)
+    lat = lbfe.Lattice([case(kappa, t_red)], precision=lbfe.FP32)
+    lat.adjoint(0, rho0, 8, 0, None, 0)  # warm-up: module load, first launches
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    La32, g32, gk32, gT32 = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt)
+    t_adj32 = time.perf_counter() - t0
+    lat.close()
+    fp32 = {"adjoint_seconds": round(t_adj32, 3), "rel_diff_loss": abs(La32 / La - 1),
+            "rel_diff_dL_dkappa": abs(gk32 / gk - 1), "rel_diff_dL_dT_trajectory": abs(gT32 / gT - 1),
+            "rel_diff_dL_drho0_max": float(np.abs(g32 - g_rho0).max() / np.abs(g_rho0).max())}
     # dL/dT: trajectory term from the adjoint, plus the explicit -2 (rho_g - rho_g^M) d rho_g^M / dT
     hT = 1e-6 * tc
     dgm = (lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc + hT)[0]
@@ -491,7 +503,8 @@ def run_adjoint(args):
             "dL_dkappa": {"adjoint": gk, "fd": fd_k, "rel_err": abs(gk - fd_k) / abs(fd_k)},
             "dL_dT_over_Tc": {"adjoint": dL_dt, "fd": fd_t, "rel_err": abs(dL_dt - fd_t) / abs(fd_t)},
             "fd_rel_step": 3e-6,
-            "dL_drho0_norm": float(np.sqrt((g_rho0 ** 2).sum())), "rho_g": rho_g, "rho_g_maxwell": gm}
+            "dL_drho0_norm": float(np.sqrt((g_rho0 ** 2).sum())), "rho_g": rho_g, "rho_g_maxwell": gm,
+            "fp32_adjoint_vs_fp64": fp32}
     print(json.dumps(line), flush=True)
 
 

@@ -194,9 +194,12 @@ lb_status lb_snapshot_bytes(const lb_handle* h, int32_t case_id, size_t* bytes);
 lb_status lb_save(lb_handle* h, int32_t case_id, void* host_buf, size_t bytes);
 lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t bytes);
 
-/* Reverse-mode gradient of a trajectory of case case_id (LB_FP64 handles,
+/* Reverse-mode gradient of a trajectory of case case_id (either precision,
  * constant relaxation times, LB_STANDARD or LB_IMPROVED), the discrete
- * adjoint of the step above:
+ * adjoint of the step above, in the handle's precision: an LB_FP32 handle
+ * runs the forward pass, the recompute and the reverse sweep in FP32 (the
+ * FP32 step kernel; loss and parameter sums in FP64), an LB_FP64 handle all
+ * in FP64:
  *   f(0) = M^-1 m_eq(rho0, 0) as lb_init_fields, then nsteps steps;
  *   L = sum_{n = u_from}^{nsteps} sum_x |u^n(x)|^2 + sum_x s_final(x) rho^N(x)
  * (u^n, rho^n of Eq. 12 after n steps; s_final may be NULL). Outputs the loss,

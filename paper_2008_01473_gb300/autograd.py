@@ -1,11 +1,12 @@
 """torch.autograd.Function around the library's adjoint (lb_adjoint_step).
 
-LBLoss.apply(kappa, T, rho0, case, nsteps, u_from, s_final, ckpt_every)
+LBLoss.apply(kappa, T, rho0, case, nsteps, u_from, s_final, ckpt_every, precision)
 returns L = sum_{n >= u_from} sum_x |u^n|^2 + sum_x s_final rho^N for a run of
 `case` (an lbfe.Case; its kappa and T are replaced by the tensors) started from
 rho0, and back-propagates dL/dkappa, dL/dT and dL/drho0 from one forward and
-one reverse sweep of the CUDA kernels (FP64, checkpointed). Gradients for
-other losses of the final density enter through s_final (dL/drho^N).
+one reverse sweep of the CUDA kernels (checkpointed; in FP64 by default, or
+in FP32 with precision=lbfe.FP32). Gradients for other losses of the final
+density enter through s_final (dL/drho^N).
 """
 from __future__ import annotations
 
@@ -18,9 +19,9 @@ from . import lbfe
 
 class LBLoss(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, kappa, T, rho0, case, nsteps, u_from, s_final=None, ckpt_every=0):
+    def forward(ctx, kappa, T, rho0, case, nsteps, u_from, s_final=None, ckpt_every=0, precision=lbfe.FP64):
         c = dataclasses.replace(case, kappa=float(kappa), T=float(T))
-        lat = lbfe.Lattice([c], precision=lbfe.FP64, device=rho0.device if rho0.is_cuda else None)
+        lat = lbfe.Lattice([c], precision=precision, device=rho0.device if rho0.is_cuda else None)
         r0 = rho0.detach().to(torch.float64)
         sf = None if s_final is None else s_final.detach().to(torch.float64).to(r0.device)
         L, g, gk, gT = lat.adjoint(0, r0, nsteps, u_from, sf, ckpt_every)
@@ -37,4 +38,4 @@ class LBLoss(torch.autograd.Function):
         go = float(gout)
         gk = torch.tensor(go * ctx.gk, dtype=torch.float64, device=ctx.kdev)
         gT = torch.tensor(go * ctx.gT, dtype=torch.float64, device=ctx.Tdev)
-        return gk, gT, go * g, None, None, None, None, None
+        return gk, gT, go * g, None, None, None, None, None, None

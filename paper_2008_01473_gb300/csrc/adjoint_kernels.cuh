@@ -1,6 +1,8 @@
-// FP64 kernels of the discrete adjoint (reverse-mode derivative) of one time
-// step, for lb_adjoint_step. One thread per node, 256-thread blocks over
-// (ceil(nx / 256), ny). Fields are dense [ny][nx] FP64 arrays; the adjoint
+// Kernels of the discrete adjoint (reverse-mode derivative) of one time step,
+// for lb_adjoint_step, in the arithmetic type T of the handle (FP64, or FP32
+// for FP32 handles; loss and parameter partials are FP64 either way). One
+// thread per node, 256-thread blocks over (ceil(nx / 256), ny). Fields are
+// dense [ny][nx] arrays of T; the adjoint
 // of the populations (lam) is kept at the nodes, lam_a(x) = dL/df_a(x), while
 // forward states are in the library's storage form (pulled on read).
 //
@@ -20,11 +22,12 @@
 
 namespace lbfe {
 
+template <typename T>
 struct AdjFields {
     // forward fields at the current state
-    double *rho, *jx, *jy, *lap, *mu, *gx, *gy, *Fx, *Fy, *ux, *uy, *phi, *A, *B, *C1, *C7;
+    T *rho, *jx, *jy, *lap, *mu, *gx, *gy, *Fx, *Fy, *ux, *uy, *phi, *A, *B, *C1, *C7;
     // adjoint fields
-    double *rb, *jxb, *jyb, *uxb, *uyb, *Fxb, *Fyb, *mub, *C1b, *C7b, *gxb, *gyb, *Lb;
+    T *rb, *jxb, *jyb, *uxb, *uyb, *Fxb, *Fyb, *mub, *C1b, *C7b, *gxb, *gyb, *Lb;
 };
 
 __device__ constexpr int kEx[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -52,87 +55,90 @@ __device__ __forceinline__ bool node_of(int nx, int ny, NodeIdx& n)
 }
 
 // Eq. 17 at node n of field v (component d = 0: x, 1: y)
-__device__ __forceinline__ double grad_at(const double* v, const NodeIdx& n, int d)
+template <typename T>
+__device__ __forceinline__ T grad_at(const T* v, const NodeIdx& n, int d)
 {
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
-    for (int a = 1; a < kQ; ++a) s += 3.0 * kW[a] * (d == 0 ? kEx[a] : kEy[a]) * v[n.at(kEx[a], kEy[a])];
+    for (int a = 1; a < kQ; ++a) s += T(3.0 * kW[a] * (d == 0 ? kEx[a] : kEy[a])) * v[n.at(kEx[a], kEy[a])];
     return s;
 }
 // transpose of the Eq. 17 component d: 3 sum_a w_a e_a v(x - e_a)
-__device__ __forceinline__ double gradT_at(const double* v, const NodeIdx& n, int d)
+template <typename T>
+__device__ __forceinline__ T gradT_at(const T* v, const NodeIdx& n, int d)
 {
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll
-    for (int a = 1; a < kQ; ++a) s += 3.0 * kW[a] * (d == 0 ? kEx[a] : kEy[a]) * v[n.at(-kEx[a], -kEy[a])];
+    for (int a = 1; a < kQ; ++a) s += T(3.0 * kW[a] * (d == 0 ? kEx[a] : kEy[a])) * v[n.at(-kEx[a], -kEy[a])];
     return s;
 }
 // transpose of the Laplacian 6 sum_a w_a (v(x + e_a) - v(x)): 6 sum_a w_a (v(x - e_a) - v(x))
-__device__ __forceinline__ double lapT_at(const double* v, const NodeIdx& n)
+template <typename T>
+__device__ __forceinline__ T lapT_at(const T* v, const NodeIdx& n)
 {
-    double s = 0.0;
-    const double c = v[n.i];
+    T s = T(0);
+    const T c = v[n.i];
 #pragma unroll
-    for (int a = 1; a < kQ; ++a) s += kW[a] * (v[n.at(-kEx[a], -kEy[a])] - c);
-    return 6.0 * s;
+    for (int a = 1; a < kQ; ++a) s += T(kW[a]) * (v[n.at(-kEx[a], -kEy[a])] - c);
+    return T(6) * s;
 }
 
-template <int EOS>
-__device__ __forceinline__ double d2Ef_dev(const DevCase<double>& c, double rho)
+template <int EOS, typename T>
+__device__ __forceinline__ T d2Ef_dev(const DevCase<T>& c, T rho)
 {
     if (EOS == 0) {
-        const double q = 1.0 / (1.0 - c.b * rho);
-        return c.RT * (1.0 / rho + c.b * q + c.b * q * q) - 2.0 * c.a;
+        const T q = T(1) / (T(1) - c.b * rho);
+        return c.RT * (T(1) / rho + c.b * q + c.b * q * q) - T(2) * c.a;
     }
-    const double n = 0.25 * c.b * rho, q = 1.0 / (1.0 - n);
-    return c.RT * (1.0 / rho + 0.25 * c.b * (8.0 - 2.0 * n) * q * q * q * q) - 2.0 * c.a;
+    const T n = T(0.25) * c.b * rho, q = T(1) / (T(1) - n);
+    return c.RT * (T(1) / rho + T(0.25) * c.b * (T(8) - T(2) * n) * q * q * q * q) - T(2) * c.a;
 }
 // R h(rho) = d E_f' / d T (R folded in: RT / T)
-template <int EOS>
-__device__ __forceinline__ double dEf_dT_dev(const DevCase<double>& c, double rho, double R)
+template <int EOS, typename T>
+__device__ __forceinline__ T dEf_dT_dev(const DevCase<T>& c, T rho, T R)
 {
-    DevCase<double> u = c;
+    DevCase<T> u = c;
     u.RT = R;
-    u.a = 0.0;
-    return dEf<EOS, double>(u, rho);
+    u.a = T(0);
+    return dEf<EOS, T>(u, rho);
 }
 
 // ---------------------------------------------------------------- forward
 // lap and mu_c of the rho field
-template <int EOS>
-__global__ void adj_fwd_mu(DevCase<double> c, AdjFields F)
+template <typename T, int EOS>
+__global__ void adj_fwd_mu(DevCase<T> c, AdjFields<T> F)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
-    double s = 0.0;
-    const double r = F.rho[n.i];
+    T s = T(0);
+    const T r = F.rho[n.i];
 #pragma unroll
-    for (int a = 1; a < kQ; ++a) s += kW[a] * (F.rho[n.at(kEx[a], kEy[a])] - r);
-    const double lap = 6.0 * s;
+    for (int a = 1; a < kQ; ++a) s += T(kW[a]) * (F.rho[n.at(kEx[a], kEy[a])] - r);
+    const T lap = T(6) * s;
     F.lap[n.i] = lap;
-    F.mu[n.i] = dEf<EOS, double>(c, r) - c.kappa * lap;
+    F.mu[n.i] = dEf<EOS, T>(c, r) - c.kappa * lap;
 }
 
 // grad mu_c, F, u, phi, A, B; loss partials: w_u sum |u|^2 + sum s rho
-template <int SCHEME>
-__global__ void __launch_bounds__(256) adj_fwd_force(DevCase<double> c, AdjFields F, double w_u,
+template <typename T, int SCHEME>
+__global__ void __launch_bounds__(256) adj_fwd_force(DevCase<T> c, AdjFields<T> F, double w_u,
                                                      const double* __restrict__ s_final, Partial* partials)
 {
     NodeIdx n;
     double loss = 0.0;
     if (node_of(c.nx, c.ny, n)) {
-        const double r = F.rho[n.i];
-        const double gx = grad_at(F.mu, n, 0), gy = grad_at(F.mu, n, 1);
-        double Fx, Fy;
+        const T r = F.rho[n.i];
+        const T gx = grad_at(F.mu, n, 0), gy = grad_at(F.mu, n, 1);
+        T Fx, Fy;
         if (SCHEME == 1) {
-            Fx = (1.0 / 3.0 - r) * gx;
-            Fy = (1.0 / 3.0 - r) * gy;
+            Fx = (T(1.0 / 3.0) - r) * gx;
+            Fy = (T(1.0 / 3.0) - r) * gy;
         } else {
-            Fx = grad_at(F.rho, n, 0) / 3.0 - r * gx;
-            Fy = grad_at(F.rho, n, 1) / 3.0 - r * gy;
+            Fx = grad_at(F.rho, n, 0) * T(1.0 / 3.0) - r * gx;
+            Fy = grad_at(F.rho, n, 1) * T(1.0 / 3.0) - r * gy;
         }
-        const double ux = (F.jx[n.i] + 0.5 * Fx) / r, uy = (F.jy[n.i] + 0.5 * Fy) / r;
-        const double phi = (r - (c.c0 + F.mu[n.i])) / 3.0;
+        const T ux = (F.jx[n.i] + T(0.5) * Fx) / r, uy = (F.jy[n.i] + T(0.5) * Fy) / r;
+        const T phi = (r - (c.c0 + F.mu[n.i])) * T(1.0 / 3.0);
         F.gx[n.i] = gx;
         F.gy[n.i] = gy;
         F.Fx[n.i] = Fx;
@@ -142,16 +148,17 @@ __global__ void __launch_bounds__(256) adj_fwd_force(DevCase<double> c, AdjField
         F.phi[n.i] = phi;
         F.A[n.i] = phi * ux;
         F.B[n.i] = phi * uy;
-        loss = w_u * (ux * ux + uy * uy) + (s_final ? s_final[n.i] * r : 0.0);
+        loss = w_u * ((double)ux * ux + (double)uy * uy) + (s_final ? s_final[n.i] * (double)r : 0.0);
     }
     block_partial(loss, 0.0, 0.0, 0.0, partials);
 }
 
-__global__ void adj_fwd_corr(DevCase<double> c, AdjFields F)
+template <typename T>
+__global__ void adj_fwd_corr(DevCase<T> c, AdjFields<T> F)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
-    const double Ax = grad_at(F.A, n, 0), By = grad_at(F.B, n, 1);
+    const T Ax = grad_at(F.A, n, 0), By = grad_at(F.B, n, 1);
     F.C1[n.i] = Ax + By;
     F.C7[n.i] = Ax - By;
 }
@@ -161,85 +168,86 @@ __global__ void adj_fwd_corr(DevCase<double> c, AdjFields F)
 // step (node form); has_next = 0 for the final state (no collision term).
 // Writes lam_direct (the part through m = M f) and initialises every adjoint
 // field, adding the |u|^2 seed when seed_u != 0.
-template <int SCHEME>
-__global__ void adj_collide(DevCase<double> c, AdjFields F, const double* __restrict__ lam_next, int has_next,
-                            int seed_u, double* __restrict__ lam_direct)
+template <typename T, int SCHEME>
+__global__ void adj_collide(DevCase<T> c, AdjFields<T> F, const T* __restrict__ lam_next, int has_next,
+                            int seed_u, T* __restrict__ lam_direct)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
     const int64_t N = (int64_t)c.nx * c.ny;
-    double rb = 0.0, jxb = 0.0, jyb = 0.0, uxb = 0.0, uyb = 0.0, Fxb = 0.0, Fyb = 0.0, mub = 0.0, C1b = 0.0,
-           C7b = 0.0;
-    double d[kQ];
-    for (int a = 0; a < kQ; ++a) d[a] = 0.0;
+    T rb = T(0), jxb = T(0), jyb = T(0), uxb = T(0), uyb = T(0), Fxb = T(0), Fyb = T(0), mub = T(0), C1b = T(0),
+      C7b = T(0);
+    T d[kQ];
+    for (int a = 0; a < kQ; ++a) d[a] = T(0);
     if (has_next) {
         // lam*(x) = lam_next(x + e_a): transpose of the streaming
-        double L[kQ];
+        T L[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) L[a] = lam_next[a * N + n.at(kEx[a], kEy[a])];
         // nu = M^-T lam* = D M lam*
-        const double sa = (L[1] + L[3]) + (L[2] + L[4]), sd = (L[5] + L[7]) + (L[6] + L[8]);
-        const double nr = (L[0] + sa + sd) / 9.0;
-        const double ne = (2.0 * sd - sa - 4.0 * L[0]) / 36.0;
-        const double ns = (sd - 2.0 * sa + 4.0 * L[0]) / 36.0;
-        const double njx = ((L[1] - L[3]) + (L[5] - L[7]) + (L[8] - L[6])) / 6.0;
-        const double nqx = (-2.0 * (L[1] - L[3]) + (L[5] - L[7]) + (L[8] - L[6])) / 12.0;
-        const double njy = ((L[2] - L[4]) + (L[5] - L[7]) + (L[6] - L[8])) / 6.0;
-        const double nqy = (-2.0 * (L[2] - L[4]) + (L[5] - L[7]) + (L[6] - L[8])) / 12.0;
-        const double npxx = ((L[1] + L[3]) - (L[2] + L[4])) / 4.0;
-        const double npxy = ((L[5] + L[7]) - (L[6] + L[8])) / 4.0;
-        const double le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
+        const T sa = (L[1] + L[3]) + (L[2] + L[4]), sd = (L[5] + L[7]) + (L[6] + L[8]);
+        const T nr = (L[0] + sa + sd) * T(1.0 / 9.0);
+        const T ne = (T(2) * sd - sa - T(4) * L[0]) * T(1.0 / 36.0);
+        const T ns = (sd - T(2) * sa + T(4) * L[0]) * T(1.0 / 36.0);
+        const T njx = ((L[1] - L[3]) + (L[5] - L[7]) + (L[8] - L[6])) * T(1.0 / 6.0);
+        const T nqx = (T(-2) * (L[1] - L[3]) + (L[5] - L[7]) + (L[8] - L[6])) * T(1.0 / 12.0);
+        const T njy = ((L[2] - L[4]) + (L[5] - L[7]) + (L[6] - L[8])) * T(1.0 / 6.0);
+        const T nqy = (T(-2) * (L[2] - L[4]) + (L[5] - L[7]) + (L[6] - L[8])) * T(1.0 / 12.0);
+        const T npxx = ((L[1] + L[3]) - (L[2] + L[4])) * T(0.25);
+        const T npxy = ((L[5] + L[7]) - (L[6] + L[8])) * T(0.25);
+        const T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
         // m* = m + lam (eq - m) + h S (non-conserved), rho* = rho, j* = j + F
-        const double mbe = (1.0 - le) * ne, mbs = (1.0 - ls) * ns, mbqx = (1.0 - lq) * nqx,
-                     mbqy = (1.0 - lq) * nqy, mbxx = (1.0 - lv) * npxx, mbxy = (1.0 - lv) * npxy;
-        const double qe = le * ne, qs = ls * ns, qqx = lq * nqx, qqy = lq * nqy, qxx = lv * npxx, qxy = lv * npxy;
-        const double Se = (1.0 - 0.5 * le) * ne, Ss = (1.0 - 0.5 * ls) * ns, Sqx = (1.0 - 0.5 * lq) * nqx,
-                     Sqy = (1.0 - 0.5 * lq) * nqy, Sxx = (1.0 - 0.5 * lv) * npxx, Sxy = (1.0 - 0.5 * lv) * npxy;
+        const T mbe = (T(1) - le) * ne, mbs = (T(1) - ls) * ns, mbqx = (T(1) - lq) * nqx, mbqy = (T(1) - lq) * nqy,
+                mbxx = (T(1) - lv) * npxx, mbxy = (T(1) - lv) * npxy;
+        const T qe = le * ne, qs = ls * ns, qqx = lq * nqx, qqy = lq * nqy, qxx = lv * npxx, qxy = lv * npxy;
+        const T Se = (T(1) - T(0.5) * le) * ne, Ss = (T(1) - T(0.5) * ls) * ns,
+                Sqx = (T(1) - T(0.5) * lq) * nqx, Sqy = (T(1) - T(0.5) * lq) * nqy,
+                Sxx = (T(1) - T(0.5) * lv) * npxx, Sxy = (T(1) - T(0.5) * lv) * npxy;
         rb += nr;
         jxb += njx;
         jyb += njy;
         Fxb += njx;
         Fyb += njy;
         // direct part: M_nc^T m-bar (rows e, eps, q_x, q_y, p_xx, p_xy of M)
-        d[0] = -4.0 * mbe + 4.0 * mbs;
-        d[1] = -mbe - 2.0 * mbs - 2.0 * mbqx + mbxx;
-        d[2] = -mbe - 2.0 * mbs - 2.0 * mbqy - mbxx;
-        d[3] = -mbe - 2.0 * mbs + 2.0 * mbqx + mbxx;
-        d[4] = -mbe - 2.0 * mbs + 2.0 * mbqy - mbxx;
-        d[5] = 2.0 * mbe + mbs + mbqx + mbqy + mbxy;
-        d[6] = 2.0 * mbe + mbs - mbqx + mbqy - mbxy;
-        d[7] = 2.0 * mbe + mbs - mbqx - mbqy + mbxy;
-        d[8] = 2.0 * mbe + mbs + mbqx - mbqy - mbxy;
+        d[0] = T(-4) * mbe + T(4) * mbs;
+        d[1] = -mbe - T(2) * mbs - T(2) * mbqx + mbxx;
+        d[2] = -mbe - T(2) * mbs - T(2) * mbqy - mbxx;
+        d[3] = -mbe - T(2) * mbs + T(2) * mbqx + mbxx;
+        d[4] = -mbe - T(2) * mbs + T(2) * mbqy - mbxx;
+        d[5] = T(2) * mbe + mbs + mbqx + mbqy + mbxy;
+        d[6] = T(2) * mbe + mbs - mbqx + mbqy - mbxy;
+        d[7] = T(2) * mbe + mbs - mbqx - mbqy + mbxy;
+        d[8] = T(2) * mbe + mbs + mbqx - mbqy - mbxy;
         // equilibria (Eq. 11 / Eq. 27)
-        const double r = F.rho[n.i], ux = F.ux[n.i], uy = F.uy[n.i], u2 = ux * ux + uy * uy;
+        const T r = F.rho[n.i], ux = F.ux[n.i], uy = F.uy[n.i], u2 = ux * ux + uy * uy;
         if (SCHEME == 0) {
-            rb += qe * (3.0 * u2 - 2.0) + qs * (1.0 - 3.0 * u2) - qqx * ux - qqy * uy;
-            uxb += qe * 6.0 * r * ux - qs * 6.0 * r * ux - qqx * r;
-            uyb += qe * 6.0 * r * uy - qs * 6.0 * r * uy - qqy * r;
+            rb += qe * (T(3) * u2 - T(2)) + qs * (T(1) - T(3) * u2) - qqx * ux - qqy * uy;
+            uxb += qe * T(6) * r * ux - qs * T(6) * r * ux - qqx * r;
+            uyb += qe * T(6) * r * uy - qs * T(6) * r * uy - qqy * r;
         } else {
-            const double s3 = c.c0 + F.mu[n.i];
-            rb += qe * (3.0 * u2 - 4.0) + qs * (4.0 - 3.0 * u2) - 2.0 * (qqx * ux + qqy * uy);
-            uxb += qe * 6.0 * r * ux - qs * 6.0 * r * ux + qqx * (s3 - 2.0 * r);
-            uyb += qe * 6.0 * r * uy - qs * 6.0 * r * uy + qqy * (s3 - 2.0 * r);
-            mub += 2.0 * qe - 3.0 * qs + qqx * ux + qqy * uy;
+            const T s3 = c.c0 + F.mu[n.i];
+            rb += qe * (T(3) * u2 - T(4)) + qs * (T(4) - T(3) * u2) - T(2) * (qqx * ux + qqy * uy);
+            uxb += qe * T(6) * r * ux - qs * T(6) * r * ux + qqx * (s3 - T(2) * r);
+            uyb += qe * T(6) * r * uy - qs * T(6) * r * uy + qqy * (s3 - T(2) * r);
+            mub += T(2) * qe - T(3) * qs + qqx * ux + qqy * uy;
         }
         rb += qxx * (ux * ux - uy * uy) + qxy * ux * uy;
-        uxb += qxx * 2.0 * r * ux + qxy * r * uy;
-        uyb += -qxx * 2.0 * r * uy + qxy * r * ux;
+        uxb += qxx * T(2) * r * ux + qxy * r * uy;
+        uyb += -qxx * T(2) * r * uy + qxy * r * ux;
         // forcing moments S = M G (Eq. 14) and correction C (Eq. 29)
-        const double Fx = F.Fx[n.i], Fy = F.Fy[n.i];
-        uxb += 6.0 * Fx * (Se - Ss) + 2.0 * Fx * Sxx + Fy * Sxy;
-        uyb += 6.0 * Fy * (Se - Ss) - 2.0 * Fy * Sxx + Fx * Sxy;
-        Fxb += 6.0 * ux * (Se - Ss) - Sqx + 2.0 * ux * Sxx + uy * Sxy;
-        Fyb += 6.0 * uy * (Se - Ss) - Sqy - 2.0 * uy * Sxx + ux * Sxy;
+        const T Fx = F.Fx[n.i], Fy = F.Fy[n.i];
+        uxb += T(6) * Fx * (Se - Ss) + T(2) * Fx * Sxx + Fy * Sxy;
+        uyb += T(6) * Fy * (Se - Ss) - T(2) * Fy * Sxx + Fx * Sxy;
+        Fxb += T(6) * ux * (Se - Ss) - Sqx + T(2) * ux * Sxx + uy * Sxy;
+        Fyb += T(6) * uy * (Se - Ss) - Sqy - T(2) * uy * Sxx + ux * Sxy;
         if (SCHEME == 1) {
-            C1b = 9.0 * Se;
-            C7b = 3.0 * Sxx;
+            C1b = T(9) * Se;
+            C7b = T(3) * Sxx;
         }
     }
     if (seed_u) {
-        uxb += 2.0 * F.ux[n.i];
-        uyb += 2.0 * F.uy[n.i];
+        uxb += T(2) * F.ux[n.i];
+        uyb += T(2) * F.uy[n.i];
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) lam_direct[a * N + n.i] = d[a];
@@ -256,34 +264,34 @@ __global__ void adj_collide(DevCase<double> c, AdjFields F, const double* __rest
 }
 
 // correction (Eq. 29), velocity (Eq. 12) and force (Eqs. 13/24) transposed
-template <int SCHEME>
-__global__ void adj_force(DevCase<double> c, AdjFields F)
+template <typename T, int SCHEME>
+__global__ void adj_force(DevCase<T> c, AdjFields<T> F)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
     const int64_t i = n.i;
-    double rb = F.rb[i], uxb = F.uxb[i], uyb = F.uyb[i], mub = F.mub[i];
+    T rb = F.rb[i], uxb = F.uxb[i], uyb = F.uyb[i], mub = F.mub[i];
     if (SCHEME == 1) {
         // A-bar = G_x^T (C1b + C7b), B-bar = G_y^T (C1b - C7b)
-        double Ab = 0.0, Bb = 0.0;
+        T Ab = T(0), Bb = T(0);
 #pragma unroll
         for (int a = 1; a < kQ; ++a) {
             const int64_t j = n.at(-kEx[a], -kEy[a]);
-            Ab += 3.0 * kW[a] * kEx[a] * (F.C1b[j] + F.C7b[j]);
-            Bb += 3.0 * kW[a] * kEy[a] * (F.C1b[j] - F.C7b[j]);
+            Ab += T(3.0 * kW[a] * kEx[a]) * (F.C1b[j] + F.C7b[j]);
+            Bb += T(3.0 * kW[a] * kEy[a]) * (F.C1b[j] - F.C7b[j]);
         }
-        const double phib = Ab * F.ux[i] + Bb * F.uy[i];
+        const T phib = Ab * F.ux[i] + Bb * F.uy[i];
         uxb += F.phi[i] * Ab;
         uyb += F.phi[i] * Bb;
-        rb += phib / 3.0;
-        mub -= phib / 3.0;
+        rb += phib * T(1.0 / 3.0);
+        mub -= phib * T(1.0 / 3.0);
     }
-    const double r = F.rho[i];
+    const T r = F.rho[i];
     F.jxb[i] += uxb / r;
     F.jyb[i] += uyb / r;
-    const double Fxb = F.Fxb[i] + 0.5 * uxb / r, Fyb = F.Fyb[i] + 0.5 * uyb / r;
+    const T Fxb = F.Fxb[i] + T(0.5) * uxb / r, Fyb = F.Fyb[i] + T(0.5) * uyb / r;
     rb -= (uxb * F.ux[i] + uyb * F.uy[i]) / r;
-    const double k = SCHEME == 1 ? 1.0 / 3.0 - r : -r;
+    const T k = SCHEME == 1 ? T(1.0 / 3.0) - r : -r;
     F.gxb[i] = k * Fxb;
     F.gyb[i] = k * Fyb;
     rb -= F.gx[i] * Fxb + F.gy[i] * Fyb;
@@ -294,77 +302,80 @@ __global__ void adj_force(DevCase<double> c, AdjFields F)
 }
 
 // grad mu_c transposed, mu_c = E_f' - kappa lap transposed; parameter partials
-template <int SCHEME, int EOS>
-__global__ void __launch_bounds__(256) adj_mu(DevCase<double> c, double R, AdjFields F, Partial* partials)
+template <typename T, int SCHEME, int EOS>
+__global__ void __launch_bounds__(256) adj_mu(DevCase<T> c, T R, AdjFields<T> F, Partial* partials)
 {
     NodeIdx n;
     double gk = 0.0, gT = 0.0;
     if (node_of(c.nx, c.ny, n)) {
         const int64_t i = n.i;
-        const double mub = F.mub[i] + gradT_at(F.gxb, n, 0) + gradT_at(F.gyb, n, 1);
-        double rb = F.rb[i];
-        if (SCHEME == 0) rb += (gradT_at(F.Fxb, n, 0) + gradT_at(F.Fyb, n, 1)) / 3.0;
-        rb += d2Ef_dev<EOS>(c, F.rho[i]) * mub;
+        const T mub = F.mub[i] + gradT_at(F.gxb, n, 0) + gradT_at(F.gyb, n, 1);
+        T rb = F.rb[i];
+        if (SCHEME == 0) rb += (gradT_at(F.Fxb, n, 0) + gradT_at(F.Fyb, n, 1)) * T(1.0 / 3.0);
+        rb += d2Ef_dev<EOS, T>(c, F.rho[i]) * mub;
         F.rb[i] = rb;
         F.Lb[i] = -c.kappa * mub;
-        gk = -mub * F.lap[i];
-        gT = mub * dEf_dT_dev<EOS>(c, F.rho[i], R);
+        gk = -(double)mub * (double)F.lap[i];
+        gT = (double)mub * (double)dEf_dT_dev<EOS, T>(c, F.rho[i], R);
     }
     block_partial(gk, gT, 0.0, 0.0, partials);
 }
 
 // lap transposed; lam(x)_a = lam_direct + rho-bar + e_a . j-bar (+ final density seed)
-__global__ void adj_lambda(DevCase<double> c, AdjFields F, const double* __restrict__ lam_direct,
-                           const double* __restrict__ s_final, double* __restrict__ lam)
+template <typename T>
+__global__ void adj_lambda(DevCase<T> c, AdjFields<T> F, const T* __restrict__ lam_direct,
+                           const double* __restrict__ s_final, T* __restrict__ lam)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
     const int64_t N = (int64_t)c.nx * c.ny;
-    const double rb = F.rb[n.i] + lapT_at(F.Lb, n) + (s_final ? s_final[n.i] : 0.0);
-    const double jxb = F.jxb[n.i], jyb = F.jyb[n.i];
+    const T rb = F.rb[n.i] + lapT_at(F.Lb, n) + (s_final ? (T)s_final[n.i] : T(0));
+    const T jxb = F.jxb[n.i], jyb = F.jyb[n.i];
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) lam[a * N + n.i] = lam_direct[a * N + n.i] + rb + kEx[a] * jxb + kEy[a] * jyb;
+    for (int a = 0; a < kQ; ++a)
+        lam[a * N + n.i] = lam_direct[a * N + n.i] + rb + T(kEx[a]) * jxb + T(kEy[a]) * jyb;
 }
 
 // Initial populations f(0) = M^-1 m_eq(rho0, 0, mu(rho0)) transposed. F.rho,
 // F.lap, F.mu hold the fields of rho0.
-template <int SCHEME, int EOS>
-__global__ void __launch_bounds__(256) adj_init(DevCase<double> c, double R, AdjFields F,
-                                                const double* __restrict__ lam0, Partial* partials)
+template <typename T, int SCHEME, int EOS>
+__global__ void __launch_bounds__(256) adj_init(DevCase<T> c, T R, AdjFields<T> F, const T* __restrict__ lam0,
+                                                Partial* partials)
 {
     NodeIdx n;
     double gk = 0.0, gT = 0.0;
     if (node_of(c.nx, c.ny, n)) {
         const int64_t N = (int64_t)c.nx * c.ny;
-        double L[kQ];
+        T L[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) L[a] = lam0[a * N + n.i];
-        const double sa = (L[1] + L[3]) + (L[2] + L[4]), sd = (L[5] + L[7]) + (L[6] + L[8]);
-        const double nr = (L[0] + sa + sd) / 9.0;
-        const double ne = (2.0 * sd - sa - 4.0 * L[0]) / 36.0;
-        const double ns = (sd - 2.0 * sa + 4.0 * L[0]) / 36.0;
+        const T sa = (L[1] + L[3]) + (L[2] + L[4]), sd = (L[5] + L[7]) + (L[6] + L[8]);
+        const T nr = (L[0] + sa + sd) * T(1.0 / 9.0);
+        const T ne = (T(2) * sd - sa - T(4) * L[0]) * T(1.0 / 36.0);
+        const T ns = (sd - T(2) * sa + T(4) * L[0]) * T(1.0 / 36.0);
         // m_eq at u = 0: rho (1, -2, 1, 0...) standard; (rho, -4 rho + 2 s, 4 rho - 3 s, 0...) improved
-        double rb = nr, mub = 0.0;
+        T rb = nr, mub = T(0);
         if (SCHEME == 0) {
-            rb += -2.0 * ne + ns;
+            rb += T(-2) * ne + ns;
         } else {
-            rb += -4.0 * ne + 4.0 * ns;
-            mub = 2.0 * ne - 3.0 * ns;
+            rb += T(-4) * ne + T(4) * ns;
+            mub = T(2) * ne - T(3) * ns;
         }
-        const double r = F.rho[n.i];
-        F.rb[n.i] = rb + d2Ef_dev<EOS>(c, r) * mub;
+        const T r = F.rho[n.i];
+        F.rb[n.i] = rb + d2Ef_dev<EOS, T>(c, r) * mub;
         F.Lb[n.i] = -c.kappa * mub;
-        gk = -mub * F.lap[n.i];
-        gT = mub * dEf_dT_dev<EOS>(c, r, R);
+        gk = -(double)mub * (double)F.lap[n.i];
+        gT = (double)mub * (double)dEf_dT_dev<EOS, T>(c, r, R);
     }
     block_partial(gk, gT, 0.0, 0.0, partials);
 }
 
-__global__ void adj_init_out(DevCase<double> c, AdjFields F, double* __restrict__ grad_rho0)
+template <typename T>
+__global__ void adj_init_out(DevCase<T> c, AdjFields<T> F, double* __restrict__ grad_rho0)
 {
     NodeIdx n;
     if (!node_of(c.nx, c.ny, n)) return;
-    grad_rho0[n.i] = F.rb[n.i] + lapT_at(F.Lb, n);
+    grad_rho0[n.i] = (double)(F.rb[n.i] + lapT_at(F.Lb, n));
 }
 
 // acc[k] += fixed-order fold of field k of the partials (k = 0: mass slot, 1: ke slot)

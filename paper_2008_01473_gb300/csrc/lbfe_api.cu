@@ -870,7 +870,9 @@ struct AdjLayout {
 
 constexpr int kAdjFields = 29;
 
-AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K)
+// es: bytes of the handle's arithmetic type (states, adjoint populations and
+// fields); rho0, s_final and the density gradient stay FP64.
+AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K, size_t es)
 {
     AdjLayout L;
     L.K = K;
@@ -887,11 +889,11 @@ AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K)
     };
     L.cases = take(sizeof(DevCase<double>));
     L.items = take(L.nitems * sizeof(Item));
-    L.ckpt = take((size_t)L.ncp * L.state * sizeof(double));
-    L.seg = take((size_t)(K + 1) * L.state * sizeof(double));
-    L.lam = take((size_t)kQ * L.N * sizeof(double));
-    L.lamd = take((size_t)kQ * L.N * sizeof(double));
-    L.fields = take((size_t)kAdjFields * align_up(L.N * sizeof(double), kAlign));
+    L.ckpt = take((size_t)L.ncp * L.state * es);
+    L.seg = take((size_t)(K + 1) * L.state * es);
+    L.lam = take((size_t)kQ * L.N * es);
+    L.lamd = take((size_t)kQ * L.N * es);
+    L.fields = take((size_t)kAdjFields * align_up(L.N * es, kAlign));
     L.partials = take(L.parts * sizeof(Partial));
     L.acc = take(8 * sizeof(double));
     L.rho0 = take(L.N * sizeof(double));
@@ -908,73 +910,84 @@ int64_t adj_default_K(int64_t nsteps)
     return K;
 }
 
-template <int SCHEME, int EOS>
+// T: the handle's arithmetic type. FP32 runs the forward and the recompute
+// with the FP32 step kernel (plain loads, deviation storage about rho_ref)
+// and the reverse sweep in FP32; the loss and the kappa / T partials are
+// summed in FP64 either way.
+template <typename T, int SCHEME, int EOS>
 lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_t* ws, const double* s_fin,
-                      int64_t nsteps, int64_t u_from)
+                      int64_t nsteps, int64_t u_from, double rho_ref)
 {
     cudaStream_t st = h->stream;
-    const DevCase<double> cd = dev_case<double>(c, 0, 0.0);
-    const DevCase<double>* dcase = reinterpret_cast<const DevCase<double>*>(ws + L.cases);
+    const DevCase<T> cd = dev_case<T>(c, 0, rho_ref);
+    const DevCase<T>* dcase = reinterpret_cast<const DevCase<T>*>(ws + L.cases);
     const Item* items = reinterpret_cast<const Item*>(ws + L.items);
-    double* ckpt = reinterpret_cast<double*>(ws + L.ckpt);
-    double* seg = reinterpret_cast<double*>(ws + L.seg);
-    double* lam = reinterpret_cast<double*>(ws + L.lam);
-    double* lamd = reinterpret_cast<double*>(ws + L.lamd);
+    T* ckpt = reinterpret_cast<T*>(ws + L.ckpt);
+    T* seg = reinterpret_cast<T*>(ws + L.seg);
+    T* lam = reinterpret_cast<T*>(ws + L.lam);
+    T* lamd = reinterpret_cast<T*>(ws + L.lamd);
     Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
     double* acc = reinterpret_cast<double*>(ws + L.acc);
     const double* rho0 = reinterpret_cast<const double*>(ws + L.rho0);
     double* grad = reinterpret_cast<double*>(ws + L.grad);
-    AdjFields F;
-    double** fp = reinterpret_cast<double**>(&F);
+    AdjFields<T> F;
+    T** fp = reinterpret_cast<T**>(&F);
     for (int k = 0; k < kAdjFields; ++k)
-        fp[k] = reinterpret_cast<double*>(ws + L.fields + k * align_up(L.N * sizeof(double), kAlign));
+        fp[k] = reinterpret_cast<T*>(ws + L.fields + k * align_up(L.N * sizeof(T), kAlign));
     const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
     const int nitems = (int)L.nitems;
+    const T R = (T)c.R;
     auto state = [&](int64_t k) { return ckpt + k * L.state; };
-    auto step = [&](const double* in, double* out) {
-        return launch_step_f64(SCHEME, c.collision, EOS, false, nitems, st, in, out, dcase, items, h->status());
+    auto step = [&](const T* in, T* out) {
+        if constexpr (sizeof(T) == 4)
+            return launch_step_f32(SCHEME, c.collision, EOS, false, false, kStepThreads, nitems, st, in, out, dcase,
+                                   items, h->status());
+        else
+            return launch_step_f64(SCHEME, c.collision, EOS, false, nitems, st, in, out, dcase, items, h->status());
     };
+    // rho0 in T (the check partials land in parts and are not used)
+    auto load_rho0 = [&]() { rho0_kernel<T><<<grd, blk, 0, st>>>(c.nx, c.eos, c.b, rho0, F.rho, parts); };
     // forward: f(0), then the checkpoints every K steps
-    cudaMemcpyAsync(F.rho, rho0, L.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    mu_field_kernel<double, EOS><<<grd, blk, 0, st>>>(cd, F.rho, F.mu);
-    init_kernel<double, SCHEME, double><<<grd, blk, 0, st>>>(cd, cd, F.rho, nullptr, nullptr, F.mu, state(0));
-    const double* cur = state(0);
+    load_rho0();
+    mu_field_kernel<T, EOS><<<grd, blk, 0, st>>>(cd, F.rho, F.mu);
+    init_kernel<T, SCHEME, T><<<grd, blk, 0, st>>>(cd, cd, F.rho, nullptr, nullptr, F.mu, state(0));
+    const T* cur = state(0);
     for (int64_t n = 0; n < nsteps; ++n) {
-        double* out = ((n + 1) % L.K == 0) ? state((n + 1) / L.K) : (cur == seg ? seg + L.state : seg);
+        T* out = ((n + 1) % L.K == 0) ? state((n + 1) / L.K) : (cur == seg ? seg + L.state : seg);
         if (step(cur, out) != cudaSuccess) return h->cuda(cudaGetLastError(), "adjoint forward");
         cur = out;
     }
     cudaMemsetAsync(acc, 0, 4 * sizeof(double), st);
-    cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(double), st);
+    cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(T), st);
     // reverse sweep over segments [s, e], states s+1..e rebuilt into seg
     for (int64_t s = (nsteps / L.K) * L.K, e = nsteps; s >= 0; e = s - 1, s -= L.K) {
         for (int64_t n = s + 1; n <= e; ++n) {
-            const double* in = n - 1 == s ? state(s / L.K) : seg + (n - 1 - s) * L.state;
+            const T* in = n - 1 == s ? state(s / L.K) : seg + (n - 1 - s) * L.state;
             if (step(in, seg + (n - s) * L.state) != cudaSuccess)
                 return h->cuda(cudaGetLastError(), "adjoint recompute");
         }
         for (int64_t n = e; n >= s; --n) {
-            const double* fn = n == s ? state(s / L.K) : seg + (n - s) * L.state;
-            pull_moments_kernel<double, double><<<grd, blk, 0, st>>>(cd, fn, F.rho, F.jx, F.jy);
-            adj_fwd_mu<EOS><<<grd, blk, 0, st>>>(cd, F);
-            adj_fwd_force<SCHEME><<<grd, blk, 0, st>>>(cd, F, n >= u_from ? 1.0 : 0.0, n == nsteps ? s_fin : nullptr,
-                                                       parts);
+            const T* fn = n == s ? state(s / L.K) : seg + (n - s) * L.state;
+            pull_moments_kernel<T, T><<<grd, blk, 0, st>>>(cd, fn, F.rho, F.jx, F.jy);
+            adj_fwd_mu<T, EOS><<<grd, blk, 0, st>>>(cd, F);
+            adj_fwd_force<T, SCHEME><<<grd, blk, 0, st>>>(cd, F, n >= u_from ? 1.0 : 0.0,
+                                                          n == nsteps ? s_fin : nullptr, parts);
             adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 0, nullptr);
-            if (SCHEME == 1) adj_fwd_corr<<<grd, blk, 0, st>>>(cd, F);
-            adj_collide<SCHEME><<<grd, blk, 0, st>>>(cd, F, lam, n < nsteps, n >= u_from, lamd);
-            adj_force<SCHEME><<<grd, blk, 0, st>>>(cd, F);
-            adj_mu<SCHEME, EOS><<<grd, blk, 0, st>>>(cd, c.R, F, parts);
+            if (SCHEME == 1) adj_fwd_corr<T><<<grd, blk, 0, st>>>(cd, F);
+            adj_collide<T, SCHEME><<<grd, blk, 0, st>>>(cd, F, lam, n < nsteps, n >= u_from, lamd);
+            adj_force<T, SCHEME><<<grd, blk, 0, st>>>(cd, F);
+            adj_mu<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, parts);
             adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
-            adj_lambda<<<grd, blk, 0, st>>>(cd, F, lamd, n == nsteps ? s_fin : nullptr, lam);
+            adj_lambda<T><<<grd, blk, 0, st>>>(cd, F, lamd, n == nsteps ? s_fin : nullptr, lam);
         }
         if (s == 0) break;
     }
     // initial populations
-    cudaMemcpyAsync(F.rho, rho0, L.N * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    adj_fwd_mu<EOS><<<grd, blk, 0, st>>>(cd, F);
-    adj_init<SCHEME, EOS><<<grd, blk, 0, st>>>(cd, c.R, F, lam, parts);
+    load_rho0();
+    adj_fwd_mu<T, EOS><<<grd, blk, 0, st>>>(cd, F);
+    adj_init<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, lam, parts);
     adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
-    adj_init_out<<<grd, blk, 0, st>>>(cd, F, grad);
+    adj_init_out<T><<<grd, blk, 0, st>>>(cd, F, grad);
     return h->cuda(cudaGetLastError(), "adjoint kernels");
 }
 
@@ -988,7 +1001,7 @@ lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_
     if (!h || !bytes || case_id < 0 || case_id >= (int)h->cases.size() || nsteps < 0 || ckpt_every < 0)
         return LB_E_INVALID;
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
-    *bytes = adj_layout(h->cases[case_id], nsteps, K).total;
+    *bytes = adj_layout(h->cases[case_id], nsteps, K, h->prec == LB_FP32 ? sizeof(float) : sizeof(double)).total;
     return LB_OK;
 }
 
@@ -1000,13 +1013,13 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     if (case_id < 0 || case_id >= (int)h->cases.size() || !rho0 || nsteps < 0 || u_from < 0 || ckpt_every < 0 ||
         !loss || !grad_kappa || !grad_T)
         return h->fail(LB_E_INVALID, "lb_adjoint_step: bad arguments");
-    if (h->prec != LB_FP64) return h->fail(LB_E_INVALID, "lb_adjoint_step: needs an LB_FP64 handle");
     const lb_case& c = h->cases[case_id];
     if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
     if (c.scheme == LB_STANDARD_PT)
         return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of the pressure-tensor force form");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
-    const AdjLayout L = adj_layout(c, nsteps, K);
+    const bool f32 = h->prec == LB_FP32;
+    const AdjLayout L = adj_layout(c, nsteps, K, f32 ? sizeof(float) : sizeof(double));
     if (!d_ws || ((uintptr_t)d_ws % kAlign) != 0 || ws_bytes < L.total)
         return h->fail(LB_E_WORKSPACE, "lb_adjoint_step: workspace misaligned or smaller than lb_adjoint_workspace_bytes");
     uint8_t* ws = static_cast<uint8_t*>(d_ws);
@@ -1015,7 +1028,6 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const DevCase<double> cd = dev_case<double>(c, 0, 0.0);
     std::vector<Item> items;
     {
         const int ns = strips_of(c, kStepThreads);
@@ -1032,10 +1044,9 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     AdjLayout Lr = L;
     Lr.nitems = (int64_t)items.size();
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    lb_status s = h->cuda(cudaMemcpyAsync(ws + L.cases, &cd, sizeof cd, cudaMemcpyHostToDevice, st), "adjoint case");
-    if (s == LB_OK)
-        s = h->cuda(cudaMemcpyAsync(ws + L.items, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, st),
-                    "adjoint items");
+    lb_status s = h->cuda(cudaMemcpyAsync(ws + L.items, items.data(), items.size() * sizeof(Item),
+                                          cudaMemcpyHostToDevice, st),
+                          "adjoint items");
     if (s == LB_OK) s = h->cuda(cudaMemcpyAsync(ws + L.rho0, rho0, L.N * sizeof(double), kind, st), "adjoint rho0");
     const double* sfin = nullptr;
     if (s == LB_OK && s_final) {
@@ -1043,7 +1054,8 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
         sfin = reinterpret_cast<const double*>(ws + L.sfin);
     }
     if (s != LB_OK) return s;
-    // validate rho0 on the device
+    // validate rho0 on the device (its sum gives the FP32 deviation reference)
+    double rho_ref = 0.0;
     {
         Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
         double* acc = reinterpret_cast<double*>(ws + L.acc);
@@ -1057,13 +1069,25 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
         if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(st), "adjoint check");
         if (s != LB_OK) return s;
         if (chk[4] != 0.0) return h->fail(LB_E_INVALID, "lb_adjoint_step: rho0 must be finite, > 0 and inside the EOS domain");
+        rho_ref = c.rho_ref > 0 ? c.rho_ref : chk[0] / (double)L.N;  // FP32 deviation reference
     }
+    // the one-case parameter record in the handle's type
+    if (f32) {
+        const DevCase<float> cd = dev_case<float>(c, 0, rho_ref);
+        s = h->cuda(cudaMemcpyAsync(ws + L.cases, &cd, sizeof cd, cudaMemcpyHostToDevice, st), "adjoint case");
+    } else {
+        const DevCase<double> cd = dev_case<double>(c, 0, 0.0);
+        s = h->cuda(cudaMemcpyAsync(ws + L.cases, &cd, sizeof cd, cudaMemcpyHostToDevice, st), "adjoint case");
+    }
+    if (s != LB_OK) return s;
+#define LBFE_ADJ(T, S, E) adjoint_run<T, S, E>(h, c, Lr, ws, sfin, nsteps, u_from, f32 ? rho_ref : 0.0)
     if (c.scheme == LB_IMPROVED)
-        s = c.eos == LB_VDW ? adjoint_run<1, 0>(h, c, Lr, ws, sfin, nsteps, u_from)
-                            : adjoint_run<1, 1>(h, c, Lr, ws, sfin, nsteps, u_from);
+        s = f32 ? (c.eos == LB_VDW ? LBFE_ADJ(float, 1, 0) : LBFE_ADJ(float, 1, 1))
+                : (c.eos == LB_VDW ? LBFE_ADJ(double, 1, 0) : LBFE_ADJ(double, 1, 1));
     else
-        s = c.eos == LB_VDW ? adjoint_run<0, 0>(h, c, Lr, ws, sfin, nsteps, u_from)
-                            : adjoint_run<0, 1>(h, c, Lr, ws, sfin, nsteps, u_from);
+        s = f32 ? (c.eos == LB_VDW ? LBFE_ADJ(float, 0, 0) : LBFE_ADJ(float, 0, 1))
+                : (c.eos == LB_VDW ? LBFE_ADJ(double, 0, 0) : LBFE_ADJ(double, 0, 1));
+#undef LBFE_ADJ
     if (s != LB_OK) return s;
     double acc[4];
     s = h->cuda(cudaMemcpyAsync(acc, ws + L.acc, sizeof acc, cudaMemcpyDeviceToHost, st), "adjoint results");

@@ -248,7 +248,8 @@ class Lattice:
     def adjoint(self, case_id: int, rho0, nsteps: int, u_from: int, s_final=None, ckpt_every: int = 0):
         """Loss L = sum_{n >= u_from} sum |u^n|^2 + sum s_final rho^N of a run from
         rho0, and (L, dL/drho0, dL/dkappa, dL/dT) by the library's adjoint
-        (LB_FP64 handles). Arrays on the host or CUDA tensors (results follow rho0)."""
+        (FP64 handles in FP64, FP32 handles in FP32). Arrays on the host or CUDA
+        tensors (results follow rho0)."""
         torch = self._torch
         sh = self._shape(case_id)
         nb = C.c_size_t()
