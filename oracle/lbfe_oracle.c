@@ -829,7 +829,11 @@ int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u
     const int64_t ncp = nsteps / K + 1;
     double* cp = malloc((size_t)ncp * Q * N * sizeof(double));
     double* f = malloc((size_t)Q * N * sizeof(double));
-    if (orc_init(c, rho0, NULL, NULL, f) != 0) return -1;
+    if (orc_init(c, rho0, NULL, NULL, f) != 0) {
+        free(cp);
+        free(f);
+        return -1;
+    }
     /* forward: loss and checkpoints of the states 0, K, 2K, ... */
     double L = 0.0;
     orc_fwd w;
