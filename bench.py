@@ -313,8 +313,9 @@ def _batched_accuracy(lbfe, cases, rhos, steps):
     run in FP64 (whose step is checked against the FP64 oracle by the GPU
     tests) for the same number of steps: pressure jump p(rho_in) -
     p(rho_out) (centre disc of radius r0/4, corner squares of side L/8),
-    equimolar radius and max |u|. Returns the worst relative errors and the
-    largest spurious currents of both runs."""
+    equimolar radius and max |u|; both runs' densities also against the
+    Young-Laplace prediction of Eq. 32 (host surface tension and inversion).
+    Returns the worst relative errors and the largest spurious currents."""
     import numpy as np
 
     lats = {}
@@ -325,6 +326,7 @@ def _batched_accuracy(lbfe, cases, rhos, steps):
         lat.step(steps)
         lats[prec] = lat
     err_dp, err_r, u = 0.0, 0.0, {}
+    eq32 = {lbfe.FP32: [0.0, 0.0], lbfe.FP64: [0.0, 0.0]}  # worst |rho / rho_Eq.32 - 1|: gas, liquid
     for prec, lat in lats.items():  # max |u| of every case, reduced on the GPU
         u[prec] = float(lat.reductions()[0][:, 2].max())
     for i, c in enumerate(cases):
@@ -338,12 +340,18 @@ def _batched_accuracy(lbfe, cases, rhos, steps):
                                                    ("rect", L - s, L - s, 2 * s, 2 * s), ("rect", 0, 0, L, L)])
             dp[prec] = _vdw_p(rin, c.T) - _vdw_p(rout, c.T)
             req[prec] = np.sqrt((rbar - rout) * L * L / (np.pi * (rin - rout)))
+            sig = lbfe.surface_tension(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], c.T, c.kappa)
+            g_th, l_th = lbfe.young_laplace(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], c.T, sig, req[prec])
+            eq32[prec][0] = max(eq32[prec][0], abs(rout / g_th - 1))
+            eq32[prec][1] = max(eq32[prec][1], abs(rin / l_th - 1))
         err_dp = max(err_dp, abs(dp[lbfe.FP32] / dp[lbfe.FP64] - 1))
         err_r = max(err_r, abs(req[lbfe.FP32] / req[lbfe.FP64] - 1))
     for lat in lats.values():
         lat.close()
     return {"cases": len(cases), "steps": steps, "max_rel_err_pressure_jump": err_dp,
-            "max_rel_err_equimolar_radius": err_r, "max_u_fp32": u[lbfe.FP32], "max_u_fp64": u[lbfe.FP64]}
+            "max_rel_err_equimolar_radius": err_r, "max_u_fp32": u[lbfe.FP32], "max_u_fp64": u[lbfe.FP64],
+            "vs_eq32_theory": {"fp32_gas": eq32[lbfe.FP32][0], "fp32_liquid": eq32[lbfe.FP32][1],
+                               "fp64_gas": eq32[lbfe.FP64][0], "fp64_liquid": eq32[lbfe.FP64][1]}}
 
 
 def _batched_r0(rho0):

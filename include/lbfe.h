@@ -221,6 +221,18 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
  * Maxwell equal-area coexistence densities rho_g < rho_l (Sec. IV A; Table II
  * lists the vdW values). eos = LB_VDW or LB_CS. */
 lb_status lb_critical(int32_t eos, double a, double b, double R, double* Tc, double* rho_c);
+
+/* Flat-interface surface tension of the square-gradient free energy (Eq. 1)
+ * at coexistence: sigma = integral over rho_g..rho_l of
+ * sqrt(2 kappa (E_f(rho) - mu rho + p)), FP64 quadrature. Needs T < T_c. */
+lb_status lb_surface_tension(int32_t eos, double a, double b, double R, double T, double kappa, double* sigma);
+
+/* Eq. 32: gas and liquid densities around a circular droplet of radius r
+ * from the Young-Laplace pressures p_sat + rho_sat / (rho_l_sat - rho_g_sat)
+ * sigma / r inverted on each branch of p_EOS. LB_E_INVALID if T >= T_c or
+ * the gas pressure exceeds the gas spinodal (droplet too small). */
+lb_status lb_young_laplace(int32_t eos, double a, double b, double R, double T, double sigma, double r,
+                           double* rho_g, double* rho_l);
 lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double* rho_g,
                      double* rho_l);
 

@@ -144,6 +144,34 @@ class EOS:
         return float(rg), float(rl)
 
 
+    def surface_tension(self, T: float, kappa: float) -> float:
+        """Flat-interface tension of the square-gradient free energy (Eq. 1):
+        sigma = int_{rho_g}^{rho_l} sqrt(2 kappa (E_f - mu rho + p)) drho at
+        coexistence (Maxwell densities, their mu and p)."""
+        from scipy.integrate import quad
+
+        rg, rl = self.maxwell(T)
+        mu, p = float(self.mu(rg, T)), float(self.p(rg, T))
+        f = lambda r: np.sqrt(max(2.0 * kappa * float(self.Ef(r, T) - mu * r + p), 0.0))
+        return float(quad(f, rg, rl, limit=400, epsabs=0.0, epsrel=1e-12)[0])
+
+    def young_laplace(self, T: float, sigma: float, r: float) -> tuple[float, float]:
+        """(rho_g, rho_l) around a circular droplet of radius r (Eq. 32): the
+        phase pressures p_sat + rho_sat / (rho_l_sat - rho_g_sat) sigma / r,
+        each inverted on its branch of p_EOS."""
+        rg, rl = self.maxwell(T)
+        p0 = float(self.p(rg, T))
+        pl = p0 + rl / (rl - rg) * sigma / r
+        pg = p0 + rg / (rl - rg) * sigma / r
+        s1, s2 = self.spinodals(T)
+        hi = s2
+        while self.p(hi, T) < pl:
+            hi = 0.5 * (hi + self.rho_max)
+        g = brentq(lambda q: self.p(q, T) - pg, rg, s1, xtol=1e-300, rtol=1e-15)
+        l = brentq(lambda q: self.p(q, T) - pl, s2, hi, xtol=1e-300, rtol=1e-15)
+        return float(g), float(l)
+
+
 # Parameter sets used with the paper's experiments and the synthetic workloads.
 def vdw_paper() -> EOS:
     """Sec. IV A: a = 9/392, b = 2/21, R = 1 (kappa = 0.02)."""

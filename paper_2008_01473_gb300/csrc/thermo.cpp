@@ -88,6 +88,20 @@ double bisect(G g, double lo, double hi)
     return 0.5 * (lo + hi);
 }
 
+// spinodal densities s1 < rho_c < s2 at T < T_c (roots of mu'(rho) = 0)
+void spinodals(const Eos& e, double T, double rc, double* s1, double* s2)
+{
+    const double target = 2.0 * e.a / (e.R * T);  // h'(rho) on the spinodal
+    const double rmax = e.rho_max();
+    // h' decreases to its minimum at rc, then increases
+    double lo = rc;
+    while (e.dh(lo) < target) lo *= 0.5;
+    *s1 = bisect([&](double r) { return e.dh(r) - target; }, lo, rc);
+    double hi = rc;
+    while (e.dh(hi) < target) hi = 0.5 * (hi + rmax);
+    *s2 = bisect([&](double r) { return e.dh(r) - target; }, rc, hi);
+}
+
 }  // namespace
 
 extern "C" lb_status lb_critical(int32_t eos, double a, double b, double R, double* Tc, double* rho_c)
@@ -108,15 +122,9 @@ extern "C" lb_status lb_maxwell(int32_t eos, double a, double b, double R, doubl
     const double rc = critical_rho(e);
     const double Tc = 2.0 * a / (R * e.dh(rc));
     if (!(T < Tc)) return LB_E_INVALID;
-    const double target = 2.0 * a / (R * T);  // h'(rho) on the spinodal
     const double rmax = e.rho_max();
-    // spinodals: h' decreases to its minimum at rc, then increases
-    double lo = rc;
-    while (e.dh(lo) < target) lo *= 0.5;
-    const double s1 = bisect([&](double r) { return e.dh(r) - target; }, lo, rc);
-    double hi = rc;
-    while (e.dh(hi) < target) hi = 0.5 * (hi + rmax);
-    const double s2 = bisect([&](double r) { return e.dh(r) - target; }, rc, hi);
+    double s1, s2;
+    spinodals(e, T, rc, &s1, &s2);
     const double mu_lo = e.mu(s2, T), mu_hi = e.mu(s1, T);
     auto gas = [&](double m) {
         double l = s1;
@@ -153,5 +161,65 @@ extern "C" lb_status lb_maxwell(int32_t eos, double a, double b, double R, doubl
     }
     *rho_g = g;
     *rho_l = l;
+    return LB_OK;
+}
+
+// Flat-interface tension of the square-gradient free energy (Eq. 1):
+// sigma = int_{rho_g}^{rho_l} sqrt(2 kappa (E_f - mu rho + p)) drho at the
+// Maxwell coexistence, by composite 5-point Gauss-Legendre quadrature over
+// 4096 panels (the integrand vanishes linearly at both ends).
+extern "C" lb_status lb_surface_tension(int32_t eos, double a, double b, double R, double T, double kappa,
+                                        double* sigma)
+{
+    if (!sigma || !(kappa > 0) || !std::isfinite(kappa)) return LB_E_INVALID;
+    double g, l;
+    const lb_status s = lb_maxwell(eos, a, b, R, T, &g, &l);
+    if (s != LB_OK) return s;
+    const Eos e{eos, a, b, R};
+    const double mu = e.mu(g, T), p = e.p(g, T);
+    auto f = [&](double r) {
+        const double w = e.Ef(r, T) - mu * r + p;
+        return w > 0.0 ? std::sqrt(2.0 * kappa * w) : 0.0;
+    };
+    // 5-point Gauss-Legendre nodes and weights on [-1, 1]
+    const double x[5] = {0.0, 0.5384693101056831, -0.5384693101056831, 0.9061798459386640, -0.9061798459386640};
+    const double w[5] = {0.5688888888888889, 0.4786286704993665, 0.4786286704993665, 0.2369268850561891,
+                         0.2369268850561891};
+    constexpr int kPanels = 4096;
+    const double hw = 0.5 * (l - g) / kPanels;
+    double sum = 0.0;
+    for (int k = 0; k < kPanels; ++k) {
+        const double c = g + (2 * k + 1) * hw;
+        double ps = 0.0;
+        for (int q = 0; q < 5; ++q) ps += w[q] * f(c + hw * x[q]);
+        sum += ps * hw;
+    }
+    *sigma = sum;
+    return LB_OK;
+}
+
+// Eq. 32: the phase pressures around a circular droplet of radius r,
+// p_sat + rho_sat / (rho_l_sat - rho_g_sat) sigma / r, each turned back into
+// a density on its own branch of p_EOS (increasing on (rho_g_sat, s1) and
+// above s2) by bisection.
+extern "C" lb_status lb_young_laplace(int32_t eos, double a, double b, double R, double T, double sigma,
+                                      double r, double* rho_g, double* rho_l)
+{
+    if (!rho_g || !rho_l || !(sigma >= 0) || !(r > 0) || !std::isfinite(sigma) || !std::isfinite(r))
+        return LB_E_INVALID;
+    double g, l;
+    const lb_status s = lb_maxwell(eos, a, b, R, T, &g, &l);
+    if (s != LB_OK) return s;
+    const Eos e{eos, a, b, R};
+    const double rc = critical_rho(e);
+    double s1, s2;
+    spinodals(e, T, rc, &s1, &s2);
+    const double p0 = e.p(g, T);
+    const double pl = p0 + l / (l - g) * sigma / r, pg = p0 + g / (l - g) * sigma / r;
+    if (!(e.p(s1, T) > pg)) return LB_E_INVALID;  // droplet too small: no gas state at that pressure
+    *rho_g = bisect([&](double q) { return e.p(q, T) - pg; }, g, s1);
+    double hi = s2;
+    while (e.p(hi, T) < pl) hi = 0.5 * (hi + e.rho_max());
+    *rho_l = bisect([&](double q) { return e.p(q, T) - pl; }, s2, hi);
     return LB_OK;
 }

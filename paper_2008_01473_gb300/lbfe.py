@@ -95,6 +95,8 @@ def lib() -> C.CDLL:
         L.lb_load.argtypes = [vp, i32, vp, sz]
         L.lb_critical.argtypes = [i32, C.c_double, C.c_double, C.c_double, dp, dp]
         L.lb_maxwell.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
+        L.lb_surface_tension.argtypes = [i32] + [C.c_double] * 5 + [dp]
+        L.lb_young_laplace.argtypes = [i32] + [C.c_double] * 6 + [dp, dp]
         L.lb_fields_static.argtypes = [cp, i32, vp, C.c_double, vp, vp, vp, vp, vp, vp]
         L.lb_adjoint_workspace_bytes.argtypes = [vp, i32, i64, i32, C.POINTER(sz)]
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
@@ -107,7 +109,8 @@ def lib() -> C.CDLL:
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means",
+                     "lb_surface_tension", "lb_young_laplace"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -124,6 +127,20 @@ def critical(eos: int, a: float, b: float, R: float = 1.0) -> tuple[float, float
     tc, rc = C.c_double(), C.c_double()
     _check(lib().lb_critical(eos, a, b, R, C.byref(tc), C.byref(rc)), what="lb_critical")
     return tc.value, rc.value
+
+
+def surface_tension(eos: int, a: float, b: float, R: float, T: float, kappa: float) -> float:
+    """Flat-interface square-gradient tension at coexistence (host solver)."""
+    out = C.c_double()
+    _check(lib().lb_surface_tension(eos, a, b, R, T, kappa, C.byref(out)), what="lb_surface_tension")
+    return out.value
+
+
+def young_laplace(eos: int, a: float, b: float, R: float, T: float, sigma: float, r: float) -> tuple[float, float]:
+    """(rho_g, rho_l) around a droplet of radius r by Eq. 32 (host solver)."""
+    g, l = C.c_double(), C.c_double()
+    _check(lib().lb_young_laplace(eos, a, b, R, T, sigma, r, C.byref(g), C.byref(l)), what="lb_young_laplace")
+    return g.value, l.value
 
 
 def maxwell(eos: int, a: float, b: float, R: float, T: float) -> tuple[float, float]:

@@ -66,6 +66,22 @@ def test_host_maxwell_matches_oracle(lib, eos, t):
     assert abs(rg / rg_o - 1) < 1e-11 and abs(rl / rl_o - 1) < 1e-12
 
 
+@pytest.mark.parametrize("t", [0.9, 0.8, 0.7])
+@pytest.mark.parametrize("eos", ["vdw", "cs"])
+def test_host_tension_and_young_laplace_match_oracle(lib, eos, t):
+    """The library's surface tension (Gauss-Legendre) and Eq. 32 densities
+    against the oracle's (adaptive quadrature, brentq)."""
+    e = thermo.vdw_paper() if eos == "vdw" else thermo.EOS(thermo.CS, 9 / 392, 9 / 98)
+    T, _, _ = thermo.maxwell_reduced(e, t)
+    sig = lbfe.surface_tension(e.kind, e.a, e.b, e.R, T, 0.02)
+    sig_o = e.surface_tension(T, 0.02)
+    assert abs(sig / sig_o - 1) < 1e-9
+    for r in (12.0, 25.0, 40.0):
+        g, l = lbfe.young_laplace(e.kind, e.a, e.b, e.R, T, sig, r)
+        g_o, l_o = e.young_laplace(T, sig_o, r)
+        assert abs(g / g_o - 1) < 1e-9 and abs(l / l_o - 1) < 1e-9
+
+
 def test_host_maxwell_rejects_supercritical(lib):
     e = thermo.vdw_paper()
     with pytest.raises(lbfe.LBError):
