@@ -556,3 +556,29 @@ def test_window_means_match_exported_fields(precision):
     with pytest.raises(lbfe.LBError):
         lat.window_means(0, [("disc", 10, 10, 31.0)])
     lat.close()
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP64, lbfe.FP32])
+def test_droplet_densities_match_eq32(precision):
+    """Sec. IV B: improved-scheme droplets (vdW 0.8 T_c, radii 16 and 24, one
+    handle) settle at the Young-Laplace densities of Eq. 32 within 0.25 %
+    (the paper's figure is 0.23 %), with rho_in / rho_out from the GPU's FP64
+    window means and sigma from the host solver."""
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    specs = ((64, 16.0), (96, 24.0))
+    cases = [lbfe.Case(nx=L, ny=L, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
+                       kappa=0.02, tau_v=1.0) for L, _ in specs]
+    lat = lbfe.Lattice(cases, precision=precision)
+    for i, (L, r0) in enumerate(specs):
+        lat.init_fields(i, inputs.droplet(L, L, r0, rl, rg))
+    lat.step(8000)
+    sig = lbfe.surface_tension(lbfe.VDW, e.a, e.b, 1.0, T, 0.02)
+    for i, (L, r0) in enumerate(specs):
+        s = L // 8
+        rin, rout, rbar = lat.window_means(i, [("disc", L / 2, L / 2, r0 / 4), ("rect", L - s, L - s, 2 * s, 2 * s),
+                                               ("rect", 0, 0, L, L)])
+        r = np.sqrt((rbar - rout) * L * L / (np.pi * (rin - rout)))
+        g_th, l_th = lbfe.young_laplace(lbfe.VDW, e.a, e.b, 1.0, T, sig, r)
+        assert abs(rout / g_th - 1) < 2.5e-3 and abs(rin / l_th - 1) < 2.5e-3, (i, rout, g_th, rin, l_th)
+    lat.close()
