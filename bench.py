@@ -255,7 +255,7 @@ def run_gpu(args):
                        "l2": f"populations {BYTES_PER_NODE[dtype] * nodes / 1e9:.2f} GB per step vs 129 MB L2 "
                              "(no flush)",
                        "stable": stable,
-                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items,
+                       "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows), "items": n_items,
                                     "narrow_blocks": narrow}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
@@ -412,7 +412,7 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched uneven droplets: " + (batched_cases.__doc__ or "").split(":")[1].strip(),
                        "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum()),
-                       "worklist": {"segment_rows": seg_rows or "slot share", "items": n_items,
+                       "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows), "items": n_items,
                                     "narrow_blocks": narrow}},
             "fp32_vs_fp64": acc,  # every 8th case of the batch
             "per_case_launches": {"value": round(nodes * args.steps / (per_case_ms * 1e-3) / 1e6, 1),

@@ -124,7 +124,8 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
  * the current populations and write only the buffer the next step
  * overwrites, so the state and every result are unchanged; the choice
  * affects speed only). LBFE_SEG_ROWS=n before lb_create fixes the segment
- * size instead (0: a share of the GPU's block slots per case), and
+ * size instead (0: a share of the GPU's block slots per case; -1: the same
+ * share, filled with up to four narrower strips per case), and
  * LBFE_PAIR_NARROW=0|1 the narrow-block choice. Groups run as parallel
  * branches that fork from and join the handle's stream. Runs of 8
  * steps replay a CUDA graph captured on the first such call (on a private
@@ -133,7 +134,8 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
  * that the autotuning call synchronises the stream. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
 
-/* The work-list in use: rows per segment (0: slot-share rule), item count,
+/* The work-list in use: rows per segment (0: slot-share rule, -1: the
+ * filled slot-share rule), item count,
  * and whether narrow blocks (64 threads, 128 columns) run the lattices that
  * fit them with fewer idle lanes. Before the first lb_step it is the untuned
  * default. Any pointer may be NULL. */

@@ -255,11 +255,28 @@ void build_items(lb_handle* h)
         Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
         for (int i : members) {
             const lb_case& c = h->cases[i];
-            const int ns = strips_of(c, width);
+            int ns = strips_of(c, width);
             const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
             const double share = slots * ((double)c.nx * c.ny) / nodes;
+            const int max_seg = std::max(1, c.ny / kMinRows);
             int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows : (int)std::floor(share / ns);
-            nseg = std::min(std::max(1, nseg), std::max(1, c.ny / kMinRows));
+            if (seg_rows < 0) {
+                // slot share, filled: up to four more (narrower) strips when
+                // strips x segments then comes closer to the case's share
+                int best = std::min(std::max(1, nseg), max_seg) * ns;
+                // never more strips than the workspace's item table allows
+                // for the case (strips of the narrowest block, see max_items_of)
+                const int m_max = std::min({ns + 4, c.nx / q, strips_of(c, kMinBlockThreads)});
+                for (int m = ns + 1; m <= m_max; ++m) {
+                    const int sm = std::min(std::max(1, (int)std::floor(share / m)), max_seg);
+                    if (sm * m > best && sm * m <= std::max(share, (double)ns)) {
+                        best = sm * m;
+                        ns = m;
+                        nseg = sm;
+                    }
+                }
+            }
+            nseg = std::min(std::max(1, nseg), max_seg);
             for (int k = 0; k < ns; ++k) {
                 const int x0 = q * (int)((int64_t)(c.nx / q) * k / ns);
                 const int x1 = q * (int)((int64_t)(c.nx / q) * (k + 1) / ns);
@@ -297,6 +314,8 @@ void build_items(lb_handle* h)
 
 lb_status upload_items(lb_handle* h)
 {
+    if ((int64_t)h->items.size() > h->L.max_items)
+        return h->fail(LB_E_STATE, "work-list larger than the workspace's item table");
     return h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
                                    cudaMemcpyHostToDevice, h->stream),
                    "upload items");
@@ -437,7 +456,7 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
         h->tma_threads = (v == 128 || v == 256) ? v : 0;
     }
     if (const char* p = std::getenv("LBFE_SEG_ROWS")) {
-        h->seg_rows = std::max(0, std::atoi(p));
+        h->seg_rows = std::max(-1, std::atoi(p));
         h->autotune = false;
     }
     if (const char* p = std::getenv("LBFE_PAIR_NARROW")) {
@@ -580,7 +599,7 @@ static lb_status autotune(lb_handle* h)
 {
     // candidates: row-segment rule x (narrow packed blocks off, on); the
     // second half only when some lattice prefers narrow blocks
-    static const int segs[] = {0, 256, 128, 64, 32, 16};
+    static const int segs[] = {0, -1, 256, 128, 64, 32, 16};
     constexpr int kSegs = (int)(sizeof segs / sizeof segs[0]);
     bool any_narrow = false;
     if (h->prec == LB_FP32 && h->path != 1 && h->tma_threads == 0 && !h->narrow_fixed)
