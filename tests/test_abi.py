@@ -48,6 +48,11 @@ def test_workspace_validation(lib):
         arr = (lbfe._CCase * 1)(c.cstruct())
         assert lib.lb_workspace_bytes(arr, 1, lbfe.FP32, C.byref(nb)) == 1, bad
     assert lib.lb_workspace_bytes(arr, 0, lbfe.FP32, C.byref(nb)) == 1
+    # largest lattice: 9 ny pitch elements must stay below 2^31 (32-bit offsets)
+    for ny, st in ((14563, 0), (14564, 1)):
+        c = lbfe.Case(**{**ok.__dict__, "nx": 16384, "ny": ny})
+        arr = (lbfe._CCase * 1)(c.cstruct())
+        assert lib.lb_workspace_bytes(arr, 1, lbfe.FP32, C.byref(nb)) == st, ny
     h = C.c_void_p()
     arr = (lbfe._CCase * 1)(ok.cstruct())
     # misaligned / too small workspace is rejected before any device call

@@ -582,3 +582,38 @@ def test_droplet_densities_match_eq32(precision):
         g_th, l_th = lbfe.young_laplace(lbfe.VDW, e.a, e.b, 1.0, T, sig, r)
         assert abs(rout / g_th - 1) < 2.5e-3 and abs(rin / l_th - 1) < 2.5e-3, (i, rout, g_th, rin, l_th)
     lat.close()
+
+
+def test_fp32_largest_lattice_sampled():
+    """The largest lattice the library accepts: 16384 x 14563 (9 ny pitch just
+    below 2^31 elements, 238.6 M nodes, 17.2 GB of FP32 populations), improved
+    MRT in the benchmark's launch configuration. After one step from the
+    initial state, rho and u at 12 sampled nodes (the first and last rows and
+    columns among them) match the oracle's step of a 15 x 15 patch of the same
+    initial density to FP32 rounding."""
+    import torch
+
+    nx, ny = 16384, 14563
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    kw = dict(scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T, kappa=0.02, tau_v=0.8,
+              tau_e=1.0, tau_s=1.0, tau_q=1.1)
+    rho0 = inputs.spinodal(nx, ny, 0.5 * (rg + rl), 0.01, seed=2)
+    lat = lbfe.Lattice([lbfe.Case(nx=nx, ny=ny, **kw)], precision=lbfe.FP32)
+    lat.init_fields(0, rho0)
+    lat.step(1)
+    m = lat.moments(0, on_device=True)
+    rng = np.random.default_rng(5)
+    pts = [(0, 0), (ny - 1, nx - 1), (0, nx - 1), (ny - 1, 0)] + [tuple(rng.integers(0, (ny, nx))) for _ in range(8)]
+    oc = O.Case(nx=15, ny=15, **kw)
+    for (y, x) in pts:
+        patch = np.ascontiguousarray(rho0[np.arange(y - 7, y + 8) % ny][:, np.arange(x - 7, x + 8) % nx])
+        f = O.init(oc, patch)
+        O.step(oc, f, 1)
+        ref = O.fields(oc, f)
+        got = {k: float(m[k][y, x]) for k in ("rho", "ux", "uy")}
+        assert abs(got["rho"] - ref.rho[7, 7]) < 5e-6 * ref.rho[7, 7], (y, x)
+        assert abs(got["ux"] - ref.ux[7, 7]) < 5e-6 and abs(got["uy"] - ref.uy[7, 7]) < 5e-6, (y, x)
+    del m
+    lat.close()
+    torch.cuda.empty_cache()
