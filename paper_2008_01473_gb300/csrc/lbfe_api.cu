@@ -744,7 +744,8 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
         unstable |= bad;
     }
     if (timeout) {
-        cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream);
+        if (h->cuda(cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream), "clear status") != LB_OK)
+            return LB_E_CUDA;
         return h->fail(LB_E_TIMEOUT, "a bounded wait for a bulk copy gave up; results since the last "
                                      "lb_reductions are unreliable");
     }
@@ -976,8 +977,9 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
         if (step(cur, out) != cudaSuccess) return h->cuda(cudaGetLastError(), "adjoint forward");
         cur = out;
     }
-    cudaMemsetAsync(acc, 0, 4 * sizeof(double), st);
-    cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(T), st);
+    lb_status ms = h->cuda(cudaMemsetAsync(acc, 0, 4 * sizeof(double), st), "adjoint clear");
+    if (ms == LB_OK) ms = h->cuda(cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(T), st), "adjoint clear");
+    if (ms != LB_OK) return ms;
     // reverse sweep over segments [s, e], states s+1..e rebuilt into seg
     for (int64_t s = (nsteps / L.K) * L.K, e = nsteps; s >= 0; e = s - 1, s -= L.K) {
         for (int64_t n = s + 1; n <= e; ++n) {

@@ -234,11 +234,14 @@ def test_fp32_droplet_500_steps(scheme):
     assert max(np.abs(m["ux"] - ref.ux).max(), np.abs(m["uy"] - ref.uy).max()) < 2e-6
 
 
-def test_fp32_full_size_sampled_nodes():
+@pytest.mark.parametrize("precision", [lbfe.FP32, lbfe.FP64])
+def test_full_size_sampled_nodes(precision):
     """The 4096 x 4096 spinodal lattice in the benchmark's launch
-    configuration (improved, MRT, FP32): for 24 sampled nodes the oracle's
-    one-step update of a 13 x 13 patch around the node (whose centre depends
-    on nodes within 4 sites) matches the GPU's post-step populations."""
+    configuration (improved, MRT; FP32 as the default line, FP64 as the
+    --precision fp64 line, each with its autotuned work-list): for 24 sampled
+    nodes the oracle's one-step update of a 13 x 13 patch around the node
+    (whose centre depends on nodes within 4 sites) matches the GPU's
+    post-step populations (FP32: 3e-6 of max |f|; FP64: 1e-13)."""
     e = thermo.vdw_paper()
     T, rg, rl = thermo.maxwell_reduced(e, 0.8)
     n = 4096
@@ -246,7 +249,8 @@ def test_fp32_full_size_sampled_nodes():
                    kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
     oc = O.Case(nx=13, ny=13, scheme=O.IMPROVED, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02,
                 tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
-    lat = lbfe.Lattice([gc], precision=lbfe.FP32)
+    tol = 3e-6 if precision == lbfe.FP32 else 1e-13
+    lat = lbfe.Lattice([gc], precision=precision)
     lat.init_fields(0, inputs.spinodal(n, n, 0.5 * (rg + rl), 0.01, seed=3))
     lat.step(20)
     f0 = _gpu_pops(lat, 0)
@@ -261,7 +265,7 @@ def test_fp32_full_size_sampled_nodes():
         patch = np.ascontiguousarray(f0[:, ys][:, :, xs])
         O.step(oc, patch, 1)
         got = f1[:, y, x]
-        assert np.abs(got - patch[:, 6, 6]).max() < 3e-6 * np.abs(patch[:, 6, 6]).max(), (y, x)
+        assert np.abs(got - patch[:, 6, 6]).max() < tol * np.abs(patch[:, 6, 6]).max(), (y, x)
 
 
 @pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
