@@ -41,7 +41,8 @@ class _CCase(C.Structure):
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("T", C.c_double),
                 ("kappa", C.c_double), ("tau_v", C.c_double), ("tau_e", C.c_double),
                 ("tau_s", C.c_double), ("tau_q", C.c_double), ("pm_c0", C.c_double),
-                ("nu", C.c_double)]
+                ("nu", C.c_double), ("walls", C.c_int32), ("pad_", C.c_int32), ("wall_u", C.c_double),
+                ("rho_wall", C.c_double)]
 
 
 @dataclass
@@ -64,12 +65,16 @@ class Case:
     pm_c0: float = 1.0
     nu: float = 0.0
     flags: int = 0
+    walls: int = 0          # 1: moving no-slip walls below y = 0 and above y = ny - 1
+    wall_u: float = 0.0     # x velocity of both walls
+    rho_wall: float = 0.0   # density in the moving-wall term
     _c: _CCase = field(default=None, repr=False, compare=False)
 
     def cstruct(self) -> _CCase:
         return _CCase(self.nx, self.ny, self.scheme, self.collision, self.eos, self.flags,
                       self.a, self.b, self.R, self.T, self.kappa, self.tau_v, self.tau_e,
-                      self.tau_s, self.tau_q, self.pm_c0, self.nu)
+                      self.tau_s, self.tau_q, self.pm_c0, self.nu, self.walls, 0, self.wall_u,
+                      self.rho_wall)
 
     def thermo(self) -> thermo.EOS:
         return thermo.EOS(self.eos, self.a, self.b, self.R)

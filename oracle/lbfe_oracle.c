@@ -50,6 +50,7 @@ static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WA[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0; /* c_s^2, Eq. 13 */
+static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; /* e_OPP[a] = -e_a */
 
 /* Lallemand-Luo transformation matrix, rows = moments. */
 static const double MM[Q][Q] = {
@@ -79,6 +80,11 @@ typedef struct {
     double pm_c0;                      /* p_m = (c0 + mu_c)/3; the paper's c0 is 1 */
     double nu;                         /* > 0: constant kinematic viscosity, tau_v set per
                                           node from it (Sec. III below Eq. 29; Sec. II A) */
+    int32_t walls;                     /* 0: periodic in y; 1: no-slip walls half a node
+                                          below y = 0 and above y = ny - 1 (Sec. IV C) */
+    int32_t pad_;
+    double wall_u;                     /* x velocity of both walls */
+    double rho_wall;                   /* wall density of the moving-wall bounce-back term */
 } orc_case;
 
 /* ------------------------------------------------------------------ EOS */
@@ -117,14 +123,23 @@ double orc_pEOS(const orc_case* c, double rho) { return rho * orc_dEf(c, rho) - 
 
 static inline int wrap(int i, int n) { return ((i % n) + n) % n; }
 
-/* Eq. 17: grad_h phi = (1/c_s^2) sum_a w_a phi(x + e_a) e_a, periodic. */
-void orc_grad(int nx, int ny, const double* phi, double* gx, double* gy)
+/* Row of a stencil neighbour: periodic, or, with walls, the mirror image in
+ * the wall (row -1 reads row 0, row ny reads row ny - 1): every field is
+ * continued evenly across a wall (a zero normal gradient at the wall). */
+static inline int yrow(int walls, int y, int ny)
+{
+    if (!walls) return wrap(y, ny);
+    return y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+}
+
+/* Eq. 17: grad_h phi = (1/c_s^2) sum_a w_a phi(x + e_a) e_a. */
+static void grad_w(int nx, int ny, int walls, const double* phi, double* gx, double* gy)
 {
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double sx = 0.0, sy = 0.0;
             for (int a = 0; a < Q; ++a) {
-                double v = phi[wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)];
+                double v = phi[yrow(walls, y + EY[a], ny) * nx + wrap(x + EX[a], nx)];
                 sx += WA[a] * v * EX[a];
                 sy += WA[a] * v * EY[a];
             }
@@ -136,17 +151,21 @@ void orc_grad(int nx, int ny, const double* phi, double* gx, double* gy)
 /* Isotropic Laplacian: (2/c_s^2) sum_a w_a (phi(x + e_a) - phi(x)). The paper
  * needs a Laplacian in Eq. 2 but does not print its stencil; this is the
  * 9-point isotropic form built from the same weights as Eq. 17. */
-void orc_laplacian(int nx, int ny, const double* phi, double* out)
+static void lap_w(int nx, int ny, int walls, const double* phi, double* out)
 {
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double c0 = phi[y * nx + x];
             double s = 0.0;
             for (int a = 0; a < Q; ++a)
-                s += WA[a] * (phi[wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)] - c0);
+                s += WA[a] * (phi[yrow(walls, y + EY[a], ny) * nx + wrap(x + EX[a], nx)] - c0);
             out[y * nx + x] = 2.0 * s / CS2;
         }
 }
+
+/* The periodic forms. */
+void orc_grad(int nx, int ny, const double* phi, double* gx, double* gy) { grad_w(nx, ny, 0, phi, gx, gy); }
+void orc_laplacian(int nx, int ny, const double* phi, double* out) { lap_w(nx, ny, 0, phi, out); }
 
 /* ------------------------------------------------------- moment algebra */
 
@@ -302,14 +321,14 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
         if (!(s > 0.0) || !isfinite(s)) bad = 1;
     }
     /* 2-3. chemical potential */
-    orc_laplacian(nx, ny, rho, lap);
+    lap_w(nx, ny, c->walls, rho, lap);
     for (int i = 0; i < N; ++i) mu[i] = orc_dEf(c, rho[i]) - c->kappa * lap[i];
     /* 4-5. force */
-    orc_grad(nx, ny, mu, gmx, gmy);
+    grad_w(nx, ny, c->walls, mu, gmx, gmy);
     if (c->scheme == 0) {
         double* r3 = calloc(N, sizeof(double));
         for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
-        orc_grad(nx, ny, r3, grx, gry);
+        grad_w(nx, ny, c->walls, r3, grx, gry);
         free(r3);
         for (int i = 0; i < N; ++i) {
             Fx[i] = grx[i] - rho[i] * gmx[i];
@@ -329,8 +348,8 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
         double* gx = calloc(N, sizeof(double));
         double* gy = calloc(N, sizeof(double));
         for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
-        orc_grad(nx, ny, r3, grx, gry);
-        orc_grad(nx, ny, rho, drx, dry);
+        grad_w(nx, ny, c->walls, r3, grx, gry);
+        grad_w(nx, ny, c->walls, rho, drx, dry);
         for (int i = 0; i < N; ++i) {
             double p = orc_pEOS(c, rho[i]) - c->kappa * rho[i] * lap[i] -
                        0.5 * c->kappa * (drx[i] * drx[i] + dry[i] * dry[i]);
@@ -339,11 +358,11 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
             Pxy[i] = c->kappa * drx[i] * dry[i];
         }
         for (int i = 0; i < N; ++i) Fx[i] = grx[i], Fy[i] = gry[i];
-        orc_grad(nx, ny, Pxx, gx, gy);
+        grad_w(nx, ny, c->walls, Pxx, gx, gy);
         for (int i = 0; i < N; ++i) Fx[i] -= gx[i];
-        orc_grad(nx, ny, Pxy, gx, gy);
+        grad_w(nx, ny, c->walls, Pxy, gx, gy);
         for (int i = 0; i < N; ++i) Fx[i] -= gy[i], Fy[i] -= gx[i];
-        orc_grad(nx, ny, Pyy, gx, gy);
+        grad_w(nx, ny, c->walls, Pyy, gx, gy);
         for (int i = 0; i < N; ++i) Fy[i] -= gy[i];
         free(r3); free(drx); free(dry); free(Pxx); free(Pxy); free(Pyy); free(gx); free(gy);
     } else {
@@ -371,8 +390,8 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
             A[i] = phi * ux[i];
             B[i] = phi * uy[i];
         }
-        orc_grad(nx, ny, A, Ax, Ay);
-        orc_grad(nx, ny, B, Bx, By);
+        grad_w(nx, ny, c->walls, A, Ax, Ay);
+        grad_w(nx, ny, c->walls, B, Bx, By);
     }
     for (int i = 0; i < N; ++i) {
         if (!isfinite(mu[i]) || !isfinite(ux[i]) || !isfinite(uy[i])) bad = 1;
@@ -410,6 +429,11 @@ int64_t orc_step(const orc_case* c, double* f, int64_t nsteps)
     double* C1 = malloc(N * sizeof(double));
     double* C7 = malloc(N * sizeof(double));
     double* fn = malloc((size_t)Q * N * sizeof(double));
+    /* moving-wall bounce-back (walls): the returning population gains the
+     * difference of the running scheme's equilibria at the wall state
+     * (rho_wall, u = (wall_u, 0), mu_c = E_f'(rho_wall)) */
+    double wall_feq[Q];
+    if (c->walls) orc_feq(c, c->rho_wall, c->wall_u, 0.0, orc_dEf(c, c->rho_wall), wall_feq);
     int64_t done = 0;
     for (int64_t n = 0; n < nsteps; ++n) {
         if (orc_fields(c, f, rho, ux, uy, mu, Fx, Fy, C1, C7) != 0) break;
@@ -434,9 +458,19 @@ int64_t orc_step(const orc_case* c, double* f, int64_t nsteps)
                     ms[k] = m[k] - lam[k] * (m[k] - meq[k]) + (1.0 - 0.5 * lam[k]) * (S[k] + Cv[k]);
                 /* 10. back to populations */
                 matvec(Mi, ms, fs);
-                /* 11. push streaming */
-                for (int a = 0; a < Q; ++a)
-                    fn[a * N + wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)] = fs[a];
+                /* 11. push streaming; with walls, a population that would
+                 * cross a wall returns to its node in the opposite direction
+                 * (halfway bounce-back) plus the moving-wall term
+                 * f_eq,b - f_eq,a of the wall state */
+                for (int a = 0; a < Q; ++a) {
+                    const int yy = y + EY[a];
+                    if (c->walls && (yy < 0 || yy >= ny)) {
+                        const int b = OPP[a];
+                        fn[b * N + y * nx + x] = fs[a] + (wall_feq[b] - wall_feq[a]);
+                    } else {
+                        fn[a * N + wrap(yy, ny) * nx + wrap(x + EX[a], nx)] = fs[a];
+                    }
+                }
             }
         memcpy(f, fn, (size_t)Q * N * sizeof(double));
         ++done;
@@ -454,7 +488,7 @@ int orc_init(const orc_case* c, const double* rho0, const double* ux0, const dou
     double* lap = malloc(N * sizeof(double));
     double Mi[Q * Q];
     orc_Minv(Mi);
-    orc_laplacian(nx, ny, rho0, lap);
+    lap_w(nx, ny, c->walls, rho0, lap);
     int bad = 0;
     for (int i = 0; i < N; ++i) {
         if (!(rho0[i] > 0.0)) bad = 1;
@@ -823,7 +857,7 @@ int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u
                 double* loss, double* g_rho0, double* g_kappa, double* g_T)
 {
     const int nx = c->nx, ny = c->ny, N = nx * ny;
-    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2) return -1; /* no pressure-tensor adjoint */
+    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2 || c->walls) return -1; /* periodic, chemical-potential forms */
     int64_t K = 1;
     while (K * K < nsteps) ++K;
     const int64_t ncp = nsteps / K + 1;

@@ -540,6 +540,65 @@ def test_translating_droplet_needs_the_correction():
         assert np.sqrt(ev[1] / ev[0]) < 1.02
 
 
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED])
+def test_walls_channel_startup_series(scheme):
+    """Moving no-slip walls (halfway bounce-back; both walls at u = U from
+    t = 0, fluid of uniform density at rest): the velocity follows the
+    Fourier-series solution of the start-up of flow in a channel of width
+    ny bounded at y = -1/2 and ny - 1/2, with the scheme's kinematic
+    viscosity ((tau - 1/2)/3 standard; p_m (tau - 1/2)/rho improved), to
+    1e-3 U after 600 steps. A moving-wall term other than the scheme's own
+    equilibrium difference, or a wall at the wrong place, misses by far."""
+    H, U, tau, rho = 32, 0.01, 0.8, 2.0
+    c, _, _ = vdw_case(0.8, scheme=scheme, nx=4, ny=H, tau_v=tau, walls=1, wall_u=U, rho_wall=rho)
+    f = O.init(c, np.full((H, 4), rho))
+    m0 = f.sum()
+    assert O.step(c, f, 600) == 600
+    fl = O.fields(c, f)
+    nu = (tau - 0.5) / 3 if scheme == O.STANDARD else (1 + O.dEf(c, rho)) / 3 * (tau - 0.5) / rho
+    y = np.arange(H)
+    th = np.full(H, U)
+    for k in range(1, 400, 2):
+        th -= 4 * U / (k * np.pi) * np.sin(k * np.pi * (y + 0.5) / H) * np.exp(-nu * (k * np.pi / H) ** 2 * 600)
+    assert np.abs(fl.ux - th[:, None]).max() < 1e-3 * U
+    assert np.abs(fl.uy).max() < 1e-14 and abs(f.sum() / m0 - 1) < 1e-13
+
+
+def test_walls_at_rest_keep_a_quiescent_state():
+    c, _, _ = vdw_case(0.8, nx=6, ny=9, collision=O.MRT, tau_v=0.8, walls=1, wall_u=0.0, rho_wall=2.5)
+    f = O.init(c, np.full((9, 6), 2.5))
+    f0 = f.copy()
+    O.step(c, f, 50)
+    np.testing.assert_allclose(f, f0, atol=1e-13)
+
+
+def test_droplet_carried_between_moving_walls():
+    """Sec. IV C (Fig. 6), scaled down: walls moving at U = 0.05 from t = 0
+    carry a droplet (64 x 64, r = 14, 0.8 T_c, improved scheme) along x; it
+    stays round (inertia-tensor aspect ratio below 1.005) and centred in y,
+    and the total mass is conserved to round-off."""
+    L = 64
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    rho0 = inputs.droplet(L, L, 14.0, rl, rg)
+    c = O.Case(nx=L, ny=L, scheme=O.IMPROVED, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02, tau_v=0.8, walls=1,
+               wall_u=0.05, rho_wall=float(rho0.mean()))
+    f = O.init(c, rho0)
+    m0 = f.sum()
+    assert O.step(c, f, 3000) == 3000
+    rho = O.fields(c, f).rho
+    w = np.clip(rho - rg, 0.0, None)
+    y, x = np.mgrid[0:L, 0:L]
+    k = 2 * np.pi / L
+    cx = (np.angle((w * np.exp(1j * k * x)).sum()) / k) % L
+    cy = (w * y).sum() / w.sum()
+    dx, dy = (x - cx + L / 2) % L - L / 2, y - cy
+    ev = np.linalg.eigvalsh([[(w * dx * dx).sum(), (w * dx * dy).sum()], [(w * dx * dy).sum(), (w * dy * dy).sum()]])
+    assert np.sqrt(ev[1] / ev[0]) < 1.005 and abs(cy - L / 2) < 0.1
+    assert (cx - L / 2) % L > 5.0  # carried downstream
+    assert abs(f.sum() / m0 - 1) < 1e-12
+
+
 def test_spurious_currents_table1():
     """Table I: at T = 0.8 Tc the improved scheme's spurious currents fall to
     round-off (1e-15..1e-14) while the standard scheme keeps ~5e-4; a 32 x 32
