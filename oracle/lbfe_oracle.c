@@ -287,11 +287,11 @@ static void relax_rates(const orc_case* c, double tau_v, double* lam)
 
 /* ------------------------------------------------- macroscopic fields */
 
-/* Stages 1-6 (and p_m, C of stage 7) over the lattice, from the populations
- * at the start of a step. Any output pointer may be NULL except as noted.
- * Returns 0, or -1 when rho <= 0 or a value is not finite somewhere. */
-int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
-               double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
+/* Stages 2-7 of the fields on a periodic lattice from given density and
+ * momentum (the populations' moments). */
+static int fields_core(const orc_case* c, const double* rho_in, const double* jx_in, const double* jy_in,
+                       double* rho_o, double* ux_o, double* uy_o, double* mu_o, double* Fx_o, double* Fy_o,
+                       double* C1_o, double* C7_o)
 {
     const int nx = c->nx, ny = c->ny, N = nx * ny;
     double* rho = calloc(N, sizeof(double));
@@ -313,22 +313,20 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
     double* By = calloc(N, sizeof(double));
     int bad = 0;
 
-    /* 1. density */
+    /* 1. density (summed by the caller) */
     for (int i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int a = 0; a < Q; ++a) s += f[a * N + i];
-        rho[i] = s;
-        if (!(s > 0.0) || !isfinite(s)) bad = 1;
+        rho[i] = rho_in[i];
+        if (!(rho[i] > 0.0) || !isfinite(rho[i])) bad = 1;
     }
     /* 2-3. chemical potential */
-    lap_w(nx, ny, c->walls, rho, lap);
+    lap_w(nx, ny, 0, rho, lap);
     for (int i = 0; i < N; ++i) mu[i] = orc_dEf(c, rho[i]) - c->kappa * lap[i];
     /* 4-5. force */
-    grad_w(nx, ny, c->walls, mu, gmx, gmy);
+    grad_w(nx, ny, 0, mu, gmx, gmy);
     if (c->scheme == 0) {
         double* r3 = calloc(N, sizeof(double));
         for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
-        grad_w(nx, ny, c->walls, r3, grx, gry);
+        grad_w(nx, ny, 0, r3, grx, gry);
         free(r3);
         for (int i = 0; i < N; ++i) {
             Fx[i] = grx[i] - rho[i] * gmx[i];
@@ -348,8 +346,8 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
         double* gx = calloc(N, sizeof(double));
         double* gy = calloc(N, sizeof(double));
         for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
-        grad_w(nx, ny, c->walls, r3, grx, gry);
-        grad_w(nx, ny, c->walls, rho, drx, dry);
+        grad_w(nx, ny, 0, r3, grx, gry);
+        grad_w(nx, ny, 0, rho, drx, dry);
         for (int i = 0; i < N; ++i) {
             double p = orc_pEOS(c, rho[i]) - c->kappa * rho[i] * lap[i] -
                        0.5 * c->kappa * (drx[i] * drx[i] + dry[i] * dry[i]);
@@ -358,11 +356,11 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
             Pxy[i] = c->kappa * drx[i] * dry[i];
         }
         for (int i = 0; i < N; ++i) Fx[i] = grx[i], Fy[i] = gry[i];
-        grad_w(nx, ny, c->walls, Pxx, gx, gy);
+        grad_w(nx, ny, 0, Pxx, gx, gy);
         for (int i = 0; i < N; ++i) Fx[i] -= gx[i];
-        grad_w(nx, ny, c->walls, Pxy, gx, gy);
+        grad_w(nx, ny, 0, Pxy, gx, gy);
         for (int i = 0; i < N; ++i) Fx[i] -= gy[i], Fy[i] -= gx[i];
-        grad_w(nx, ny, c->walls, Pyy, gx, gy);
+        grad_w(nx, ny, 0, Pyy, gx, gy);
         for (int i = 0; i < N; ++i) Fy[i] -= gy[i];
         free(r3); free(drx); free(dry); free(Pxx); free(Pxy); free(Pyy); free(gx); free(gy);
     } else {
@@ -374,13 +372,8 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
     /* 6. velocity */
     double half = (c->flags & 2) ? -0.5 : 0.5;
     for (int i = 0; i < N; ++i) {
-        double jx = 0.0, jy = 0.0;
-        for (int a = 0; a < Q; ++a) {
-            jx += EX[a] * f[a * N + i];
-            jy += EY[a] * f[a * N + i];
-        }
-        ux[i] = (jx + half * Fx[i]) / rho[i];
-        uy[i] = (jy + half * Fy[i]) / rho[i];
+        ux[i] = (jx_in[i] + half * Fx[i]) / rho[i];
+        uy[i] = (jy_in[i] + half * Fy[i]) / rho[i];
     }
     /* 7. correction term (improved scheme) */
     if (c->scheme == 1) {
@@ -390,8 +383,8 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
             A[i] = phi * ux[i];
             B[i] = phi * uy[i];
         }
-        grad_w(nx, ny, c->walls, A, Ax, Ay);
-        grad_w(nx, ny, c->walls, B, Bx, By);
+        grad_w(nx, ny, 0, A, Ax, Ay);
+        grad_w(nx, ny, 0, B, Bx, By);
     }
     for (int i = 0; i < N; ++i) {
         if (!isfinite(mu[i]) || !isfinite(ux[i]) || !isfinite(uy[i])) bad = 1;
@@ -408,6 +401,67 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
     free(ux); free(uy); free(Fx); free(Fy); free(A); free(B);
     free(Ax); free(Ay); free(Bx); free(By);
     return bad ? -1 : 0;
+}
+
+/* Stages 1-6 (and p_m, C of stage 7) over the lattice, from the populations
+ * at the start of a step. Any output pointer may be NULL except as noted.
+ * Returns 0, or -1 when rho <= 0 or a value is not finite somewhere.
+ *
+ * With walls, the stencils see the lattice continued across each wall by
+ * its mirror image: G ghost rows below y = 0 and above y = ny - 1 carry the
+ * density and momentum of the mirrored rows (row -k those of row k - 1), and
+ * every field (mu_c, gradients, F, u, phi u, C, P) is then computed by the
+ * same stencils on the extended lattice. */
+int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
+               double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    double* rho = malloc(N * sizeof(double));
+    double* jx = malloc(N * sizeof(double));
+    double* jy = malloc(N * sizeof(double));
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0, sx = 0.0, sy = 0.0;
+        for (int a = 0; a < Q; ++a) {
+            s += f[a * N + i];
+            sx += EX[a] * f[a * N + i];
+            sy += EY[a] * f[a * N + i];
+        }
+        rho[i] = s;
+        jx[i] = sx;
+        jy[i] = sy;
+    }
+    int rc;
+    if (!c->walls) {
+        rc = fields_core(c, rho, jx, jy, rho_o, ux_o, uy_o, mu_o, Fx_o, Fy_o, C1_o, C7_o);
+    } else {
+        enum { G = 4 };  /* ghost rows each side: the deepest stencil chain (C) reaches 3 */
+        orc_case ce = *c;
+        ce.ny = ny + 2 * G;
+        ce.walls = 0;
+        const int Ne = nx * ce.ny;
+        double* buf = malloc((size_t)11 * Ne * sizeof(double));
+        double *re = buf, *xe = buf + Ne, *ye = buf + 2 * Ne;
+        double* out[8];
+        for (int k = 0; k < 8; ++k) out[k] = buf + (3 + k) * Ne;
+        for (int g = 0; g < ce.ny; ++g) {
+            const int y = yrow(1, g - G, ny);
+            for (int x = 0; x < nx; ++x) {
+                re[g * nx + x] = rho[y * nx + x];
+                xe[g * nx + x] = jx[y * nx + x];
+                ye[g * nx + x] = jy[y * nx + x];
+            }
+        }
+        rc = fields_core(&ce, re, xe, ye, out[0], out[1], out[2], out[3], out[4], out[5], out[6], out[7]);
+        /* a bad value in a ghost row is a bad value of its mirrored row */
+        double* dst[8] = {rho_o, ux_o, uy_o, mu_o, Fx_o, Fy_o, C1_o, C7_o};
+        for (int k = 0; k < 8; ++k)
+            if (dst[k]) memcpy(dst[k], out[k] + G * nx, (size_t)N * sizeof(double));
+        free(buf);
+    }
+    free(rho);
+    free(jx);
+    free(jy);
+    return rc;
 }
 
 /* ---------------------------------------------------------------- step */
