@@ -73,19 +73,33 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * below Eq. 29) or rho c_s^2 (tau_v - 1/2) (standard, below Eq. 8).
  * p_m = (pm_c0 + mu_c)/3 (Eq. 24 uses pm_c0 = 1). rho_ref is the reference
  * density of FP32 storage (populations are stored as f_a - w_a rho_ref);
- * rho_ref = 0 asks lb_init_fields to use the mean of the initial density. */
+ * rho_ref = 0 asks lb_init_fields to use the mean of the initial density.
+ *
+ * walls = 1 (Sec. IV C: a droplet carried between moving plates): periodic in
+ * x, no-slip walls half a node below y = 0 and above y = ny - 1, both moving
+ * at (wall_u, 0). A population that streams into a wall returns to its node
+ * in the opposite direction (halfway bounce-back) plus the difference of the
+ * running scheme's equilibria in the two directions at the wall state
+ * (rho_wall, velocity (wall_u, 0), mu_c = E_f'(rho_wall)). The stencils
+ * (Laplacian, Eq. 17 gradients) see the lattice continued across each wall
+ * by its mirror image: ghost rows carry the density and momentum of the
+ * mirrored rows (row -k those of row k - 1) and every field is computed
+ * there by the same formulas. Needs ny >= 8; runs on the one-column step
+ * kernel; no adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
     int32_t scheme;      /* LB_STANDARD, LB_IMPROVED or LB_STANDARD_PT */
     int32_t collision;   /* LB_BGK or LB_MRT */
     int32_t eos;         /* LB_VDW or LB_CS */
-    int32_t reserved;    /* must be 0 */
+    int32_t walls;       /* 0: periodic in y; 1: moving no-slip walls (below) */
     double a, b, R, T;   /* EOS parameters; T absolute */
     double kappa;        /* > 0, Eq. 1 */
     double tau_v, tau_e, tau_s, tau_q; /* each > 1/2 */
     double pm_c0;        /* Eq. 24 constant */
     double nu;           /* 0 or > 0 */
     double rho_ref;      /* FP32 storage reference, >= 0 */
+    double wall_u;       /* walls: x velocity of both walls, |wall_u| <= 0.3 */
+    double rho_wall;     /* walls: density of the wall state, > 0 */
 } lb_case;
 
 typedef struct lb_handle lb_handle;

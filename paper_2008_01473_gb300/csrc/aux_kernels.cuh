@@ -78,7 +78,8 @@ __global__ void mu_field_kernel(DevCase<C> c, const C* __restrict__ rho, C* __re
     if (x >= c.nx) return;
     const int nx = c.nx, ny = c.ny;
     const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx, yp = (int64_t)wrapi(y + 1, ny) * nx;
+    (void)ny;
+    const int64_t ym = (int64_t)nb_row(c, y - 1) * nx, y0 = (int64_t)y * nx, yp = (int64_t)nb_row(c, y + 1) * nx;
     const C Cc = rho[y0 + x];
     const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
                           rho[ym + xp], rho[ym + xm]);
@@ -95,7 +96,8 @@ __global__ void ptensor_kernel(DevCase<C> c, const C* __restrict__ rho, C* __res
     if (x >= c.nx) return;
     const int nx = c.nx, ny = c.ny;
     const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx, yp = (int64_t)wrapi(y + 1, ny) * nx;
+    (void)ny;
+    const int64_t ym = (int64_t)nb_row(c, y - 1) * nx, y0 = (int64_t)y * nx, yp = (int64_t)nb_row(c, y + 1) * nx;
     const C Cc = rho[y0 + x];
     const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
                           rho[ym + xp], rho[ym + xm]);
@@ -133,8 +135,28 @@ __global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ r
     constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     for (int a = 0; a < kQ; ++a) {
-        const int64_t o = (int64_t)wrapi(y - ey[a], c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
+        const int ys = y - ey[a];
+        if (c.walls && (ys < 0 || ys >= c.ny)) continue;  // these arrive from a wall
+        const int64_t o = (int64_t)wrapi(ys, c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
         f[c.off + a * c.plane + o] = (T)d[a];
+    }
+    if (c.walls) {
+        // A population that enters from a wall is the node's own outgoing one
+        // in the opposite direction plus the moving-wall term (+-wall_d on the
+        // diagonals); store those outgoing slots so that the first pull
+        // returns f_a(0). No other node writes them.
+        const int64_t o = (int64_t)y * c.pitch + x;
+        const C w = (C)cc.wall_d;
+        if (y == 0) {
+            f[c.off + 4 * c.plane + o] = (T)d[2];
+            f[c.off + 7 * c.plane + o] = (T)(d[5] - w);
+            f[c.off + 8 * c.plane + o] = (T)(d[6] + w);
+        }
+        if (y == c.ny - 1) {
+            f[c.off + 2 * c.plane + o] = (T)d[4];
+            f[c.off + 5 * c.plane + o] = (T)(d[7] + w);
+            f[c.off + 6 * c.plane + o] = (T)(d[8] - w);
+        }
     }
 }
 
@@ -162,6 +184,16 @@ __global__ void pull_moments_kernel(DevCase<T> c, const T* __restrict__ f, C* __
     F[6] = (C)f[6 * P + rm + xp];
     F[7] = (C)f[7 * P + rp + xp];
     F[8] = (C)f[8 * P + rp + xm];
+    if (c.walls && y == 0) {  // bounce-back from the bottom wall
+        F[2] = (C)f[4 * P + r0 + x];
+        F[5] = (C)(f[7 * P + r0 + x] + c.wall_d);
+        F[6] = (C)(f[8 * P + r0 + x] - c.wall_d);
+    }
+    if (c.walls && y == ny - 1) {  // and from the top wall
+        F[4] = (C)f[2 * P + r0 + x];
+        F[7] = (C)(f[5 * P + r0 + x] - c.wall_d);
+        F[8] = (C)(f[6 * P + r0 + x] + c.wall_d);
+    }
     const C dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
     const int64_t i = (int64_t)y * nx + x;
     rho[i] = (C)c.rho_ref + dr;
@@ -187,9 +219,12 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
     double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
     if (x < nx) {
         const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-        const int64_t ym = (int64_t)wrapi(y - 1, ny) * nx, y0 = (int64_t)y * nx,
-                      yp = (int64_t)wrapi(y + 1, ny) * nx;
+        const int64_t ym = (int64_t)nb_row(cc, y - 1) * nx, y0 = (int64_t)y * nx,
+                      yp = (int64_t)nb_row(cc, y + 1) * nx;
         const int64_t i = y0 + x;
+        // across a wall P_xy continues oddly (the mirrored rows' y gradients
+        // change sign), every other field evenly
+        const C sxm = cc.walls && y == 0 ? C(-1) : C(1), sxp = cc.walls && y == ny - 1 ? C(-1) : C(1);
         const C r = rho[i];
         const C gmx = gradx9<C>(mu[y0 + xp], mu[y0 + xm], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
         const C gmy = grady9<C>(mu[yp + x], mu[ym + x], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
@@ -205,10 +240,10 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
             if (SCHEME == 2) {
                 const C divx = gradx9<C>(pxx[y0 + xp], pxx[y0 + xm], pxx[yp + xp], pxx[yp + xm], pxx[ym + xp],
                                          pxx[ym + xm]) +
-                               grady9<C>(pxy[yp + x], pxy[ym + x], pxy[yp + xp], pxy[yp + xm], pxy[ym + xp],
-                                         pxy[ym + xm]);
-                const C divy = gradx9<C>(pxy[y0 + xp], pxy[y0 + xm], pxy[yp + xp], pxy[yp + xm], pxy[ym + xp],
-                                         pxy[ym + xm]) +
+                               grady9<C>(sxp * pxy[yp + x], sxm * pxy[ym + x], sxp * pxy[yp + xp],
+                                         sxp * pxy[yp + xm], sxm * pxy[ym + xp], sxm * pxy[ym + xm]);
+                const C divy = gradx9<C>(pxy[y0 + xp], pxy[y0 + xm], sxp * pxy[yp + xp], sxp * pxy[yp + xm],
+                                         sxm * pxy[ym + xp], sxm * pxy[ym + xm]) +
                                grady9<C>(pyy[yp + x], pyy[ym + x], pyy[yp + xp], pyy[yp + xm], pyy[ym + xp],
                                          pyy[ym + xm]);
                 Fx = grx * C(1.0 / 3.0) - divx;

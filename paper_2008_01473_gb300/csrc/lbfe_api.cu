@@ -101,16 +101,46 @@ std::string check_case(const lb_case& c, int i)
         return bad("unknown scheme");
     if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
     if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");
-    if (c.reserved != 0) return bad("reserved must be 0");
+    if (c.walls != 0 && c.walls != 1) return bad("walls must be 0 or 1");
     const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.tau_v, c.tau_e, c.tau_s, c.tau_q, c.pm_c0,
-                        c.nu, c.rho_ref};
+                        c.nu, c.rho_ref, c.wall_u, c.rho_wall};
     for (double x : v)
         if (!std::isfinite(x)) return bad("non-finite parameter");
     if (!(c.a > 0 && c.b > 0 && c.R > 0 && c.T > 0 && c.kappa > 0)) return bad("a, b, R, T, kappa must be > 0");
     if (!(c.tau_v > 0.5 && c.tau_e > 0.5 && c.tau_s > 0.5 && c.tau_q > 0.5))
         return bad("relaxation times must be > 1/2");
     if (c.nu < 0 || c.rho_ref < 0) return bad("nu and rho_ref must be >= 0");
+    if (c.walls) {
+        // the row pipeline mirrors up to four rows across each wall
+        if (c.ny < 8) return bad("walls need ny >= 8");
+        if (!(c.rho_wall > 0) || !(std::fabs(c.wall_u) <= 0.3))
+            return bad("walls need rho_wall > 0 and |wall_u| <= 0.3");
+    }
     return std::string();
+}
+
+// E_f'(rho) on the host (Eq. 30 without the kappa term; Carnahan-Starling)
+double host_dEf(const lb_case& c, double rho)
+{
+    if (c.eos == LB_VDW) {
+        const double q = 1.0 / (1.0 - c.b * rho);
+        return c.R * c.T * (std::log(rho * q) + q) - 2.0 * c.a * rho;
+    }
+    const double n = 0.25 * c.b * rho, q = 1.0 / (1.0 - n);
+    return c.R * c.T * (std::log(rho) + 1.0 + n * (4.0 - 3.0 * n) * q * q + n * (4.0 - 2.0 * n) * q * q * q) -
+           2.0 * c.a * rho;
+}
+
+// Moving-wall term of the diagonal directions: f_eq,5 - f_eq,7 of the running
+// scheme at the wall state (rho_wall, (wall_u, 0), E_f'(rho_wall)), which is
+// P u_wall / 2 with P = rho_wall / 3 (standard equilibrium, Eq. 11) or the
+// modified pressure p_m = (c0 + mu_c) / 3 (Eq. 27); the axis directions normal
+// to the walls get no term.
+double wall_delta(const lb_case& c)
+{
+    if (!c.walls) return 0.0;
+    const double P = c.scheme == LB_IMPROVED ? (c.pm_c0 + host_dEf(c, c.rho_wall)) / 3.0 : c.rho_wall / 3.0;
+    return 0.5 * P * c.wall_u;
 }
 
 template <typename T>
@@ -128,6 +158,8 @@ DevCase<T> dev_case(const lb_case& c, int64_t off, double rho_ref)
     d.kappa = (T)c.kappa;
     d.c0 = (T)c.pm_c0;
     d.rho_ref = (T)rho_ref;
+    d.walls = c.walls;
+    d.wall_d = (T)wall_delta(c);
     const bool bgk = c.collision == LB_BGK;
     d.lam_v = (T)(1.0 / c.tau_v);
     d.lam_e = (T)(1.0 / (bgk ? c.tau_v : c.tau_e));
@@ -296,15 +328,17 @@ void build_items(lb_handle* h)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
-                    for (int al = 0; al < 2; ++al) {
-                        // al: lattices with nx % 4 == 0 (TMA-eligible) or not
+                    for (int al = 0; al < 3; ++al) {
+                        // al: lattices with nx % 4 == 0 (TMA-eligible), without, and
+                        // lattices with walls (the plain-load kernel pulls across them)
                         const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
                         const bool pair = tma && h->tma_threads == 0;
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {
                             const lb_case& c = h->cases[i];
+                            const int kind = c.walls ? 2 : (c.nx % 4 == 0 ? 1 : 0);
                             if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
-                                (c.nx % 4 == 0) == (al == 1))
+                                kind == al)
                                 (pair && h->narrow && prefers_narrow(c) ? narrow : members).push_back(i);
                         }
                         emit(members, s, co, e, nu, tma, !tma ? kStepThreads : pair ? kPairWide : h->tma_threads);
@@ -1038,6 +1072,7 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
     if (c.scheme == LB_STANDARD_PT)
         return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of the pressure-tensor force form");
+    if (c.walls) return h->fail(LB_E_INVALID, "lb_adjoint_step: periodic lattices only (no walls)");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
     const bool f32 = h->prec == LB_FP32;
     const AdjLayout L = adj_layout(c, nsteps, K, f32 ? sizeof(float) : sizeof(double));

@@ -14,7 +14,8 @@ constexpr int kQ = 9;
 // arithmetic type T of the launch).
 template <typename T>
 struct DevCase {
-    int32_t nx, ny, pitch, pad_;
+    int32_t nx, ny, pitch;
+    int32_t walls;  // 1: moving no-slip walls below y = 0 and above y = ny - 1
     int64_t off;    // element offset of the case inside a population buffer
     int64_t plane;  // elements between two velocity planes: ny * pitch
     T RT, a, b, kappa;
@@ -22,7 +23,9 @@ struct DevCase {
     T rho_ref;      // populations are stored as f - w rho_ref
     T lam_e, lam_s, lam_q, lam_v;  // 1/tau of Eq. 8 (all 1/tau_v for BGK)
     T nu;           // > 0: tau_v from constant kinematic viscosity
+    T wall_d;       // walls: moving-wall term f_eq,5 - f_eq,7 of the wall state
 };
+
 
 // One block of work: output columns [x0, x0 + wv) and rows [y0, y0 + h) of a
 // case. A block computes a halo of columns around the strip itself.
@@ -34,6 +37,16 @@ __host__ __device__ __forceinline__ int wrapi(int i, int n)
 {
     int r = i % n;
     return r < 0 ? r + n : r;
+}
+
+// Lattice row of a neighbour row y (y may lie one row outside): periodic, or,
+// with walls, the mirror image in the wall (row -1 is row 0, row ny is
+// row ny - 1).
+template <typename T>
+__host__ __device__ __forceinline__ int nb_row(const DevCase<T>& c, int y)
+{
+    if (!c.walls) return wrapi(y, c.ny);
+    return y < 0 ? -1 - y : (y >= c.ny ? 2 * c.ny - 1 - y : y);
 }
 
 // ---------------------------------------------------------------------- EOS

@@ -42,6 +42,7 @@ bool valid_case(const lb_case& c)
 {
     if (c.nx < 3 || c.ny < 3) return false;
     if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return false;
+    if (c.walls) return false;  // periodic lattices only
     if (c.eos != LB_VDW && c.eos != LB_CS) return false;
     const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.pm_c0};
     for (double x : v)

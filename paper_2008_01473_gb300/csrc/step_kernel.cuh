@@ -69,10 +69,12 @@ struct StepLane {
     bool a, b, c, d;  // active in stages A..D
 };
 
-// Row bookkeeping: the periodic lattice row of stage A and of stage D.
+// Row bookkeeping: the periodic lattice row of stage A and of stage D, and
+// the window row of stage A before wrapping (walls mirror it instead).
 struct StepRows {
     int ra;  // lattice row of stage A (wrapped)
     int rd;  // lattice row of stage D (wrapped)
+    int sa;  // window row of stage A (may lie outside [0, ny))
 };
 
 __device__ __forceinline__ int inc_wrap(int r, int n) { return r + 1 == n ? 0 : r + 1; }
@@ -86,6 +88,9 @@ template <>
 __device__ __forceinline__ double rcp_fast<double>(double x) { return 1.0 / x; }
 
 // Stage A source of the pulled populations: plain read-only global loads.
+// With walls, window rows outside the lattice pull their mirror rows, and
+// the populations that reach row 0 or ny - 1 from a wall are the node's own
+// outgoing ones in the opposite direction plus the moving-wall term.
 template <typename T>
 struct PullGlobal {
     __device__ __forceinline__ void pull(int, T* F, const T* __restrict__ fin, const DevCase<T>& c,
@@ -93,6 +98,34 @@ struct PullGlobal {
     {
         const int ny = c.ny, pitch = c.pitch;
         const uint32_t P = (uint32_t)c.plane;
+        if (c.walls) {
+            const int m = nb_row(c, rows.sa);  // mirror of a ghost row; |sa| stays well inside ny
+            const uint32_t r0 = (uint32_t)m * pitch;
+            F[0] = __ldg(fin + (0 * P + r0 + L.xc));
+            F[1] = __ldg(fin + (1 * P + r0 + L.xm));
+            F[3] = __ldg(fin + (3 * P + r0 + L.xp));
+            if (m > 0) {
+                const uint32_t rm = r0 - (uint32_t)pitch;
+                F[2] = __ldg(fin + (2 * P + rm + L.xc));
+                F[5] = __ldg(fin + (5 * P + rm + L.xm));
+                F[6] = __ldg(fin + (6 * P + rm + L.xp));
+            } else {  // bottom wall
+                F[2] = __ldg(fin + (4 * P + r0 + L.xc));
+                F[5] = __ldg(fin + (7 * P + r0 + L.xc)) + c.wall_d;
+                F[6] = __ldg(fin + (8 * P + r0 + L.xc)) - c.wall_d;
+            }
+            if (m < ny - 1) {
+                const uint32_t rp = r0 + (uint32_t)pitch;
+                F[4] = __ldg(fin + (4 * P + rp + L.xc));
+                F[7] = __ldg(fin + (7 * P + rp + L.xp));
+                F[8] = __ldg(fin + (8 * P + rp + L.xm));
+            } else {  // top wall
+                F[4] = __ldg(fin + (2 * P + r0 + L.xc));
+                F[7] = __ldg(fin + (5 * P + r0 + L.xc)) - c.wall_d;
+                F[8] = __ldg(fin + (6 * P + r0 + L.xc)) + c.wall_d;
+            }
+            return;
+        }
         const uint32_t r0 = (uint32_t)rows.ra * pitch;
         const uint32_t rm = (uint32_t)dec_wrap(rows.ra, ny) * pitch;
         const uint32_t rp = (uint32_t)inc_wrap(rows.ra, ny) * pitch;
@@ -260,6 +293,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         }
     }
     rows.ra = inc_wrap(rows.ra, ny);
+    rows.sa += 1;
     if (it >= G::ND) rows.rd = inc_wrap(rows.rd, ny);
 }
 
@@ -294,6 +328,7 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
     StepRows rows;
     rows.ra = wrapi(item.y0 - G::HX, c.ny);
     rows.rd = item.y0;
+    rows.sa = item.y0 - G::HX;
 
     StepRegs<T> R;
     const int niter = item.h + 2 * G::HX;

@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
     StepRows rows;
     rows.ra = wrapi(item.y0 - G::HX, c.ny);
     rows.rd = item.y0;
+    rows.sa = item.y0 - G::HX;  // (this kernel never runs lattices with walls)
 
     StepRegs<T> R;
     for (int base = 0; base < niter; base += 4) {

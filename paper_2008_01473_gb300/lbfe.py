@@ -40,10 +40,11 @@ WIN_RECT, WIN_DISC = 0, 1
 
 class _CCase(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("scheme", C.c_int32), ("collision", C.c_int32),
-                ("eos", C.c_int32), ("reserved", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("eos", C.c_int32), ("walls", C.c_int32), ("a", C.c_double), ("b", C.c_double),
                 ("R", C.c_double), ("T", C.c_double), ("kappa", C.c_double), ("tau_v", C.c_double),
                 ("tau_e", C.c_double), ("tau_s", C.c_double), ("tau_q", C.c_double),
-                ("pm_c0", C.c_double), ("nu", C.c_double), ("rho_ref", C.c_double)]
+                ("pm_c0", C.c_double), ("nu", C.c_double), ("rho_ref", C.c_double), ("wall_u", C.c_double),
+                ("rho_wall", C.c_double)]
 
 
 @dataclass
@@ -66,10 +67,13 @@ class Case:
     pm_c0: float = 1.0
     nu: float = 0.0
     rho_ref: float = 0.0
+    walls: int = 0          # 1: moving no-slip walls below y = 0 and above y = ny - 1
+    wall_u: float = 0.0     # x velocity of both walls
+    rho_wall: float = 0.0   # density of the wall state (> 0 with walls)
 
     def cstruct(self) -> _CCase:
         kw = {f.name: getattr(self, f.name) for f in dc_fields(self)}
-        return _CCase(reserved=0, **kw)
+        return _CCase(**kw)
 
 
 _lib = None
