@@ -84,8 +84,12 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * (Laplacian, Eq. 17 gradients) see the lattice continued across each wall
  * by its mirror image: ghost rows carry the density and momentum of the
  * mirrored rows (row -k those of row k - 1) and every field is computed
- * there by the same formulas. Needs ny >= 8; runs on the one-column step
- * kernel; no adjoint and no lb_fields_static. */
+ * there by the same formulas. The wall term carries momentum in proportion
+ * to the wall state's pressure (rho_wall / 3, or p_m of Eq. 24), so rho_wall
+ * is the density of the fluid that touches the walls (rho_g for a droplet in
+ * its vapour): another value drives that fluid at wall_u times the ratio of
+ * the two pressures. Needs ny >= 8; runs on the one-column step kernel; no
+ * adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
     int32_t scheme;      /* LB_STANDARD, LB_IMPROVED or LB_STANDARD_PT */

@@ -582,7 +582,7 @@ def test_droplet_carried_between_moving_walls():
     T, rg, rl = thermo.maxwell_reduced(e, 0.8)
     rho0 = inputs.droplet(L, L, 14.0, rl, rg)
     c = O.Case(nx=L, ny=L, scheme=O.IMPROVED, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02, tau_v=0.8, walls=1,
-               wall_u=0.05, rho_wall=float(rho0.mean()))
+               wall_u=0.05, rho_wall=rg)
     f = O.init(c, rho0)
     m0 = f.sum()
     assert O.step(c, f, 3000) == 3000
