@@ -729,7 +729,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=150)
+    ap.add_argument("--cpu-steps", type=int, default=450)
     ap.add_argument("--accuracy-steps", type=int, default=10000,
                     help="batched workload: steps of the FP32-vs-FP64 droplet check (0 skips it)")
     ap.add_argument("--no-cpu", action="store_true")
