@@ -26,6 +26,7 @@ _OUT = os.path.join(_HERE, "_build", "liblbfe_oracle.so")
 _lib = None
 
 STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
+IMPROVED_SMOOTH = 3  # improved scheme, Eq. 29's derivatives of the lattice-weight average of phi u
 BGK, MRT = 0, 1
 VDW, CS = thermo.VDW, thermo.CS
 

@@ -68,7 +68,9 @@ static const double MM[Q][Q] = {
 typedef struct {
     int32_t nx, ny;
     int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28),
-                          2 = standard with the pressure-tensor force (Eq. 13 left) */
+                          2 = standard with the pressure-tensor force (Eq. 13 left),
+                          3 = improved with the derivatives of Eq. 29 taken on the
+                              lattice-weight average of phi u (periodic only) */
     int32_t collision; /* 0 = BGK (all rates 1/tau_v), 1 = MRT (Eq. 8) */
     int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
@@ -163,6 +165,17 @@ static void lap_w(int nx, int ny, int walls, const double* phi, double* out)
         }
 }
 
+/* Periodic lattice-weight average sum_a w_a phi(x + e_a) (scheme 3). */
+static void avg_w(int nx, int ny, const double* phi, double* out)
+{
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double s = 0.0;
+            for (int a = 0; a < Q; ++a) s += WA[a] * phi[wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx)];
+            out[y * nx + x] = s;
+        }
+}
+
 /* The periodic forms. */
 void orc_grad(int nx, int ny, const double* phi, double* gx, double* gy) { grad_w(nx, ny, 0, phi, gx, gy); }
 void orc_laplacian(int nx, int ny, const double* phi, double* out) { lap_w(nx, ny, 0, phi, out); }
@@ -211,10 +224,13 @@ static void matvec(const double* A, const double* v, double* out)
 
 /* Moment-space equilibrium: Eq. 11 (standard) or Eq. 27 with
  * gamma = 3 p_m / rho and p_m = (c0 + mu_c)/3 (improved, Eq. 24). */
+/* Schemes 1 and 3 share Eqs. 24-28 and differ only in how Eq. 29 is discretised. */
+static int improved(const orc_case* c) { return c->scheme == 1 || c->scheme == 3; }
+
 void orc_meq(const orc_case* c, double rho, double ux, double uy, double mu, double* meq)
 {
     double u2 = ux * ux + uy * uy;
-    if (c->scheme != 1) {
+    if (!improved(c)) {
         meq[0] = rho;
         meq[1] = rho * (-2.0 + 3.0 * u2);
         meq[2] = rho * (1.0 - 3.0 * u2);
@@ -263,7 +279,7 @@ void orc_guo(double ux, double uy, double Fx, double Fy, double* G)
 double orc_tau_v(const orc_case* c, double rho, double mu)
 {
     if (!(c->nu > 0.0)) return c->tau_v;
-    if (c->scheme == 1) return 0.5 + c->nu * rho / ((c->pm_c0 + mu) / 3.0);
+    if (improved(c)) return 0.5 + c->nu * rho / ((c->pm_c0 + mu) / 3.0);
     return 0.5 + c->nu / CS2;
 }
 
@@ -376,12 +392,22 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
         uy[i] = (jy_in[i] + half * Fy[i]) / rho[i];
     }
     /* 7. correction term (improved scheme) */
-    if (c->scheme == 1) {
+    if (improved(c)) {
         for (int i = 0; i < N; ++i) {
             double pm = (c->pm_c0 + mu[i]) / 3.0;
             double phi = rho[i] * CS2 - pm;
             A[i] = phi * ux[i];
             B[i] = phi * uy[i];
+        }
+        if (c->scheme == 3) {
+            /* the fields phi u_x, phi u_y replaced by their averages
+             * sum_a w_a (phi u)(x + e_a) before the Eq. 17 gradient */
+            double* t = malloc(N * sizeof(double));
+            avg_w(nx, ny, A, t);
+            memcpy(A, t, N * sizeof(double));
+            avg_w(nx, ny, B, t);
+            memcpy(B, t, N * sizeof(double));
+            free(t);
         }
         grad_w(nx, ny, 0, A, Ax, Ay);
         grad_w(nx, ny, 0, B, Bx, By);
@@ -394,8 +420,8 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
         if (mu_o) mu_o[i] = mu[i];
         if (Fx_o) Fx_o[i] = Fx[i];
         if (Fy_o) Fy_o[i] = Fy[i];
-        if (C1_o) C1_o[i] = (c->scheme == 1) ? Ax[i] + By[i] : 0.0;
-        if (C7_o) C7_o[i] = (c->scheme == 1) ? Ax[i] - By[i] : 0.0;
+        if (C1_o) C1_o[i] = improved(c) ? Ax[i] + By[i] : 0.0;
+        if (C7_o) C7_o[i] = improved(c) ? Ax[i] - By[i] : 0.0;
     }
     free(rho); free(lap); free(mu); free(gmx); free(gmy); free(grx); free(gry);
     free(ux); free(uy); free(Fx); free(Fy); free(A); free(B);
@@ -415,6 +441,7 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
 int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
                double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
 {
+    if (c->scheme == 3 && c->walls) return -1; /* scheme 3 is periodic only */
     const int nx = c->nx, ny = c->ny, N = nx * ny;
     double* rho = malloc(N * sizeof(double));
     double* jx = malloc(N * sizeof(double));
@@ -502,7 +529,7 @@ int64_t orc_step(const orc_case* c, double* f, int64_t nsteps)
                 matvec(&MM[0][0], fl, m);
                 orc_meq(c, rho[i], ux[i], uy[i], mu[i], meq);
                 for (int k = 0; k < Q; ++k) Cv[k] = 0.0;
-                if (c->scheme == 1 && !(c->flags & 1)) {
+                if (improved(c) && !(c->flags & 1)) {
                     Cv[1] = 9.0 * C1[i];
                     Cv[7] = 3.0 * C7[i];
                 }
@@ -911,7 +938,8 @@ int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u
                 double* loss, double* g_rho0, double* g_kappa, double* g_T)
 {
     const int nx = c->nx, ny = c->ny, N = nx * ny;
-    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2 || c->walls) return -1; /* periodic, chemical-potential forms */
+    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2 || c->scheme == 3 || c->walls)
+        return -1; /* periodic, chemical-potential forms, Eq. 17 correction */
     int64_t K = 1;
     while (K * K < nsteps) ++K;
     const int64_t ncp = nsteps / K + 1;
