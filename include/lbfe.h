@@ -54,11 +54,22 @@ typedef enum {
 } lb_status;
 
 /* LB_STANDARD: standard scheme, chemical-potential force (Eq. 13 right);
- * LB_IMPROVED: the improved scheme (Eqs. 24-29); LB_STANDARD_PT: standard
+ * LB_IMPROVED: the improved scheme (Eqs. 24-29), the derivatives of Eq. 29
+ * by the Eq. 17 gradient of phi u_x and phi u_y; LB_STANDARD_PT: standard
  * scheme with the pressure-tensor force F = grad(rho c_s^2) - div P (Eq. 13
  * left), P of Eqs. 4-5 built from the Eq. 17 gradient and the isotropic
- * Laplacian of rho, div P by Eq. 17 on each component. */
-enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2 };
+ * Laplacian of rho, div P by Eq. 17 on each component.
+ * LB_IMPROVED_SMOOTH: the improved scheme with Eq. 29's derivatives taken as
+ * the Eq. 17 gradient of the lattice-weight average sum_a w_a (phi u)(x + e_a)
+ * (a 5 x 5 stencil). The paper does not state its discretisation of these
+ * derivatives (Sec. III). With the plain Eq. 17 difference the improved
+ * scheme's vapour is linearly unstable at 0.7 T_c (vdW set of Sec. IV, any
+ * relaxation times); the averaged form damps the grid-scale modes that drive
+ * that instability and keeps 0.7 T_c stable for tau_v >= 0.8, or with MRT at
+ * the constant kinematic viscosity 0.04 of Table II. Same steady states as
+ * LB_IMPROVED (C vanishes at u = 0). Periodic lattices only (walls = 0);
+ * runs on the one-column plain-load step kernel; no lb_adjoint_step. */
+enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2, LB_IMPROVED_SMOOTH = 3 };
 enum { LB_BGK = 0, LB_MRT = 1 };            /* single rate 1/tau_v / Eq. 8 */
 enum { LB_VDW = 0, LB_CS = 1 };             /* Eq. 30 / Carnahan-Starling */
 enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic */
@@ -92,7 +103,7 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
-    int32_t scheme;      /* LB_STANDARD, LB_IMPROVED or LB_STANDARD_PT */
+    int32_t scheme;      /* LB_STANDARD, LB_IMPROVED, LB_STANDARD_PT or LB_IMPROVED_SMOOTH */
     int32_t collision;   /* LB_BGK or LB_MRT */
     int32_t eos;         /* LB_VDW or LB_CS */
     int32_t walls;       /* 0: periodic in y; 1: moving no-slip walls (below) */
@@ -230,7 +241,8 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
  * are device pointers if on_device, else host. Runs on the handle's stream,
  * synchronises it, and leaves the handle's own state untouched. It is the
  * reverse-time counterpart of lb_init_fields followed by lb_step(nsteps): one
- * call runs all nsteps adjoint steps, newest first. */
+ * call runs all nsteps adjoint steps, newest first. LB_STANDARD_PT and
+ * LB_IMPROVED_SMOOTH cases, walls and nu > 0 give LB_E_INVALID. */
 lb_status lb_adjoint_workspace_bytes(const lb_handle* h, int32_t case_id, int64_t nsteps, int32_t ckpt_every,
                                      size_t* bytes);
 lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int64_t nsteps, int64_t u_from,
@@ -268,8 +280,8 @@ lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double
  * and d_pops, a device array of its populations in the snapshot layout of
  * lb_save ([9][ny][pitch], pitch = nx rounded up to 32, storage form of the
  * library; FP32 planes hold f_a - w_a rho_ref). Outputs (device pointers):
- * (LB_STANDARD or LB_IMPROVED cases; LB_STANDARD_PT is rejected with
- * LB_E_INVALID) d_rho, d_ux, d_uy, d_mu [ny][nx] as in lb_moments (each may
+ * (LB_STANDARD, LB_IMPROVED or LB_IMPROVED_SMOOTH cases; LB_STANDARD_PT is
+ * rejected with LB_E_INVALID) d_rho, d_ux, d_uy, d_mu [ny][nx] as in lb_moments (each may
  * be NULL) and
  * d_red[5] = {mass, kinetic energy, max |u|, 0, count of nodes with rho <= 0
  * or non-finite values}. Work is enqueued on cuda_stream; nothing is

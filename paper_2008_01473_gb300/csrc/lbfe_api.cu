@@ -30,7 +30,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
 
-int halo_of(int scheme) { return scheme == LB_IMPROVED ? 3 : 2; }
+int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
 // Widest strip of output columns a block of nt threads can own. Lattices with
 // nx % 4 == 0 get strips of a multiple of 4 columns, at most nt - 8 wide, as
@@ -97,7 +97,8 @@ std::string check_case(const lb_case& c, int i)
     if (c.nx < 3 || c.ny < 3) return bad("nx and ny must be >= 3");
     // the step kernel addresses a case's nine planes with 32-bit offsets
     if ((int64_t)kQ * c.ny * pitch_of(c.nx) >= (int64_t)1 << 31) return bad("lattice too large");
-    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED && c.scheme != LB_STANDARD_PT)
+    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED && c.scheme != LB_STANDARD_PT &&
+        c.scheme != LB_IMPROVED_SMOOTH)
         return bad("unknown scheme");
     if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
     if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");
@@ -110,6 +111,7 @@ std::string check_case(const lb_case& c, int i)
     if (!(c.tau_v > 0.5 && c.tau_e > 0.5 && c.tau_s > 0.5 && c.tau_q > 0.5))
         return bad("relaxation times must be > 1/2");
     if (c.nu < 0 || c.rho_ref < 0) return bad("nu and rho_ref must be >= 0");
+    if (c.walls && c.scheme == LB_IMPROVED_SMOOTH) return bad("LB_IMPROVED_SMOOTH is periodic only (walls = 0)");
     if (c.walls) {
         // the row pipeline mirrors up to four rows across each wall
         if (c.ny < 8) return bad("walls need ny >= 8");
@@ -139,7 +141,7 @@ double host_dEf(const lb_case& c, double rho)
 double wall_delta(const lb_case& c)
 {
     if (!c.walls) return 0.0;
-    const double P = c.scheme == LB_IMPROVED ? (c.pm_c0 + host_dEf(c, c.rho_wall)) / 3.0 : c.rho_wall / 3.0;
+    const double P = improved_scheme(c.scheme) ? (c.pm_c0 + host_dEf(c, c.rho_wall)) / 3.0 : c.rho_wall / 3.0;
     return 0.5 * P * c.wall_u;
 }
 
@@ -324,19 +326,20 @@ void build_items(lb_handle* h)
                          [](const Item& a, const Item& b) { return a.h > b.h; });
         h->groups.push_back(g);
     };
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < 4; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
                     for (int al = 0; al < 3; ++al) {
                         // al: lattices with nx % 4 == 0 (TMA-eligible), without, and
-                        // lattices with walls (the plain-load kernel pulls across them)
+                        // lattices with walls (the plain-load kernel pulls across them) or
+                        // with scheme 3 (whose wider stencil only that kernel has)
                         const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
                         const bool pair = tma && h->tma_threads == 0;
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {
                             const lb_case& c = h->cases[i];
-                            const int kind = c.walls ? 2 : (c.nx % 4 == 0 ? 1 : 0);
+                            const int kind = c.walls || c.scheme == LB_IMPROVED_SMOOTH ? 2 : (c.nx % 4 == 0 ? 1 : 0);
                             if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
                                 kind == al)
                                 (pair && h->narrow && prefers_narrow(c) ? narrow : members).push_back(i);
@@ -389,7 +392,7 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
         mu_field_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
     else
         mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
-    if (c.scheme == LB_IMPROVED) {
+    if (improved_scheme(c.scheme)) {
         velocity_kernel<1, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
                                                           o_uy, o_mu, h->partials());
     } else if (c.scheme == LB_STANDARD_PT) {
@@ -442,7 +445,7 @@ lb_status init_pass_t(lb_handle* h, int i, const double* d_rho0, const double* p
         mu_field_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, r0, mu);
     else
         mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, r0, mu);
-    if (c.scheme == LB_IMPROVED)
+    if (improved_scheme(c.scheme))
         init_kernel<T, 1, C><<<grd, blk, 0, h->stream>>>(ct, cc, r0, pux, puy, mu, (T*)h->fbuf(h->cur));
     else
         init_kernel<T, 0, C><<<grd, blk, 0, h->stream>>>(ct, cc, r0, pux, puy, mu, (T*)h->fbuf(h->cur));
@@ -1072,6 +1075,8 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
     if (c.scheme == LB_STANDARD_PT)
         return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of the pressure-tensor force form");
+    if (c.scheme == LB_IMPROVED_SMOOTH)
+        return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of LB_IMPROVED_SMOOTH");
     if (c.walls) return h->fail(LB_E_INVALID, "lb_adjoint_step: periodic lattices only (no walls)");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
     const bool f32 = h->prec == LB_FP32;

@@ -10,6 +10,12 @@ namespace lbfe {
 
 constexpr int kQ = 9;
 
+// Scheme codes of the kernels (the lb_case codes): 0 standard, 1 improved,
+// 2 standard with the pressure-tensor force, 3 improved with the derivatives
+// of Eq. 29 taken on the lattice-weight average of phi u. Schemes 1 and 3
+// share the equilibrium, force and collision of Eqs. 24-28.
+__host__ __device__ constexpr bool improved_scheme(int s) { return s == 1 || s == 3; }
+
 // Per-case parameters as the kernels read them (one record per case, in the
 // arithmetic type T of the launch).
 template <typename T>
@@ -159,7 +165,7 @@ __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T
     // rho_ref (1, -2, 1, 0, ...)
     const T uxx = ux * ux, uyy = uy * uy, u2 = uxx + uyy;
     T eq_e, eq_s, eq_qx, eq_qy;
-    if (SCHEME != 1) {  // standard scheme, either force form: Eq. 11
+    if (!improved_scheme(SCHEME)) {  // standard scheme, either force form: Eq. 11
         eq_e = T(3) * rho * u2 - T(2) * drho;
         eq_s = drho - T(3) * rho * u2;
         eq_qx = -rho * ux;
@@ -225,7 +231,7 @@ template <int SCHEME, bool NU, typename T>
 __device__ __forceinline__ T shear_rate(const DevCase<T>& c, T rho, T mu)
 {
     if (!NU) return c.lam_v;
-    if (SCHEME == 1) return T(1) / (T(0.5) + c.nu * rho * T(3) / (c.c0 + mu));
+    if (improved_scheme(SCHEME)) return T(1) / (T(0.5) + c.nu * rho * T(3) / (c.c0 + mu));
     return T(1) / (T(0.5) + T(3) * c.nu);
 }
 

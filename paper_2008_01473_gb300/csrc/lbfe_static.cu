@@ -41,7 +41,7 @@ DevCase<T> make_case(const lb_case& c, double rho_ref)
 bool valid_case(const lb_case& c)
 {
     if (c.nx < 3 || c.ny < 3) return false;
-    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED) return false;
+    if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED && c.scheme != LB_IMPROVED_SMOOTH) return false;
     if (c.walls) return false;  // periodic lattices only
     if (c.eos != LB_VDW && c.eos != LB_CS) return false;
     const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.pm_c0};
@@ -96,7 +96,7 @@ void fields_static(const lb_case& c, double rho_ref, const T* d_pops, unsigned c
         mu_field_kernel<T, 0><<<grd, blk, 0, st>>>(ct, s0, s3);
     else
         mu_field_kernel<T, 1><<<grd, blk, 0, st>>>(ct, s0, s3);
-    if (c.scheme == LB_IMPROVED)
+    if (improved_scheme(c.scheme))  // the exported fields do not involve Eq. 29
         velocity_kernel<1, T><<<grd, blk, 0, st>>>(ct, s0, s1, s2, s3, nullptr, nullptr, nullptr, d_rho, d_ux, d_uy,
                                                    d_mu, parts);
     else

@@ -37,21 +37,27 @@
 
 namespace lbfe {
 
+// Scheme 3 (the correction's derivatives of the lattice-weight average of
+// phi u) reaches phi u two rows and two columns away from the node, so its
+// column halo and its lag between stages A and D are one larger than the
+// improved scheme's. HX == LAG for every scheme, so stage D's first row is y0.
 template <int SCHEME>
 struct StepGeom {
-    static constexpr int HX = SCHEME == 1 ? 3 : 2;   // column halo of rho
-    static constexpr int LAG = SCHEME == 1 ? 3 : 2;  // rows between stage A and D
-    static constexpr int NB = SCHEME == 1 ? 2 : 2;   // first iteration with stage B
-    static constexpr int NC = 4;                     // first iteration with stage C (improved)
-    static constexpr int ND = 2 * LAG;               // first iteration with stage D
+    static constexpr int HX = SCHEME == 3 ? 4 : SCHEME == 1 ? 3 : 2;   // column halo of rho
+    static constexpr int LAG = SCHEME == 3 ? 4 : SCHEME == 1 ? 3 : 2;  // rows between stage A and D
+    static constexpr int NB = 2;                                       // first iteration with stage B
+    static constexpr int NC = 4;        // first iteration with stage C (improved schemes)
+    static constexpr int ND = 2 * LAG;  // first iteration with stage D
+    // rows of the phi u rings: scheme 3 reads rows ra - 6 .. ra - 2
+    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 6 : 4;
 };
 
 template <typename T, int NT, int SCHEME>
 struct StepSmem {
     T rho[4][NT];
     T mu[4][NT];
-    T pux[SCHEME == 0 ? 1 : 4][NT];  // phi u_x (improved) or P_xy (pressure tensor)
-    T puy[SCHEME == 0 ? 1 : 4][NT];  // phi u_y (improved) or P_yy (pressure tensor)
+    T pux[StepGeom<SCHEME>::NPU][NT];  // phi u_x (improved) or P_xy (pressure tensor)
+    T puy[StepGeom<SCHEME>::NPU][NT];  // phi u_y (improved) or P_yy (pressure tensor)
 };
 
 template <typename T>
@@ -59,7 +65,7 @@ struct StepRegs {
     T f[4][kQ];  // pulled populations (deviation form) of the own column
     T drho[4];
     T jx[4], jy[4];
-    T ux[2], uy[2], Fx[2], Fy[2];  // stage C results of two rows (improved)
+    T ux[4], uy[4], Fx[4], Fy[4];  // stage C results of the last rows (improved schemes)
     T grx, gry;                    // stage B grad rho (standard)
 };
 
@@ -143,6 +149,71 @@ struct PullGlobal {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// Stage D of scheme 3 at row rd = ra - 4. The correction takes the Eq. 17
+// gradient of the lattice-weight average A' = sum_a w_a A(x + e_a) of
+// A = phi u_x (and of B = phi u_y). Both stencils factor into 1-D pieces
+// (w = w1 x w1 with w1 = (1, 4, 1)/6, and Eq. 17's x part is half the central
+// difference times w1 across y), so
+//   d_x A'(x, y) = sum_dy s(dy) [ (A(x+1) - A(x-1)) / 3 + (A(x+2) - A(x-2)) / 12 ](y + dy)
+// with s = (1, 8, 18, 8, 1)/36 over dy = -2..2, and d_y B' likewise with the
+// roles of x and y exchanged. The populations of row rd are pulled again
+// (L2-resident: stage A read them four iterations earlier) instead of being
+// kept in registers for four rows.
+template <typename T, int NT, int COLL, int EOS, bool NU, int SLOT>
+__device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin, T* __restrict__ fout,
+                                              const DevCase<T>& c, const StepLane& L, const StepRows& rows,
+                                              StepSmem<T, NT, 3>& sm, StepRegs<T>& R)
+{
+    using G = StepGeom<3>;
+    constexpr int S0 = SLOT, S2 = (SLOT + 2) & 3;
+    const int t = L.t;
+    // phi u rows ra - 6 .. ra - 2 (dy = -2 .. 2 around rd = ra - 4)
+    const T* Ar[5];
+    const T* Br[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int slot = (it + 2 * G::NPU - 6 + k) % G::NPU;
+        Ar[k] = sm.pux[slot];
+        Br[k] = sm.puy[slot];
+    }
+    const T s0 = T(1.0 / 36.0), s1 = T(8.0 / 36.0), s2 = T(18.0 / 36.0);
+    const T g1 = T(1.0 / 3.0), g2 = T(1.0 / 12.0);
+    T hx[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+        hx[k] = g1 * (Ar[k][t + 1] - Ar[k][t - 1]) + g2 * (Ar[k][t + 2] - Ar[k][t - 2]);
+    const T Ax = s0 * (hx[0] + hx[4]) + s1 * (hx[1] + hx[3]) + s2 * hx[2];
+    T sb[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (k == 2) continue;
+        const T* b = Br[k];
+        sb[k] = s0 * (b[t - 2] + b[t + 2]) + s1 * (b[t - 1] + b[t + 1]) + s2 * b[t];
+    }
+    const T By = g1 * (sb[3] - sb[1]) + g2 * (sb[4] - sb[0]);
+    const T C1 = Ax + By, C7 = Ax - By;
+
+    T F[kQ];
+    const StepRows rr{rows.rd, rows.rd, rows.rd};
+    PullGlobal<T>().pull(it, F, fin, c, L, rr);
+    const T drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+    const T jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+    const T jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+    const T rho = c.rho_ref + drho;
+    const T mu = sm.mu[S0][t];  // row ra - 4
+    T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
+    if (NU) {
+        lv = shear_rate<3, NU, T>(c, rho, mu);
+        if (COLL == 0) le = ls = lq = lv;
+    }
+    collide<3, T>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c.rho_ref, c.c0, le,
+                  ls, lq, lv);
+    const uint32_t P = (uint32_t)c.plane;
+    const uint32_t o = (uint32_t)rows.rd * c.pitch + L.xc;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) fout[a * P + o] = F[a];
+}
+
 template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A>
 __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restrict__ fin, T* __restrict__ fout,
                                           const DevCase<T>& c, const StepLane& L, StepRows& rows,
@@ -187,7 +258,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         } else {
             sm.mu[S1][t] = dEf<EOS, T>(c, rc) - c.kappa * lap;
         }
-        if constexpr (SCHEME != 1) {
+        if constexpr (!improved_scheme(SCHEME)) {
             // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
             if (it >= G::ND) {
                 const T* Qm = sm.rho[S3];
@@ -198,9 +269,12 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
     }
     A_.sync();
 
-    if constexpr (SCHEME == 1) {
+    if constexpr (improved_scheme(SCHEME)) {
         // ------------------------------------------------------------ C
-        constexpr int U2 = SLOT & 1;  // stage C output slot of row ra - 2
+        // stage C output slots of row ra - 2: registers (two rows deep for
+        // scheme 1, four for scheme 3) and phi u rows (ring of NPU rows)
+        constexpr int U2 = SCHEME == 3 ? SLOT : (SLOT & 1);
+        const int P2 = SCHEME == 3 ? (it + 4) % G::NPU : S2;
         if (L.c && it >= G::NC) {
             const T* Mm = sm.mu[S3];
             const T* Mc = sm.mu[S2];
@@ -214,14 +288,18 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T ux = (R.jx[S2] + T(0.5) * Fx) * inv;
             const T uy = (R.jy[S2] + T(0.5) * Fy) * inv;
             const T phi = (rho - (c.c0 + Mc[t])) * T(1.0 / 3.0);
-            sm.pux[S2][t] = phi * ux;
-            sm.puy[S2][t] = phi * uy;
+            sm.pux[P2][t] = phi * ux;
+            sm.puy[P2][t] = phi * uy;
             R.ux[U2] = ux;
             R.uy[U2] = uy;
             R.Fx[U2] = Fx;
             R.Fy[U2] = Fy;
         }
         A_.sync();
+        if constexpr (SCHEME == 3) {
+            // -------------------------------------------------------- D (3)
+            if (L.d && it >= G::ND) step_d_smooth<T, NT, COLL, EOS, NU, SLOT>(it, fin, fout, c, L, rows, sm, R);
+        } else {
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
         if (L.d && it >= G::ND) {
@@ -246,6 +324,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const uint32_t o = (uint32_t)rows.rd * pitch + L.xc;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) fout[a * P + o] = R.f[S3][a];
+        }
         }
     } else {
         // ------------------------------------------------------- D (standard)

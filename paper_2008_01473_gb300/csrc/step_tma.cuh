@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
                                                            const Item* __restrict__ items,
                                                            int* __restrict__ status)
 {
+    static_assert(SCHEME != 3, "scheme 3 runs on the plain-load kernel only");
     using G = StepGeom<SCHEME>;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ StepSmem<T, NT, SCHEME> sm;

@@ -121,9 +121,10 @@ def test_adjoint_rejects_bad_rho0_and_pressure_tensor():
     bad[2, 3] = -1.0
     with pytest.raises(lbfe.LBError):
         lbfe.Lattice([gc], precision=lbfe.FP64).adjoint(0, bad, 5, 0)
-    pt, _, _, _ = _setup(12, 10, lbfe.STANDARD_PT, lbfe.BGK)
-    with pytest.raises(lbfe.LBError):
-        lbfe.Lattice([pt], precision=lbfe.FP64).adjoint(0, rho0, 5, 0)
+    for scheme in (lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH):
+        other, _, _, _ = _setup(12, 10, scheme, lbfe.BGK)
+        with pytest.raises(lbfe.LBError):
+            lbfe.Lattice([other], precision=lbfe.FP64).adjoint(0, rho0, 5, 0)
 
 
 def test_gpu_adjoint_matches_oracle_droplet_64():
