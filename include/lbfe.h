@@ -67,8 +67,8 @@ typedef enum {
  * relaxation times); the averaged form damps the grid-scale modes that drive
  * that instability and keeps 0.7 T_c stable for tau_v >= 0.8, or with MRT at
  * the constant kinematic viscosity 0.04 of Table II. Same steady states as
- * LB_IMPROVED (C vanishes at u = 0). Periodic lattices only (walls = 0);
- * runs on the one-column plain-load step kernel; no lb_adjoint_step. */
+ * LB_IMPROVED (C vanishes at u = 0). Runs on the one-column plain-load step
+ * kernel; no lb_adjoint_step. */
 enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2, LB_IMPROVED_SMOOTH = 3 };
 enum { LB_BGK = 0, LB_MRT = 1 };            /* single rate 1/tau_v / Eq. 8 */
 enum { LB_VDW = 0, LB_CS = 1 };             /* Eq. 30 / Carnahan-Starling */

@@ -70,7 +70,7 @@ typedef struct {
     int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28),
                           2 = standard with the pressure-tensor force (Eq. 13 left),
                           3 = improved with the derivatives of Eq. 29 taken on the
-                              lattice-weight average of phi u (periodic only) */
+                              lattice-weight average of phi u */
     int32_t collision; /* 0 = BGK (all rates 1/tau_v), 1 = MRT (Eq. 8) */
     int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
@@ -441,7 +441,6 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
 int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
                double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
 {
-    if (c->scheme == 3 && c->walls) return -1; /* scheme 3 is periodic only */
     const int nx = c->nx, ny = c->ny, N = nx * ny;
     double* rho = malloc(N * sizeof(double));
     double* jx = malloc(N * sizeof(double));
@@ -461,7 +460,9 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
     if (!c->walls) {
         rc = fields_core(c, rho, jx, jy, rho_o, ux_o, uy_o, mu_o, Fx_o, Fy_o, C1_o, C7_o);
     } else {
-        enum { G = 4 };  /* ghost rows each side: the deepest stencil chain (C) reaches 3 */
+        /* ghost rows each side: the deepest stencil chain (C of scheme 3) reaches
+         * 4 rows; the periodic wrap of the extended lattice corrupts only ghost rows */
+        enum { G = 4 };
         orc_case ce = *c;
         ce.ny = ny + 2 * G;
         ce.walls = 0;

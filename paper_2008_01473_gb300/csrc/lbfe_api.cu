@@ -111,7 +111,6 @@ std::string check_case(const lb_case& c, int i)
     if (!(c.tau_v > 0.5 && c.tau_e > 0.5 && c.tau_s > 0.5 && c.tau_q > 0.5))
         return bad("relaxation times must be > 1/2");
     if (c.nu < 0 || c.rho_ref < 0) return bad("nu and rho_ref must be >= 0");
-    if (c.walls && c.scheme == LB_IMPROVED_SMOOTH) return bad("LB_IMPROVED_SMOOTH is periodic only (walls = 0)");
     if (c.walls) {
         // the row pipeline mirrors up to four rows across each wall
         if (c.ny < 8) return bad("walls need ny >= 8");

@@ -16,7 +16,7 @@ import numpy as np
 from .build import LIB
 
 STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
-IMPROVED_SMOOTH = 3  # improved scheme, Eq. 29 on the lattice-weight average of phi u (periodic only)
+IMPROVED_SMOOTH = 3  # improved scheme, Eq. 29 on the lattice-weight average of phi u
 BGK, MRT = 0, 1
 VDW, CS = 0, 1
 FP64, FP32 = 0, 1

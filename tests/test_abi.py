@@ -45,7 +45,7 @@ def test_workspace_validation(lib):
     c3 = lbfe.Case(**{**ok.__dict__, "scheme": lbfe.IMPROVED_SMOOTH})
     assert lib.lb_workspace_bytes((lbfe._CCase * 1)(c3.cstruct()), 1, lbfe.FP32, C.byref(nb)) == 0
     for bad in (dict(nx=2), dict(tau_v=0.5), dict(kappa=0.0), dict(scheme=5), dict(T=float("nan")),
-                dict(nu=-1.0), dict(scheme=lbfe.IMPROVED_SMOOTH, walls=1, rho_wall=1.0)):
+                dict(nu=-1.0)):
         c = lbfe.Case(**{**ok.__dict__, **bad})
         arr = (lbfe._CCase * 1)(c.cstruct())
         assert lib.lb_workspace_bytes(arr, 1, lbfe.FP32, C.byref(nb)) == 1, bad

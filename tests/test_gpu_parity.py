@@ -652,7 +652,7 @@ def test_fp32_largest_lattice_sampled():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("shape", [(37, 24), (64, 8), (130, 41)])
 def test_fp64_walls(scheme, collision, shape):

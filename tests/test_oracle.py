@@ -561,7 +561,7 @@ def test_translating_droplet_needs_the_correction():
         assert np.sqrt(ev[1] / ev[0]) < 1.02
 
 
-@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED])
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.IMPROVED_SMOOTH])
 def test_walls_channel_startup_series(scheme):
     """Moving no-slip walls (halfway bounce-back; both walls at u = U from
     t = 0, fluid of uniform density at rest): the velocity follows the
