@@ -143,7 +143,8 @@ __device__ __forceinline__ T grady9(T N, T S, T NE, T NW, T SE, T SW)
 // the force F, velocity u (Eq. 12), mu_c (for p_m), C1 and C7 (Eq. 29; zero for
 // the standard scheme) and the rates. Output: post-collision deviations.
 // SCHEME: 0 standard, 1 improved, 2 standard with the pressure-tensor force
-// (the same collision as 0).
+// (the same collision as 0), 3 improved with the averaged correction (the
+// same collision as 1; only C1, C7 are computed differently).
 template <int SCHEME, typename T>
 __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T ux, T uy, T Fx, T Fy,
                                         T mu, T C1, T C7, T rho_ref, T c0, T lam_e, T lam_s,
