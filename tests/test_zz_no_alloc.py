@@ -73,10 +73,12 @@ def _case(nx, ny, scheme, eos, t):
 
 
 def test_static_matches_handle_path_two_calls():
-    """Two calls in a row (a larger FP32 improved case, then a smaller FP64
-    standard one) each equal lb_moments and lb_reductions within 1e-12."""
+    """Calls in a row (a larger FP32 improved case, a smaller FP64 standard
+    one, then an FP64 case of the averaged-correction scheme) each equal
+    lb_moments and lb_reductions within 1e-12."""
     runs = [(_case(300, 200, lbfe.IMPROVED, lbfe.VDW, 0.8), lbfe.FP32, 30),
-            (_case(97, 61, lbfe.STANDARD, lbfe.CS, 0.9), lbfe.FP64, 25)]
+            (_case(97, 61, lbfe.STANDARD, lbfe.CS, 0.9), lbfe.FP64, 25),
+            (_case(64, 40, lbfe.IMPROVED_SMOOTH, lbfe.VDW, 0.7), lbfe.FP64, 20)]
     for (case, rho0), prec, steps in runs:
         ref, red_ref, pops, rho_ref = _reference_and_pops(case, rho0, steps, prec)
         got, red = _static(case, prec, pops, rho_ref)
