@@ -17,9 +17,10 @@
 // columns [x0 - 4, x0 + wv + 4)), one full-mbarrier each. Stored row i = s - s0
 // lives in slot i % kPairSlots, phase (i / kPairSlots) & 1. Stage A of
 // iteration it reads rows it .. it + 2; after the block barrier that follows
-// it, row it is dead and lanes of warps 0..2 refill its slot with row
-// it + kPairSlots (one lane per plane and run), so no producer warp is needed
-// and three blocks fit on an SM.
+// it, row it is dead, and at the end of the iteration (after stage D's
+// stores, off the path of the three barrier intervals) lanes of warps 0..2
+// refill its slot with row it + kPairSlots (one lane per plane and run), so no
+// producer warp is needed and three blocks fit on an SM.
 //
 // Two block shapes share the code: NP = 128 threads (256 ring columns,
 // strips of up to 248 outputs; copies issued by warps 0-2, three planes
@@ -311,9 +312,6 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         st2(sm.rho[S0] + j, v2(c.rho_ref) + dr);
     }
     __syncthreads();
-    // stored row it (ra - 1) has no reader left: refill its slot
-    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last)
-        pair_issue<NP>(X, c, it + kPairSlots, X.ks);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -442,6 +440,11 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S2][a]);
         }
     }
+    // stored row it (ra - 1) has had no reader since stage A's barrier: refill
+    // its slot now, with the iteration's arithmetic issued (the copy still has
+    // two iterations of lead before stage A needs it)
+    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last)
+        pair_issue<NP>(X, c, it + kPairSlots, X.ks);
     X.ks = X.ks + 1 == kPairSlots ? 0 : X.ks + 1;
     if (it >= G::ND) X.rd = X.rd + 1 == c.ny ? 0 : X.rd + 1;
 }
