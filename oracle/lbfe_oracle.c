@@ -19,12 +19,16 @@
  *   6. u = (sum_a e_a f_a + F/2) / rho                   (Eq. 12)
  *   7. improved only: p_m = (c0 + mu_c)/3, phi = rho/3 - p_m,
  *      C1 = d_x(phi u_x) + d_y(phi u_y), C7 = d_x(phi u_x) - d_y(phi u_y),
- *      derivatives by the Eq. 17 stencil                  (Eqs. 24, 29)
+ *      derivatives by the Eq. 17 stencil                  (Eqs. 24, 29);
+ *      scheme 3 first replaces phi u_x, phi u_y by their lattice-weight
+ *      averages sum_a w_a (phi u)(x + e_a) (a reading: the paper does not
+ *      state how these derivatives are discretised)
  *   8. G_a from Eq. 14 for all nine a; S = M G; m = M f; m_eq from Eq. 11
  *      (standard) or Eq. 27 (improved), all as dense 9x9 products
  *   9. m* = m - Lambda (m - m_eq) + (I - Lambda/2)(S + C)  (Eqs. 9, 28, 8)
  *  10. f* = M^-1 m*, with M^-1 obtained by Gauss-Jordan elimination
- *  11. push streaming f_a(x + e_a) = f*_a(x), periodic     (Eq. 10)
+ *  11. push streaming f_a(x + e_a) = f*_a(x), periodic     (Eq. 10); with
+ *      walls, halfway bounce-back with the moving-wall term (Sec. IV C)
  *
  * M is the Lallemand-Luo D2Q9 moment matrix with moments ordered
  * (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy): the order of the relaxation
