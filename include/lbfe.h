@@ -146,7 +146,10 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
  * Eq. 10): one fused kernel launch per step and per group of cases that
  * share scheme, collision, EOS, viscosity mode and nx % 4 == 0; each launch
- * runs a work-list of (case, column strip, row segment) items. The first
+ * runs a work-list of (case, column strip, row segment) items. FP32 cases
+ * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
+ * FP64 cases, other widths, walled cases and LB_IMPROVED_SMOOTH cases run
+ * the one-column plain-load kernel. The first
  * call with nsteps > 0 autotunes the work-list: it times one step under
  * several row-segment sizes, with and without narrow blocks for the lattices
  * that fit them better, and keeps the fastest (these trial launches read
