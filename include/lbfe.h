@@ -93,9 +93,10 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * running scheme's equilibria in the two directions at the wall state
  * (rho_wall, velocity (wall_u, 0), mu_c = E_f'(rho_wall)). The stencils
  * (Laplacian, Eq. 17 gradients) see the lattice continued across each wall
- * by its mirror image: ghost rows carry the density and momentum of the
- * mirrored rows (row -k those of row k - 1) and every field is computed
- * there by the same formulas. The wall term carries momentum in proportion
+ * by its mirror image: ghost row -k holds row k - 1 reflected in the wall
+ * (the same density and j_x, j_y with its sign changed) and every field is
+ * computed there by the same formulas, so that scalar fields continue evenly
+ * and the y components of vector fields oddly. The wall term carries momentum in proportion
  * to the wall state's pressure (rho_wall / 3, or p_m of Eq. 24), so rho_wall
  * is the density of the fluid that touches the walls (rho_g for a droplet in
  * its vapour): another value drives that fluid at wall_u times the ratio of

@@ -34,6 +34,9 @@ VDW, CS = thermo.VDW, thermo.CS
 FLAG_DROP_C = 1
 FLAG_FLIP_HALF_FORCE = 2
 FLAG_ADJOINT_DROP_C = 4
+FLAG_WALL_EVEN_JY = 8
+FLAG_NU_SWAPPED = 16
+FLAG_NU_STANDARD_MAP = 32
 
 
 class _CCase(C.Structure):

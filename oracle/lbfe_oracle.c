@@ -80,7 +80,13 @@ typedef struct {
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
                           bit 0: drop the correction term C of Eq. 28
                           bit 1: flip the sign of the F/2 shift in Eq. 12
-                          bit 2: the adjoint ignores C (forward unchanged) */
+                          bit 2: the adjoint ignores C (forward unchanged)
+                          bit 3: wall ghost rows copy j_y of the mirrored row
+                                 unchanged instead of reflecting it
+                          bit 4: constant-nu map with p_m / rho in place of
+                                 rho / p_m (improved scheme)
+                          bit 5: the improved scheme takes the standard
+                                 scheme's constant-nu map */
     double a, b, R, T, kappa;
     double tau_v, tau_e, tau_s, tau_q; /* MRT rates of Eq. 8; tau_c = 1 */
     double pm_c0;                      /* p_m = (c0 + mu_c)/3; the paper's c0 is 1 */
@@ -130,8 +136,10 @@ double orc_pEOS(const orc_case* c, double rho) { return rho * orc_dEf(c, rho) - 
 static inline int wrap(int i, int n) { return ((i % n) + n) % n; }
 
 /* Row of a stencil neighbour: periodic, or, with walls, the mirror image in
- * the wall (row -1 reads row 0, row ny reads row ny - 1): every field is
- * continued evenly across a wall (a zero normal gradient at the wall). */
+ * the wall (row -1 reads row 0, row ny reads row ny - 1). Scalar fields
+ * (rho, mu_c) are continued evenly across a wall; orc_fields reflects the
+ * momentum (j_y changes sign) so that every vector field is the mirror
+ * image of the real one. */
 static inline int yrow(int walls, int y, int ny)
 {
     if (!walls) return wrap(y, ny);
@@ -283,7 +291,9 @@ void orc_guo(double ux, double uy, double Fx, double Fy, double* G)
 double orc_tau_v(const orc_case* c, double rho, double mu)
 {
     if (!(c->nu > 0.0)) return c->tau_v;
-    if (improved(c)) return 0.5 + c->nu * rho / ((c->pm_c0 + mu) / 3.0);
+    const double pm = (c->pm_c0 + mu) / 3.0;
+    if (improved(c) && (c->flags & 16)) return 0.5 + c->nu * pm / rho;
+    if (improved(c) && !(c->flags & 32)) return 0.5 + c->nu * rho / pm;
     return 0.5 + c->nu / CS2;
 }
 
@@ -438,10 +448,13 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
  * Returns 0, or -1 when rho <= 0 or a value is not finite somewhere.
  *
  * With walls, the stencils see the lattice continued across each wall by
- * its mirror image: G ghost rows below y = 0 and above y = ny - 1 carry the
- * density and momentum of the mirrored rows (row -k those of row k - 1), and
- * every field (mu_c, gradients, F, u, phi u, C, P) is then computed by the
- * same stencils on the extended lattice. */
+ * its mirror image in the wall plane (y = -1/2 and y = ny - 1/2): G ghost
+ * rows below y = 0 and above y = ny - 1 carry the reflected state of the
+ * mirrored rows (row -k that of row k - 1): the same density and j_x, and
+ * j_y with its sign changed, as reflecting the populations across the wall
+ * gives. Every field (mu_c, gradients, F, u, phi u, C, P) is then computed
+ * by the same stencils on the extended lattice, so that scalar fields come
+ * out even across the wall and the y components of vector fields odd. */
 int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, double* uy_o,
                double* mu_o, double* Fx_o, double* Fy_o, double* C1_o, double* C7_o)
 {
@@ -477,10 +490,12 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
         for (int k = 0; k < 8; ++k) out[k] = buf + (3 + k) * Ne;
         for (int g = 0; g < ce.ny; ++g) {
             const int y = yrow(1, g - G, ny);
+            const int ghost = g < G || g >= G + ny;
+            const double sy = ghost && !(c->flags & 8) ? -1.0 : 1.0;
             for (int x = 0; x < nx; ++x) {
                 re[g * nx + x] = rho[y * nx + x];
                 xe[g * nx + x] = jx[y * nx + x];
-                ye[g * nx + x] = jy[y * nx + x];
+                ye[g * nx + x] = sy * jy[y * nx + x];
             }
         }
         rc = fields_core(&ce, re, xe, ye, out[0], out[1], out[2], out[3], out[4], out[5], out[6], out[7]);

@@ -130,6 +130,14 @@ struct PullGlobal {
                 F[7] = __ldg(fin + (5 * P + r0 + L.xc)) - c.wall_d;
                 F[8] = __ldg(fin + (6 * P + r0 + L.xc)) + c.wall_d;
             }
+            if (rows.sa != m) {
+                // a ghost row is the mirror image of row m: its populations
+                // reflected in y (2 <-> 4, 5 <-> 8, 6 <-> 7), so that rho and
+                // j_x continue evenly across the wall and j_y oddly
+                T t = F[2]; F[2] = F[4]; F[4] = t;
+                t = F[5]; F[5] = F[8]; F[8] = t;
+                t = F[6]; F[6] = F[7]; F[7] = t;
+            }
             return;
         }
         const uint32_t r0 = (uint32_t)rows.ra * pitch;

@@ -383,6 +383,33 @@ def test_shear_wave_viscosity(scheme):
     assert abs(got / (nu * k * k) - 1) < 0.01
 
 
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED])
+@pytest.mark.parametrize("collision", [O.BGK, O.MRT])
+def test_constant_viscosity_shear_wave_at_two_densities(scheme, collision):
+    """Constant kinematic viscosity (Sec. III below Eq. 29 for the improved
+    scheme, Sec. II A below Eq. 8 for the standard one): tau_v follows from
+    eta = nu rho per node, so a shear wave decays at nu k^2 whatever the
+    density. Checked in a uniform gas (rho_g) and a uniform liquid (rho_l) of
+    the vdW set at 0.8 T_c, whose ratio rho / p_m differs by a factor of
+    eight; the planted maps (p_m / rho in place of rho / p_m, or the standard
+    scheme's map in the improved scheme) miss by more than 15 %."""
+    ny, nu, n, amp = 64, 0.05, 400, 1e-6
+    k = 2 * np.pi / ny
+    y = np.arange(ny)[:, None] * np.ones((1, 4))
+    for rho_key in ("gas", "liquid"):
+        for flags in (0, O.FLAG_NU_SWAPPED, O.FLAG_NU_STANDARD_MAP):
+            c, rg, rl = vdw_case(0.8, scheme=scheme, nx=4, ny=ny, collision=collision, tau_v=1.0, nu=nu, flags=flags)
+            rho = rg if rho_key == "gas" else rl
+            f = O.init(c, np.full((ny, 4), rho), ux0=amp * np.sin(k * y))
+            assert O.step(c, f, n) == n
+            ux = O.fields(c, f).ux[:, 0]
+            nu_got = -np.log((ux @ np.sin(k * np.arange(ny))) / (ny / 2) / amp) / n / (k * k)
+            if flags == 0 or scheme == O.STANDARD:  # the flags plant mistakes in the improved map only
+                assert abs(nu_got / nu - 1) < 0.015, (rho_key, flags, nu_got)
+            else:
+                assert abs(nu_got / nu - 1) > 0.15, (rho_key, flags, nu_got)
+
+
 # ------------------------------------------------ the paper's printed results
 @pytest.mark.parametrize("row", [r for r in _table2() if r[0] != 0.7])
 def test_improved_flat_interface_table2(row):
@@ -664,3 +691,67 @@ def test_spurious_currents_table1():
         out[scheme] = np.sqrt(fl.ux**2 + fl.uy**2).max()
     assert out[O.IMPROVED] < imp_hi
     assert std_lo / 3 < out[O.STANDARD] < 3 * std_lo
+
+
+REFL_Y = np.array([0, 1, 4, 3, 2, 8, 7, 6, 5])  # e_REFL_Y[a] = (e_a,x, -e_a,y)
+
+
+@pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.STANDARD_PT, O.IMPROVED_SMOOTH])
+def test_walls_are_mirror_planes_of_the_doubled_lattice(scheme):
+    """Sec. IV C's plates with the stencils continued across each wall by its
+    mirror image. A periodic lattice of height 2 ny whose upper half is the
+    reflection of the lower half (rows reversed, populations reflected in y)
+    keeps that symmetry, and its stencils at rows 0 .. ny - 1 then see
+    exactly the mirror image of the walled lattice. So one step of the walled
+    lattice equals one step of the doubled periodic lattice at every
+    population that does not cross a wall (interior rows, and the wall rows'
+    populations from inside), to round-off; the population normal to the wall
+    agrees too (halfway bounce-back of e_2 and specular reflection coincide).
+    A non-uniform density, a random velocity field and non-equilibrium
+    populations make every stencil depend on the ghost rows; for the improved
+    schemes the reflected momentum (j_y odd) is what makes phi u_y odd, and
+    the planted even copy of j_y misses by ~1e-2."""
+    nx, ny = 12, 10
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    rng = np.random.default_rng(3)
+    y, x = np.mgrid[0:ny, 0:nx]
+    rho = rg + (rl - rg) * (0.5 + 0.4 * np.sin(2 * np.pi * x / nx + 0.3) * np.cos(1.3 * np.pi * (y + 0.5) / ny + 0.2))
+    rho += 0.05 * rng.standard_normal((ny, nx))
+    ux, uy = 0.02 * rng.standard_normal((2, ny, nx))
+    kw = dict(scheme=scheme, eos=O.VDW, a=e.a, b=e.b, R=1.0, T=T, kappa=0.02, collision=O.MRT, tau_v=0.8)
+    f0 = O.init(O.Case(nx=nx, ny=ny, **kw), rho, ux, uy) + 1e-3 * rng.standard_normal((9, ny, nx))
+    for flags in (0, O.FLAG_WALL_EVEN_JY):
+        f = f0.copy()
+        f2 = np.ascontiguousarray(np.concatenate([f0, f0[REFL_Y][:, ::-1, :]], axis=1))
+        assert O.step(O.Case(nx=nx, ny=ny, walls=1, wall_u=0.1, rho_wall=rg, flags=flags, **kw), f, 1) == 1
+        assert O.step(O.Case(nx=nx, ny=2 * ny, flags=flags, **kw), f2, 1) == 1
+        d = np.abs(f - f2[:, :ny])
+        worst = max(d[:, 1:ny - 1].max(), d[[0, 1, 2, 3, 4, 7, 8], 0].max(), d[[0, 1, 2, 3, 4, 5, 6], ny - 1].max())
+        if flags == 0 or scheme in (O.STANDARD, O.STANDARD_PT):  # the standard collision takes u at the node only
+            assert worst < 1e-14, (flags, worst)
+        else:
+            assert worst > 1e-3, (flags, worst)
+        # the diagonal populations that return from a wall differ (no-slip, not specular)
+        assert d[[5, 6], 0].max() > 1e-3
+
+
+def test_walls_keep_a_flat_slab_at_rest():
+    """Improved scheme, Sec. IV C's plates at rest across a flat liquid slab
+    whose interfaces meet the walls (density varies along the walls): the
+    converged periodic flat interface (uniform mu_c, u at round-off, Table
+    I's improved level) stays an exact steady state between the walls, with
+    max |u| at round-off and mu_c uniform, after 3000 steps."""
+    nx, ny = 64, 12
+    c, rg, rl = vdw_case(0.8, nx=nx, ny=4, tau_v=1.0)
+    f = O.init(c, inputs.slab(nx, 4, rl, rg))
+    assert O.step(c, f, 16000) == 16000
+    fl = O.fields(c, f)
+    assert np.abs(fl.ux).max() < 1e-14 and fl.mu.max() - fl.mu.min() < 1e-14
+    cw, _, _ = vdw_case(0.8, nx=nx, ny=ny, tau_v=1.0, walls=1, wall_u=0.0, rho_wall=rg)
+    fw = np.ascontiguousarray(np.concatenate([f[:, :1, :]] * ny, axis=1))
+    assert O.step(cw, fw, 3000) == 3000
+    fl = O.fields(cw, fw)
+    assert np.sqrt(fl.ux ** 2 + fl.uy ** 2).max() < 1e-13
+    assert fl.mu.max() - fl.mu.min() < 1e-13
+    np.testing.assert_allclose(fl.rho, np.broadcast_to(fl.rho[:1], fl.rho.shape), atol=1e-12)
