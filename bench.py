@@ -61,7 +61,7 @@ def _dist():
     return ws, rank, local
 
 
-PROFILE = os.path.join(ROOT, "profiles", "step_kernel_pair_spinodal4096.md")
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_pair_spinodal4096.json")
 # files that define the FP32 step kernel and its launch
 STEP_SOURCES = ("launch.h", "lbfe_device.cuh", "step_f32.cu", "step_kernel.cuh", "step_pair.cuh", "step_tma.cuh")
 
@@ -79,23 +79,17 @@ def _kernel_source_sha256() -> str:
 
 
 def _profiled_traffic(n_side: int):
-    """DRAM bytes per step launch from the committed ncu summary of this
-    workload, or None if the kernel sources changed since it was taken."""
-    if n_side != N_SIDE:
-        return None
+    """DRAM bytes per step launch from the committed ncu record of this
+    workload (profiles/*.json), or None if the kernel sources changed since it
+    was taken or the lattice differs."""
     try:
         with open(PROFILE) as fh:
-            txt = fh.read()
-    except OSError:
+            rec = json.load(fh)
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for line in txt.splitlines():
-        for key in ("source_sha256:", "traffic_bytes_per_launch:"):
-            if line.startswith(key):
-                vals[key] = line.split(":", 1)[1].strip()
-    if vals.get("source_sha256:") != _kernel_source_sha256() or "traffic_bytes_per_launch:" not in vals:
+    if rec.get("nx") != n_side or rec.get("source_sha256") != _kernel_source_sha256():
         return None
-    return int(vals["traffic_bytes_per_launch:"])
+    return int(rec["traffic_bytes_per_launch"])
 
 
 # FP64 step (one column per thread): FP64 instructions executed per node update,
@@ -137,8 +131,8 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, index: str):
+        self.index = index  # nvidia-smi id of the GPU (PCI bus id, or its index)
         self.p = None
 
     def start(self):
@@ -212,20 +206,55 @@ def _parse_cpulist(txt: str) -> set:
     return cpus
 
 
-def _bind_to_gpu_node(index: int):
-    """Restrict this process to the host cores local to GPU `index` (from
-    sysfs), so that its pinned host buffers are allocated on that GPU's memory
-    node; returns the core list, or None where the topology is not exposed."""
+def _format_cpulist(cpus) -> str:
+    """The inverse of _parse_cpulist: sorted ranges, e.g. '0-7,64-71'."""
+    out, run = [], []
+    for c in sorted(cpus):
+        if run and c == run[-1] + 1:
+            run.append(c)
+            continue
+        if run:
+            out.append(f"{run[0]}-{run[-1]}" if len(run) > 1 else str(run[0]))
+        run = [c]
+    if run:
+        out.append(f"{run[0]}-{run[-1]}" if len(run) > 1 else str(run[0]))
+    return ",".join(out)
+
+
+def _pci_ids(props):
+    """(nvidia-smi id, sysfs name) of a CUDA device from its PCI location
+    (torch device properties: pci_domain_id, pci_bus_id, pci_device_id). The
+    CUDA ordinal is not nvidia-smi's index once CUDA_VISIBLE_DEVICES remaps
+    the devices; the bus id names the same GPU for both."""
+    dom, bus, dev = (int(getattr(props, k)) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+    return f"{dom:08X}:{bus:02X}:{dev:02X}.0", f"{dom:04x}:{bus:02x}:{dev:02x}.0"
+
+
+def _gpu_ids(local: int):
+    """PCI ids of CUDA device `local`, or (str(local), None) where torch does
+    not expose the PCI location."""
+    import torch
+
     try:
-        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
-                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
-        dom, rest = out.split(":", 1)
-        with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist") as fh:
+        return _pci_ids(torch.cuda.get_device_properties(local))
+    except Exception:
+        return str(local), None
+
+
+def _bind_to_gpu_node(sysfs_name):
+    """Restrict this process to the host cores local to the GPU at PCI
+    location `sysfs_name`, so that its pinned host buffers are allocated on
+    that GPU's memory node; returns the core list, or None where the topology
+    is not exposed."""
+    if not sysfs_name:
+        return None
+    try:
+        with open(f"/sys/bus/pci/devices/{sysfs_name}/local_cpulist") as fh:
             cpus = _parse_cpulist(fh.read()) & os.sched_getaffinity(0)
         if not cpus:
             return None
         os.sched_setaffinity(0, cpus)
-        return f"{min(cpus)}-{max(cpus)} ({len(cpus)} cores)"
+        return f"{_format_cpulist(cpus)} ({len(cpus)} cores)"
     except Exception:
         return None
 
@@ -236,8 +265,9 @@ def run_gpu(args):
     from paper_2008_01473_gb300 import build, inputs, lbfe
 
     ws, rank, local = _dist()
-    host_cpus = _bind_to_gpu_node(local)
     torch.cuda.set_device(local)
+    smi_id, sysfs_name = _gpu_ids(local)
+    host_cpus = _bind_to_gpu_node(sysfs_name)
     if ws > 1:
         import torch.distributed as dist
 
@@ -267,7 +297,7 @@ def run_gpu(args):
     lat.init_fields(0, rho0_pin)
     lat.step(args.warmup)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    clocks = Clocks(local)
+    clocks = Clocks(smi_id)
     clocks.start()
     time.sleep(0.4)
     barrier()
@@ -284,20 +314,31 @@ def run_gpu(args):
     stable = bool(st[0] == 0)
 
     # ------------------------------------------------------------ end to end
-    res = {k: torch.empty((n_side, n_side), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
-    barrier()
-    t0 = time.perf_counter()
-    lat.init_fields(0, rho0_pin)
-    lat.step(args.steps)
     import ctypes as C
 
-    rc = lbfe.lib().lb_moments(lat._h, 0, C.c_void_p(res["rho"].data_ptr()), C.c_void_p(res["ux"].data_ptr()),
-                               C.c_void_p(res["uy"].data_ptr()), None, 0)
-    lbfe._check(rc, lat._h)
+    res = {k: torch.empty((n_side, n_side), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
+
+    def end_to_end():
+        lat.init_fields(0, rho0_pin)
+        lat.step(args.steps)
+        rc = lbfe.lib().lb_moments(lat._h, 0, C.c_void_p(res["rho"].data_ptr()), C.c_void_p(res["ux"].data_ptr()),
+                                   C.c_void_p(res["uy"].data_ptr()), None, 0)
+        lbfe._check(rc, lat._h)
+
+    end_to_end()  # warm-up: graphs for both buffer parities, first-touch of the pinned outputs
+    barrier()
+    t0 = time.perf_counter()
+    end_to_end()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, ws, f"cuda:{local}")
     seg_rows, n_items, narrow = lat.worklist()
     lat.close()
     cs = _cs_variant(lbfe, inputs, n_side, prec, local, rank) if ws == 1 else None
+    extras = {}
+    if ws == 1 and dtype == "f32" and not args.no_extras:
+        # the other measured targets, outside the timed region, a few seconds each
+        extras["batched"] = _batched_throughput(lbfe, steps=20, warmup=5)
+        extras["fp64"] = _fp64_spinodal(lbfe, inputs, n_side, steps=5, warmup=3, local=local, rank=rank)
+        extras["adjoint"] = _adjoint_check(lbfe, inputs, steps=200, window=20, ckpt=20)
 
     if rank == 0:
         peak, src = _peaks()
@@ -339,6 +380,7 @@ def run_gpu(args):
         }
         if cs is not None:
             line["eos_cs"] = cs
+        line.update(extras)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
         print(json.dumps(line), flush=True)
@@ -433,6 +475,55 @@ def _batched_r0(rho0):
     return float(np.argmax(row < mid))
 
 
+def _batched_throughput(lbfe, steps: int, warmup: int) -> dict:
+    """The uneven 256-case batch in one handle (one launch per step) and with
+    one handle per case (one launch per case per step): MLUPS of each, CUDA
+    events on the handles' stream around `steps` steps after `warmup`."""
+    import torch
+
+    cases, rhos = batched_cases(lbfe)
+    nodes = sum(c.nx * c.ny for c in cases)
+    lat = lbfe.Lattice(cases, precision=lbfe.FP32)
+    for i, r in enumerate(rhos):
+        lat.init_fields(i, r)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    _, st = lat.reductions()
+    seg_rows, n_items, narrow = lat.worklist()
+    lat.close()
+    lats = []
+    for c, r in zip(cases, rhos):
+        l1 = lbfe.Lattice([c], precision=lbfe.FP32)
+        l1.init_fields(0, r)
+        l1.step(warmup)
+        lats.append(l1)
+    torch.cuda.synchronize()
+    e0.record(lats[0].stream)
+    for l1 in lats:
+        l1.step(steps)
+    e1.record(lats[0].stream)
+    torch.cuda.synchronize()
+    per_case_ms = e0.elapsed_time(e1)
+    for l1 in lats:
+        l1.close()
+    return {"value": round(nodes * steps / (batched_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps,
+            "ms_per_step": round(batched_ms / steps, 4), "n_cases": len(cases), "nodes": nodes,
+            "stable_cases": int((st == 0).sum()),
+            "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows),
+                         "items": n_items, "narrow_blocks": narrow},
+            "per_case_launches": {"value": round(nodes * steps / (per_case_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
+                                  "ms_per_step": round(per_case_ms / steps, 4)},
+            "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / steps * 1e-3) / 1e9, 1),
+                         "peak": _peaks()[0], "unit": "GB/s",
+                         "frac": round(72 * nodes / (batched_ms / steps * 1e-3) / 1e9 / _peaks()[0], 4)}}
+
+
 def run_batched(args):
     """Throughput of the uneven batch in one handle (one launch per step)
     against one handle per case (one launch per case per step)."""
@@ -443,50 +534,16 @@ def run_batched(args):
     build.build()
     torch.cuda.set_device(0)
     cases, rhos = batched_cases(lbfe)
-    nodes = sum(c.nx * c.ny for c in cases)
-    lat = lbfe.Lattice(cases, precision=lbfe.FP32)
-    for i, r in enumerate(rhos):
-        lat.init_fields(i, r)
-    lat.step(args.warmup)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(lat.stream)
-    lat.step(args.steps)
-    e1.record(lat.stream)
-    torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1)
-    _, st = lat.reductions()
-    seg_rows, n_items, narrow = lat.worklist()
-    lat.close()
+    b = _batched_throughput(lbfe, args.steps, args.warmup)
     acc = _batched_accuracy(lbfe, cases[::8], rhos[::8], args.accuracy_steps) if args.accuracy_steps else None
-    lats = []
-    for c, r in zip(cases, rhos):
-        l1 = lbfe.Lattice([c], precision=lbfe.FP32)
-        l1.init_fields(0, r)
-        l1.step(args.warmup)
-        lats.append(l1)
-    torch.cuda.synchronize()
-    e0.record(lats[0].stream)
-    for l1 in lats:
-        l1.step(args.steps)
-    e1.record(lats[0].stream)
-    torch.cuda.synchronize()
-    per_case_ms = e0.elapsed_time(e1)
-    for l1 in lats:
-        l1.close()
-    v = nodes * args.steps / (batched_ms * 1e-3) / 1e6
-    line = {"metric": METRIC, "value": round(v, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(batched_ms / args.steps, 4), "higher_is_better": True,
+    line = {"metric": METRIC, "value": b["value"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched uneven droplets: " + (batched_cases.__doc__ or "").split(":")[1].strip(),
-                       "n_cases": len(cases), "nodes": nodes, "stable_cases": int((st == 0).sum()),
-                       "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows), "items": n_items,
-                                    "narrow_blocks": narrow}},
+                       "n_cases": b["n_cases"], "nodes": b["nodes"], "stable_cases": b["stable_cases"],
+                       "worklist": b["worklist"]},
             "fp32_vs_fp64": acc,  # every 8th case of the batch
-            "per_case_launches": {"value": round(nodes * args.steps / (per_case_ms * 1e-3) / 1e6, 1),
-                                  "unit": "MLUPS", "ms_per_step": round(per_case_ms / args.steps, 4)},
-            "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / args.steps * 1e-3) / 1e9, 1),
-                         "peak": _peaks()[0], "unit": "GB/s"}}
+            "per_case_launches": b["per_case_launches"], "roofline": b["roofline"]}
     if not args.no_cpu:
         import numpy as np
 
@@ -498,24 +555,21 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def run_adjoint(args):
-    """Differentiation workload: 256^2 periodic droplet of radius 64 (vdW, T =
-    0.8 T_c, kappa 0.02, BGK tau 0.8, FP64), 2000 steps checkpointed every 100;
-    L = sum of |u|^2 over the last 100 steps + (rho_g - rho_g^Maxwell(T))^2 with
-    rho_g the mean density over the four corner squares of side L/8. Times the
-    gradient (forward + reverse sweep) and checks dL/dkappa and dL/d(T/T_c)
-    against central differences (h = 3e-6 relative) of the GPU forward loss."""
+def _adjoint_check(lbfe, inputs, steps: int, window: int, ckpt: int, n: int = 256) -> dict:
+    """Gradient of the droplet loss (n^2 periodic droplet of radius n/4, vdW
+    at T = 0.8 T_c, kappa 0.02, BGK tau 0.8, FP64): L = sum of |u|^2 over the
+    last `window` steps of `steps` + (rho_g - rho_g^Maxwell(T))^2, rho_g the
+    mean density over the four corner squares of side n/8. Times the
+    lb_adjoint_step sweep (checkpoints every `ckpt` steps) and checks dL/dkappa
+    and dL/d(T/T_c) against central differences (h = 3e-6 relative) of the
+    GPU forward loss; also the same gradient from an FP32 handle."""
     import numpy as np
     import torch
 
-    from paper_2008_01473_gb300 import build, inputs, lbfe
-
-    build.build()
-    n, steps, window, ckpt = 256, 2000, 100, 100
     tc, _ = lbfe.critical(lbfe.VDW, **VDW)
     t_red = 0.8
     rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc)
-    rho0 = inputs.droplet(n, n, 64.0, rl, rg)
+    rho0 = inputs.droplet(n, n, n / 4.0, rl, rg)
     m = n // 8
     w = np.zeros((n, n))
     for ys in (slice(0, m), slice(n - m, n)):
@@ -545,21 +599,16 @@ def run_adjoint(args):
     kappa = 0.02
     L0, rho_g, gm = forward_loss(kappa, t_red)
     s_final = 2.0 * (rho_g - gm) * w
-    lat = lbfe.Lattice([case(kappa, t_red)], precision=lbfe.FP64)
-    lat.adjoint(0, rho0, 8, 0, None, 0)  # warm-up: module load, first launches
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    La, g_rho0, gk, gT = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt)
-    t_adj = time.perf_counter() - t0
-    lat.close()
-    # the same gradient from an FP32 handle (FP32 forward, recompute and reverse sweep)
-    lat = lbfe.Lattice([case(kappa, t_red)], precision=lbfe.FP32)
-    lat.adjoint(0, rho0, 8, 0, None, 0)  # warm-up: module load, first launches
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    La32, g32, gk32, gT32 = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt)
-    t_adj32 = time.perf_counter() - t0
-    lat.close()
+    out = {}
+    for prec in (lbfe.FP64, lbfe.FP32):
+        lat = lbfe.Lattice([case(kappa, t_red)], precision=prec)
+        lat.adjoint(0, rho0, 8, 0, None, 0)  # warm-up: module load, first launches
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out[prec] = lat.adjoint(0, rho0, steps, steps - window, s_final, ckpt) + (time.perf_counter() - t0,)
+        lat.close()
+    La, g_rho0, gk, gT, t_adj = out[lbfe.FP64]
+    La32, g32, gk32, gT32, t_adj32 = out[lbfe.FP32]
     fp32 = {"adjoint_seconds": round(t_adj32, 3), "rel_diff_loss": abs(La32 / La - 1),
             "rel_diff_dL_dkappa": abs(gk32 / gk - 1), "rel_diff_dL_dT_trajectory": abs(gT32 / gT - 1),
             "rel_diff_dL_drho0_max": float(np.abs(g32 - g_rho0).max() / np.abs(g_rho0).max())}
@@ -568,20 +617,62 @@ def run_adjoint(args):
     dgm = (lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc + hT)[0]
            - lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t_red * tc - hT)[0]) / (2 * hT)
     dL_dt = tc * (gT - 2.0 * (rho_g - gm) * dgm)
-    # h = 1e-4 relative leaves an O(h^2) truncation error of 3e-4 in dL/dT here
-    # (the loss is strongly curved in T); 3e-6 brings it below 1e-6
+    # h = 1e-4 relative leaves an O(h^2) truncation error of 3e-4 in dL/dT on
+    # the 2000-step horizon (the loss is strongly curved in T); 3e-6 brings it
+    # below 1e-6
     hk, ht = 3e-6 * kappa, 3e-6 * t_red
     fd_k = (forward_loss(kappa + hk, t_red)[0] - forward_loss(kappa - hk, t_red)[0]) / (2 * hk)
     fd_t = (forward_loss(kappa, t_red + ht)[0] - forward_loss(kappa, t_red - ht)[0]) / (2 * ht)
-    line = {"metric": "adjoint gradient (lb_adjoint_step) vs central differences", "workload": run_adjoint.__doc__.split(".")[0],
-            "loss": L0, "adjoint_seconds": round(t_adj, 3),
+    return {"workload": f"{n}x{n} droplet r={n // 4}, vdW 0.8 T_c, BGK tau 0.8, {steps} steps, |u|^2 over the last "
+                        f"{window}, checkpoints every {ckpt}, FP64",
+            "loss": L0, "rel_diff_loss_adjoint_vs_forward": abs(La / L0 - 1), "adjoint_seconds": round(t_adj, 3),
             "adjoint_node_steps_per_s": round(n * n * steps / t_adj, 1),
             "dL_dkappa": {"adjoint": gk, "fd": fd_k, "rel_err": abs(gk - fd_k) / abs(fd_k)},
             "dL_dT_over_Tc": {"adjoint": dL_dt, "fd": fd_t, "rel_err": abs(dL_dt - fd_t) / abs(fd_t)},
             "fd_rel_step": 3e-6,
             "dL_drho0_norm": float(np.sqrt((g_rho0 ** 2).sum())), "rho_g": rho_g, "rho_g_maxwell": gm,
             "fp32_adjoint_vs_fp64": fp32}
+
+
+def run_adjoint(args):
+    """Differentiation workload: the 256^2 droplet of radius 64, 2000 steps
+    checkpointed every 100, loss over the last 100 steps (_adjoint_check)."""
+    from paper_2008_01473_gb300 import build, inputs, lbfe
+
+    build.build()
+    line = {"metric": "adjoint gradient (lb_adjoint_step) vs central differences",
+            **_adjoint_check(lbfe, inputs, steps=2000, window=100, ckpt=100)}
     print(json.dumps(line), flush=True)
+
+
+def _fp64_spinodal(lbfe, inputs, n_side: int, steps: int, warmup: int, local: int, rank: int) -> dict:
+    """The same spinodal lattice with FP64 populations and arithmetic: MLUPS
+    and the FP64-pipe roofline of the one-column step kernel."""
+    import torch
+
+    tc, _ = lbfe.critical(lbfe.VDW, **VDW)
+    T = T_RED * tc
+    rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], T)
+    case = lbfe.Case(nx=n_side, ny=n_side, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, T=T,
+                     kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW)
+    lat = lbfe.Lattice([case], precision=lbfe.FP64, device=f"cuda:{local}")
+    lat.init_fields(0, inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), 0.01, seed=1 + rank))
+    lat.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    _, st = lat.reductions()
+    lat.close()
+    nodes = n_side * n_side
+    peak, _ = _peaks()
+    return {"value": round(nodes / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps, "ms_per_step": round(ms, 4),
+            "workload": f"spinodal {n_side}x{n_side}, improved, MRT, vdW at T/Tc={T_RED}, FP64 populations",
+            "stable": bool(st[0] == 0),
+            "roofline": _fp64_roofline(nodes, ms, 144 * nodes / (ms * 1e-3) / 1e9 / peak)}
 
 
 def _droplet_shape(rho, rho_g):
@@ -741,7 +832,7 @@ def _oracle_pool_baseline(cases, rhos, steps, what):
     keys = ("nx", "ny", "scheme", "collision", "eos", "a", "b", "R", "T", "kappa", "tau_v", "tau_e", "tau_s",
             "tau_q", "nu")
     jobs = [({k: getattr(c, k) for k in keys}, r, steps) for c, r in zip(cases, rhos)]
-    cores = min(len(jobs), os.cpu_count() or 1)
+    cores = min(len(jobs), len(os.sched_getaffinity(0)))
     with mp.get_context("spawn").Pool(cores) as pool:
         res = pool.map(_oracle_case_steps, jobs, chunksize=1)
     per_proc = {}
@@ -809,6 +900,8 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=10000,
                     help="batched workload: steps of the FP32-vs-FP64 droplet check (0 skips it)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the batched, fp64 and adjoint sub-measurements")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "adjoint", "sweep", "galilean"],

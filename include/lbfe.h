@@ -164,8 +164,44 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
  * steps replay a CUDA graph captured on the first such call (on a private
  * stream, then launched on the handle's stream; set LBFE_GRAPH=0 before
  * lb_create to launch every step directly). Enqueued asynchronously, except
- * that the autotuning call synchronises the stream. */
+ * that the autotuning call synchronises the stream.
+ * Instability: a step kernel that meets a node with rho <= 0 or a
+ * non-finite density flags the case on the device; from the next launch on
+ * the case's blocks return at once, so it stops advancing (its buffers keep
+ * its last two states) while the other cases of the handle go on, with no
+ * host round trip. lb_reductions reports the case as LB_E_UNSTABLE until
+ * lb_init_fields or lb_load gives it a new state. */
 lb_status lb_step(lb_handle* h, int64_t nsteps);
+
+/* Persistent multi-step launch. For a handle whose cases all share one
+ * kernel group (same scheme, collision, EOS and viscosity mode), lb_step can
+ * run n steps as cooperative launches of a persistent kernel (up to 1024
+ * steps each) instead of one launch per step: the blocks stay resident,
+ * each owning items of the work-list, and an item's step waits (bounded)
+ * until the neighbouring items have completed the step before. It serves
+ * lattices small enough to live in L2, where one launch per step is bound
+ * by launch latency. The persistent kernel is the one-column kernel.
+ * mode: 0 never; 1 always (an FP32 group with nx % 4 == 0 then leaves the
+ * packed kernel for the one-column one, whose FP32 rounding differs in the
+ * last bits); 2 (default) automatic: for a handle whose group already runs
+ * the one-column kernel (FP64; FP32 with nx % 4 != 0, walls or
+ * LB_IMPROVED_SMOOTH), the first lb_step of at least 40 steps times 16 steps
+ * of graph replay against 16 persistent steps (its own steps: results are
+ * identical either way) and keeps the faster; -1 leaves the mode unchanged.
+ * *persistent (may be NULL) tells whether the persistent launch is in use.
+ * A wait that gives up (about one second) sets the status word that
+ * lb_reductions reports as LB_E_TIMEOUT, and the launch returns. */
+lb_status lb_launch_mode(lb_handle* h, int32_t mode, int32_t* persistent);
+
+/* Failure-detection self-test of the persistent launch (the paper has no
+ * counterpart): runs nsteps (2 .. 1024) persistent steps in which work item
+ * 0 never publishes its progress and every wait gives up after about 10 ms
+ * of SM clock. The first block that waits for item 0 gives up and sets the
+ * launch's abort word, every other waiting block returns, and the next
+ * lb_reductions reports LB_E_TIMEOUT. The handle's populations are then
+ * unreliable (reinitialise them); the GPU context stays usable. Needs a
+ * one-group handle whose work-list has at least two items. */
+lb_status lb_persistent_selftest(lb_handle* h, int64_t nsteps);
 
 /* The work-list in use: rows per segment (0: slot-share rule, -1: the
  * filled slot-share rule), item count,
@@ -184,7 +220,8 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
 /* Reductions of every case's current state, FP64 sums in a fixed order:
  * out[5*c + {0,1,2,3,4}] = {mass sum rho, kinetic energy sum rho|u|^2/2,
  * max |u|, step count, 0} with rho, u of Eq. 12; case_status[c] = LB_OK or
- * LB_E_UNSTABLE (rho <= 0 or a non-finite value at some node). Host
+ * LB_E_UNSTABLE (rho <= 0 or a non-finite value at some node now, or the
+ * case was flagged by a step kernel and frozen, see lb_step). Host
  * pointers (case_status may be NULL); synchronises the stream. Returns
  * LB_E_UNSTABLE if any case is unstable; every entry is still written. */
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
@@ -299,7 +336,9 @@ lb_status lb_maxwell(int32_t eos, double a, double b, double R, double T, double
  * runtime call); make that first call before any stream capture. Every call
  * on a device shares the one array: calls whose work may overlap on the GPU
  * (different streams without ordering, or concurrent host threads) race and
- * must be serialised by the caller. */
+ * must be serialised by the caller. A CUDA error already pending on the
+ * calling thread when the call starts gives LB_E_CUDA with nothing enqueued
+ * and the error left in place for its owner. */
 #define LB_STATIC_MAX_SIDE 4096
 #define LB_STATIC_MAX_NODES 262144
 lb_status lb_fields_static(const lb_case* c, int32_t precision, const void* d_pops, double rho_ref,

@@ -3,11 +3,36 @@
 // step, through scratch fields of type C in the workspace: C is the storage
 // precision of the populations (per-node arithmetic in C; every sum over the
 // lattice in FP64).
+//
+// Launch shape of the per-node kernels: 256-thread blocks over
+// field_grid(nx, ny); thread x of block (bx, by) handles column
+// 256 bx + x of the kFieldRows rows from kFieldRows by, so that a thread
+// accumulates its sums over several nodes in FP64 registers and each block
+// reduces once. Neighbour rows and columns wrap by comparison, not by
+// integer division.
 #pragma once
 
 #include "lbfe_device.cuh"
 
 namespace lbfe {
+
+constexpr int kFieldRows = 16;  // rows per block of the per-node field kernels
+
+inline dim3 field_grid(int nx, int ny) { return dim3((nx + 255) / 256, (ny + kFieldRows - 1) / kFieldRows); }
+
+// periodic neighbour columns, and neighbour rows (periodic, or mirrored in a wall)
+__device__ __forceinline__ int col_m1(int x, int nx) { return x == 0 ? nx - 1 : x - 1; }
+__device__ __forceinline__ int col_p1(int x, int nx) { return x + 1 == nx ? 0 : x + 1; }
+template <typename T>
+__device__ __forceinline__ int row_m1(const DevCase<T>& c, int y)
+{
+    return y > 0 ? y - 1 : (c.walls ? 0 : c.ny - 1);
+}
+template <typename T>
+__device__ __forceinline__ int row_p1(const DevCase<T>& c, int y)
+{
+    return y + 1 < c.ny ? y + 1 : (c.walls ? c.ny - 1 : 0);
+}
 
 // Per-block partial sums: mass (or any sum), kinetic energy, max |u|^2 and a
 // count of non-physical nodes.
@@ -47,78 +72,116 @@ __device__ __forceinline__ void block_partial(double mass, double ke, double um,
     }
 }
 
+// Block reduction of per-thread accumulators (blockDim.x == 256, every
+// thread calls it) into partials[block index]: sums of mass and kinetic
+// energy, max |u|^2 and the count of non-physical nodes.
+__device__ __forceinline__ void block_sums(double mass, double ke, double um2, int bad,
+                                           Partial* __restrict__ partials)
+{
+    __shared__ double s[3][8];
+    __shared__ int sb[8];
+    for (int o = 16; o > 0; o >>= 1) {
+        mass += __shfl_xor_sync(0xffffffffu, mass, o);
+        ke += __shfl_xor_sync(0xffffffffu, ke, o);
+        um2 = fmax(um2, __shfl_xor_sync(0xffffffffu, um2, o));
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s[0][w] = mass;
+        s[1][w] = ke;
+        s[2][w] = um2;
+        sb[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Partial p{0.0, 0.0, 0.0, 0.0};
+        int nb = 0;
+        for (int k = 0; k < 8; ++k) {
+            p.mass += s[0][k];
+            p.ke += s[1][k];
+            p.umax2 = fmax(p.umax2, s[2][k]);
+            nb += sb[k];
+        }
+        p.bad = (double)nb;
+        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = p;
+    }
+}
+
 // Copy the FP64 initial density into C scratch and check it: one Partial per
 // block with the sum of rho0 and the count of values that are not finite,
 // not > 0, or outside the EOS domain (b rho < 1 for vdW, b rho / 4 < 1 for CS).
 template <typename C>
-__global__ void __launch_bounds__(256) rho0_kernel(int nx, int eos, double b, const double* __restrict__ rho0,
-                                                   C* __restrict__ out, Partial* __restrict__ partials)
+__global__ void __launch_bounds__(256) rho0_kernel(int nx, int ny, int eos, double b,
+                                                   const double* __restrict__ rho0, C* __restrict__ out,
+                                                   Partial* __restrict__ partials)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    double sum = 0.0, bad = 0.0;
-    if (x < nx) {
-        const int64_t i = (int64_t)y * nx + x;
-        const double r = rho0[i];
-        const double lim = eos == 0 ? b * r : 0.25 * b * r;
-        const bool ok = r > 0.0 && isfinite(r) && lim < 1.0;
-        sum = ok ? r : 0.0;
-        bad = ok ? 0.0 : 1.0;
-        out[i] = (C)r;
-    }
-    block_partial(sum, 0.0, 0.0, bad, partials);
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(ny, y0 + kFieldRows);
+    const double bl = eos == 0 ? b : 0.25 * b;
+    double sum = 0.0;
+    int bad = 0;
+    if (x < nx)
+        for (int y = y0; y < y1; ++y) {
+            const int64_t i = (int64_t)y * nx + x;
+            const double r = rho0[i];
+            const bool ok = r > 0.0 && r <= 1.7976931348623157e308 && bl * r < 1.0;
+            sum += ok ? r : 0.0;
+            bad += ok ? 0 : 1;
+            out[i] = (C)r;
+        }
+    block_sums(sum, 0.0, 0.0, bad, partials);
 }
 
 // mu_c = E_f'(rho) - kappa lap(rho) on a C field (Eq. 2).
 template <typename C, int EOS>
-__global__ void mu_field_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ mu)
+__global__ void __launch_bounds__(256) mu_field_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ mu)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
     if (x >= c.nx) return;
-    const int nx = c.nx, ny = c.ny;
-    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    (void)ny;
-    const int64_t ym = (int64_t)nb_row(c, y - 1) * nx, y0 = (int64_t)y * nx, yp = (int64_t)nb_row(c, y + 1) * nx;
-    const C Cc = rho[y0 + x];
-    const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
-                          rho[ym + xp], rho[ym + xm]);
-    mu[y0 + x] = dEf<EOS, C>(c, Cc) - c.kappa * lap;
+    const int nx = c.nx;
+    const int xm = col_m1(x, nx), xp = col_p1(x, nx);
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(c.ny, y0 + kFieldRows);
+    for (int y = y0; y < y1; ++y) {
+        const int64_t ym = (int64_t)row_m1(c, y) * nx, yc = (int64_t)y * nx, yp = (int64_t)row_p1(c, y) * nx;
+        const C Cc = rho[yc + x];
+        const C lap = lap9<C>(Cc, rho[yc + xp], rho[yc + xm], rho[yp + x], rho[ym + x], rho[yp + xp],
+                              rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+        mu[yc + x] = dEf<EOS, C>(c, Cc) - c.kappa * lap;
+    }
 }
 
 // Pressure tensor P of Eqs. 4-5 on C fields (pressure-tensor force form).
 template <typename C, int EOS>
-__global__ void ptensor_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ pxx,
-                               C* __restrict__ pxy, C* __restrict__ pyy)
+__global__ void __launch_bounds__(256) ptensor_kernel(DevCase<C> c, const C* __restrict__ rho, C* __restrict__ pxx,
+                                                      C* __restrict__ pxy, C* __restrict__ pyy)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
     if (x >= c.nx) return;
-    const int nx = c.nx, ny = c.ny;
-    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    (void)ny;
-    const int64_t ym = (int64_t)nb_row(c, y - 1) * nx, y0 = (int64_t)y * nx, yp = (int64_t)nb_row(c, y + 1) * nx;
-    const C Cc = rho[y0 + x];
-    const C lap = lap9<C>(Cc, rho[y0 + xp], rho[y0 + xm], rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm],
-                          rho[ym + xp], rho[ym + xm]);
-    const C gx = gradx9<C>(rho[y0 + xp], rho[y0 + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
-    const C gy = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
-    C a, b, d;
-    pressure_tensor<C>(pEOS<EOS, C>(c, Cc), Cc, gx, gy, lap, c.kappa, a, b, d);
-    pxx[y0 + x] = a;
-    pxy[y0 + x] = b;
-    pyy[y0 + x] = d;
+    const int nx = c.nx;
+    const int xm = col_m1(x, nx), xp = col_p1(x, nx);
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(c.ny, y0 + kFieldRows);
+    for (int y = y0; y < y1; ++y) {
+        const int64_t ym = (int64_t)row_m1(c, y) * nx, yc = (int64_t)y * nx, yp = (int64_t)row_p1(c, y) * nx;
+        const C Cc = rho[yc + x];
+        const C lap = lap9<C>(Cc, rho[yc + xp], rho[yc + xm], rho[yp + x], rho[ym + x], rho[yp + xp],
+                              rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+        const C gx = gradx9<C>(rho[yc + xp], rho[yc + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+        const C gy = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp], rho[ym + xm]);
+        C a, b, d;
+        pressure_tensor<C>(pEOS<EOS, C>(c, Cc), Cc, gx, gy, lap, c.kappa, a, b, d);
+        pxx[yc + x] = a;
+        pxy[yc + x] = b;
+        pyy[yc + x] = d;
+    }
 }
 
 // f(0) = M^-1 m_eq(rho0, u0) with mu_c of rho0, stored as f - w rho_ref in T.
 template <typename T, int SCHEME, typename C>
-__global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ rho0,
-                            const double* __restrict__ ux0, const double* __restrict__ uy0,
-                            const C* __restrict__ mu0, T* __restrict__ f)
+__device__ __forceinline__ void init_node(const DevCase<T>& c, const DevCase<C>& cc, const C* __restrict__ rho0,
+                                          const double* __restrict__ ux0, const double* __restrict__ uy0,
+                                          const C* __restrict__ mu0, T* __restrict__ f, int x, int y)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= c.nx) return;
     const int64_t i = (int64_t)y * c.nx + x;
     const C rho = rho0[i];
     const C ux = ux0 ? (C)ux0[i] : C(0), uy = uy0 ? (C)uy0[i] : C(0);
@@ -134,10 +197,13 @@ __global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ r
     // pulls f_a(x) from x - e_a), so f_a(0) of node x is stored at x - e_a.
     constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int xs[3] = {col_p1(x, c.nx), x, col_m1(x, c.nx)};  // x - e for e = -1, 0, 1
+    const bool wall_m = c.walls && y == 0, wall_p = c.walls && y == c.ny - 1;
+    const int ysv[3] = {y + 1 == c.ny ? 0 : y + 1, y, y == 0 ? c.ny - 1 : y - 1};
+#pragma unroll
     for (int a = 0; a < kQ; ++a) {
-        const int ys = y - ey[a];
-        if (c.walls && (ys < 0 || ys >= c.ny)) continue;  // these arrive from a wall
-        const int64_t o = (int64_t)wrapi(ys, c.ny) * c.pitch + wrapi(x - ex[a], c.nx);
+        if ((ey[a] == 1 && wall_m) || (ey[a] == -1 && wall_p)) continue;  // these arrive from a wall
+        const int64_t o = (int64_t)ysv[ey[a] + 1] * c.pitch + xs[ex[a] + 1];
         f[c.off + a * c.plane + o] = (T)d[a];
     }
     if (c.walls) {
@@ -160,50 +226,67 @@ __global__ void init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ r
     }
 }
 
-// Pull the populations of the current state into C fields rho, j_x, j_y.
-template <typename T, typename C>
-__global__ void pull_moments_kernel(DevCase<T> c, const T* __restrict__ f, C* __restrict__ rho,
-                                    C* __restrict__ jx, C* __restrict__ jy)
+template <typename T, int SCHEME, typename C>
+__global__ void __launch_bounds__(256) init_kernel(DevCase<T> c, DevCase<C> cc, const C* __restrict__ rho0,
+                                                   const double* __restrict__ ux0, const double* __restrict__ uy0,
+                                                   const C* __restrict__ mu0, T* __restrict__ f)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    if (x >= c.nx) return;
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(c.ny, y0 + kFieldRows);
+    for (int y = y0; y < y1; ++y) init_node<T, SCHEME, C>(c, cc, rho0, ux0, uy0, mu0, f, x, y);
+}
+
+// Pull the populations of the current state into C fields rho, j_x, j_y.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) pull_moments_kernel(DevCase<T> c, const T* __restrict__ f,
+                                                           C* __restrict__ rho, C* __restrict__ jx,
+                                                           C* __restrict__ jy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= c.nx) return;
     const int nx = c.nx, ny = c.ny, pitch = c.pitch;
     const int64_t P = c.plane;
     f += c.off;
-    const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-    const int64_t rm = (int64_t)wrapi(y - 1, ny) * pitch, r0 = (int64_t)y * pitch,
-                  rp = (int64_t)wrapi(y + 1, ny) * pitch;
-    C F[kQ];
-    F[0] = (C)f[0 * P + r0 + x];
-    F[1] = (C)f[1 * P + r0 + xm];
-    F[2] = (C)f[2 * P + rm + x];
-    F[3] = (C)f[3 * P + r0 + xp];
-    F[4] = (C)f[4 * P + rp + x];
-    F[5] = (C)f[5 * P + rm + xm];
-    F[6] = (C)f[6 * P + rm + xp];
-    F[7] = (C)f[7 * P + rp + xp];
-    F[8] = (C)f[8 * P + rp + xm];
-    if (c.walls && y == 0) {  // bounce-back from the bottom wall
-        F[2] = (C)f[4 * P + r0 + x];
-        F[5] = (C)(f[7 * P + r0 + x] + c.wall_d);
-        F[6] = (C)(f[8 * P + r0 + x] - c.wall_d);
+    const int xm = col_m1(x, nx), xp = col_p1(x, nx);
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(ny, y0 + kFieldRows);
+    for (int y = y0; y < y1; ++y) {
+        const int64_t rm = (int64_t)(y == 0 ? ny - 1 : y - 1) * pitch, r0 = (int64_t)y * pitch,
+                      rp = (int64_t)(y + 1 == ny ? 0 : y + 1) * pitch;
+        C F[kQ];
+        F[0] = (C)f[0 * P + r0 + x];
+        F[1] = (C)f[1 * P + r0 + xm];
+        F[2] = (C)f[2 * P + rm + x];
+        F[3] = (C)f[3 * P + r0 + xp];
+        F[4] = (C)f[4 * P + rp + x];
+        F[5] = (C)f[5 * P + rm + xm];
+        F[6] = (C)f[6 * P + rm + xp];
+        F[7] = (C)f[7 * P + rp + xp];
+        F[8] = (C)f[8 * P + rp + xm];
+        if (c.walls && y == 0) {  // bounce-back from the bottom wall
+            F[2] = (C)f[4 * P + r0 + x];
+            F[5] = (C)(f[7 * P + r0 + x] + c.wall_d);
+            F[6] = (C)(f[8 * P + r0 + x] - c.wall_d);
+        }
+        if (c.walls && y == ny - 1) {  // and from the top wall
+            F[4] = (C)f[2 * P + r0 + x];
+            F[7] = (C)(f[5 * P + r0 + x] - c.wall_d);
+            F[8] = (C)(f[6 * P + r0 + x] + c.wall_d);
+        }
+        const C dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+        const int64_t i = (int64_t)y * nx + x;
+        rho[i] = (C)c.rho_ref + dr;
+        jx[i] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+        jy[i] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
     }
-    if (c.walls && y == ny - 1) {  // and from the top wall
-        F[4] = (C)f[2 * P + r0 + x];
-        F[7] = (C)(f[5 * P + r0 + x] - c.wall_d);
-        F[8] = (C)(f[6 * P + r0 + x] + c.wall_d);
-    }
-    const C dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
-    const int64_t i = (int64_t)y * nx + x;
-    rho[i] = (C)c.rho_ref + dr;
-    jx[i] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
-    jy[i] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
 }
 
 // Velocity of Eq. 12 from rho, j and the force of the case's scheme; writes
-// the requested FP64 outputs and one Partial per block (blockDim.x == 256).
-// SCHEME 2 takes its force from the pressure tensor P (pxx, pxy, pyy).
+// the requested FP64 outputs and one Partial per block (blockDim.x == 256,
+// grid field_grid(nx, ny)): per-node arithmetic in C, the thread's sums over
+// its kFieldRows nodes in FP64 registers, max |u|^2 in C, the bad-node count
+// as an integer. SCHEME 2 takes its force from the pressure tensor P (pxx,
+// pxy, pyy).
 template <int SCHEME, typename C>
 __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* __restrict__ rho,
                                                        const C* __restrict__ jx, const C* __restrict__ jy,
@@ -215,57 +298,61 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
 {
     const int nx = cc.nx, ny = cc.ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    double mass = 0.0, ke = 0.0, um = 0.0, bad = 0.0;
+    const int y0 = blockIdx.y * kFieldRows, y1 = min(ny, y0 + kFieldRows);
+    double mass = 0.0, ke = 0.0;
+    C um2 = C(0);
+    int bad = 0;
     if (x < nx) {
-        const int xm = wrapi(x - 1, nx), xp = wrapi(x + 1, nx);
-        const int64_t ym = (int64_t)nb_row(cc, y - 1) * nx, y0 = (int64_t)y * nx,
-                      yp = (int64_t)nb_row(cc, y + 1) * nx;
-        const int64_t i = y0 + x;
-        // across a wall P_xy continues oddly (the mirrored rows' y gradients
-        // change sign), every other field evenly
-        const C sxm = cc.walls && y == 0 ? C(-1) : C(1), sxp = cc.walls && y == ny - 1 ? C(-1) : C(1);
-        const C r = rho[i];
-        const C gmx = gradx9<C>(mu[y0 + xp], mu[y0 + xm], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
-        const C gmy = grady9<C>(mu[yp + x], mu[ym + x], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
-        C Fx, Fy;
-        if (SCHEME == 1) {
-            Fx = (C(1.0 / 3.0) - r) * gmx;
-            Fy = (C(1.0 / 3.0) - r) * gmy;
-        } else {
-            const C grx = gradx9<C>(rho[y0 + xp], rho[y0 + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp],
-                                    rho[ym + xm]);
-            const C gry = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp],
-                                    rho[ym + xm]);
-            if (SCHEME == 2) {
-                const C divx = gradx9<C>(pxx[y0 + xp], pxx[y0 + xm], pxx[yp + xp], pxx[yp + xm], pxx[ym + xp],
-                                         pxx[ym + xm]) +
-                               grady9<C>(sxp * pxy[yp + x], sxm * pxy[ym + x], sxp * pxy[yp + xp],
-                                         sxp * pxy[yp + xm], sxm * pxy[ym + xp], sxm * pxy[ym + xm]);
-                const C divy = gradx9<C>(pxy[y0 + xp], pxy[y0 + xm], sxp * pxy[yp + xp], sxp * pxy[yp + xm],
-                                         sxm * pxy[ym + xp], sxm * pxy[ym + xm]) +
-                               grady9<C>(pyy[yp + x], pyy[ym + x], pyy[yp + xp], pyy[yp + xm], pyy[ym + xp],
-                                         pyy[ym + xm]);
-                Fx = grx * C(1.0 / 3.0) - divx;
-                Fy = gry * C(1.0 / 3.0) - divy;
+        const int xm = col_m1(x, nx), xp = col_p1(x, nx);
+        for (int y = y0; y < y1; ++y) {
+            const int64_t ym = (int64_t)row_m1(cc, y) * nx, yc = (int64_t)y * nx, yp = (int64_t)row_p1(cc, y) * nx;
+            const int64_t i = yc + x;
+            // across a wall P_xy continues oddly (the mirrored rows' y
+            // gradients change sign), every other field evenly
+            const C sxm = cc.walls && y == 0 ? C(-1) : C(1), sxp = cc.walls && y == ny - 1 ? C(-1) : C(1);
+            const C r = rho[i];
+            const C gmx = gradx9<C>(mu[yc + xp], mu[yc + xm], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
+            const C gmy = grady9<C>(mu[yp + x], mu[ym + x], mu[yp + xp], mu[yp + xm], mu[ym + xp], mu[ym + xm]);
+            C Fx, Fy;
+            if (SCHEME == 1) {
+                Fx = (C(1.0 / 3.0) - r) * gmx;
+                Fy = (C(1.0 / 3.0) - r) * gmy;
             } else {
-                Fx = grx * C(1.0 / 3.0) - r * gmx;
-                Fy = gry * C(1.0 / 3.0) - r * gmy;
+                const C grx = gradx9<C>(rho[yc + xp], rho[yc + xm], rho[yp + xp], rho[yp + xm], rho[ym + xp],
+                                        rho[ym + xm]);
+                const C gry = grady9<C>(rho[yp + x], rho[ym + x], rho[yp + xp], rho[yp + xm], rho[ym + xp],
+                                        rho[ym + xm]);
+                if (SCHEME == 2) {
+                    const C divx = gradx9<C>(pxx[yc + xp], pxx[yc + xm], pxx[yp + xp], pxx[yp + xm], pxx[ym + xp],
+                                             pxx[ym + xm]) +
+                                   grady9<C>(sxp * pxy[yp + x], sxm * pxy[ym + x], sxp * pxy[yp + xp],
+                                             sxp * pxy[yp + xm], sxm * pxy[ym + xp], sxm * pxy[ym + xm]);
+                    const C divy = gradx9<C>(pxy[yc + xp], pxy[yc + xm], sxp * pxy[yp + xp], sxp * pxy[yp + xm],
+                                             sxm * pxy[ym + xp], sxm * pxy[ym + xm]) +
+                                   grady9<C>(pyy[yp + x], pyy[ym + x], pyy[yp + xp], pyy[yp + xm], pyy[ym + xp],
+                                             pyy[ym + xm]);
+                    Fx = grx * C(1.0 / 3.0) - divx;
+                    Fy = gry * C(1.0 / 3.0) - divy;
+                } else {
+                    Fx = grx * C(1.0 / 3.0) - r * gmx;
+                    Fy = gry * C(1.0 / 3.0) - r * gmy;
+                }
             }
+            const C ux = (jx[i] + C(0.5) * Fx) / r;
+            const C uy = (jy[i] + C(0.5) * Fy) / r;
+            const C m = mu[i];
+            if (out_rho) out_rho[i] = (double)r;
+            if (out_ux) out_ux[i] = (double)ux;
+            if (out_uy) out_uy[i] = (double)uy;
+            if (out_mu) out_mu[i] = (double)m;
+            const C u2 = ux * ux + uy * uy;
+            mass += (double)r;
+            ke += (double)(C(0.5) * r * u2);
+            um2 = u2 > um2 ? u2 : um2;  // a NaN leaves it (and counts as bad)
+            bad += (r > C(0) && isfinite(u2) && isfinite(m)) ? 0 : 1;
         }
-        const C ux = (jx[i] + C(0.5) * Fx) / r;
-        const C uy = (jy[i] + C(0.5) * Fy) / r;
-        if (out_rho) out_rho[i] = (double)r;
-        if (out_ux) out_ux[i] = (double)ux;
-        if (out_uy) out_uy[i] = (double)uy;
-        if (out_mu) out_mu[i] = (double)mu[i];
-        const double u2 = (double)ux * (double)ux + (double)uy * (double)uy;
-        mass = (double)r;
-        ke = 0.5 * (double)r * u2;
-        um = u2;
-        bad = (r > C(0) && isfinite(u2) && isfinite((double)mu[i])) ? 0.0 : 1.0;
     }
-    block_partial(mass, ke, um, bad, partials);
+    block_sums(mass, ke, (double)um2, bad, partials);
 }
 
 // Sum and node count of a window of a C density field [ny][nx]: the grid

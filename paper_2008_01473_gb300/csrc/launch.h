@@ -26,4 +26,24 @@ cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks,
 int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt);
 int occupancy_step_f64(int scheme, int coll, int eos, bool nu);
 
+// Arguments of the persistent multi-step kernel (step_persist.cuh).
+struct PersistArgs {
+    const int* nb_off;     // [nitems + 1]: CSR offsets of each item's neighbour list
+    const int* nb_idx;     // neighbour item indices (the item itself excluded)
+    int* progress;         // [nitems]: steps completed in this launch; [nitems]: abort word
+    int nitems;
+    int nsteps;
+    long long spin_limit;  // clock cycles a wait may spin before it gives up
+    int silent_item;       // self-test: this item never publishes its progress (-1: none)
+};
+
+// One cooperative launch of the persistent one-column kernel over `grid`
+// blocks (at most occupancy_persist() x SMs, so that all are resident):
+// nsteps steps starting from buf0 (see step_persist.cuh for where the state
+// ends). prec: LB_FP32 (1) or LB_FP64 (0).
+cudaError_t launch_persist(int prec, int scheme, int coll, int eos, bool nu, int grid, cudaStream_t s, void* buf0,
+                           void* buf1, const void* cases, const Item* items, int* status, const PersistArgs& pa);
+// resident blocks per SM of that kernel (0 if it has no instantiation)
+int occupancy_persist(int prec, int scheme, int coll, int eos, bool nu);
+
 }  // namespace lbfe

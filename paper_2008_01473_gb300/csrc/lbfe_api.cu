@@ -28,8 +28,6 @@ constexpr int kPairCols256 = 256, kPairCols128 = 128;  // ring columns of the wi
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
-
 int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
 // Widest strip of output columns a block of nt threads can own. Lattices with
@@ -46,8 +44,10 @@ int64_t max_items_of(const lb_case& c)
     return (int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinRows - 1) / kMinRows);
 }
 
+constexpr int kMaxNeighbours = 32;  // neighbour items per item that the persistent launch tracks
+
 struct Layout {
-    size_t cases32, cases64, items, f[2], scratch, partials, red, status, total;
+    size_t cases32, cases64, items, f[2], scratch, partials, red, status, nb_off, nb_idx, progress, total;
     std::vector<int64_t> off;  // element offset of each case in a population buffer
     int64_t max_items = 0, max_nodes = 0, max_parts = 0;
 };
@@ -81,8 +81,15 @@ Layout layout_of(const lb_case* cs, int n, int prec)
     p = align_up(p + L.max_parts * sizeof(Partial), kAlign);
     L.red = p;
     p = align_up(p + n * 8 * sizeof(double), kAlign);
-    L.status = p;
-    p = align_up(p + sizeof(int), kAlign);
+    L.status = p;  // [0]: a bounded wait gave up; [1 + case]: the case went unstable
+    p = align_up(p + (1 + n) * sizeof(int), kAlign);
+    // persistent launch: neighbour lists (CSR) and per-item progress + abort word
+    L.nb_off = p;
+    p = align_up(p + (L.max_items + 1) * sizeof(int), kAlign);
+    L.nb_idx = p;
+    p = align_up(p + L.max_items * kMaxNeighbours * sizeof(int), kAlign);
+    L.progress = p;
+    p = align_up(p + (L.max_items + 1) * sizeof(int), kAlign);
     L.total = p;
     return L;
 }
@@ -204,6 +211,15 @@ struct lb_handle {
     std::vector<cudaStream_t> aux;       // capture branches for groups after the first
     std::vector<cudaEvent_t> fork_join;  // [2 * branch]: fork, join
     bool tuned = false;
+    // persistent multi-step launch (step_persist.cuh): 0 never, 1 always (a
+    // one-group handle; its group runs the one-column kernel), 2 timed
+    // against graph replay on the first long enough lb_step and kept if faster
+    int persist_mode = 2;
+    bool persist = false;        // in use
+    bool persist_tuned = false;  // the choice of mode 2 has been made
+    bool nb_ok = false;          // neighbour lists built for the current work-list
+    int persist_grid = 0;
+    long long spin_limit = kWaitCycles;
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -217,6 +233,9 @@ struct lb_handle {
     }
     Partial* partials() const { return reinterpret_cast<Partial*>(ws + L.partials); }
     int* status() const { return reinterpret_cast<int*>(ws + L.status); }
+    int* nb_off() const { return reinterpret_cast<int*>(ws + L.nb_off); }
+    int* nb_idx() const { return reinterpret_cast<int*>(ws + L.nb_idx); }
+    int* progress() const { return reinterpret_cast<int*>(ws + L.progress); }
     double* red() const { return reinterpret_cast<double*>(ws + L.red); }
 
     lb_status fail(lb_status s, const std::string& m)
@@ -350,6 +369,7 @@ void build_items(lb_handle* h)
 
 lb_status upload_items(lb_handle* h)
 {
+    h->nb_ok = false;
     if ((int64_t)h->items.size() > h->L.max_items)
         return h->fail(LB_E_STATE, "work-list larger than the workspace's item table");
     return h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
@@ -381,7 +401,7 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
     const lb_case& c = h->cases[i];
     const DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
     const DevCase<C> cc = dev_case<C>(c, h->L.off[i], h->rho_ref[i]);
-    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    const dim3 blk(256), grd = field_grid(c.nx, c.ny);
     C* s0 = reinterpret_cast<C*>(h->scratch(0));
     C* s1 = reinterpret_cast<C*>(h->scratch(1));
     C* s2 = reinterpret_cast<C*>(h->scratch(2));
@@ -425,10 +445,10 @@ lb_status init_pass_t(lb_handle* h, int i, const double* d_rho0, const double* p
 {
     const lb_case& c = h->cases[i];
     const int64_t N = (int64_t)c.nx * c.ny;
-    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    const dim3 blk(256), grd = field_grid(c.nx, c.ny);
     C* r0 = reinterpret_cast<C*>(h->scratch(4));
     C* mu = reinterpret_cast<C*>(h->scratch(5));
-    rho0_kernel<C><<<grd, blk, 0, h->stream>>>(c.nx, c.eos, c.b, d_rho0, r0, h->partials());
+    rho0_kernel<C><<<grd, blk, 0, h->stream>>>(c.nx, c.ny, c.eos, c.b, d_rho0, r0, h->partials());
     finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), (int64_t)grd.x * grd.y, 0.0, h->red() + 8 * i);
     double chk[5];
     lb_status s = h->cuda(cudaMemcpyAsync(chk, h->red() + 8 * i, sizeof chk, cudaMemcpyDeviceToHost, h->stream),
@@ -501,7 +521,8 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     }
     build_items(h);
     lb_status s = upload_items(h);
-    if (s == LB_OK) s = h->cuda(cudaMemsetAsync(h->status(), 0, sizeof(int), h->stream), "clear status");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemsetAsync(h->status(), 0, (1 + ncases) * sizeof(int), h->stream), "clear status");
     for (int i = 0; i < ncases && s == LB_OK; ++i) s = h->upload_case(i);
     if (s != LB_OK) {
         delete h;
@@ -541,6 +562,8 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     if (s != LB_OK) return s;
     s = h->prec == LB_FP32 ? init_pass_t<float, float>(h, case_id, d_rho0, pux, puy)
                            : init_pass_t<double, double>(h, case_id, d_rho0, pux, puy);
+    if (s == LB_OK)  // a fresh state clears the case's instability flag
+        s = h->cuda(cudaMemsetAsync(h->status() + 1 + case_id, 0, sizeof(int), h->stream), "clear case flag");
     if (s != LB_OK) return s;
     h->steps[case_id] = 0;
     h->inited[case_id] = 1;
@@ -683,6 +706,138 @@ static lb_status autotune(lb_handle* h)
     return s != LB_OK ? s : u;
 }
 
+// ------------------------------------------------------ persistent launch
+constexpr int kPersistChunk = 1024;  // steps per persistent launch
+
+// Column / row halo around an item that its step reads: the pull and the
+// stencil halo (HX + 1 either side).
+static int persist_reach(const lb_case& c) { return halo_of(c.scheme) + 1; }
+
+// circular intervals [a0, a0 + la) and [b0, b0 + lb) modulo n intersect
+static bool circ_overlap(int a0, int la, int b0, int lb, int n)
+{
+    if (la >= n || lb >= n) return true;
+    const int d1 = ((b0 - a0) % n + n) % n, d2 = ((a0 - b0) % n + n) % n;
+    return d1 < la || d2 < lb;
+}
+
+// A one-group handle can use the persistent kernel (mode 2 only where its
+// group already runs the one-column kernel, so that results do not change).
+static bool persist_possible(const lb_handle* h, bool strict)
+{
+    if (h->groups.size() != 1) return false;
+    const Group& g = h->groups[0];
+    if (strict && g.tma) return false;
+    return occupancy_persist(h->prec, g.scheme, g.coll, g.eos, g.nu) > 0;
+}
+
+// Neighbour lists of the group's items (every other item of the same case
+// whose output overlaps the item's input), uploaded as CSR; false if an item
+// has more than kMaxNeighbours of them.
+static lb_status build_neighbours(lb_handle* h, bool* ok)
+{
+    *ok = false;
+    const Group& g = h->groups[0];
+    std::vector<int> off(1, 0), idx;
+    for (int64_t i = 0; i < g.count; ++i) {
+        const Item& a = h->items[g.first + i];
+        const lb_case& c = h->cases[a.case_id];
+        const int r = persist_reach(c);
+        int cnt = 0;
+        for (int64_t j = 0; j < g.count; ++j) {
+            if (j == i) continue;
+            const Item& b = h->items[g.first + j];
+            if (b.case_id != a.case_id) continue;
+            if (circ_overlap(a.x0 - r, a.wv + 2 * r, b.x0, b.wv, c.nx) &&
+                circ_overlap(a.y0 - r, a.h + 2 * r, b.y0, b.h, c.ny)) {
+                idx.push_back((int)j);
+                if (++cnt > kMaxNeighbours) return LB_OK;
+            }
+        }
+        off.push_back((int)idx.size());
+    }
+    lb_status s = h->cuda(cudaMemcpyAsync(h->nb_off(), off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                          h->stream),
+                          "upload neighbours");
+    if (s == LB_OK && !idx.empty())
+        s = h->cuda(cudaMemcpyAsync(h->nb_idx(), idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                    h->stream),
+                    "upload neighbours");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "upload neighbours");
+    if (s != LB_OK) return s;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = occupancy_persist(h->prec, g.scheme, g.coll, g.eos, g.nu);
+    h->persist_grid = (int)std::min<int64_t>(g.count, (int64_t)occ * sms);
+    h->nb_ok = *ok = true;
+    return LB_OK;
+}
+
+// nsteps steps of the single group by persistent launches of up to
+// kPersistChunk steps; silent_item >= 0 is the self-test (that item never
+// publishes its progress, so its neighbours' waits give up after spin).
+static lb_status enqueue_persist(lb_handle* h, int64_t nsteps, int silent_item, long long spin)
+{
+    const Group& g = h->groups[0];
+    for (int64_t done = 0; done < nsteps;) {
+        const int chunk = (int)std::min<int64_t>(kPersistChunk, nsteps - done);
+        lb_status s = h->cuda(cudaMemsetAsync(h->progress(), 0, (g.count + 1) * sizeof(int), h->stream),
+                              "clear progress");
+        if (s != LB_OK) return s;
+        PersistArgs pa;
+        pa.nb_off = h->nb_off();
+        pa.nb_idx = h->nb_idx();
+        pa.progress = h->progress();
+        pa.nitems = (int)g.count;
+        pa.nsteps = chunk;
+        pa.spin_limit = spin;
+        pa.silent_item = silent_item;
+        const void* cases = h->prec == LB_FP32 ? (const void*)h->dc32() : (const void*)h->dc64();
+        s = h->cuda(launch_persist(h->prec, g.scheme, g.coll, g.eos, g.nu, h->persist_grid, h->stream,
+                                   h->fbuf(h->cur), h->fbuf(h->cur ^ 1), cases, h->ditems() + g.first, h->status(),
+                                   pa),
+                    "persistent launch");
+        if (s != LB_OK) return s;
+        if (chunk & 1) h->cur ^= 1;
+        done += chunk;
+    }
+    return LB_OK;
+}
+
+// Mode 2: time 16 steps of graph replay against 16 steps of the persistent
+// launch (after 8 untimed persistent steps that load the kernel), with the
+// call's own steps, and keep the faster mode. Both modes run the same
+// per-node arithmetic, so the choice changes no result. Consumes 40 steps.
+static lb_status tune_persist(lb_handle* h)
+{
+    h->persist_tuned = true;
+    if (!h->graph[h->cur]) {
+        lb_status s = capture_graph(h, h->cur);
+        if (s != LB_OK) return s;
+    }
+    cudaEvent_t e[4] = {};
+    lb_status s = LB_OK;
+    for (auto& x : e)
+        if (s == LB_OK) s = h->cuda(cudaEventCreate(&x), "tune event");
+    if (s == LB_OK) s = enqueue_persist(h, kGraphSteps, -1, h->spin_limit);
+    if (s == LB_OK) s = h->cuda(cudaEventRecord(e[0], h->stream), "tune record");
+    for (int k = 0; k < 2 && s == LB_OK; ++k)
+        s = h->cuda(cudaGraphLaunch(h->graph[h->cur], h->stream), "graph launch");
+    if (s == LB_OK) s = h->cuda(cudaEventRecord(e[1], h->stream), "tune record");
+    if (s == LB_OK) s = h->cuda(cudaEventRecord(e[2], h->stream), "tune record");
+    if (s == LB_OK) s = enqueue_persist(h, 2 * kGraphSteps, -1, h->spin_limit);
+    if (s == LB_OK) s = h->cuda(cudaEventRecord(e[3], h->stream), "tune record");
+    if (s == LB_OK) s = h->cuda(cudaEventSynchronize(e[3]), "tune sync");
+    float tg = 0.f, tp = 0.f;
+    if (s == LB_OK) s = h->cuda(cudaEventElapsedTime(&tg, e[0], e[1]), "tune time");
+    if (s == LB_OK) s = h->cuda(cudaEventElapsedTime(&tp, e[2], e[3]), "tune time");
+    for (auto& x : e)
+        if (x) cudaEventDestroy(x);
+    if (s == LB_OK) h->persist = tp < 0.98f * tg;
+    return s;
+}
+
 lb_status lb_step(lb_handle* h, int64_t nsteps)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
@@ -694,6 +849,25 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
         if (s != LB_OK) return s;
     }
     int64_t n = nsteps;
+    if (h->persist_mode != 0 && n > 0 && persist_possible(h, h->persist_mode == 2)) {
+        if (!h->nb_ok) {
+            bool ok = false;
+            lb_status s = build_neighbours(h, &ok);
+            if (s != LB_OK) return s;
+            if (!ok) h->persist = false, h->persist_tuned = true;
+        }
+        if (h->nb_ok && h->persist_mode == 1) h->persist = true;
+        if (h->nb_ok && h->persist_mode == 2 && !h->persist_tuned && n >= 5 * kGraphSteps) {
+            lb_status s = tune_persist(h);
+            if (s != LB_OK) return s;
+            n -= 5 * kGraphSteps;
+        }
+        if (h->persist && h->nb_ok) {
+            lb_status s = enqueue_persist(h, n, -1, h->spin_limit);
+            if (s != LB_OK) return s;
+            n = 0;
+        }
+    }
     if (h->use_graph && n >= kGraphSteps) {
         if (!h->graph[h->cur]) {
             lb_status s = capture_graph(h, h->cur);
@@ -711,6 +885,43 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
     }
     for (auto& st : h->steps) st += nsteps;
     return LB_OK;
+}
+
+lb_status lb_launch_mode(lb_handle* h, int32_t mode, int32_t* persistent)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (mode < -1 || mode > 2) return h->fail(LB_E_INVALID, "lb_launch_mode: mode must be -1, 0, 1 or 2");
+    if (mode >= 0) {
+        if (mode == 1 && !persist_possible(h, false))
+            return h->fail(LB_E_INVALID, "lb_launch_mode: the persistent launch needs a handle whose cases all "
+                                         "share one kernel group");
+        h->persist_mode = mode;
+        h->persist = mode == 1;
+        h->persist_tuned = mode != 2;
+    }
+    if (persistent) *persistent = h->persist ? 1 : 0;
+    return LB_OK;
+}
+
+lb_status lb_persistent_selftest(lb_handle* h, int64_t nsteps)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (nsteps < 2 || !persist_possible(h, false))
+        return h->fail(LB_E_INVALID, "lb_persistent_selftest: needs nsteps >= 2 and a one-group handle");
+    for (size_t i = 0; i < h->cases.size(); ++i)
+        if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_persistent_selftest: every case needs lb_init_fields");
+    if (!h->nb_ok) {
+        bool ok = false;
+        lb_status s = build_neighbours(h, &ok);
+        if (s != LB_OK) return s;
+        if (!ok) return h->fail(LB_E_INVALID, "lb_persistent_selftest: an item has too many neighbours");
+    }
+    if (h->groups[0].count < 2) return h->fail(LB_E_INVALID, "lb_persistent_selftest: needs at least two items");
+    // about 10 ms of SM clock per wait; item 0 never publishes, so the first
+    // neighbour that waits for it gives up, and every block then returns
+    lb_status s = enqueue_persist(h, std::min<int64_t>(nsteps, kPersistChunk), 0, 20000000LL);
+    for (auto& st : h->steps) st += std::min<int64_t>(nsteps, kPersistChunk);
+    return s;
 }
 
 lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, int32_t* narrow)
@@ -757,24 +968,28 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
         lb_status s = fields_pass(h, i, nullptr, nullptr, nullptr, nullptr);
         if (s != LB_OK) return s;
         const lb_case& c = h->cases[i];
-        const int64_t parts = (int64_t)((c.nx + 255) / 256) * c.ny;
-        finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), parts, (double)h->steps[i], h->red() + 8 * i);
+        const dim3 g = field_grid(c.nx, c.ny);
+        finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), (int64_t)g.x * g.y, (double)h->steps[i],
+                                                  h->red() + 8 * i);
         if ((s = h->cuda(cudaGetLastError(), "finalize")) != LB_OK) return s;
     }
     std::vector<double> red((size_t)n * 8);
-    int timeout = 0;
+    std::vector<int> flags((size_t)n + 1);
     lb_status s = h->cuda(cudaMemcpyAsync(red.data(), h->red(), red.size() * sizeof(double),
                                           cudaMemcpyDeviceToHost, h->stream),
                           "copy reductions");
     if (s == LB_OK)
-        s = h->cuda(cudaMemcpyAsync(&timeout, h->status(), sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+        s = h->cuda(cudaMemcpyAsync(flags.data(), h->status(), flags.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                    h->stream),
                     "copy status");
     if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "reductions sync");
     if (s != LB_OK) return s;
+    const int timeout = flags[0];
     bool unstable = false;
     for (int i = 0; i < n; ++i) {
         for (int k = 0; k < 5; ++k) out[5 * i + k] = red[8 * i + k];
-        const bool bad = red[8 * i + 4] != 0.0 || !std::isfinite(red[8 * i]);
+        // flagged by a step kernel (and since then frozen), or non-physical now
+        const bool bad = flags[1 + i] != 0 || red[8 * i + 4] != 0.0 || !std::isfinite(red[8 * i]);
         out[5 * i + 4] = 0.0;
         if (case_status) case_status[i] = bad ? LB_E_UNSTABLE : LB_OK;
         unstable |= bad;
@@ -907,6 +1122,8 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
         s = h->cuda(cudaMemcpyAsync((uint8_t*)h->fbuf(h->cur) + h->L.off[case_id] * es, p + 16, need - 16,
                                     cudaMemcpyHostToDevice, h->stream),
                     "load");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemsetAsync(h->status() + 1 + case_id, 0, sizeof(int), h->stream), "clear case flag");
     if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "load sync");
     if (s != LB_OK) return s;
     h->steps[case_id] = st;
@@ -920,7 +1137,7 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
 namespace {
 
 struct AdjLayout {
-    size_t cases, items, ckpt, seg, lam, lamd, fields, partials, acc, rho0, sfin, grad, total;
+    size_t cases, items, ckpt, seg, lam, lamd, fields, partials, acc, rho0, sfin, grad, status, total;
     int64_t K, ncp, state, nitems, N, parts;
 };
 
@@ -955,6 +1172,7 @@ AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K, size_t es)
     L.rho0 = take(L.N * sizeof(double));
     L.sfin = take(L.N * sizeof(double));
     L.grad = take(L.N * sizeof(double));
+    L.status = take(2 * sizeof(int));  // step-kernel status words of the one-case work-list
     L.total = p;
     return L;
 }
@@ -978,6 +1196,7 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
     const DevCase<T> cd = dev_case<T>(c, 0, rho_ref);
     const DevCase<T>* dcase = reinterpret_cast<const DevCase<T>*>(ws + L.cases);
     const Item* items = reinterpret_cast<const Item*>(ws + L.items);
+    int* status = reinterpret_cast<int*>(ws + L.status);
     T* ckpt = reinterpret_cast<T*>(ws + L.ckpt);
     T* seg = reinterpret_cast<T*>(ws + L.seg);
     T* lam = reinterpret_cast<T*>(ws + L.lam);
@@ -990,23 +1209,26 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
     T** fp = reinterpret_cast<T**>(&F);
     for (int k = 0; k < kAdjFields; ++k)
         fp[k] = reinterpret_cast<T*>(ws + L.fields + k * align_up(L.N * sizeof(T), kAlign));
-    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
+    const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);  // the adj_* kernels: one node per thread
+    const dim3 fgrd = field_grid(c.nx, c.ny);             // the field kernels of aux_kernels.cuh
     const int nitems = (int)L.nitems;
     const T R = (T)c.R;
     auto state = [&](int64_t k) { return ckpt + k * L.state; };
     auto step = [&](const T* in, T* out) {
         if constexpr (sizeof(T) == 4)
             return launch_step_f32(SCHEME, c.collision, EOS, false, false, kStepThreads, nitems, st, in, out, dcase,
-                                   items, h->status());
+                                   items, status);
         else
-            return launch_step_f64(SCHEME, c.collision, EOS, false, nitems, st, in, out, dcase, items, h->status());
+            return launch_step_f64(SCHEME, c.collision, EOS, false, nitems, st, in, out, dcase, items, status);
     };
     // rho0 in T (the check partials land in parts and are not used)
-    auto load_rho0 = [&]() { rho0_kernel<T><<<grd, blk, 0, st>>>(c.nx, c.eos, c.b, rho0, F.rho, parts); };
+    auto load_rho0 = [&]() { rho0_kernel<T><<<fgrd, blk, 0, st>>>(c.nx, c.ny, c.eos, c.b, rho0, F.rho, parts); };
+    lb_status cs0 = h->cuda(cudaMemsetAsync(status, 0, 2 * sizeof(int), st), "adjoint status");
+    if (cs0 != LB_OK) return cs0;
     // forward: f(0), then the checkpoints every K steps
     load_rho0();
-    mu_field_kernel<T, EOS><<<grd, blk, 0, st>>>(cd, F.rho, F.mu);
-    init_kernel<T, SCHEME, T><<<grd, blk, 0, st>>>(cd, cd, F.rho, nullptr, nullptr, F.mu, state(0));
+    mu_field_kernel<T, EOS><<<fgrd, blk, 0, st>>>(cd, F.rho, F.mu);
+    init_kernel<T, SCHEME, T><<<fgrd, blk, 0, st>>>(cd, cd, F.rho, nullptr, nullptr, F.mu, state(0));
     const T* cur = state(0);
     for (int64_t n = 0; n < nsteps; ++n) {
         T* out = ((n + 1) % L.K == 0) ? state((n + 1) / L.K) : (cur == seg ? seg + L.state : seg);
@@ -1025,7 +1247,7 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
         }
         for (int64_t n = e; n >= s; --n) {
             const T* fn = n == s ? state(s / L.K) : seg + (n - s) * L.state;
-            pull_moments_kernel<T, T><<<grd, blk, 0, st>>>(cd, fn, F.rho, F.jx, F.jy);
+            pull_moments_kernel<T, T><<<fgrd, blk, 0, st>>>(cd, fn, F.rho, F.jx, F.jy);
             adj_fwd_mu<T, EOS><<<grd, blk, 0, st>>>(cd, F);
             adj_fwd_force<T, SCHEME><<<grd, blk, 0, st>>>(cd, F, n >= u_from ? 1.0 : 0.0,
                                                           n == nsteps ? s_fin : nullptr, parts);
@@ -1120,10 +1342,10 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
         Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
         double* acc = reinterpret_cast<double*>(ws + L.acc);
         double* scratch = reinterpret_cast<double*>(ws + L.grad);
-        const dim3 blk(256), grd((c.nx + 255) / 256, c.ny);
-        rho0_kernel<double><<<grd, blk, 0, st>>>(c.nx, c.eos, c.b, reinterpret_cast<const double*>(ws + L.rho0),
-                                                 scratch, parts);
-        finalize_kernel<<<1, 256, 0, st>>>(parts, L.parts, 0.0, acc);
+        const dim3 blk(256), grd = field_grid(c.nx, c.ny);
+        rho0_kernel<double><<<grd, blk, 0, st>>>(c.nx, c.ny, c.eos, c.b,
+                                                 reinterpret_cast<const double*>(ws + L.rho0), scratch, parts);
+        finalize_kernel<<<1, 256, 0, st>>>(parts, (int64_t)grd.x * grd.y, 0.0, acc);
         double chk[5];
         s = h->cuda(cudaMemcpyAsync(chk, acc, sizeof chk, cudaMemcpyDeviceToHost, st), "adjoint check");
         if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(st), "adjoint check");
@@ -1150,7 +1372,10 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
 #undef LBFE_ADJ
     if (s != LB_OK) return s;
     double acc[4];
+    int stw[2] = {0, 0};
     s = h->cuda(cudaMemcpyAsync(acc, ws + L.acc, sizeof acc, cudaMemcpyDeviceToHost, st), "adjoint results");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemcpyAsync(stw, ws + L.status, sizeof stw, cudaMemcpyDeviceToHost, st), "adjoint status");
     if (s == LB_OK && grad_rho0)
         s = h->cuda(cudaMemcpyAsync(grad_rho0, ws + L.grad, L.N * sizeof(double),
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
@@ -1160,8 +1385,9 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     *loss = acc[0];
     *grad_kappa = acc[1];
     *grad_T = acc[2];
-    if (!std::isfinite(acc[0]) || !std::isfinite(acc[1]) || !std::isfinite(acc[2]))
-        return h->fail(LB_E_UNSTABLE, "lb_adjoint_step: non-finite loss or gradient");
+    if (stw[0]) return h->fail(LB_E_TIMEOUT, "lb_adjoint_step: a bounded wait of a step kernel gave up");
+    if (stw[1] || !std::isfinite(acc[0]) || !std::isfinite(acc[1]) || !std::isfinite(acc[2]))
+        return h->fail(LB_E_UNSTABLE, "lb_adjoint_step: unstable forward run, or non-finite loss or gradient");
     return LB_OK;
 }
 

@@ -39,6 +39,11 @@ struct Item {
     int32_t case_id, x0, wv, y0, h, pad_;
 };
 
+// Elements per stored row of a population plane: nx rounded up to 32, so
+// that every row starts on a 128-byte boundary. The snapshot layout of
+// lb_save and the input of lb_fields_static follow it.
+__host__ __device__ constexpr int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
 __host__ __device__ __forceinline__ int wrapi(int i, int n)
 {
     int r = i % n;

@@ -14,7 +14,7 @@ namespace {
 
 constexpr int64_t kMaxNodes = LB_STATIC_MAX_NODES;
 constexpr int kMaxSide = LB_STATIC_MAX_SIDE;
-// partials of velocity_kernel: ceil(nx / 256) * ny <= nodes / 256 + ny
+// partials of velocity_kernel: at most ceil(nx / 256) * ny <= nodes / 256 + ny
 constexpr int64_t kMaxParts = kMaxNodes / 256 + kMaxSide;
 constexpr size_t kFieldBytes = kMaxNodes * sizeof(double);
 constexpr size_t kScratchBytes = 4 * kFieldBytes + kMaxParts * sizeof(Partial);
@@ -26,7 +26,7 @@ DevCase<T> make_case(const lb_case& c, double rho_ref)
     DevCase<T> d{};
     d.nx = c.nx;
     d.ny = c.ny;
-    d.pitch = (c.nx + 31) / 32 * 32;
+    d.pitch = pitch_of(c.nx);
     d.off = 0;
     d.plane = (int64_t)c.ny * d.pitch;
     d.RT = (T)(c.R * c.T);
@@ -112,6 +112,9 @@ extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const
     if (precision != LB_FP32 && precision != LB_FP64) return LB_E_INVALID;
     if (!std::isfinite(rho_ref) || rho_ref < 0) return LB_E_INVALID;
     if (c->nx > kMaxSide || c->ny > kMaxSide || (int64_t)c->nx * c->ny > kMaxNodes) return LB_E_INVALID;
+    // an error left pending by earlier work is not this call's to report or
+    // to clear: leave it in place and enqueue nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return LB_E_CUDA;
     void* base = nullptr;
     if (scratch_ptr(&base) != cudaSuccess) return LB_E_CUDA;
     unsigned char* p = static_cast<unsigned char*>(base);
@@ -120,7 +123,7 @@ extern "C" lb_status lb_fields_static(const lb_case* c, int32_t precision, const
     // (all nodes of the four fields, all partials of the grid), so nothing
     // needs clearing between calls.
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const dim3 blk(256), grd((c->nx + 255) / 256, c->ny);
+    const dim3 blk(256), grd = field_grid(c->nx, c->ny);
     if (precision == LB_FP32)
         fields_static<float>(*c, rho_ref, (const float*)d_pops, p, parts, d_rho, d_ux, d_uy, d_mu, grd, blk, st);
     else

@@ -67,7 +67,12 @@ struct StepRegs {
     T jx[4], jy[4];
     T ux[4], uy[4], Fx[4], Fy[4];  // stage C results of the last rows (improved schemes)
     T grx, gry;                    // stage B grad rho (standard)
+    bool bad;                      // a stage D node had rho <= 0 or a non-finite density
 };
+
+// rho > 0 and finite (NaN fails both comparisons)
+__device__ __forceinline__ bool rho_ok(float r) { return r > 0.0f && r <= 3.402823466e38f; }
+__device__ __forceinline__ bool rho_ok(double r) { return r > 0.0 && r <= 1.7976931348623157e308; }
 
 struct StepLane {
     int t;            // thread index = window column
@@ -93,11 +98,23 @@ __device__ __forceinline__ float rcp_fast<float>(float x) { return __fdividef(1.
 template <>
 __device__ __forceinline__ double rcp_fast<double>(double x) { return 1.0 / x; }
 
-// Stage A source of the pulled populations: plain read-only global loads.
+// Population load of stage A: through the read-only cache, or (COHERENT, for
+// the persistent kernel, whose populations other blocks of the same launch
+// write) at L2 only, so that no stale line of an earlier step is read.
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_pop(const T* p)
+{
+    if constexpr (COHERENT)
+        return __ldcg(p);
+    else
+        return __ldg(p);
+}
+
+// Stage A source of the pulled populations: plain global loads.
 // With walls, window rows outside the lattice pull their mirror rows, and
 // the populations that reach row 0 or ny - 1 from a wall are the node's own
 // outgoing ones in the opposite direction plus the moving-wall term.
-template <typename T>
+template <typename T, bool COHERENT = false>
 struct PullGlobal {
     __device__ __forceinline__ void pull(int, T* F, const T* __restrict__ fin, const DevCase<T>& c,
                                          const StepLane& L, const StepRows& rows) const
@@ -107,28 +124,28 @@ struct PullGlobal {
         if (c.walls) {
             const int m = nb_row(c, rows.sa);  // mirror of a ghost row; |sa| stays well inside ny
             const uint32_t r0 = (uint32_t)m * pitch;
-            F[0] = __ldg(fin + (0 * P + r0 + L.xc));
-            F[1] = __ldg(fin + (1 * P + r0 + L.xm));
-            F[3] = __ldg(fin + (3 * P + r0 + L.xp));
+            F[0] = ld_pop<COHERENT>(fin + (0 * P + r0 + L.xc));
+            F[1] = ld_pop<COHERENT>(fin + (1 * P + r0 + L.xm));
+            F[3] = ld_pop<COHERENT>(fin + (3 * P + r0 + L.xp));
             if (m > 0) {
                 const uint32_t rm = r0 - (uint32_t)pitch;
-                F[2] = __ldg(fin + (2 * P + rm + L.xc));
-                F[5] = __ldg(fin + (5 * P + rm + L.xm));
-                F[6] = __ldg(fin + (6 * P + rm + L.xp));
+                F[2] = ld_pop<COHERENT>(fin + (2 * P + rm + L.xc));
+                F[5] = ld_pop<COHERENT>(fin + (5 * P + rm + L.xm));
+                F[6] = ld_pop<COHERENT>(fin + (6 * P + rm + L.xp));
             } else {  // bottom wall
-                F[2] = __ldg(fin + (4 * P + r0 + L.xc));
-                F[5] = __ldg(fin + (7 * P + r0 + L.xc)) + c.wall_d;
-                F[6] = __ldg(fin + (8 * P + r0 + L.xc)) - c.wall_d;
+                F[2] = ld_pop<COHERENT>(fin + (4 * P + r0 + L.xc));
+                F[5] = ld_pop<COHERENT>(fin + (7 * P + r0 + L.xc)) + c.wall_d;
+                F[6] = ld_pop<COHERENT>(fin + (8 * P + r0 + L.xc)) - c.wall_d;
             }
             if (m < ny - 1) {
                 const uint32_t rp = r0 + (uint32_t)pitch;
-                F[4] = __ldg(fin + (4 * P + rp + L.xc));
-                F[7] = __ldg(fin + (7 * P + rp + L.xp));
-                F[8] = __ldg(fin + (8 * P + rp + L.xm));
+                F[4] = ld_pop<COHERENT>(fin + (4 * P + rp + L.xc));
+                F[7] = ld_pop<COHERENT>(fin + (7 * P + rp + L.xp));
+                F[8] = ld_pop<COHERENT>(fin + (8 * P + rp + L.xm));
             } else {  // top wall
-                F[4] = __ldg(fin + (2 * P + r0 + L.xc));
-                F[7] = __ldg(fin + (5 * P + r0 + L.xc)) - c.wall_d;
-                F[8] = __ldg(fin + (6 * P + r0 + L.xc)) + c.wall_d;
+                F[4] = ld_pop<COHERENT>(fin + (2 * P + r0 + L.xc));
+                F[7] = ld_pop<COHERENT>(fin + (5 * P + r0 + L.xc)) - c.wall_d;
+                F[8] = ld_pop<COHERENT>(fin + (6 * P + r0 + L.xc)) + c.wall_d;
             }
             if (rows.sa != m) {
                 // a ghost row is the mirror image of row m: its populations
@@ -143,15 +160,15 @@ struct PullGlobal {
         const uint32_t r0 = (uint32_t)rows.ra * pitch;
         const uint32_t rm = (uint32_t)dec_wrap(rows.ra, ny) * pitch;
         const uint32_t rp = (uint32_t)inc_wrap(rows.ra, ny) * pitch;
-        F[0] = __ldg(fin + (0 * P + r0 + L.xc));
-        F[1] = __ldg(fin + (1 * P + r0 + L.xm));
-        F[2] = __ldg(fin + (2 * P + rm + L.xc));
-        F[3] = __ldg(fin + (3 * P + r0 + L.xp));
-        F[4] = __ldg(fin + (4 * P + rp + L.xc));
-        F[5] = __ldg(fin + (5 * P + rm + L.xm));
-        F[6] = __ldg(fin + (6 * P + rm + L.xp));
-        F[7] = __ldg(fin + (7 * P + rp + L.xp));
-        F[8] = __ldg(fin + (8 * P + rp + L.xm));
+        F[0] = ld_pop<COHERENT>(fin + (0 * P + r0 + L.xc));
+        F[1] = ld_pop<COHERENT>(fin + (1 * P + r0 + L.xm));
+        F[2] = ld_pop<COHERENT>(fin + (2 * P + rm + L.xc));
+        F[3] = ld_pop<COHERENT>(fin + (3 * P + r0 + L.xp));
+        F[4] = ld_pop<COHERENT>(fin + (4 * P + rp + L.xc));
+        F[5] = ld_pop<COHERENT>(fin + (5 * P + rm + L.xm));
+        F[6] = ld_pop<COHERENT>(fin + (6 * P + rm + L.xp));
+        F[7] = ld_pop<COHERENT>(fin + (7 * P + rp + L.xp));
+        F[8] = ld_pop<COHERENT>(fin + (8 * P + rp + L.xm));
     }
     __device__ __forceinline__ void after_sync(int) const {}
     __device__ __forceinline__ void sync() const { __syncthreads(); }
@@ -167,7 +184,7 @@ struct PullGlobal {
 // roles of x and y exchanged. The populations of row rd are pulled again
 // (L2-resident: stage A read them four iterations earlier) instead of being
 // kept in registers for four rows.
-template <typename T, int NT, int COLL, int EOS, bool NU, int SLOT>
+template <typename T, int NT, int COLL, int EOS, bool NU, int SLOT, bool COHERENT>
 __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin, T* __restrict__ fout,
                                               const DevCase<T>& c, const StepLane& L, const StepRows& rows,
                                               StepSmem<T, NT, 3>& sm, StepRegs<T>& R)
@@ -203,11 +220,12 @@ __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin,
 
     T F[kQ];
     const StepRows rr{rows.rd, rows.rd, rows.rd};
-    PullGlobal<T>().pull(it, F, fin, c, L, rr);
+    PullGlobal<T, COHERENT>().pull(it, F, fin, c, L, rr);
     const T drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
     const T jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
     const T jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
     const T rho = c.rho_ref + drho;
+    R.bad |= !rho_ok(rho);
     const T mu = sm.mu[S0][t];  // row ra - 4
     T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
     if (NU) {
@@ -222,7 +240,7 @@ __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin,
     for (int a = 0; a < kQ; ++a) fout[a * P + o] = F[a];
 }
 
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A>
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A, bool COHERENT = false>
 __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restrict__ fin, T* __restrict__ fout,
                                           const DevCase<T>& c, const StepLane& L, StepRows& rows,
                                           StepSmem<T, NT, SCHEME>& sm, StepRegs<T>& R)
@@ -306,7 +324,8 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         A_.sync();
         if constexpr (SCHEME == 3) {
             // -------------------------------------------------------- D (3)
-            if (L.d && it >= G::ND) step_d_smooth<T, NT, COLL, EOS, NU, SLOT>(it, fin, fout, c, L, rows, sm, R);
+            if (L.d && it >= G::ND)
+                step_d_smooth<T, NT, COLL, EOS, NU, SLOT, COHERENT>(it, fin, fout, c, L, rows, sm, R);
         } else {
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
@@ -321,6 +340,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T C1 = Ax + By, C7 = Ax - By;
             const T drho = R.drho[S3];
             const T rho = c.rho_ref + drho;
+            R.bad |= !rho_ok(rho);
             const T mu = sm.mu[S3][t];
             T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
             if (NU) {
@@ -342,6 +362,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T* Mp = sm.mu[S1];
             const T drho = R.drho[S2];
             const T rho = c.rho_ref + drho;
+            R.bad |= !rho_ok(rho);
             T mu, Fx, Fy;
             if constexpr (SCHEME == 2) {
                 // F = grad(rho/3) - div P, each component of P through Eq. 17
@@ -384,19 +405,15 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
     if (it >= G::ND) rows.rd = inc_wrap(rows.rd, ny);
 }
 
-// One launch advances every case listed in the work-list by one time step.
-// fin/fout: population buffers (all cases, each at DevCase::off). One block
-// per work item; blockDim.x == NT.
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU>
-__global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* __restrict__ fout,
-                                                  const DevCase<T>* __restrict__ cases,
-                                                  const Item* __restrict__ items, int* __restrict__ status)
+// One work item of one time step (the body of step_kernel): the block walks
+// the item's rows through stages A-D, reading fin and writing fout, and
+// returns whether a stage D node had rho <= 0 or a non-finite density (the
+// same value in every thread). COHERENT selects L2-only population loads.
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, bool COHERENT>
+__device__ __forceinline__ bool step_item(const T* __restrict__ fin, T* __restrict__ fout, const DevCase<T>& c,
+                                          const Item& item, StepSmem<T, NT, SCHEME>& sm)
 {
-    (void)status;
     using G = StepGeom<SCHEME>;
-    __shared__ StepSmem<T, NT, SCHEME> sm;
-    const Item item = items[blockIdx.x];
-    const DevCase<T> c = cases[item.case_id];
     fin += c.off;
     fout += c.off;
 
@@ -418,17 +435,43 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
     rows.sa = item.y0 - G::HX;
 
     StepRegs<T> R;
+    R.bad = false;
     const int niter = item.h + 2 * G::HX;
-    const PullGlobal<T> A;
+    const PullGlobal<T, COHERENT> A;
     for (int base = 0; base < niter; base += 4) {
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, A, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0, PullGlobal<T, COHERENT>, COHERENT>(base, A, fin, fout, c, L, rows,
+                                                                                     sm, R);
         if (base + 1 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, A, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1, PullGlobal<T, COHERENT>, COHERENT>(base + 1, A, fin, fout, c, L,
+                                                                                     rows, sm, R);
         if (base + 2 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, A, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2, PullGlobal<T, COHERENT>, COHERENT>(base + 2, A, fin, fout, c, L,
+                                                                                     rows, sm, R);
         if (base + 3 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3, PullGlobal<T, COHERENT>, COHERENT>(base + 3, A, fin, fout, c, L,
+                                                                                     rows, sm, R);
     }
+    return __syncthreads_or(R.bad) != 0;
+}
+
+// One launch advances every case listed in the work-list by one time step.
+// fin/fout: population buffers (all cases, each at DevCase::off). One block
+// per work item; blockDim.x == NT. status[0]: set by a bounded wait that gave
+// up (TMA variants); status[1 + case]: set when a node of the case had
+// rho <= 0 or a non-finite density in stage D. The blocks of a flagged case
+// return at once, so it no longer advances while the other cases go on.
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU>
+__global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* __restrict__ fout,
+                                                  const DevCase<T>* __restrict__ cases,
+                                                  const Item* __restrict__ items, int* __restrict__ status)
+{
+    __shared__ StepSmem<T, NT, SCHEME> sm;
+    const Item item = items[blockIdx.x];
+    // thread 0 decides for the block: another block may set the word meanwhile
+    if (__syncthreads_or(threadIdx.x == 0 && status[1 + item.case_id] != 0)) return;
+    const DevCase<T> c = cases[item.case_id];
+    const bool bad = step_item<T, NT, SCHEME, COLL, EOS, NU, false>(fin, fout, c, item, sm);
+    if (bad && threadIdx.x == 0) atomicOr(status + 1 + item.case_id, 1);
 }
 
 }  // namespace lbfe

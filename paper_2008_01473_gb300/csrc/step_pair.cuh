@@ -232,7 +232,14 @@ struct PairCtx {
     int ks;             // ring slot of stored row ra - 1 (= s0 + it)
     int rd;             // lattice row of stage D
     float* out;         // fout + column of the pair's first node (stage D pairs)
+    int* bad;           // shared: a stage D node had rho <= 0 or a non-finite density
 };
+
+// rho > 0 and finite for both nodes of a pair (NaN fails both comparisons)
+__device__ __forceinline__ bool pair_ok(float2 rho)
+{
+    return rho.x > 0.0f && rho.x <= 3.402823466e38f && rho.y > 0.0f && rho.y <= 3.402823466e38f;
+}
 
 __device__ __forceinline__ void pair_timeout(const PairCtx& X)
 {
@@ -379,6 +386,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             const float2 C1 = Ax + By, C7 = Ax - By;
             const float2 drho = R.drho[S3];
             const float2 rho = v2(c.rho_ref) + drho;
+            if (!pair_ok(rho)) *X.bad = 1;
             const float2 mu = R.mu[S3];
             float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
             if (NU) {
@@ -398,6 +406,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         if (X.d && it >= G::ND) {
             const float2 drho = R.drho[S2];
             const float2 rho = v2(c.rho_ref) + drho;
+            if (!pair_ok(rho)) *X.bad = 1;
             float2 mu, Fx, Fy;
             if constexpr (SCHEME == 2) {
                 // F = grad(rho/3) - div P, each component of P through Eq. 17
@@ -469,8 +478,11 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     static_assert(SCHEME != 3, "scheme 3 runs on the plain-load kernel only");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
-    __shared__ int flag;
+    __shared__ int flag, bad;
     const Item item = items[blockIdx.x];
+    // a case flagged unstable by an earlier step no longer advances (thread 0
+    // decides for the block: another block may set the word meanwhile)
+    if (__syncthreads_or(threadIdx.x == 0 && status[1 + item.case_id] != 0)) return;
     const DevCase<float> c = cases[item.case_id];
     fin += c.off;
     fout += c.off;
@@ -504,6 +516,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     }
     if (threadIdx.x == 0) {
         flag = 0;
+        bad = 0;
         for (int k = 0; k < kPairSlots; ++k) mbar_init(X.full + k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -519,6 +532,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     X.ks = 0;
     X.rd = item.y0;
     X.out = fout + (X.d ? item.x0 - 4 + 2 * p : 0);
+    X.bad = &bad;
 
     PairRegs R;
     for (int base = 0; base < niter; base += 4) {
@@ -532,6 +546,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
     __syncthreads();
+    if (threadIdx.x == 0 && bad) atomicOr(status + 1 + item.case_id, 1);
     if (threadIdx.x == 0 && flag) {
         for (int s = max(X.s0, X.s_last - kPairSlots + 1); s <= X.s_last; ++s) {
             const int i = s - X.s0;

@@ -194,6 +194,8 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
     __shared__ StepSmem<T, NT, SCHEME> sm;
     __shared__ int flag;
     const Item item = items[blockIdx.x];
+    // a case flagged unstable no longer advances (thread 0 decides for the block)
+    if (__syncthreads_or(threadIdx.x == 0 && status[1 + item.case_id] != 0)) return;
     const DevCase<T> c = cases[item.case_id];
     fin += c.off;
     fout += c.off;
@@ -219,6 +221,8 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
     }
     __syncthreads();
 
+    StepRegs<T> R;
+    R.bad = false;
     if (threadIdx.x >= NT) {
         // producer warp
         if (threadIdx.x == NT) {
@@ -239,44 +243,44 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
             }
             tma_produce<T, NT, SCHEME>(A, fin, c, runs, (uint32_t)(kQ * (end - start) * sizeof(T)));
         }
-        return;
-    }
+    } else {
+        StepLane L;
+        L.t = threadIdx.x;
+        const int span = item.wv + 2 * G::HX;
+        const int xw = item.x0 - G::HX + L.t;
+        L.xc = wrapi(xw, c.nx);
+        L.xm = wrapi(xw - 1, c.nx);
+        L.xp = wrapi(xw + 1, c.nx);
+        L.a = L.t < span;
+        L.b = L.t >= 1 && L.t < span - 1;
+        L.c = L.t >= 2 && L.t < span - 2;
+        L.d = L.t >= G::HX && L.t < span - G::HX;
 
-    StepLane L;
-    L.t = threadIdx.x;
-    const int span = item.wv + 2 * G::HX;
-    const int xw = item.x0 - G::HX + L.t;
-    L.xc = wrapi(xw, c.nx);
-    L.xm = wrapi(xw - 1, c.nx);
-    L.xp = wrapi(xw + 1, c.nx);
-    L.a = L.t < span;
-    L.b = L.t >= 1 && L.t < span - 1;
-    L.c = L.t >= 2 && L.t < span - 2;
-    L.d = L.t >= G::HX && L.t < span - G::HX;
+        StepRows rows;
+        rows.ra = wrapi(item.y0 - G::HX, c.ny);
+        rows.rd = item.y0;
+        rows.sa = item.y0 - G::HX;  // (this kernel never runs lattices with walls)
 
-    StepRows rows;
-    rows.ra = wrapi(item.y0 - G::HX, c.ny);
-    rows.rd = item.y0;
-    rows.sa = item.y0 - G::HX;  // (this kernel never runs lattices with walls)
-
-    StepRegs<T> R;
-    for (int base = 0; base < niter; base += 4) {
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, A, fin, fout, c, L, rows, sm, R);
-        if (base + 1 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, A, fin, fout, c, L, rows, sm, R);
-        if (base + 2 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, A, fin, fout, c, L, rows, sm, R);
-        if (base + 3 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
-    }
-    // every issued row was waited on by stage A; after a timeout, drain (bounded)
-    A.sync();
-    if (L.t == 0 && flag) {
-        for (int s = max(A.s0, A.s_last - kTmaSlots + 1); s <= A.s_last; ++s) {
-            const int i = s - A.s0;
-            mbar_wait(A.full + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u);
+        for (int base = 0; base < niter; base += 4) {
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, A, fin, fout, c, L, rows, sm, R);
+            if (base + 1 >= niter) break;
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, A, fin, fout, c, L, rows, sm, R);
+            if (base + 2 >= niter) break;
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, A, fin, fout, c, L, rows, sm, R);
+            if (base + 3 >= niter) break;
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
+        }
+        // every issued row was waited on by stage A; after a timeout, drain (bounded)
+        A.sync();
+        if (L.t == 0 && flag) {
+            for (int s = max(A.s0, A.s_last - kTmaSlots + 1); s <= A.s_last; ++s) {
+                const int i = s - A.s0;
+                mbar_wait(A.full + i % kTmaSlots, (uint32_t)(i / kTmaSlots) & 1u);
+            }
         }
     }
+    // the producer warp joins with R.bad == false
+    if (__syncthreads_or(R.bad) && threadIdx.x == 0) atomicOr(status + 1 + item.case_id, 1);
 }
 
 }  // namespace lbfe

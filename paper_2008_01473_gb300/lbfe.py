@@ -107,6 +107,8 @@ def lib() -> C.CDLL:
         L.lb_adjoint_step.argtypes = [vp, i32, vp, i64, i64, vp, i32, i32, vp, sz, dp, vp, dp, dp]
         L.lb_worklist.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
         L.lb_wait_selftest.argtypes = [vp]
+        L.lb_launch_mode.argtypes = [vp, i32, C.POINTER(i32)]
+        L.lb_persistent_selftest.argtypes = [vp, i64]
         L.lb_window_means.argtypes = [vp, i32, i32, C.POINTER(_CWindow), dp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
@@ -114,7 +116,7 @@ def lib() -> C.CDLL:
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means",
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means", "lb_launch_mode", "lb_persistent_selftest",
                      "lb_surface_tension", "lb_young_laplace"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -235,6 +237,19 @@ class Lattice:
         """Enqueue the failure-detection self-test (a bounded wait that gives
         up); the next reductions() call reports LB_E_TIMEOUT."""
         _check(lib().lb_wait_selftest(self._h), self._h)
+
+    def launch_mode(self, mode: int = -1) -> bool:
+        """Set the persistent-launch mode (0 never, 1 always, 2 automatic;
+        -1 keeps it) and return whether the persistent launch is in use."""
+        p = C.c_int32()
+        _check(lib().lb_launch_mode(self._h, int(mode), C.byref(p)), self._h)
+        return bool(p.value)
+
+    def persistent_selftest(self, nsteps: int = 8):
+        """Enqueue the persistent launch's failure-detection self-test (a
+        wait that nothing completes gives up); the next reductions() call
+        reports LB_E_TIMEOUT."""
+        _check(lib().lb_persistent_selftest(self._h, int(nsteps)), self._h)
 
     def worklist(self):
         """(rows per segment, item count, narrow blocks used) of the work-list

@@ -35,3 +35,20 @@ def test_cpulist_parser():
     assert bench._parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
     assert bench._parse_cpulist("5") == {5}
     assert bench._parse_cpulist("") == set()
+
+
+def test_cpulist_format_round_trip():
+    assert bench._format_cpulist({0, 1, 2, 3, 64, 65, 66, 67, 9}) == "0-3,9,64-67"
+    assert bench._parse_cpulist(bench._format_cpulist({5, 7, 8, 9})) == {5, 7, 8, 9}
+
+
+def test_gpu_ids_follow_the_pci_location_not_the_cuda_ordinal():
+    """Under CUDA_VISIBLE_DEVICES=3, cuda:0 is the fourth GPU of the node:
+    the ids used for nvidia-smi and the sysfs topology come from the
+    device's PCI location, whatever its CUDA ordinal."""
+    class Props:  # what torch reports for cuda:0 when it is the GPU at 0000:1B:00.0
+        pci_domain_id, pci_bus_id, pci_device_id = 0, 0x1B, 0
+
+    smi, sysfs = bench._pci_ids(Props())
+    assert smi == "00000000:1B:00.0"
+    assert sysfs == "0000:1b:00.0"

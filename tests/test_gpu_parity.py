@@ -5,6 +5,8 @@ GPU fuses multiply-adds and sums in another order). FP32 runs store
 populations as deviations from w_a rho_ref and compute in FP32; their
 tolerances are stated per test.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -184,6 +186,50 @@ def test_unstable_case_flagged_others_kept():
         lat.reductions(raise_unstable=True)
     _, ref = _oracle_run(oc, r_ok, 50)
     assert _maxerr(lat.moments(1), ref) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP64, lbfe.FP32])
+def test_unstable_case_frozen_by_the_step_kernel(precision):
+    """A case that blows up inside one lb_step call (Carnahan-Starling a=1,
+    b=4 at 0.5 T_c: the oracle stops it within a few steps) is flagged by the
+    step kernel itself and frozen: its stored populations no longer change
+    (its blocks return at once), lb_reductions names it, and the stable case
+    of the same launches runs on unchanged (bit-identical to running it
+    alone). A new state from lb_init_fields clears the flag."""
+    e = thermo.cs_unit()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.5)
+    bad = lbfe.Case(nx=64, ny=8, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.CS, a=1.0, b=4.0, T=T,
+                    kappa=0.02, tau_v=1.0)
+    r_bad = inputs.slab(64, 8, rl, rg)
+    oc_bad = O.Case(nx=64, ny=8, scheme=O.IMPROVED, collision=O.BGK, eos=O.CS, a=1.0, b=4.0, T=T, kappa=0.02,
+                    tau_v=1.0)
+    assert O.step(oc_bad, O.init(oc_bad, r_bad), 50) < 20
+    gc, oc, rg2, rl2 = _pair(48, 40, lbfe.IMPROVED, lbfe.MRT)
+    r_ok = inputs.droplet(48, 40, 10.0, rl2, rg2)
+    lat = lbfe.Lattice([bad, gc], precision=precision)
+    lat.init_fields(0, r_bad)
+    lat.init_fields(1, r_ok)
+    lat.step(50)
+    _, st = lat.reductions()
+    assert st[0] == 3 and st[1] == 0
+    frozen = lat.save(0)[16:]  # populations (the header holds the step counter)
+    lat.step(16)
+    assert lat.save(0)[16:] == frozen
+    _, st = lat.reductions()
+    assert st[0] == 3 and st[1] == 0
+    alone = lbfe.Lattice([gc], precision=precision)
+    alone.init_fields(0, r_ok)
+    alone.step(66)
+    a, b = alone.moments(0), lat.moments(1)
+    for k in ("rho", "ux", "uy"):
+        assert np.array_equal(a[k], b[k])
+    alone.close()
+    # a fresh state clears the flag: the uniform gas at rest is an exact steady state
+    lat.init_fields(0, np.full((8, 64), rg))
+    lat.step(8)
+    _, st = lat.reductions()
+    assert st[0] == 0 and st[1] == 0
+    lat.close()
 
 
 def test_invalid_inputs_rejected():
@@ -698,3 +744,95 @@ def test_walls_channel_startup_on_gpu(precision):
     for k in range(1, 400, 2):
         th -= 4 * U / (k * np.pi) * np.sin(k * np.pi * (yy + 0.5) / H) * np.exp(-nu * (k * np.pi / H) ** 2 * 600)
     assert np.abs(m["ux"] - th[:, None]).max() < 1e-3 * U
+
+
+def _moments_after(cases, rho0s, steps, precision, mode):
+    lat = lbfe.Lattice(cases, precision=precision)
+    persistent = lat.launch_mode(mode)
+    for i, r in enumerate(rho0s):
+        lat.init_fields(i, r)
+    lat.step(steps)
+    out = [lat.moments(i) for i in range(len(cases))]
+    persistent = lat.launch_mode()
+    _, st = lat.reductions()
+    lat.close()
+    return out, persistent, st
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP64, lbfe.FP32])
+@pytest.mark.parametrize("kind", ["strips", "walls", "smooth", "droplet"])
+def test_persistent_launch_bit_identical(precision, kind):
+    """The persistent multi-step launch (one cooperative launch for many
+    steps, blocks waiting on their neighbour items' progress) gives the same
+    bits as one launch per step: several strips of uneven width in one
+    work-list, a walled lattice, the averaged correction, and a lattice of
+    odd width (FP32 groups on the one-column kernel). 101 steps: odd, so the
+    state ends in the other buffer, and more than one chunk boundary-free
+    launch."""
+    e = thermo.vdw_paper()
+    if kind == "strips":
+        cases, rhos = [], []
+        for k, t in enumerate((0.9, 0.85, 0.8, 0.8)):
+            T, rg, rl = thermo.maxwell_reduced(e, t)
+            nx, ny = ((130, 8), (97, 8), (203, 8), (601, 40))[k]  # the last one splits into several items
+            cases.append(lbfe.Case(nx=nx, ny=ny, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, a=e.a,
+                                   b=e.b, T=T, kappa=0.02, tau_v=1.0))
+            rhos.append(inputs.slab(nx, ny, rl, rg))
+    else:
+        T, rg, rl = thermo.maxwell_reduced(e, 0.8 if kind != "smooth" else 0.7)
+        nx, ny = (66, 40) if kind == "walls" else (61, 45)
+        scheme = lbfe.IMPROVED_SMOOTH if kind == "smooth" else lbfe.IMPROVED
+        kw = dict(walls=1, wall_u=0.05, rho_wall=rg) if kind == "walls" else {}
+        cases = [lbfe.Case(nx=nx, ny=ny, scheme=scheme, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
+                           kappa=0.02, tau_v=0.9, **kw)]
+        rhos = [inputs.droplet(nx, ny, 10.0, rl, rg, noise=1e-3, seed=2)]
+    ref, p0, _ = _moments_after(cases, rhos, 101, precision, 0)
+    got, p1, st = _moments_after(cases, rhos, 101, precision, 1)
+    assert not p0 and p1 and (st == 0).all()
+    for a, b in zip(ref, got):
+        for k in ("rho", "ux", "uy", "mu"):
+            assert np.array_equal(a[k], b[k]), k
+
+
+def test_persistent_launch_auto_mode_and_oracle():
+    """Automatic mode on an FP64 handle (its group runs the one-column
+    kernel): the first long lb_step times both launch modes with its own
+    steps and keeps one; the result equals the oracle to 1e-11 whichever it
+    kept, over two calls (the second in the chosen mode)."""
+    gc, oc, rg, rl = _pair(40, 33, lbfe.IMPROVED, lbfe.MRT)
+    rho0 = inputs.droplet(40, 33, 9.0, rl, rg, noise=1e-4, seed=0)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    lat.init_fields(0, rho0)
+    lat.step(60)
+    lat.step(41)
+    mode = lat.launch_mode()
+    m = lat.moments(0)
+    lat.close()
+    _, ref = _oracle_run(oc, rho0, 101)
+    assert _maxerr(m, ref) < 1e-11, mode
+
+
+def test_persistent_wait_gives_up_and_is_reported():
+    """Failure detection of the persistent launch without a fault: in the
+    self-test one work item never publishes its progress, the neighbour that
+    waits for it gives up after its bounded spin and aborts the launch, the
+    next lb_reductions reports LB_E_TIMEOUT (status 4), and after a fresh
+    initialisation the handle steps on and matches the oracle."""
+    gc, oc, rg, rl = _pair(64, 64, lbfe.IMPROVED, lbfe.BGK)
+    rho0 = inputs.droplet(64, 64, 14.0, rl, rg)
+    lat = lbfe.Lattice([gc], precision=lbfe.FP64)
+    lat.init_fields(0, rho0)
+    n_items = lat.worklist()[1]
+    assert n_items >= 2
+    lat.persistent_selftest(8)
+    n = lbfe.lib().lb_reductions(lat._h, np.zeros(5).ctypes.data_as(C.POINTER(C.c_double)), None)
+    assert n == 4
+    lat.init_fields(0, rho0)
+    lat.launch_mode(1)
+    lat.step(30)
+    out, st = lat.reductions()
+    assert st[0] == 0
+    m = lat.moments(0)
+    lat.close()
+    _, ref = _oracle_run(oc, rho0, 30)
+    assert _maxerr(m, ref) < 1e-11

@@ -90,6 +90,34 @@ def test_static_matches_handle_path_two_calls():
         assert red[3] == 0.0 and red[4] == 0.0
 
 
+def test_static_allocates_nothing_and_reduces_without_field_outputs():
+    """The contract itself: the device's free memory is the same before and
+    after a call (the first call on the device may load the library's module,
+    so the measured call is the second one), and a call with every field
+    output NULL still writes the reductions, equal to lb_reductions."""
+    import torch
+
+    (case, rho0), prec, steps = _case(200, 150, lbfe.IMPROVED, lbfe.VDW, 0.8), lbfe.FP32, 20
+    ref, red_ref, pops, rho_ref = _reference_and_pops(case, rho0, steps, prec)
+    red = torch.full((5,), np.nan, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    cs = case.cstruct()
+
+    def call():
+        rc = lbfe.lib().lb_fields_static(C.byref(cs), prec, C.c_void_p(pops.data_ptr()), rho_ref, None, None, None,
+                                         None, C.c_void_p(red.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert rc == 0
+        torch.cuda.synchronize()
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    r = red.cpu().numpy()
+    assert abs(r[0] / red_ref[0] - 1) < 1e-12 and abs(r[2] - red_ref[2]) < 1e-12 and r[4] == 0.0
+
+
 def test_static_rejects_oversized_case():
     import torch
 
