@@ -27,6 +27,7 @@ _lib = None
 
 STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
 IMPROVED_SMOOTH = 3  # improved scheme, Eq. 29's derivatives of the lattice-weight average of phi u
+LAX_WENDROFF = 4  # the comparison scheme of Appendix A (Eqs. A1-A4): BGK, standard force, dt = A
 BGK, MRT = 0, 1
 VDW, CS = thermo.VDW, thermo.CS
 
@@ -46,7 +47,7 @@ class _CCase(C.Structure):
                 ("kappa", C.c_double), ("tau_v", C.c_double), ("tau_e", C.c_double),
                 ("tau_s", C.c_double), ("tau_q", C.c_double), ("pm_c0", C.c_double),
                 ("nu", C.c_double), ("walls", C.c_int32), ("pad_", C.c_int32), ("wall_u", C.c_double),
-                ("rho_wall", C.c_double)]
+                ("rho_wall", C.c_double), ("lw_A", C.c_double), ("lw_B", C.c_double)]
 
 
 @dataclass
@@ -72,13 +73,15 @@ class Case:
     walls: int = 0          # 1: moving no-slip walls below y = 0 and above y = ny - 1
     wall_u: float = 0.0     # x velocity of both walls
     rho_wall: float = 0.0   # density in the moving-wall term
+    lw_A: float = 0.0       # LAX_WENDROFF: CFL number A (the time step, Appendix A)
+    lw_B: float = 0.0       # LAX_WENDROFF: B of Eq. A3 (nu = c_s^2 (tau - 1/2 - B) A)
     _c: _CCase = field(default=None, repr=False, compare=False)
 
     def cstruct(self) -> _CCase:
         return _CCase(self.nx, self.ny, self.scheme, self.collision, self.eos, self.flags,
                       self.a, self.b, self.R, self.T, self.kappa, self.tau_v, self.tau_e,
                       self.tau_s, self.tau_q, self.pm_c0, self.nu, self.walls, 0, self.wall_u,
-                      self.rho_wall)
+                      self.rho_wall, self.lw_A, self.lw_B)
 
     def thermo(self) -> thermo.EOS:
         return thermo.EOS(self.eos, self.a, self.b, self.R)

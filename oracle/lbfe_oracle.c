@@ -30,6 +30,14 @@
  *  11. push streaming f_a(x + e_a) = f*_a(x), periodic     (Eq. 10); with
  *      walls, halfway bounce-back with the moving-wall term (Sec. IV C)
  *
+ * Scheme 4 is the Lax-Wendroff propagation scheme the paper compares with
+ * (Appendix A): stages 1-6 with the standard force (Eq. 13 right) and
+ * u = (sum_a e_a f_a + dt F / 2) / rho, dt = A the CFL number; then the
+ * BGK collision of Eq. A1 with the equilibrium of Eq. A3, whose tensor T
+ * comes from the second moment of the populations by Eq. A4, and the
+ * three-point propagation of Eq. A2 with a_0 = 1 - A^2,
+ * a_1 = A (A - 1) / 2, a_-1 = A (A + 1) / 2.
+ *
  * M is the Lallemand-Luo D2Q9 moment matrix with moments ordered
  * (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy): the order of the relaxation
  * vector of Eq. 8 and of the equilibria of Eqs. 11 and 27 (the paper cites
@@ -74,7 +82,8 @@ typedef struct {
     int32_t scheme;    /* 0 = standard (Eq. 13 right), 1 = improved (Eqs. 24, 27, 28),
                           2 = standard with the pressure-tensor force (Eq. 13 left),
                           3 = improved with the derivatives of Eq. 29 taken on the
-                              lattice-weight average of phi u */
+                              lattice-weight average of phi u,
+                          4 = Lax-Wendroff propagation (Appendix A, Eqs. A1-A4) */
     int32_t collision; /* 0 = BGK (all rates 1/tau_v), 1 = MRT (Eq. 8) */
     int32_t eos;       /* 0 = van der Waals (Eq. 30), 1 = Carnahan-Starling */
     int32_t flags;     /* planted-mistake hooks for pin tests; 0 in normal use.
@@ -97,6 +106,7 @@ typedef struct {
     int32_t pad_;
     double wall_u;                     /* x velocity of both walls */
     double rho_wall;                   /* wall density of the moving-wall bounce-back term */
+    double lw_A, lw_B;                 /* scheme 4: CFL number A (the time step) and B of Eq. A3 */
 } orc_case;
 
 /* ------------------------------------------------------------------ EOS */
@@ -353,7 +363,7 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
     for (int i = 0; i < N; ++i) mu[i] = orc_dEf(c, rho[i]) - c->kappa * lap[i];
     /* 4-5. force */
     grad_w(nx, ny, 0, mu, gmx, gmy);
-    if (c->scheme == 0) {
+    if (c->scheme == 0 || c->scheme == 4) {
         double* r3 = calloc(N, sizeof(double));
         for (int i = 0; i < N; ++i) r3[i] = rho[i] * CS2;
         grad_w(nx, ny, 0, r3, grx, gry);
@@ -399,8 +409,9 @@ static int fields_core(const orc_case* c, const double* rho_in, const double* jx
             Fy[i] = (CS2 - rho[i]) * gmy[i];
         }
     }
-    /* 6. velocity */
+    /* 6. velocity; the Lax-Wendroff scheme's time step is A (Appendix A) */
     double half = (c->flags & 2) ? -0.5 : 0.5;
+    if (c->scheme == 4) half *= c->lw_A;
     for (int i = 0; i < N; ++i) {
         ux[i] = (jx_in[i] + half * Fx[i]) / rho[i];
         uy[i] = (jy_in[i] + half * Fy[i]) / rho[i];
@@ -513,6 +524,69 @@ int orc_fields(const orc_case* c, const double* f, double* rho_o, double* ux_o, 
 
 /* ---------------------------------------------------------------- step */
 
+/* Scheme 4, the Lax-Wendroff propagation scheme of Appendix A, nsteps steps
+ * of dt = A. Per node, from the populations f at the start of a step:
+ * rho, u, F from orc_fields (standard force, u with dt F / 2), the second
+ * moment Pi = sum_a e_a e_a f_a, the tensor T of Eq. A4,
+ *   rho c_s^2 dt (B - tau) T = Pi - rho c_s^2 I - rho u u - (tau - 1/2) dt (u F + F u),
+ * the equilibrium of Eq. A3,
+ *   f_eq,a = rho w_a [1 + e.u/c_s^2 + (e.u)^2/(2 c_s^4) - u^2/(2 c_s^2)
+ *                     + B dt (e_a e_a - c_s^2 I) : T / (2 c_s^2)],
+ * the guo term G of Eq. 14 and the BGK collision of Eq. A1,
+ *   f*_a = f_a - (f_a - f_eq,a) / tau + dt (1 - 1/(2 tau)) G_a;
+ * then the propagation of Eq. A2 over the periodic lattice,
+ *   f_a(x) <- a_0 f*_a(x) + a_1 f*_a(x + e_a) + a_-1 f*_a(x - e_a). */
+static int64_t lw_step(const orc_case* c, double* f, int64_t nsteps, double* rho, double* ux, double* uy,
+                       double* mu, double* Fx, double* Fy, double* C1, double* C7, double* fs_all)
+{
+    const int nx = c->nx, ny = c->ny, N = nx * ny;
+    const double A = c->lw_A, B = c->lw_B, dt = A, tau = c->tau_v;
+    const double a0 = 1.0 - A * A, a1 = A * (A - 1.0) / 2.0, am1 = A * (A + 1.0) / 2.0;
+    int64_t done = 0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (orc_fields(c, f, rho, ux, uy, mu, Fx, Fy, C1, C7) != 0) break;
+        for (int i = 0; i < N; ++i) {
+            double fl[Q], G[Q];
+            for (int a = 0; a < Q; ++a) fl[a] = f[a * N + i];
+            const double r = rho[i], u[2] = {ux[i], uy[i]}, F[2] = {Fx[i], Fy[i]};
+            double Pi[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+            for (int a = 0; a < Q; ++a) {
+                const double e[2] = {(double)EX[a], (double)EY[a]};
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) Pi[p][q] += e[p] * e[q] * fl[a];
+            }
+            double Tt[2][2];
+            for (int p = 0; p < 2; ++p)
+                for (int q = 0; q < 2; ++q)
+                    Tt[p][q] = (Pi[p][q] - r * CS2 * (p == q ? 1.0 : 0.0) - r * u[p] * u[q] -
+                                (tau - 0.5) * dt * (u[p] * F[q] + F[p] * u[q])) /
+                               (r * CS2 * dt * (B - tau));
+            orc_guo(u[0], u[1], F[0], F[1], G);
+            for (int a = 0; a < Q; ++a) {
+                const double e[2] = {(double)EX[a], (double)EY[a]};
+                const double eu = e[0] * u[0] + e[1] * u[1], u2 = u[0] * u[0] + u[1] * u[1];
+                double eeT = 0.0;
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) eeT += (e[p] * e[q] - CS2 * (p == q ? 1.0 : 0.0)) * Tt[p][q];
+                const double feq = r * WA[a] *
+                                   (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2) +
+                                    B * dt * eeT / (2.0 * CS2));
+                fs_all[a * N + i] = fl[a] - (fl[a] - feq) / tau + dt * (1.0 - 1.0 / (2.0 * tau)) * G[a];
+            }
+        }
+        for (int a = 0; a < Q; ++a)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const double* fs = fs_all + a * N;
+                    const int ip = wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx);
+                    const int im = wrap(y - EY[a], ny) * nx + wrap(x - EX[a], nx);
+                    f[a * N + y * nx + x] = a0 * fs[y * nx + x] + a1 * fs[ip] + am1 * fs[im];
+                }
+        ++done;
+    }
+    return done;
+}
+
 /* Advance f (in place, f[a][y][x]) by nsteps time steps. Returns the number
  * of steps completed; fewer than nsteps means the state became non-physical
  * (rho <= 0 or a non-finite value) before the step that was not taken. */
@@ -536,6 +610,10 @@ int64_t orc_step(const orc_case* c, double* f, int64_t nsteps)
     double wall_feq[Q];
     if (c->walls) orc_feq(c, c->rho_wall, c->wall_u, 0.0, orc_dEf(c, c->rho_wall), wall_feq);
     int64_t done = 0;
+    if (c->scheme == 4) {
+        done = lw_step(c, f, nsteps, rho, ux, uy, mu, Fx, Fy, C1, C7, fn);
+        nsteps = 0;
+    }
     for (int64_t n = 0; n < nsteps; ++n) {
         if (orc_fields(c, f, rho, ux, uy, mu, Fx, Fy, C1, C7) != 0) break;
         for (int y = 0; y < ny; ++y)
@@ -958,7 +1036,7 @@ int orc_adjoint(const orc_case* c, const double* rho0, int64_t nsteps, int64_t u
                 double* loss, double* g_rho0, double* g_kappa, double* g_T)
 {
     const int nx = c->nx, ny = c->ny, N = nx * ny;
-    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2 || c->scheme == 3 || c->walls)
+    if (c->nu > 0.0 || nsteps < 0 || c->scheme == 2 || c->scheme == 3 || c->scheme == 4 || c->walls)
         return -1; /* periodic, chemical-potential forms, Eq. 17 correction */
     int64_t K = 1;
     while (K * K < nsteps) ++K;

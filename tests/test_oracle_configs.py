@@ -71,3 +71,22 @@ def test_paper_vdw_set_runs_on_the_same_lattices(scheme):
         assert O.step(c, f, 400) == 400
         assert abs(f.sum() / m0 - 1) < 1e-12
         assert np.isfinite(f).all()
+
+
+@pytest.mark.parametrize("scheme", [O.IMPROVED, O.IMPROVED_SMOOTH])
+def test_vdw_spinodal_stability_limit(scheme):
+    """The 4096^2 spinodal configuration with the paper's vdW set instead of
+    the CS one, on a 64^2 sample: at 0.7 T_c (the configuration's
+    temperature) the phase separation from the uniform mean density drives
+    the vapour below zero within a few hundred steps with either reading of
+    Eq. 29's derivatives (plain Eq. 17, R4; weight-averaged, R4s), MRT with
+    tau_v 0.8, tau_e = tau_s = 1, tau_q 1.1; at 0.75 T_c both run (and run on
+    for 20,000 steps). The throughput workload therefore runs at 0.8 T_c."""
+    e = thermo.vdw_paper()
+    for t, runs in ((0.7, False), (0.75, True)):
+        T, rg, rl = thermo.maxwell_reduced(e, t)
+        c = O.Case(nx=L, ny=L, scheme=scheme, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b, R=1.0, T=T, kappa=0.02,
+                   tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
+        f = O.init(c, inputs.spinodal(L, L, 0.5 * (rg + rl), 0.01, seed=1))
+        done = O.step(c, f, 600)
+        assert (done == 600) == runs, (t, done)
