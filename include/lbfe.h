@@ -69,7 +69,19 @@ typedef enum {
  * the constant kinematic viscosity 0.04 of Table II. Same steady states as
  * LB_IMPROVED (C vanishes at u = 0). Runs on the one-column plain-load step
  * kernel; no lb_adjoint_step. */
-enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2, LB_IMPROVED_SMOOTH = 3 };
+/* LB_LAX_WENDROFF: the comparison scheme of Appendix A (Lou and Guo's
+ * Lax-Wendroff propagation): the standard force (Eq. 13 right), velocity
+ * u = (sum_a e_a f_a + A F / 2) / rho, the BGK collision of Eq. A1 (rate
+ * 1 / tau_v, source A (1 - 1/(2 tau_v)) G of Eq. 14) with the equilibrium of
+ * Eq. A3 and its tensor T of Eq. A4, and the three-point propagation of
+ * Eq. A2, a_0 = 1 - A^2, a_1 = A (A - 1)/2, a_-1 = A (A + 1)/2, over a time
+ * step A (lw_A, the CFL number; lw_B is B of Eq. A3, kinematic viscosity
+ * c_s^2 (tau_v - 1/2 - B) A). A step advances time by A, so it takes 1/A
+ * steps per unit of the other schemes' time. BGK only, periodic, nu = 0; the
+ * one-column kernel; no adjoint and no lb_fields_static. Storage: at step 0
+ * the populations are f(0) (pre-collision, unshifted), after that the
+ * post-collision values before Eq. A2's propagation. */
+enum { LB_STANDARD = 0, LB_IMPROVED = 1, LB_STANDARD_PT = 2, LB_IMPROVED_SMOOTH = 3, LB_LAX_WENDROFF = 4 };
 enum { LB_BGK = 0, LB_MRT = 1 };            /* single rate 1/tau_v / Eq. 8 */
 enum { LB_VDW = 0, LB_CS = 1 };             /* Eq. 30 / Carnahan-Starling */
 enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic */
@@ -104,7 +116,7 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
-    int32_t scheme;      /* LB_STANDARD, LB_IMPROVED, LB_STANDARD_PT or LB_IMPROVED_SMOOTH */
+    int32_t scheme;      /* LB_STANDARD, LB_IMPROVED, LB_STANDARD_PT, LB_IMPROVED_SMOOTH or LB_LAX_WENDROFF */
     int32_t collision;   /* LB_BGK or LB_MRT */
     int32_t eos;         /* LB_VDW or LB_CS */
     int32_t walls;       /* 0: periodic in y; 1: moving no-slip walls (below) */
@@ -116,6 +128,8 @@ typedef struct {
     double rho_ref;      /* FP32 storage reference, >= 0 */
     double wall_u;       /* walls: x velocity of both walls, |wall_u| <= 0.3 */
     double rho_wall;     /* walls: density of the wall state, > 0 */
+    double lw_A;         /* LB_LAX_WENDROFF: CFL number A, 0 < A <= 1 (unused otherwise) */
+    double lw_B;         /* LB_LAX_WENDROFF: B of Eq. A3, B < tau_v - 1/2 (unused otherwise) */
 } lb_case;
 
 typedef struct lb_handle lb_handle;

@@ -193,6 +193,13 @@ __device__ __forceinline__ void init_node(const DevCase<T>& c, const DevCase<C>&
     for (int a = 0; a < kQ; ++a) d[a] = C(0);
     collide<SCHEME, C>(d, rho - rr, rho, rho * ux, rho * uy, ux, uy, C(0), C(0), mu0[i], C(0), C(0), rr, cc.c0,
                        C(1), C(1), C(1), C(1));
+    if (c.lw_dt > T(0)) {
+        // Lax-Wendroff scheme: at step 0 the storage holds f(0) at its own
+        // node (the first step pulls it without Eq. A2's propagation)
+        const int64_t o = (int64_t)y * c.pitch + x;
+        for (int a = 0; a < kQ; ++a) f[c.off + a * c.plane + o] = (T)d[a];
+        return;
+    }
     // Storage holds post-collision populations before streaming (the step
     // pulls f_a(x) from x - e_a), so f_a(0) of node x is stored at x - e_a.
     constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -254,15 +261,29 @@ __global__ void __launch_bounds__(256) pull_moments_kernel(DevCase<T> c, const T
         const int64_t rm = (int64_t)(y == 0 ? ny - 1 : y - 1) * pitch, r0 = (int64_t)y * pitch,
                       rp = (int64_t)(y + 1 == ny ? 0 : y + 1) * pitch;
         C F[kQ];
-        F[0] = (C)f[0 * P + r0 + x];
-        F[1] = (C)f[1 * P + r0 + xm];
-        F[2] = (C)f[2 * P + rm + x];
-        F[3] = (C)f[3 * P + r0 + xp];
-        F[4] = (C)f[4 * P + rp + x];
-        F[5] = (C)f[5 * P + rm + xm];
-        F[6] = (C)f[6 * P + rm + xp];
-        F[7] = (C)f[7 * P + rp + xp];
-        F[8] = (C)f[8 * P + rp + xm];
+        if (c.lw_dt > T(0)) {
+            // Lax-Wendroff scheme: the three-point propagation of Eq. A2 (at
+            // step 0 the stored values are f(0) itself)
+            constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            const int64_t rr[3] = {rm, r0, rp};
+            const int xs[3] = {xm, x, xp};
+            const T a0 = c.lw_first ? T(1) : c.lw_a0, a1 = c.lw_first ? T(0) : c.lw_a1;
+            const T am1 = c.lw_first ? T(0) : c.lw_am1;
+            for (int a = 0; a < kQ; ++a)
+                F[a] = (C)(a0 * f[a * P + r0 + x] + a1 * f[a * P + rr[1 + ey[a]] + xs[1 + ex[a]]] +
+                           am1 * f[a * P + rr[1 - ey[a]] + xs[1 - ex[a]]]);
+        } else {
+            F[0] = (C)f[0 * P + r0 + x];
+            F[1] = (C)f[1 * P + r0 + xm];
+            F[2] = (C)f[2 * P + rm + x];
+            F[3] = (C)f[3 * P + r0 + xp];
+            F[4] = (C)f[4 * P + rp + x];
+            F[5] = (C)f[5 * P + rm + xm];
+            F[6] = (C)f[6 * P + rm + xp];
+            F[7] = (C)f[7 * P + rp + xp];
+            F[8] = (C)f[8 * P + rp + xm];
+        }
         if (c.walls && y == 0) {  // bounce-back from the bottom wall
             F[2] = (C)f[4 * P + r0 + x];
             F[5] = (C)(f[7 * P + r0 + x] + c.wall_d);
@@ -338,8 +359,9 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
                     Fy = gry * C(1.0 / 3.0) - r * gmy;
                 }
             }
-            const C ux = (jx[i] + C(0.5) * Fx) / r;
-            const C uy = (jy[i] + C(0.5) * Fy) / r;
+            const C half = SCHEME == 4 ? C(0.5) * cc.lw_dt : C(0.5);  // Lax-Wendroff: time step A
+            const C ux = (jx[i] + half * Fx) / r;
+            const C uy = (jy[i] + half * Fy) / r;
             const C m = mu[i];
             if (out_rho) out_rho[i] = (double)r;
             if (out_ux) out_ux[i] = (double)ux;

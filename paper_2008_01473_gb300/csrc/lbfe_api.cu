@@ -30,6 +30,12 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
+// schemes that only the one-column plain-load kernel runs
+bool one_column_only(const lb_case& c)
+{
+    return c.walls || c.scheme == LB_IMPROVED_SMOOTH || c.scheme == LB_LAX_WENDROFF;
+}
+
 // Widest strip of output columns a block of nt threads can own. Lattices with
 // nx % 4 == 0 get strips of a multiple of 4 columns, at most nt - 8 wide, as
 // the TMA-staged kernel needs (16-byte aligned runs of [x0 - 4, x0 + wv + 4)).
@@ -105,19 +111,25 @@ std::string check_case(const lb_case& c, int i)
     // the step kernel addresses a case's nine planes with 32-bit offsets
     if ((int64_t)kQ * c.ny * pitch_of(c.nx) >= (int64_t)1 << 31) return bad("lattice too large");
     if (c.scheme != LB_STANDARD && c.scheme != LB_IMPROVED && c.scheme != LB_STANDARD_PT &&
-        c.scheme != LB_IMPROVED_SMOOTH)
+        c.scheme != LB_IMPROVED_SMOOTH && c.scheme != LB_LAX_WENDROFF)
         return bad("unknown scheme");
     if (c.collision != LB_BGK && c.collision != LB_MRT) return bad("unknown collision");
     if (c.eos != LB_VDW && c.eos != LB_CS) return bad("unknown eos");
     if (c.walls != 0 && c.walls != 1) return bad("walls must be 0 or 1");
     const double v[] = {c.a, c.b, c.R, c.T, c.kappa, c.tau_v, c.tau_e, c.tau_s, c.tau_q, c.pm_c0,
-                        c.nu, c.rho_ref, c.wall_u, c.rho_wall};
+                        c.nu, c.rho_ref, c.wall_u, c.rho_wall, c.lw_A, c.lw_B};
     for (double x : v)
         if (!std::isfinite(x)) return bad("non-finite parameter");
     if (!(c.a > 0 && c.b > 0 && c.R > 0 && c.T > 0 && c.kappa > 0)) return bad("a, b, R, T, kappa must be > 0");
     if (!(c.tau_v > 0.5 && c.tau_e > 0.5 && c.tau_s > 0.5 && c.tau_q > 0.5))
         return bad("relaxation times must be > 1/2");
     if (c.nu < 0 || c.rho_ref < 0) return bad("nu and rho_ref must be >= 0");
+    if (c.scheme == LB_LAX_WENDROFF) {
+        if (c.collision != LB_BGK || c.walls || c.nu != 0.0)
+            return bad("the Lax-Wendroff scheme is BGK, periodic and has nu = 0");
+        if (!(c.lw_A > 0.0 && c.lw_A <= 1.0) || !(c.lw_B < c.tau_v - 0.5))
+            return bad("Lax-Wendroff needs 0 < lw_A <= 1 and lw_B < tau_v - 1/2");
+    }
     if (c.walls) {
         // the row pipeline mirrors up to four rows across each wall
         if (c.ny < 8) return bad("walls need ny >= 8");
@@ -174,6 +186,17 @@ DevCase<T> dev_case(const lb_case& c, int64_t off, double rho_ref)
     d.lam_s = (T)(1.0 / (bgk ? c.tau_v : c.tau_s));
     d.lam_q = (T)(1.0 / (bgk ? c.tau_v : c.tau_q));
     d.nu = (T)c.nu;
+    if (c.scheme == LB_LAX_WENDROFF) {
+        const double A = c.lw_A, B = c.lw_B, tau = c.tau_v;
+        d.lw_dt = (T)A;
+        d.lw_a0 = (T)(1.0 - A * A);
+        d.lw_a1 = (T)(A * (A - 1.0) / 2.0);
+        d.lw_am1 = (T)(A * (A + 1.0) / 2.0);
+        d.lw_kT = (T)(1.0 / ((1.0 / 3.0) * A * (B - tau)));
+        d.lw_fd = (T)((tau - 0.5) * A);
+        d.lw_bt = (T)(B * A * 1.5);
+        d.lw_g = (T)(A * (1.0 - 0.5 / tau));
+    }
     return d;
 }
 
@@ -251,8 +274,10 @@ struct lb_handle {
     }
     lb_status upload_case(int i)
     {
-        const DevCase<float> c32 = dev_case<float>(cases[i], L.off[i], rho_ref[i]);
-        const DevCase<double> c64 = dev_case<double>(cases[i], L.off[i], rho_ref[i]);
+        DevCase<float> c32 = dev_case<float>(cases[i], L.off[i], rho_ref[i]);
+        DevCase<double> c64 = dev_case<double>(cases[i], L.off[i], rho_ref[i]);
+        // a Lax-Wendroff case at step 0 holds f(0) itself (see pull_lw)
+        c32.lw_first = c64.lw_first = cases[i].scheme == LB_LAX_WENDROFF && steps[i] == 0;
         lb_status s = cuda(cudaMemcpyAsync(dc32() + i, &c32, sizeof c32, cudaMemcpyHostToDevice, stream),
                            "upload case");
         if (s != LB_OK) return s;
@@ -344,7 +369,7 @@ void build_items(lb_handle* h)
                          [](const Item& a, const Item& b) { return a.h > b.h; });
         h->groups.push_back(g);
     };
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 5; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
@@ -357,7 +382,7 @@ void build_items(lb_handle* h)
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {
                             const lb_case& c = h->cases[i];
-                            const int kind = c.walls || c.scheme == LB_IMPROVED_SMOOTH ? 2 : (c.nx % 4 == 0 ? 1 : 0);
+                            const int kind = one_column_only(c) ? 2 : (c.nx % 4 == 0 ? 1 : 0);
                             if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
                                 kind == al)
                                 (pair && h->narrow && prefers_narrow(c) ? narrow : members).push_back(i);
@@ -399,8 +424,9 @@ template <typename T, typename C>
 lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
 {
     const lb_case& c = h->cases[i];
-    const DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
+    DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
     const DevCase<C> cc = dev_case<C>(c, h->L.off[i], h->rho_ref[i]);
+    ct.lw_first = c.scheme == LB_LAX_WENDROFF && h->steps[i] == 0;  // f(0) stored unpropagated
     const dim3 blk(256), grd = field_grid(c.nx, c.ny);
     C* s0 = reinterpret_cast<C*>(h->scratch(0));
     C* s1 = reinterpret_cast<C*>(h->scratch(1));
@@ -424,6 +450,9 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
             ptensor_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, p0, p1, p2);
         velocity_kernel<2, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, p0, p1, p2, o_rho, o_ux, o_uy, o_mu,
                                                           h->partials());
+    } else if (c.scheme == LB_LAX_WENDROFF) {
+        velocity_kernel<4, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+                                                          o_uy, o_mu, h->partials());
     } else {
         velocity_kernel<0, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
                                                           o_uy, o_mu, h->partials());
@@ -543,6 +572,7 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     const size_t bytes = N * sizeof(double);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2);
+    h->steps[case_id] = 0;  // before the case table is uploaded (Lax-Wendroff step-0 flag)
     lb_status s = LB_OK;
     const double* d_rho0 = rho0;
     if (!on_device) {
@@ -849,6 +879,22 @@ lb_status lb_step(lb_handle* h, int64_t nsteps)
         if (s != LB_OK) return s;
     }
     int64_t n = nsteps;
+    // a Lax-Wendroff case at step 0 holds f(0) unpropagated: run that step on
+    // its own, then mark the case's populations as post-collision
+    bool lw0 = false;
+    for (size_t i = 0; i < h->cases.size(); ++i)
+        lw0 = lw0 || (h->cases[i].scheme == LB_LAX_WENDROFF && h->steps[i] == 0);
+    if (lw0 && n > 0) {
+        lb_status s = enqueue_step(h, h->cur, h->stream);
+        if (s != LB_OK) return s;
+        h->cur ^= 1;
+        for (auto& st : h->steps) st += 1;
+        for (size_t i = 0; i < h->cases.size() && s == LB_OK; ++i)
+            if (h->cases[i].scheme == LB_LAX_WENDROFF) s = h->upload_case((int)i);
+        if (s != LB_OK) return s;
+        --n;
+        nsteps = n;
+    }
     if (h->persist_mode != 0 && n > 0 && persist_possible(h, h->persist_mode == 2)) {
         if (!h->nb_ok) {
             bool ok = false;
@@ -1117,6 +1163,7 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
     memcpy(&rr, p + 8, 8);
     if (st < 0 || !std::isfinite(rr) || rr < 0) return h->fail(LB_E_INVALID, "lb_load: corrupt snapshot header");
     h->rho_ref[case_id] = h->prec == LB_FP32 ? rr : 0.0;
+    h->steps[case_id] = st;  // before the case table is uploaded (Lax-Wendroff step-0 flag)
     lb_status s = h->upload_case(case_id);
     if (s == LB_OK)
         s = h->cuda(cudaMemcpyAsync((uint8_t*)h->fbuf(h->cur) + h->L.off[case_id] * es, p + 16, need - 16,
@@ -1296,8 +1343,8 @@ lb_status lb_adjoint_step(lb_handle* h, int32_t case_id, const double* rho0, int
     if (c.nu > 0) return h->fail(LB_E_INVALID, "lb_adjoint_step: constant relaxation times only (nu = 0)");
     if (c.scheme == LB_STANDARD_PT)
         return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of the pressure-tensor force form");
-    if (c.scheme == LB_IMPROVED_SMOOTH)
-        return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of LB_IMPROVED_SMOOTH");
+    if (c.scheme == LB_IMPROVED_SMOOTH || c.scheme == LB_LAX_WENDROFF)
+        return h->fail(LB_E_INVALID, "lb_adjoint_step: no adjoint of LB_IMPROVED_SMOOTH or LB_LAX_WENDROFF");
     if (c.walls) return h->fail(LB_E_INVALID, "lb_adjoint_step: periodic lattices only (no walls)");
     const int64_t K = ckpt_every > 0 ? ckpt_every : adj_default_K(nsteps);
     const bool f32 = h->prec == LB_FP32;

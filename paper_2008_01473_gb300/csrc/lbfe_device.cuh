@@ -12,8 +12,9 @@ constexpr int kQ = 9;
 
 // Scheme codes of the kernels (the lb_case codes): 0 standard, 1 improved,
 // 2 standard with the pressure-tensor force, 3 improved with the derivatives
-// of Eq. 29 taken on the lattice-weight average of phi u. Schemes 1 and 3
-// share the equilibrium, force and collision of Eqs. 24-28.
+// of Eq. 29 taken on the lattice-weight average of phi u, 4 the Lax-Wendroff
+// propagation scheme of Appendix A (standard force, Eqs. A1-A4). Schemes 1
+// and 3 share the equilibrium, force and collision of Eqs. 24-28.
 __host__ __device__ constexpr bool improved_scheme(int s) { return s == 1 || s == 3; }
 
 // Per-case parameters as the kernels read them (one record per case, in the
@@ -30,6 +31,12 @@ struct DevCase {
     T lam_e, lam_s, lam_q, lam_v;  // 1/tau of Eq. 8 (all 1/tau_v for BGK)
     T nu;           // > 0: tau_v from constant kinematic viscosity
     T wall_d;       // walls: moving-wall term f_eq,5 - f_eq,7 of the wall state
+    // Lax-Wendroff scheme (Appendix A): time step dt = A; coefficients of
+    // Eq. A2; 1/(c_s^2 dt (B - tau)), (tau - 1/2) dt and B dt / (2 c_s^2) of
+    // Eqs. A3-A4; dt (1 - 1/(2 tau)) of Eq. A1
+    T lw_dt, lw_a0, lw_a1, lw_am1, lw_kT, lw_fd, lw_bt, lw_g;
+    int32_t lw_first;  // 1: the stored populations are the pre-collision f(0) (step 0)
+    int32_t pad_;
 };
 
 
@@ -229,6 +236,45 @@ __device__ __forceinline__ void collide(T (&d)[kQ], T drho, T rho, T jx, T jy, T
     // rest population from the conserved density: equal to the M^-1 row
     // a0 - 4 (a1 - a2) in exact arithmetic, and in finite precision keeps
     // the stored density equal to the pulled one up to two rounded sums
+    d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
+}
+
+// BGK collision of the Lax-Wendroff scheme (Eq. A1) in population space, on
+// populations stored as deviations d_a = f_a - w_a rho_ref, with the
+// equilibrium of Eq. A3 (the second-order equilibrium plus
+// B dt (e_a e_a - c_s^2 I) : T / (2 c_s^2)) and the tensor of Eq. A4,
+//   T = [Pi - rho c_s^2 I - rho u u - (tau - 1/2) dt (u F + F u)] / (rho c_s^2 dt (B - tau)),
+// Pi = sum_a e_a e_a f_a taken here as its deviation from rho c_s^2 I. The
+// source is dt (1 - 1/(2 tau)) G_a with G of Eq. 14. The rest population
+// is closed from the conserved density, as in collide().
+template <typename T>
+__device__ __forceinline__ void collide_lw(T (&d)[kQ], T drho, T rho, T ux, T uy, T Fx, T Fy, const DevCase<T>& c)
+{
+    constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const T dg = (d[5] + d[7]) + (d[6] + d[8]);
+    const T Pxx = (d[1] + d[3]) + dg - drho * T(1.0 / 3.0);  // Pi_xx - rho c_s^2
+    const T Pyy = (d[2] + d[4]) + dg - drho * T(1.0 / 3.0);
+    const T Pxy = (d[5] + d[7]) - (d[6] + d[8]);
+    const T kT = c.lw_kT / rho;
+    const T Txx = (Pxx - rho * ux * ux - T(2) * c.lw_fd * ux * Fx) * kT;
+    const T Tyy = (Pyy - rho * uy * uy - T(2) * c.lw_fd * uy * Fy) * kT;
+    const T Txy = (Pxy - rho * ux * uy - c.lw_fd * (ux * Fy + Fx * uy)) * kT;
+    const T u2 = ux * ux + uy * uy;
+    const T lam = c.lam_v;
+    const T w[kQ] = {T(4.0 / 9.0), T(1.0 / 9.0), T(1.0 / 9.0), T(1.0 / 9.0), T(1.0 / 9.0),
+                     T(1.0 / 36.0), T(1.0 / 36.0), T(1.0 / 36.0), T(1.0 / 36.0)};
+#pragma unroll
+    for (int a = 1; a < kQ; ++a) {
+        const T eu = T(ex[a]) * ux + T(ey[a]) * uy;
+        const T eeT = (T(ex[a] * ex[a]) - T(1.0 / 3.0)) * Txx + T(2 * ex[a] * ey[a]) * Txy +
+                      (T(ey[a] * ey[a]) - T(1.0 / 3.0)) * Tyy;
+        // f_eq,a - w_a rho_ref
+        const T feq = w[a] * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * u2 + c.lw_bt * eeT));
+        const T G = w[a] * ((T(3) * (T(ex[a]) - ux) + T(9) * eu * T(ex[a])) * Fx +
+                            (T(3) * (T(ey[a]) - uy) + T(9) * eu * T(ey[a])) * Fy);
+        d[a] = d[a] - lam * (d[a] - feq) + c.lw_g * G;
+    }
     d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 

@@ -10,8 +10,8 @@ namespace {
 template <int S, int C, int E, bool NU, bool TMA, int NT>
 void* kernel_ptr()
 {
-    if constexpr (S == 3 && TMA)
-        return nullptr;  // scheme 3 runs on the plain-load kernel only
+    if constexpr ((S == 3 || S == 4) && TMA)
+        return nullptr;  // schemes 3 and 4 run on the plain-load kernel only
     else if constexpr (TMA && NT == kPairWide)
         return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads>);
     else if constexpr (TMA && NT == kPairNarrow)
@@ -32,6 +32,7 @@ void* pick(int scheme, int coll, int eos, bool nu)
     LBFE_PICK(1, 0, 0) LBFE_PICK(1, 0, 1) LBFE_PICK(1, 1, 0) LBFE_PICK(1, 1, 1)
     LBFE_PICK(2, 0, 0) LBFE_PICK(2, 0, 1) LBFE_PICK(2, 1, 0) LBFE_PICK(2, 1, 1)
     LBFE_PICK(3, 0, 0) LBFE_PICK(3, 0, 1) LBFE_PICK(3, 1, 0) LBFE_PICK(3, 1, 1)
+    LBFE_PICK(4, 0, 0) LBFE_PICK(4, 0, 1)  // Lax-Wendroff: BGK only
 #undef LBFE_PICK
     return nullptr;
 }

@@ -49,7 +49,7 @@ struct StepGeom {
     static constexpr int NC = 4;        // first iteration with stage C (improved schemes)
     static constexpr int ND = 2 * LAG;  // first iteration with stage D
     // rows of the phi u rings: scheme 3 reads rows ra - 6 .. ra - 2
-    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 6 : 4;
+    static constexpr int NPU = (SCHEME == 0 || SCHEME == 4) ? 1 : SCHEME == 3 ? 6 : 4;
 };
 
 template <typename T, int NT, int SCHEME>
@@ -174,6 +174,33 @@ struct PullGlobal {
     __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// Stage A of the Lax-Wendroff scheme (Eq. A2 in pull form): the population
+// a at node x is a_0 f*_a(x) + a_1 f*_a(x + e_a) + a_-1 f*_a(x - e_a) of
+// the stored post-collision values, over the same three rows and columns
+// as the plain pull; at step 0 (lw_first) the stored values are f(0)
+// itself and are taken as they are. Periodic lattices only.
+template <typename T, bool COHERENT>
+__device__ __forceinline__ void pull_lw(T* F, const T* __restrict__ fin, const DevCase<T>& c, const StepLane& L,
+                                        const StepRows& rows)
+{
+    constexpr int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    constexpr int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int ny = c.ny, pitch = c.pitch;
+    const uint32_t P = (uint32_t)c.plane;
+    const uint32_t r[3] = {(uint32_t)dec_wrap(rows.ra, ny) * pitch, (uint32_t)rows.ra * pitch,
+                           (uint32_t)inc_wrap(rows.ra, ny) * pitch};
+    const int xs[3] = {L.xm, L.xc, L.xp};
+    const T a0 = c.lw_first ? T(1) : c.lw_a0, a1 = c.lw_first ? T(0) : c.lw_a1, am1 = c.lw_first ? T(0) : c.lw_am1;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        const T* pa = fin + a * P;
+        const T f0 = ld_pop<COHERENT>(pa + r[1] + L.xc);
+        const T fp = ld_pop<COHERENT>(pa + r[1 + ey[a]] + xs[1 + ex[a]]);
+        const T fm = ld_pop<COHERENT>(pa + r[1 - ey[a]] + xs[1 - ex[a]]);
+        F[a] = a0 * f0 + a1 * fp + am1 * fm;
+    }
+}
+
 // Stage D of scheme 3 at row rd = ra - 4. The correction takes the Eq. 17
 // gradient of the lattice-weight average A' = sum_a w_a A(x + e_a) of
 // A = phi u_x (and of B = phi u_y). Both stencils factor into 1-D pieces
@@ -254,7 +281,10 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
     // ---------------------------------------------------------------- A
     if (L.a) {
         T* F = R.f[S0];
-        A_.pull(it, F, fin, c, L, rows);
+        if constexpr (SCHEME == 4)
+            pull_lw<T, COHERENT>(F, fin, c, L, rows);
+        else
+            A_.pull(it, F, fin, c, L, rows);
         const T dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
         R.drho[S0] = dr;
         R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
@@ -386,15 +416,20 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
                 Fy = R.gry * T(1.0 / 3.0) - rho * gmy;
             }
             const T inv = rcp_fast<T>(rho);
-            const T ux = (R.jx[S2] + T(0.5) * Fx) * inv;
-            const T uy = (R.jy[S2] + T(0.5) * Fy) * inv;
-            T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
-            if (NU) {
-                lv = shear_rate<SCHEME, NU, T>(c, rho, mu);
-                if (COLL == 0) le = ls = lq = lv;
+            const T half = SCHEME == 4 ? T(0.5) * c.lw_dt : T(0.5);  // Lax-Wendroff: time step dt = A
+            const T ux = (R.jx[S2] + half * Fx) * inv;
+            const T uy = (R.jy[S2] + half * Fy) * inv;
+            if constexpr (SCHEME == 4) {
+                collide_lw<T>(R.f[S2], drho, rho, ux, uy, Fx, Fy, c);
+            } else {
+                T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
+                if (NU) {
+                    lv = shear_rate<SCHEME, NU, T>(c, rho, mu);
+                    if (COLL == 0) le = ls = lq = lv;
+                }
+                collide<SCHEME, T>(R.f[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, T(0), T(0),
+                                   c.rho_ref, c.c0, le, ls, lq, lv);
             }
-            collide<SCHEME, T>(R.f[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, T(0), T(0),
-                               c.rho_ref, c.c0, le, ls, lq, lv);
             const uint32_t o = (uint32_t)rows.rd * pitch + L.xc;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) fout[a * P + o] = R.f[S2][a];

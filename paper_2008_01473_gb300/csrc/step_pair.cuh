@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
                                                                     int* __restrict__ status)
 {
     using G = StepGeom<SCHEME>;
-    static_assert(SCHEME != 3, "scheme 3 runs on the plain-load kernel only");
+    static_assert(SCHEME != 3 && SCHEME != 4, "schemes 3 and 4 run on the plain-load kernel only");
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
     __shared__ int flag, bad;

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
                                                            const Item* __restrict__ items,
                                                            int* __restrict__ status)
 {
-    static_assert(SCHEME != 3, "scheme 3 runs on the plain-load kernel only");
+    static_assert(SCHEME != 3 && SCHEME != 4, "schemes 3 and 4 run on the plain-load kernel only");
     using G = StepGeom<SCHEME>;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ StepSmem<T, NT, SCHEME> sm;

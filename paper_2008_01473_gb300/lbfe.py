@@ -17,6 +17,7 @@ from .build import LIB
 
 STANDARD, IMPROVED, STANDARD_PT = 0, 1, 2  # STANDARD_PT: Eq. 13 left (pressure-tensor force)
 IMPROVED_SMOOTH = 3  # improved scheme, Eq. 29 on the lattice-weight average of phi u
+LAX_WENDROFF = 4  # the comparison scheme of Appendix A (Eqs. A1-A4)
 BGK, MRT = 0, 1
 VDW, CS = 0, 1
 FP64, FP32 = 0, 1
@@ -45,7 +46,7 @@ class _CCase(C.Structure):
                 ("R", C.c_double), ("T", C.c_double), ("kappa", C.c_double), ("tau_v", C.c_double),
                 ("tau_e", C.c_double), ("tau_s", C.c_double), ("tau_q", C.c_double),
                 ("pm_c0", C.c_double), ("nu", C.c_double), ("rho_ref", C.c_double), ("wall_u", C.c_double),
-                ("rho_wall", C.c_double)]
+                ("rho_wall", C.c_double), ("lw_A", C.c_double), ("lw_B", C.c_double)]
 
 
 @dataclass
@@ -71,6 +72,8 @@ class Case:
     walls: int = 0          # 1: moving no-slip walls below y = 0 and above y = ny - 1
     wall_u: float = 0.0     # x velocity of both walls
     rho_wall: float = 0.0   # density of the wall state (> 0 with walls)
+    lw_A: float = 0.0       # LAX_WENDROFF: CFL number A, the time step (Appendix A)
+    lw_B: float = 0.0       # LAX_WENDROFF: B of Eq. A3 (nu = c_s^2 (tau - 1/2 - B) A)
 
     def cstruct(self) -> _CCase:
         kw = {f.name: getattr(self, f.name) for f in dc_fields(self)}

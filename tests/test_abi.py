@@ -44,8 +44,12 @@ def test_workspace_validation(lib):
     assert nb.value > n32 > 2 * 9 * 64 * 48 * 4
     c3 = lbfe.Case(**{**ok.__dict__, "scheme": lbfe.IMPROVED_SMOOTH})
     assert lib.lb_workspace_bytes((lbfe._CCase * 1)(c3.cstruct()), 1, lbfe.FP32, C.byref(nb)) == 0
+    lw = dict(scheme=lbfe.LAX_WENDROFF, collision=lbfe.BGK, lw_A=0.1, lw_B=-0.7)
+    c4 = lbfe.Case(**{**ok.__dict__, **lw})
+    assert lib.lb_workspace_bytes((lbfe._CCase * 1)(c4.cstruct()), 1, lbfe.FP64, C.byref(nb)) == 0
     for bad in (dict(nx=2), dict(tau_v=0.5), dict(kappa=0.0), dict(scheme=5), dict(T=float("nan")),
-                dict(nu=-1.0)):
+                dict(nu=-1.0), {**lw, "lw_A": 0.0}, {**lw, "lw_A": 1.5}, {**lw, "collision": lbfe.MRT},
+                {**lw, "lw_B": 0.5}, {**lw, "nu": 0.1}, {**lw, "walls": 1, "rho_wall": 1.0}):
         c = lbfe.Case(**{**ok.__dict__, **bad})
         arr = (lbfe._CCase * 1)(c.cstruct())
         assert lib.lb_workspace_bytes(arr, 1, lbfe.FP32, C.byref(nb)) == 1, bad
