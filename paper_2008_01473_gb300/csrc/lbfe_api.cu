@@ -20,7 +20,8 @@ using namespace lbfe;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMinRows = 8;  // smallest row segment of a work item
+constexpr int kMinRows = 8;     // smallest row segment of the slot-share rules
+constexpr int kMinSegRows = 2;  // smallest explicit row segment (latency-bound small lattices)
 // scratch fields: rho, j_x, j_y, mu (0-3), host staging of outputs / init
 // inputs (4-7), pressure tensor P_xx, P_xy, P_yy (8-10)
 constexpr int kScratchFields = 11;
@@ -47,7 +48,7 @@ constexpr int kMinBlockThreads = 128;  // narrowest block any path uses
 
 int64_t max_items_of(const lb_case& c)
 {
-    return (int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinRows - 1) / kMinRows);
+    return (int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinSegRows - 1) / kMinSegRows);
 }
 
 constexpr int kMaxNeighbours = 32;  // neighbour items per item that the persistent launch tracks
@@ -294,7 +295,7 @@ constexpr int kGraphSteps = 8;  // steps per captured graph (even: buffer parity
 // Split every case into column strips and row segments. seg_rows == 0: each
 // case gets a share of the resident block slots proportional to its node
 // count, so that one launch fills the GPU about once; seg_rows > 0: segments
-// of about seg_rows rows (at least kMinRows). Within a group the items run
+// of about seg_rows rows (at least kMinSegRows). Within a group the items run
 // longest first, so the block scheduler hands the short ones to the slots
 // that free up last. The decomposition changes no result: every node's
 // update is the same arithmetic on the same inputs whichever item owns it.
@@ -335,7 +336,8 @@ void build_items(lb_handle* h)
             int ns = strips_of(c, width);
             const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
             const double share = slots * ((double)c.nx * c.ny) / nodes;
-            const int max_seg = std::max(1, c.ny / kMinRows);
+            const int min_rows = seg_rows > 0 ? std::max(kMinSegRows, std::min(kMinRows, seg_rows)) : kMinRows;
+            const int max_seg = std::max(1, c.ny / min_rows);
             int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows : (int)std::floor(share / ns);
             if (seg_rows < 0) {
                 // slot share, filled: up to four more (narrower) strips when
@@ -688,7 +690,9 @@ static lb_status autotune(lb_handle* h)
 {
     // candidates: row-segment rule x (narrow packed blocks off, on); the
     // second half only when some lattice prefers narrow blocks
-    static const int segs[] = {0, -1, 256, 128, 64, 32, 16};
+    // (short segments serve lattices small enough that a step is bound by the
+    // latency of its row pipeline: fewer rows per item, more items at once)
+    static const int segs[] = {0, -1, 256, 128, 64, 32, 16, 8, 4, 2};
     constexpr int kSegs = (int)(sizeof segs / sizeof segs[0]);
     bool any_narrow = false;
     if (h->prec == LB_FP32 && h->path != 1 && h->tma_threads == 0 && !h->narrow_fixed)

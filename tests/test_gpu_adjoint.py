@@ -95,6 +95,13 @@ def test_autograd_function():
     assert abs(float(kappa.grad) - 3 * gk) < 1e-12 * abs(gk)
     assert abs(float(T.grad) - 3 * gT) < 1e-12 * abs(gT)
     np.testing.assert_allclose(r0.grad.cpu().numpy(), 3 * g, rtol=1e-12, atol=0)
+    # no input needs a gradient: the steps alone give the same loss (no reverse sweep)
+    with torch.no_grad():
+        Ln = LBLoss.apply(kappa, T, r0, gc, 30, 20, torch.tensor(sf, device="cuda"), 0)
+    assert abs(float(Ln) - Lr) < 1e-12 * abs(Lr)
+    Ld = LBLoss.apply(kappa.detach(), T.detach(), r0.detach(), gc, 30, 0, None, 0)
+    assert not Ld.requires_grad and abs(float(Ld) - lat.adjoint(0, rho0, 30, 0, None)[0]) < 1e-12 * float(Ld)
+    lat.close()
 
 
 @pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED])
