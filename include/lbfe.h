@@ -67,8 +67,10 @@ typedef enum {
  * relaxation times); the averaged form damps the grid-scale modes that drive
  * that instability and keeps 0.7 T_c stable for tau_v >= 0.8, or with MRT at
  * the constant kinematic viscosity 0.04 of Table II. Same steady states as
- * LB_IMPROVED (C vanishes at u = 0). Runs on the one-column plain-load step
- * kernel; no lb_adjoint_step. */
+ * LB_IMPROVED (C vanishes at u = 0). FP32 cases with nx % 4 == 0 and
+ * nx >= 8 run on the packed kernel (its stage D pulls the row's populations
+ * a second time from L2), the others on the one-column plain-load kernel;
+ * no lb_adjoint_step. */
 /* LB_LAX_WENDROFF: the comparison scheme of Appendix A (Lou and Guo's
  * Lax-Wendroff propagation): the standard force (Eq. 13 right), velocity
  * u = (sum_a e_a f_a + A F / 2) / rho, the BGK collision of Eq. A1 (rate
@@ -163,8 +165,9 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
  * share scheme, collision, EOS, viscosity mode and nx % 4 == 0; each launch
  * runs a work-list of (case, column strip, row segment) items. FP32 cases
  * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
- * FP64 cases, other widths, walled cases and LB_IMPROVED_SMOOTH cases run
- * the one-column plain-load kernel. The first
+ * FP64 cases, other widths, walled cases, Lax-Wendroff cases and
+ * LB_IMPROVED_SMOOTH cases narrower than 8 run the one-column plain-load
+ * kernel. The first
  * call with nsteps > 0 autotunes the work-list: it times one step under
  * several row-segment sizes, with and without narrow blocks for the lattices
  * that fit them better, and keeps the fastest (these trial launches read

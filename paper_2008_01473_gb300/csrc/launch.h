@@ -24,6 +24,14 @@ cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks,
                             const double* fin, double* fout, const DevCase<double>* cases,
                             const Item* items, int* status);
 int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt);
+// the packed FP32 kernel of scheme S for a collision / EOS / viscosity mode,
+// wide or narrow shape (instantiated per scheme in step_f32_pair<S>.cu)
+template <int S>
+void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow);
+extern template void* pick_pair_scheme<0>(int, int, bool, bool);
+extern template void* pick_pair_scheme<1>(int, int, bool, bool);
+extern template void* pick_pair_scheme<2>(int, int, bool, bool);
+extern template void* pick_pair_scheme<3>(int, int, bool, bool);
 int occupancy_step_f64(int scheme, int coll, int eos, bool nu);
 
 // Arguments of the persistent multi-step kernel (step_persist.cuh).

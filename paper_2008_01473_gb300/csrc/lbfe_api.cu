@@ -31,16 +31,22 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
-// schemes that only the one-column plain-load kernel runs
+// cases that only the one-column plain-load kernel runs: walls, the
+// Lax-Wendroff scheme, and the averaged correction on lattices narrower than
+// its 8-column ring margin
 bool one_column_only(const lb_case& c)
 {
-    return c.walls || c.scheme == LB_IMPROVED_SMOOTH || c.scheme == LB_LAX_WENDROFF;
+    return c.walls || c.scheme == LB_LAX_WENDROFF || (c.scheme == LB_IMPROVED_SMOOTH && c.nx < 8);
 }
 
 // Widest strip of output columns a block of nt threads can own. Lattices with
 // nx % 4 == 0 get strips of a multiple of 4 columns, at most nt - 8 wide, as
 // the TMA-staged kernel needs (16-byte aligned runs of [x0 - 4, x0 + wv + 4)).
-int strip_width(const lb_case& c, int nt) { return c.nx % 4 == 0 ? nt - 8 : nt - 2 * halo_of(c.scheme); }
+int strip_width(const lb_case& c, int nt)
+{
+    if (c.nx % 4 != 0) return nt - 2 * halo_of(c.scheme);
+    return nt - (c.scheme == LB_IMPROVED_SMOOTH ? 16 : 8);  // the packed kernel's ring margins (4 or 8)
+}
 
 int strips_of(const lb_case& c, int nt) { return (c.nx + strip_width(c, nt) - 1) / strip_width(c, nt); }
 
@@ -379,7 +385,9 @@ void build_items(lb_handle* h)
                         // al: lattices with nx % 4 == 0 (TMA-eligible), without, and
                         // lattices with walls (the plain-load kernel pulls across them) or
                         // with scheme 3 (whose wider stencil only that kernel has)
-                        const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1;
+                        // (the one-column TMA shapes of LBFE_STEP_THREADS do not run scheme 3)
+                        const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1 &&
+                                         !(s == LB_IMPROVED_SMOOTH && h->tma_threads != 0);
                         const bool pair = tma && h->tma_threads == 0;
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {

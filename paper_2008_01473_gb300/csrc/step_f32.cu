@@ -1,21 +1,31 @@
-// Instantiations of the fused step kernels with FP32 populations and arithmetic.
+// Instantiations of the one-column FP32 step kernels (plain loads and the TMA
+// variant) and the FP32 launch; the packed kernels are instantiated per
+// scheme in the step_f32_pair<S>.cu units (compiled in parallel).
 #include "launch.h"
 #include "step_pair.cuh"
 
 namespace lbfe {
 
 namespace {
+// the packed kernel (nullptr for the Lax-Wendroff scheme, which it does not run)
+void* pick_pair(int scheme, int coll, int eos, bool nu, bool narrow)
+{
+    switch (scheme) {
+    case 0: return pick_pair_scheme<0>(coll, eos, nu, narrow);
+    case 1: return pick_pair_scheme<1>(coll, eos, nu, narrow);
+    case 2: return pick_pair_scheme<2>(coll, eos, nu, narrow);
+    case 3: return pick_pair_scheme<3>(coll, eos, nu, narrow);
+    default: return nullptr;
+    }
+}
+
 // NT = kPairWide / kPairNarrow select the two-columns-per-thread packed
-// kernel with 128 / 64 threads
+// kernel with 128 / 64 threads (pick_pair, step_f32_pair.cu)
 template <int S, int C, int E, bool NU, bool TMA, int NT>
 void* kernel_ptr()
 {
     if constexpr ((S == 3 || S == 4) && TMA)
-        return nullptr;  // schemes 3 and 4 run on the plain-load kernel only
-    else if constexpr (TMA && NT == kPairWide)
-        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads>);
-    else if constexpr (TMA && NT == kPairNarrow)
-        return reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow>);
+        return nullptr;  // the one-column TMA kernel runs neither scheme 3 nor the Lax-Wendroff scheme
     else if constexpr (TMA)
         return reinterpret_cast<void*>(&step_kernel_tma<float, NT, S, C, E, NU>);
     else
@@ -53,8 +63,8 @@ int block_threads(bool tma, int nt)
 void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 {
     void* k = !tma           ? pick<false, kStepThreads>(scheme, coll, eos, nu)
-              : nt == kPairWide   ? pick<true, kPairWide>(scheme, coll, eos, nu)
-              : nt == kPairNarrow ? pick<true, kPairNarrow>(scheme, coll, eos, nu)
+              : nt == kPairWide   ? pick_pair(scheme, coll, eos, nu, false)
+              : nt == kPairNarrow ? pick_pair(scheme, coll, eos, nu, true)
               : nt == 128    ? pick<true, 128>(scheme, coll, eos, nu)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;

@@ -35,6 +35,15 @@
 //   D: pairs 2 .. (wv + 4)/2 - 1   -> columns [4, wv + 4) = the strip
 // The improved scheme needs rho on [1, wv + 7), mu_c on [2, wv + 6) and phi u
 // on [3, wv + 5); the standard one rho on [2, wv + 6) and mu_c on [3, wv + 5).
+//
+// Scheme 3 (Eq. 29's derivatives of the lattice-weight average of phi u, a
+// 5 x 5 stencil) reaches one column and one row further: the ring spans
+// [x0 - 8, x0 + wv + 8) (a margin of 8 keeps the copies 16-byte aligned), phi u
+// is needed on [6, wv + 10), mu_c on [5, wv + 11), rho on [3, wv + 13); stage
+// D runs four rows behind stage A, on a six-row phi u ring, and pulls its
+// row's populations again from global memory (L2: stage A's bulk copies
+// brought those rows in four iterations earlier) instead of holding five rows
+// of them in registers, as the one-column kernel does for this scheme.
 #pragma once
 
 #include "step_tma.cuh"
@@ -140,7 +149,7 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     const float2 uxx = ux * ux, uyy = uy * uy;
     const float2 ru2 = rho * (uxx + uyy);
     float2 eq_e, eq_s, eq_qx, eq_qy;
-    if (SCHEME != 1) {  // standard equilibrium (Eq. 11), either force form
+    if (!improved_scheme(SCHEME)) {  // standard equilibrium (Eq. 11), either force form
         eq_e = fma2(v2(3.0f), ru2, v2(-2.0f) * drho);
         eq_s = fma2(v2(-3.0f), ru2, drho);
         eq_qx = v2(0.0f) - rho * ux;
@@ -202,20 +211,30 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 
+// Ring columns on each side of a strip (a multiple of 4, for 16-byte aligned
+// bulk copies): the stencil chain's column halo plus one for the pull.
+template <int SCHEME>
+struct PairGeom {
+    static constexpr int M = SCHEME == 3 ? 8 : 4;
+    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 6 : 4;  // rows of the phi u rings
+};
+
 template <int SCHEME, int COLS>
 struct PairSmem {
     float rho[4][COLS];
     float mu[4][COLS];
-    float pux[SCHEME == 0 ? 1 : 4][COLS];  // phi u_x (improved) or P_xy (pressure tensor)
-    float puy[SCHEME == 0 ? 1 : 4][COLS];  // phi u_y (improved) or P_yy (pressure tensor)
+    float pux[PairGeom<SCHEME>::NPU][COLS];  // phi u_x (improved) or P_xy (pressure tensor)
+    float puy[PairGeom<SCHEME>::NPU][COLS];  // phi u_y (improved) or P_yy (pressure tensor)
 };
 
+template <int SCHEME>
 struct PairRegs {
-    float2 f[4][kQ];  // pulled populations (deviation form) of the pair
+    float2 f[SCHEME == 3 ? 1 : 4][kQ];  // pulled populations of the pair (scheme 3 pulls again in D)
     float2 drho[4], jx[4], jy[4];
     float2 mu[4];
-    float2 ux[2], uy[2], Fx[2], Fy[2];  // stage C results of two rows (improved)
-    float2 grx, gry;                    // stage B grad rho (standard)
+    float2 ux[SCHEME == 3 ? 4 : 2], uy[SCHEME == 3 ? 4 : 2];  // stage C results (improved)
+    float2 Fx[SCHEME == 3 ? 4 : 2], Fy[SCHEME == 3 ? 4 : 2];
+    float2 grx, gry;  // stage B grad rho (standard)
 };
 
 struct PairCtx {
@@ -233,7 +252,42 @@ struct PairCtx {
     int rd;             // lattice row of stage D
     float* out;         // fout + column of the pair's first node (stage D pairs)
     int* bad;           // shared: a stage D node had rho <= 0 or a non-finite density
+    int xc, xm1, xp2;   // scheme 3: lattice columns x (even), x - 1 and x + 2 of the pair
 };
+
+// Populations of the pair at lattice row r pulled from global memory (the
+// pull of Eq. 10): two columns per plane from one 64-bit load at the pair's
+// own columns and, for the planes that shift in x, one scalar load of the
+// column beyond it. Periodic lattices.
+__device__ __forceinline__ void pull_pair(float2 (&F)[kQ], const PairCtx& X, const DevCase<float>& c, int r)
+{
+    const int ny = c.ny;
+    const uint32_t P = (uint32_t)c.plane;
+    const uint32_t r0 = (uint32_t)r * c.pitch;
+    const uint32_t rm = (uint32_t)(r == 0 ? ny - 1 : r - 1) * c.pitch;
+    const uint32_t rp = (uint32_t)(r + 1 == ny ? 0 : r + 1) * c.pitch;
+    const float* f = X.fin;
+    auto pair_at = [&](uint32_t a, uint32_t row) {
+        return __ldg(reinterpret_cast<const float2*>(f + a * P + row + (uint32_t)X.xc));
+    };
+    auto one_at = [&](uint32_t a, uint32_t row, int x) { return __ldg(f + a * P + row + (uint32_t)x); };
+    F[0] = pair_at(0, r0);
+    F[2] = pair_at(2, rm);
+    F[4] = pair_at(4, rp);
+    float2 t;
+    t = pair_at(1, r0);
+    F[1] = make_float2(one_at(1, r0, X.xm1), t.x);
+    t = pair_at(5, rm);
+    F[5] = make_float2(one_at(5, rm, X.xm1), t.x);
+    t = pair_at(8, rp);
+    F[8] = make_float2(one_at(8, rp, X.xm1), t.x);
+    t = pair_at(3, r0);
+    F[3] = make_float2(t.y, one_at(3, r0, X.xp2));
+    t = pair_at(6, rm);
+    F[6] = make_float2(t.y, one_at(6, rm, X.xp2));
+    t = pair_at(7, rp);
+    F[7] = make_float2(t.y, one_at(7, rp, X.xp2));
+}
 
 // rho > 0 and finite for both nodes of a pair (NaN fails both comparisons)
 __device__ __forceinline__ bool pair_ok(float2 rho)
@@ -278,7 +332,7 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, const DevCase<float
 
 template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT>
 __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME, 2 * NP>& sm,
-                                          PairRegs& R)
+                                          PairRegs<SCHEME>& R)
 {
     using G = StepGeom<SCHEME>;
     constexpr int S0 = SLOT, S1 = (SLOT + 3) & 3, S2 = (SLOT + 2) & 3, S3 = (SLOT + 1) & 3;
@@ -302,7 +356,8 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         // of the block read a clamped pair and produce unused values
         const int jl = j >= 2 ? j - 2 : 0;
         const int jr = j + 2 <= SW - 2 ? j + 2 : SW - 2;
-        float2* F = R.f[S0];
+        float2 Floc[kQ];
+        float2* F = SCHEME == 3 ? Floc : R.f[S0];  // scheme 3 keeps only the sums
         F[0] = ld2(R0 + 0 * SW + j);
         F[1] = make_float2(ld2(R0 + 1 * SW + jl).y, ld2(R0 + 1 * SW + j).x);
         F[2] = ld2(Rm + 2 * SW + j);
@@ -341,7 +396,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             R.mu[S1] = mu;
             st2(sm.mu[S1] + j, mu);
         }
-        if constexpr (SCHEME != 1) {
+        if constexpr (!improved_scheme(SCHEME)) {
             if (it >= G::ND) {  // grad rho of row ra - 2 from rows ra - 3 .. ra - 1
                 const Row2 Qm = row2(sm.rho[S3], j, rr + R.drho[S3]);
                 R.grx = gx2(Qm, Sm, Sc);
@@ -351,10 +406,15 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
     __syncthreads();
 
-    if constexpr (SCHEME == 1) {
+    if constexpr (improved_scheme(SCHEME)) {
         // ------------------------------------------------------------ C
-        constexpr int U2 = SLOT & 1;
-        if (X.b && it >= G::NC) {
+        // results of row ra - 2: u, F in registers (two rows deep; four for
+        // scheme 3, whose stage D is two rows further behind) and phi u in
+        // the shared rows (a ring of six rows for scheme 3)
+        constexpr int U2 = SCHEME == 3 ? SLOT : (SLOT & 1);
+        float* const pux_w = SCHEME == 3 ? sm.pux[(it + 4) % 6] : sm.pux[S2];
+        float* const puy_w = SCHEME == 3 ? sm.puy[(it + 4) % 6] : sm.puy[S2];
+        if (X.c && it >= G::NC) {
             const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
             const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
             const Row2 Mp = row2(sm.mu[S1], j, R.mu[S1]);
@@ -366,14 +426,61 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             const float2 ux = fma2(v2(0.5f), Fx, R.jx[S2]) * inv;
             const float2 uy = fma2(v2(0.5f), Fy, R.jy[S2]) * inv;
             const float2 phi = (rho - (v2(c.c0) + Mc.c)) * v2(1.0f / 3.0f);
-            st2(sm.pux[S2] + j, phi * ux);
-            st2(sm.puy[S2] + j, phi * uy);
+            st2(pux_w + j, phi * ux);
+            st2(puy_w + j, phi * uy);
             R.ux[U2] = ux;
             R.uy[U2] = uy;
             R.Fx[U2] = Fx;
             R.Fy[U2] = Fy;
         }
         __syncthreads();
+        if constexpr (SCHEME == 3) {
+            // -------------------------------------------------------- D (3)
+            // row rd = ra - 4. C1 = d_x A' + d_y B', C7 = d_x A' - d_y B' with
+            // A' = sum_a w_a (phi u_x)(x + e_a), B' likewise: the Eq. 17
+            // gradient of the averages factors into
+            //   d_x A' = sum_dy s(dy) [(A(x+1) - A(x-1))/3 + (A(x+2) - A(x-2))/12](y + dy)
+            // with s = (1, 8, 18, 8, 1)/36 over dy = -2 .. 2, and d_y B' with
+            // the roles of x and y exchanged.
+            if (X.d && it >= G::ND) {
+                const float2 g1 = v2(1.0f / 3.0f), g2 = v2(1.0f / 12.0f);
+                const float2 s0 = v2(1.0f / 36.0f), s1 = v2(8.0f / 36.0f), s2 = v2(18.0f / 36.0f);
+                float2 hx[5], sb[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int slot = (it + k) % 6;  // phi u of row ra - 6 + k
+                    const float* a = sm.pux[slot] + j;
+                    const float2 aL = ld2(a - 2), aO = ld2(a), aR = ld2(a + 2);
+                    hx[k] = fma2(g1, make_float2(aO.y, aR.x) - make_float2(aL.y, aO.x), g2 * (aR - aL));
+                    const float* b = sm.puy[slot] + j;
+                    const float2 bL = ld2(b - 2), bO = ld2(b), bR = ld2(b + 2);
+                    sb[k] = fma2(s0, bL + bR, fma2(s1, make_float2(bL.y, bO.x) + make_float2(bO.y, bR.x), s2 * bO));
+                }
+                const float2 Ax = fma2(s0, hx[0] + hx[4], fma2(s1, hx[1] + hx[3], s2 * hx[2]));
+                const float2 By = fma2(g1, sb[3] - sb[1], g2 * (sb[4] - sb[0]));
+                const float2 C1 = Ax + By, C7 = Ax - By;
+                float2 F[kQ];
+                pull_pair(F, X, c, X.rd);
+                const float2 drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+                const float2 jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+                const float2 jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+                const float2 rho = v2(c.rho_ref) + drho;
+                if (!pair_ok(rho)) *X.bad = 1;
+                const float2 mu = R.mu[S0];  // row ra - 4
+                float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
+                if (NU) {
+                    lv = make_float2(shear_rate<SCHEME, NU, float>(c, rho.x, mu.x),
+                                     shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
+                    if (COLL == 0) le = ls = lq = lv;
+                }
+                collide2<SCHEME>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c, le,
+                                 ls, lq, lv);
+                float* o = X.out + (uint32_t)X.rd * c.pitch;
+                const uint32_t P = (uint32_t)c.plane;
+#pragma unroll
+                for (int a = 0; a < kQ; ++a) st2(o + a * P, F[a]);
+            }
+        } else {
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
         if (X.d && it >= G::ND) {
@@ -400,6 +507,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S3][a]);
+        }
         }
     } else {
         // ------------------------------------------------------- D (standard)
@@ -465,8 +573,10 @@ constexpr size_t pair_dynamic_smem()
 }
 
 // FP32 step with NP threads of two columns each: blockDim.x == NP (128 or
-// 64). Every case of the launch has nx % 4 == 0; every item x0 % 4 == 0,
-// wv % 4 == 0, wv + 8 <= 2 NP.
+// 64). Every case of the launch has nx % 4 == 0 (and nx >= 8 for scheme 3,
+// so that each margin of the ring is one copy run); every item x0 % 4 == 0,
+// wv % 4 == 0, wv + 2 M <= 2 NP with M = PairGeom<SCHEME>::M (4, or 8 for
+// scheme 3).
 template <int SCHEME, int COLL, int EOS, bool NU, int NP>
 __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pair(const float* __restrict__ fin,
                                                                     float* __restrict__ fout,
@@ -475,7 +585,8 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
                                                                     int* __restrict__ status)
 {
     using G = StepGeom<SCHEME>;
-    static_assert(SCHEME != 3 && SCHEME != 4, "schemes 3 and 4 run on the plain-load kernel only");
+    static_assert(SCHEME != 4, "scheme 4 runs on the plain-load kernel only");
+    constexpr int M = PairGeom<SCHEME>::M;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
     __shared__ int flag, bad;
@@ -498,7 +609,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     X.s_last = X.s0 + niter + 1;
     {
         // runs of [x0 - 4, x0 + wv + 4) split at the periodic edges
-        const int start = item.x0 - 4, end = item.x0 + item.wv + 4;
+        const int start = item.x0 - M, end = item.x0 + item.wv + M;
         X.runs.n = 0;
         int x = start, jj = 0;
 #pragma unroll
@@ -526,15 +637,24 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
 
     const int p = threadIdx.x;
     X.j = 2 * p;
-    X.b = p >= 1 && 2 * p < item.wv + 6;
-    X.d = p >= 2 && 2 * p < item.wv + 4;
-    X.c = X.b;
+    if constexpr (SCHEME == 3) {  // ring columns: mu [4, wv + 12), phi u [6, wv + 10), strip [8, wv + 8)
+        X.b = p >= 2 && 2 * p < item.wv + 12;
+        X.c = p >= 3 && 2 * p < item.wv + 10;
+        X.d = p >= 4 && 2 * p < item.wv + 8;
+    } else {
+        X.b = p >= 1 && 2 * p < item.wv + 6;
+        X.d = p >= 2 && 2 * p < item.wv + 4;
+        X.c = X.b;
+    }
     X.ks = 0;
     X.rd = item.y0;
-    X.out = fout + (X.d ? item.x0 - 4 + 2 * p : 0);
+    X.out = fout + (X.d ? item.x0 - M + 2 * p : 0);
+    X.xc = X.d ? item.x0 - M + 2 * p : 0;
+    X.xm1 = X.xc == 0 ? c.nx - 1 : X.xc - 1;
+    X.xp2 = X.xc + 2 >= c.nx ? X.xc + 2 - c.nx : X.xc + 2;
     X.bad = &bad;
 
-    PairRegs R;
+    PairRegs<SCHEME> R;
     for (int base = 0; base < niter; base += 4) {
         pair_iter<SCHEME, COLL, EOS, NU, NP, 0>(base, X, c, sm, R);
         if (base + 1 >= niter) break;

@@ -280,20 +280,22 @@ def test_fp32_droplet_500_steps(scheme):
     assert max(np.abs(m["ux"] - ref.ux).max(), np.abs(m["uy"] - ref.uy).max()) < 2e-6
 
 
-@pytest.mark.parametrize("precision", [lbfe.FP32, lbfe.FP64])
-def test_full_size_sampled_nodes(precision):
+@pytest.mark.parametrize("precision,scheme", [(lbfe.FP32, lbfe.IMPROVED), (lbfe.FP64, lbfe.IMPROVED),
+                                              (lbfe.FP32, lbfe.IMPROVED_SMOOTH)])
+def test_full_size_sampled_nodes(precision, scheme):
     """The 4096 x 4096 spinodal lattice in the benchmark's launch
     configuration (improved, MRT; FP32 as the default line, FP64 as the
-    --precision fp64 line, each with its autotuned work-list): for 24 sampled
-    nodes the oracle's one-step update of a 13 x 13 patch around the node
-    (whose centre depends on nodes within 4 sites) matches the GPU's
-    post-step populations (FP32: 3e-6 of max |f|; FP64: 1e-13)."""
+    --precision fp64 line, each with its autotuned work-list; and the
+    averaged correction on the packed FP32 kernel): for 24 sampled nodes the
+    oracle's one-step update of a 13 x 13 patch around the node (whose centre
+    depends on nodes within 4 sites, 5 for the averaged correction) matches
+    the GPU's post-step populations (FP32: 3e-6 of max |f|; FP64: 1e-13)."""
     e = thermo.vdw_paper()
     T, rg, rl = thermo.maxwell_reduced(e, 0.8)
     n = 4096
-    gc = lbfe.Case(nx=n, ny=n, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
+    gc = lbfe.Case(nx=n, ny=n, scheme=scheme, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, T=T,
                    kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
-    oc = O.Case(nx=13, ny=13, scheme=O.IMPROVED, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02,
+    oc = O.Case(nx=13, ny=13, scheme=scheme, collision=O.MRT, eos=O.VDW, a=e.a, b=e.b, T=T, kappa=0.02,
                 tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1)
     tol = 3e-6 if precision == lbfe.FP32 else 1e-13
     lat = lbfe.Lattice([gc], precision=precision)
@@ -314,7 +316,7 @@ def test_full_size_sampled_nodes(precision):
         assert np.abs(got - patch[:, 6, 6]).max() < tol * np.abs(patch[:, 6, 6]).max(), (y, x)
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 @pytest.mark.parametrize("shape", [(4, 5), (8, 9), (12, 7), (532, 37), (496, 300), (1000, 16), (2048, 64)])
 def test_fp32_kernel_shapes_agree(scheme, shape, monkeypatch):
     """The one-column TMA-staged kernels (bulk copies of row runs into a
@@ -540,7 +542,7 @@ def test_fp32_batched_workload_full_size_sampled():
             assert np.abs(after[i][:, y, x] - ref).max() < 3e-6 * np.abs(ref).max(), (i, y, x)
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 def test_narrow_packed_blocks_bit_identical(scheme, monkeypatch):
     """Narrow packed blocks (64 threads, 128 columns, copies issued by two
     warps) for the lattices they fit better, running as a parallel branch of
