@@ -20,7 +20,15 @@
 // it, row it is dead, and at the end of the iteration (after stage D's
 // stores, off the path of the three barrier intervals) lanes of warps 0..2
 // refill its slot with row it + kPairSlots (one lane per plane and run), so no
-// producer warp is needed and three blocks fit on an SM.
+// producer warp is needed and three blocks fit on an SM. The slots, their
+// mbarriers and phases, the refill row and the output row advance by one per
+// iteration through wrapping pointer and offset updates: no row modulo or
+// multiply sits on the iteration's path.
+//
+// Stage A reduces the pulled populations at once to the conserved sums and
+// the six non-conserved moments of Eq. 9; the register rows carry those
+// (12 registers per row instead of 18) until stage D relaxes them and
+// transforms back.
 //
 // Two block shapes share the code: NP = 128 threads (256 ring columns,
 // strips of up to 248 outputs; copies issued by warps 0-2, three planes
@@ -61,19 +69,29 @@ __host__ __device__ constexpr int pair_issuers(int np) { return np == kPairThrea
 // ------------------------------------------------------------ packed FP32
 __device__ __forceinline__ float2 v2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __ffma2_rn(b, v2(-1.0f), a); }
+// packed subtraction (sub.rn.f32x2; an FFMA2 with a (-1, -1) operand would
+// need a register pair holding the constant)
+__device__ __forceinline__ float2 operator-(float2 a, float2 b)
+{
+    unsigned long long r;
+    const unsigned long long x = *reinterpret_cast<const unsigned long long*>(&a);
+    const unsigned long long y = *reinterpret_cast<const unsigned long long*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    return *reinterpret_cast<const float2*>(&r);
+}
 __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
 
 // Row of a field around the pair: own (x = col j, y = col j + 1) plus the
-// neighbours at j - 1 (l) and j + 2 (r).
+// neighbours at j - 1 (l) and j + 2 (r). The stencils below combine the
+// shifted neighbours with scalar adds that write each half of a pair
+// directly (a packed operation on the shifted pair (c.y, r) would first
+// have to assemble it in an aligned register pair), then go on packed.
 struct Row2 {
     float2 c;
     float l, r;
-    __device__ __forceinline__ float2 E() const { return make_float2(c.y, r); }
-    __device__ __forceinline__ float2 W() const { return make_float2(l, c.x); }
 };
 
 // neighbours through aligned 64-bit loads (a stride-2 scalar pattern would
@@ -90,19 +108,27 @@ __device__ __forceinline__ Row2 row2(const float* row, int j, float2 own)
 // 6 sum_a w_a (phi(x + e_a) - phi(x)) with rows S (y-1), C (y), N (y+1)
 __device__ __forceinline__ float2 lap2(const Row2& S, const Row2& C, const Row2& N)
 {
-    const float2 edges = (C.E() + C.W()) + (N.c + S.c);
-    const float2 corners = (N.E() + S.W()) + (N.W() + S.E());
+    const float2 ew = make_float2(C.c.y + C.l, C.r + C.c.x);      // E + W
+    const float2 nesw = make_float2(N.c.y + S.l, N.r + S.c.x);    // NE + SW
+    const float2 nwse = make_float2(N.l + S.c.y, N.c.x + S.r);    // NW + SE
+    const float2 edges = ew + (N.c + S.c);
+    const float2 corners = nesw + nwse;
     return fma2(edges, v2(4.0f / 6.0f), fma2(corners, v2(1.0f / 6.0f), C.c * v2(-20.0f / 6.0f)));
 }
 
 // Eq. 17 components
 __device__ __forceinline__ float2 gx2(const Row2& S, const Row2& C, const Row2& N)
 {
-    return fma2(C.E() - C.W(), v2(1.0f / 3.0f), ((N.E() - S.W()) + (S.E() - N.W())) * v2(1.0f / 12.0f));
+    const float2 d = make_float2(C.c.y - C.l, C.r - C.c.x);       // E - W
+    const float2 a = make_float2(N.c.y - S.l, N.r - S.c.x);       // NE - SW
+    const float2 b = make_float2(S.c.y - N.l, S.r - N.c.x);       // SE - NW
+    return fma2(d, v2(1.0f / 3.0f), (a + b) * v2(1.0f / 12.0f));
 }
 __device__ __forceinline__ float2 gy2(const Row2& S, const Row2& N)
 {
-    return fma2(N.c - S.c, v2(1.0f / 3.0f), ((N.E() - S.W()) + (N.W() - S.E())) * v2(1.0f / 12.0f));
+    const float2 a = make_float2(N.c.y - S.l, N.r - S.c.x);       // NE - SW
+    const float2 b = make_float2(N.l - S.c.y, N.c.x - S.r);       // NW - SE
+    return fma2(N.c - S.c, v2(1.0f / 3.0f), (a + b) * v2(1.0f / 12.0f));
 }
 
 template <int EOS>
@@ -126,25 +152,36 @@ __device__ __forceinline__ float2 dEf2(const DevCase<float>& c, float2 rho)
     return out;
 }
 
-// Moment-space collision (Eqs. 9 / 28) on deviation populations, packed.
-// Same algebra as collide() in lbfe_device.cuh.
-template <int SCHEME>
-__device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rho, float2 jx, float2 jy,
-                                         float2 ux, float2 uy, float2 Fx, float2 Fy, float2 mu, float2 C1,
-                                         float2 C7, const DevCase<float>& c, float2 le, float2 ls, float2 lq,
-                                         float2 lv)
+// The six non-conserved moments (e, eps, q_x, q_y, p_xx, p_xy of the
+// Lallemand-Luo basis, Eq. 9) of the pair's deviation populations. Stage A
+// takes them right after the pull and the register rows carry these six
+// instead of the nine populations until stage D collides.
+__device__ __forceinline__ void moments2(const float2 (&d)[kQ], float2 (&m)[6])
 {
     const float2 sa = (d[1] + d[3]) + (d[2] + d[4]);
     const float2 sd = (d[5] + d[7]) + (d[6] + d[8]);
-    const float2 m_e = fma2(v2(2.0f), sd, fma2(v2(-4.0f), d[0], v2(0.0f) - sa));
-    const float2 m_s = fma2(v2(-2.0f), sa, fma2(v2(4.0f), d[0], sd));
+    m[0] = fma2(v2(2.0f), sd, fma2(v2(-4.0f), d[0], v2(0.0f) - sa));
+    m[1] = fma2(v2(-2.0f), sa, fma2(v2(4.0f), d[0], sd));
     const float2 d57 = d[5] - d[7];
     const float2 dxd = d57 + (d[8] - d[6]);
     const float2 dyd = d57 + (d[6] - d[8]);
-    const float2 m_qx = fma2(v2(-2.0f), d[1] - d[3], dxd);
-    const float2 m_qy = fma2(v2(-2.0f), d[2] - d[4], dyd);
-    const float2 m_pxx = (d[1] + d[3]) - (d[2] + d[4]);
-    const float2 m_pxy = (d[5] + d[7]) - (d[6] + d[8]);
+    m[2] = fma2(v2(-2.0f), d[1] - d[3], dxd);
+    m[3] = fma2(v2(-2.0f), d[2] - d[4], dyd);
+    m[4] = (d[1] + d[3]) - (d[2] + d[4]);
+    m[5] = (d[5] + d[7]) - (d[6] + d[8]);
+}
+
+// Moment-space collision (Eqs. 9 / 28) on deviation populations, packed:
+// post-collision deviation populations d from the conserved (drho, jx, jy)
+// and the non-conserved moments m. Same algebra as collide() in
+// lbfe_device.cuh.
+template <int SCHEME>
+__device__ __forceinline__ void collide2m(float2 (&d)[kQ], const float2 (&m)[6], float2 drho, float2 rho,
+                                          float2 jx, float2 jy, float2 ux, float2 uy, float2 Fx, float2 Fy,
+                                          float2 mu, float2 C1, float2 C7, const DevCase<float>& c, float2 le,
+                                          float2 ls, float2 lq, float2 lv)
+{
+    const float2 m_e = m[0], m_s = m[1], m_qx = m[2], m_qy = m[3], m_pxx = m[4], m_pxy = m[5];
 
     const float2 uxx = ux * ux, uyy = uy * uy;
     const float2 ru2 = rho * (uxx + uyy);
@@ -211,6 +248,18 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
     d[0] = drho - (((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8])));
 }
 
+// the same collision from the populations (in place)
+template <int SCHEME>
+__device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rho, float2 jx, float2 jy,
+                                         float2 ux, float2 uy, float2 Fx, float2 Fy, float2 mu, float2 C1,
+                                         float2 C7, const DevCase<float>& c, float2 le, float2 ls, float2 lq,
+                                         float2 lv)
+{
+    float2 m[6];
+    moments2(d, m);
+    collide2m<SCHEME>(d, m, drho, rho, jx, jy, ux, uy, Fx, Fy, mu, C1, C7, c, le, ls, lq, lv);
+}
+
 // Ring columns on each side of a strip (a multiple of 4, for 16-byte aligned
 // bulk copies): the stencil chain's column halo plus one for the pull.
 template <int SCHEME>
@@ -229,7 +278,7 @@ struct PairSmem {
 
 template <int SCHEME>
 struct PairRegs {
-    float2 f[SCHEME == 3 ? 1 : 4][kQ];  // pulled populations of the pair (scheme 3 pulls again in D)
+    float2 m[SCHEME == 3 ? 1 : 4][6];  // non-conserved moments of the pulled pair (scheme 3 pulls again in D)
     float2 drho[4], jx[4], jy[4];
     float2 mu[4];
     float2 ux[SCHEME == 3 ? 4 : 2], uy[SCHEME == 3 ? 4 : 2];  // stage C results (improved)
@@ -247,12 +296,27 @@ struct PairCtx {
     TmaRuns runs;       // column runs of one stored row (periodic split)
     uint32_t row_bytes;
     int j;              // ring column of the pair's first node
+    int jm, jq;         // ring columns j - 1 and j + 2, clamped to the ring
     bool b, c, d;       // pair active in stages B/C, D
-    int ks;             // ring slot of stored row ra - 1 (= s0 + it)
+    // ring slots advance by pointer: the slots of stored rows it, it + 1,
+    // it + 2 (stage A's three rows; the first is refilled at the end of the
+    // iteration), the mbarriers of the slots of rows it and it + 2, and the
+    // phase parity that row it + 2 completes
+    float *pRm, *pR0, *pRp;
+    uint64_t *fm, *f2;
+    uint32_t par2;
+    uint32_t irow;      // row offset (row * pitch) of the next refill, stored row it + kPairSlots
+    uint32_t plane_rows; // ny * pitch
     int rd;             // lattice row of stage D
     float* out;         // fout + column of the pair's first node (stage D pairs)
+    float* orow;        // out + rd * pitch
     int* bad;           // shared: a stage D node had rho <= 0 or a non-finite density
     int xc, xm1, xp2;   // scheme 3: lattice columns x (even), x - 1 and x + 2 of the pair
+    // this thread's share of a row refill: one (plane, run) copy, or none
+    const float* iss_src;  // source of the copy in row 0
+    uint32_t iss_dst;      // ring offset of the copy within a slot (floats)
+    uint32_t iss_bytes;
+    bool iss_on;
 };
 
 // Populations of the pair at lattice row r pulled from global memory (the
@@ -301,32 +365,37 @@ __device__ __forceinline__ void pair_timeout(const PairCtx& X)
     atomicOr(X.status, 1);
 }
 
-// Copy stored row i = s - s0 into slot k, spread over the issuing warps:
-// thread 0 arms the slot's mbarrier with the byte count, and each lane of
-// an issuing warp copies one (plane, run) pair: wide shape, warp w < 3
-// takes planes 3w .. 3w + 2; narrow shape, warp 0 planes 0-4, warp 1 planes
-// 5-8. (A copy may complete before the arming arrive; the phase cannot
-// complete before it, since that arrive is the phase's only one.) Called by
-// the first pair_issuers(NP) threads only.
+// This thread's share of every row copy, fixed for the block: thread 0 arms
+// a slot's mbarrier with the row's byte count, and each lane of an issuing
+// warp copies one (plane, run) pair: wide shape, warp w < 3 takes planes
+// 3w .. 3w + 2; narrow shape, warp 0 planes 0-4, warp 1 planes 5-8.
 template <int NP>
-__device__ __forceinline__ void pair_issue(const PairCtx& X, const DevCase<float>& c, int i, int k)
+__device__ __forceinline__ void pair_issue_setup(PairCtx& X, const DevCase<float>& c)
 {
-    constexpr int COLS = 2 * NP;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint64_t* b = X.full + k;
-    if (threadIdx.x == 0) mbar_expect_tx(b, X.row_bytes);
     const int pw = NP == kPairThreads ? 3 : (w == 0 ? 5 : 4);  // planes of this warp
     const int a0 = NP == kPairThreads ? 3 * w : (w == 0 ? 0 : 5);
-    if (lane < pw * X.runs.n) {
-        const int a = a0 + lane % pw, r = lane / pw;
-        const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
-        const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
-        const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
-        const uint32_t row = (uint32_t)wrapi(X.s0 + i, c.ny) * c.pitch;
+    X.iss_on = threadIdx.x < pair_issuers(NP) && lane < pw * X.runs.n;
+    const int a = X.iss_on ? a0 + lane % pw : 0, r = X.iss_on ? lane / pw : 0;
+    const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
+    const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
+    const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
+    X.iss_src = X.fin + ((uint32_t)a * (uint32_t)c.plane + (uint32_t)g0);
+    X.iss_dst = (uint32_t)(a * 2 * NP + j0);
+    X.iss_bytes = (uint32_t)len * sizeof(float);
+}
+
+// Copy the stored row at row offset `row` (row * pitch) into a slot whose
+// mbarrier is `bar`. (A copy may complete before the arming arrive; the
+// phase cannot complete before it, since that arrive is the phase's only
+// one.) Called by the first pair_issuers(NP) threads only.
+__device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64_t* bar, uint32_t row)
+{
+    if (threadIdx.x == 0) mbar_expect_tx(bar, X.row_bytes);
+    if (X.iss_on) {
         // order earlier generic-proxy reads of the slot before the async refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(X.ring + ((size_t)k * kQ + a) * COLS + j0,
-                  X.fin + ((uint32_t)a * (uint32_t)c.plane + row + (uint32_t)g0), (uint32_t)len * sizeof(float), b);
+        bulk_load(slot + X.iss_dst, X.iss_src + row, X.iss_bytes, bar);
     }
 }
 
@@ -341,37 +410,34 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
 
     // ---------------------------------------------------------------- A
     {
-        const int i2 = it + 2;  // stored row ra + 1
-        const int k2 = X.ks + 2 >= kPairSlots ? X.ks + 2 - kPairSlots : X.ks + 2;
         if (it == 0) {
             if (!mbar_wait(X.full + 0, 0u)) pair_timeout(X);
             if (!mbar_wait(X.full + 1, 0u)) pair_timeout(X);
         }
-        if (!mbar_wait(X.full + k2, (uint32_t)(i2 / kPairSlots) & 1u)) pair_timeout(X);
-        const int k1 = X.ks + 1 >= kPairSlots ? X.ks + 1 - kPairSlots : X.ks + 1;
-        const float* Rm = X.ring + (size_t)X.ks * kQ * SW;
-        const float* R0 = X.ring + (size_t)k1 * kQ * SW;
-        const float* Rp = X.ring + (size_t)k2 * kQ * SW;
-        // aligned pairs (j-2, j-1), (j, j+1), (j+2, j+3); the outermost pairs
-        // of the block read a clamped pair and produce unused values
-        const int jl = j >= 2 ? j - 2 : 0;
-        const int jr = j + 2 <= SW - 2 ? j + 2 : SW - 2;
-        float2 Floc[kQ];
-        float2* F = SCHEME == 3 ? Floc : R.f[S0];  // scheme 3 keeps only the sums
+        if (!mbar_wait(X.f2, X.par2)) pair_timeout(X);  // stored row it + 2 (ra + 1)
+        const float* Rm = X.pRm;
+        const float* R0 = X.pR0;
+        const float* Rp = X.pRp;
+        // the planes that shift in x take one scalar load per node, straight
+        // into its half of the pair (the outermost pairs of the block read
+        // clamped columns and produce unused values)
+        const int jm = X.jm, jq = X.jq;
+        float2 F[kQ];
         F[0] = ld2(R0 + 0 * SW + j);
-        F[1] = make_float2(ld2(R0 + 1 * SW + jl).y, ld2(R0 + 1 * SW + j).x);
+        F[1] = make_float2(R0[1 * SW + jm], R0[1 * SW + j]);
         F[2] = ld2(Rm + 2 * SW + j);
-        F[3] = make_float2(ld2(R0 + 3 * SW + j).y, ld2(R0 + 3 * SW + jr).x);
+        F[3] = make_float2(R0[3 * SW + j + 1], R0[3 * SW + jq]);
         F[4] = ld2(Rp + 4 * SW + j);
-        F[5] = make_float2(ld2(Rm + 5 * SW + jl).y, ld2(Rm + 5 * SW + j).x);
-        F[6] = make_float2(ld2(Rm + 6 * SW + j).y, ld2(Rm + 6 * SW + jr).x);
-        F[7] = make_float2(ld2(Rp + 7 * SW + j).y, ld2(Rp + 7 * SW + jr).x);
-        F[8] = make_float2(ld2(Rp + 8 * SW + jl).y, ld2(Rp + 8 * SW + j).x);
+        F[5] = make_float2(Rm[5 * SW + jm], Rm[5 * SW + j]);
+        F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jq]);
+        F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jq]);
+        F[8] = make_float2(Rp[8 * SW + jm], Rp[8 * SW + j]);
         const float2 dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
         R.drho[S0] = dr;
         R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
         R.jy[S0] = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
         st2(sm.rho[S0] + j, v2(c.rho_ref) + dr);
+        if constexpr (SCHEME != 3) moments2(F, R.m[S0]);  // scheme 3 keeps only the sums
     }
     __syncthreads();
 
@@ -475,7 +541,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                 }
                 collide2<SCHEME>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c, le,
                                  ls, lq, lv);
-                float* o = X.out + (uint32_t)X.rd * c.pitch;
+                float* o = X.orow;
                 const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
                 for (int a = 0; a < kQ; ++a) st2(o + a * P, F[a]);
@@ -501,12 +567,13 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                                  shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
                 if (COLL == 0) le = ls = lq = lv;
             }
-            collide2<SCHEME>(R.f[S3], drho, rho, R.jx[S3], R.jy[S3], R.ux[U3], R.uy[U3], R.Fx[U3], R.Fy[U3], mu,
-                             C1, C7, c, le, ls, lq, lv);
-            float* o = X.out + (uint32_t)X.rd * c.pitch;
+            float2 d[kQ];
+            collide2m<SCHEME>(d, R.m[S3], drho, rho, R.jx[S3], R.jy[S3], R.ux[U3], R.uy[U3], R.Fx[U3], R.Fy[U3],
+                              mu, C1, C7, c, le, ls, lq, lv);
+            float* o = X.orow;
             const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S3][a]);
+            for (int a = 0; a < kQ; ++a) st2(o + a * P, d[a]);
         }
         }
     } else {
@@ -549,21 +616,38 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                                  shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
                 if (COLL == 0) le = ls = lq = lv;
             }
-            collide2<SCHEME>(R.f[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, v2(0.0f), v2(0.0f), c, le,
-                             ls, lq, lv);
-            float* o = X.out + (uint32_t)X.rd * c.pitch;
+            float2 d[kQ];
+            collide2m<SCHEME>(d, R.m[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, v2(0.0f), v2(0.0f), c,
+                              le, ls, lq, lv);
+            float* o = X.orow;
             const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) st2(o + a * P, R.f[S2][a]);
+            for (int a = 0; a < kQ; ++a) st2(o + a * P, d[a]);
         }
     }
     // stored row it (ra - 1) has had no reader since stage A's barrier: refill
     // its slot now, with the iteration's arithmetic issued (the copy still has
     // two iterations of lead before stage A needs it)
-    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last)
-        pair_issue<NP>(X, c, it + kPairSlots, X.ks);
-    X.ks = X.ks + 1 == kPairSlots ? 0 : X.ks + 1;
-    if (it >= G::ND) X.rd = X.rd + 1 == c.ny ? 0 : X.rd + 1;
+    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, X.pRm, X.fm, X.irow);
+    // advance the ring, the refill row and the output row by one (wrapping
+    // compares instead of row modulos and multiplies)
+    X.irow = X.irow + c.pitch == X.plane_rows ? 0u : X.irow + c.pitch;
+    {
+        constexpr int SLOTF = kQ * SW;
+        float* const ring_end = X.ring + kPairSlots * SLOTF;
+        X.fm = X.fm + 1 == X.full + kPairSlots ? X.full : X.fm + 1;
+        const bool wrap = X.f2 + 1 == X.full + kPairSlots;
+        X.f2 = wrap ? X.full : X.f2 + 1;
+        X.par2 ^= wrap ? 1u : 0u;
+        X.pRm = X.pR0;
+        X.pR0 = X.pRp;
+        X.pRp = X.pRp + SLOTF == ring_end ? X.ring : X.pRp + SLOTF;
+    }
+    if (it >= G::ND) {
+        const bool w = X.rd + 1 == c.ny;
+        X.rd = w ? 0 : X.rd + 1;
+        X.orow = w ? X.out : X.orow + c.pitch;
+    }
 }
 
 template <typename T, int NP>
@@ -625,6 +709,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
         }
         X.row_bytes = (uint32_t)(kQ * (end - start) * sizeof(float));
     }
+    pair_issue_setup<NP>(X, c);
     if (threadIdx.x == 0) {
         flag = 0;
         bad = 0;
@@ -633,7 +718,8 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     }
     __syncthreads();
     if (threadIdx.x < pair_issuers(NP))
-        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) pair_issue<NP>(X, c, i, i);
+        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i)
+            pair_issue(X, X.ring + i * kQ * (2 * NP), X.full + i, (uint32_t)wrapi(X.s0 + i, c.ny) * c.pitch);
 
     const int p = threadIdx.x;
     X.j = 2 * p;
@@ -646,9 +732,19 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
         X.d = p >= 2 && 2 * p < item.wv + 4;
         X.c = X.b;
     }
-    X.ks = 0;
+    X.jm = X.j > 0 ? X.j - 1 : 0;
+    X.jq = X.j + 2 < 2 * NP ? X.j + 2 : 2 * NP - 1;
+    X.pRm = X.ring;
+    X.pR0 = X.ring + kQ * (2 * NP);
+    X.pRp = X.ring + 2 * kQ * (2 * NP);
+    X.fm = X.full;
+    X.f2 = X.full + 2;
+    X.par2 = 0;
+    X.plane_rows = (uint32_t)c.ny * c.pitch;
+    X.irow = (uint32_t)wrapi(X.s0 + kPairSlots, c.ny) * c.pitch;
     X.rd = item.y0;
     X.out = fout + (X.d ? item.x0 - M + 2 * p : 0);
+    X.orow = X.out + (uint32_t)X.rd * c.pitch;
     X.xc = X.d ? item.x0 - M + 2 * p : 0;
     X.xm1 = X.xc == 0 ? c.nx - 1 : X.xc - 1;
     X.xp2 = X.xc + 2 >= c.nx ? X.xc + 2 - c.nx : X.xc + 2;
