@@ -63,7 +63,8 @@ def _dist():
 
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_pair_spinodal4096.json")
 # files that define the FP32 step kernel and its launch
-STEP_SOURCES = ("launch.h", "lbfe_device.cuh", "step_f32.cu", "step_kernel.cuh", "step_pair.cuh", "step_tma.cuh")
+STEP_SOURCES = ("launch.h", "lbfe_device.cuh", "step_f32.cu", "step_f32_pair.cuh", "step_f32_pair1.cu", "step_kernel.cuh",
+                "step_pair.cuh", "step_tma.cuh")
 
 
 def _kernel_source_sha256() -> str:
