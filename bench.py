@@ -370,6 +370,7 @@ def run_gpu(args):
         # the same batch down to 0.65 T_c with the averaged correction (one-column kernel)
         extras["batched_smooth_0p65"] = _batched_throughput(lbfe, steps=20, warmup=5, t_range=(0.65, 0.9),
                                                             scheme=lbfe.IMPROVED_SMOOTH, per_case=False)
+        extras["step_stats"] = _step_stats_cost(lbfe, case, rho0_pin, local, steps=40)
         extras["fp64"] = _fp64_spinodal(lbfe, inputs, n_side, steps=5, warmup=3, local=local, rank=rank)
         extras["adjoint"] = _adjoint_check(lbfe, inputs, steps=200, window=20, ckpt=20)
         extras["small_lattices"] = _small_lattices(lbfe, inputs)
@@ -563,6 +564,46 @@ def _batched_throughput(lbfe, steps: int, warmup: int, t_range=(0.8, 0.9), schem
     res["per_case_launches"] = {"value": round(nodes * steps / (per_case_ms * 1e-3) / 1e6, 1), "unit": "MLUPS",
                                 "ms_per_step": round(per_case_ms / steps, 4)}
     return res
+
+
+def _step_stats_cost(lbfe, case, rho0_pin, local: int, steps: int) -> dict:
+    """The default workload with the per-step statistics attached (mass, kinetic
+    energy and max |u| fused into every step) against the same steps without:
+    MLUPS of each (lb_step(steps) between CUDA events, best of 3) and the
+    recorded mass of the last state against lb_reductions of that state."""
+    import torch
+
+    lat = lbfe.Lattice([case], precision=lbfe.FP32, device=f"cuda:{local}")
+    lat.init_fields(0, rho0_pin)
+    lat.step(16)
+    nodes = case.nx * case.ny
+
+    def timed():
+        best = 1e30
+        with torch.cuda.stream(lat.stream):
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(lat.stream)
+                lat.step(steps)
+                e1.record(lat.stream)
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+        return nodes * steps / (best * 1e-3) / 1e6
+
+    off = timed()
+    lat.attach_step_stats(4 * steps)
+    lat.step(16)
+    on = timed()
+    out, _ = lat.reductions()  # the current state, which the next step records
+    lat.step(1)
+    first, rec = lat.step_stats(0)
+    lat.close()
+    return {"value": round(on, 1), "unit": "MLUPS", "without_stats": round(off, 1),
+            "cost": round(1.0 - on / off, 4), "steps": steps,
+            "recorded_states": int(rec.shape[0]), "first_recorded_state": int(first),
+            "last_state_vs_reductions": {"mass_rel": float(abs(rec[-1, 0] / out[0, 0] - 1.0)),
+                                         "ke_rel": float(abs(rec[-1, 1] / out[0, 1] - 1.0)),
+                                         "umax_rel": float(abs(rec[-1, 2] / out[0, 2] - 1.0))}}
 
 
 def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:

@@ -243,6 +243,41 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
  * LB_E_UNSTABLE if any case is unstable; every entry is still written. */
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status);
 
+/* Per-step statistics fused into the step kernels: the mass and kinetic
+ * energy of the macroscopic fields of Eq. 12, recorded every step instead of
+ * on demand. With a buffer attached, each step of lb_step records, for
+ * every case, the state the step starts from (the fields lb_moments would
+ * return just before it): {mass sum rho, kinetic energy sum rho|u|^2/2,
+ * max |u|, node count}. Stage D of the step kernels sums rho - rho_ref and
+ * rho|u|^2 per thread in the storage precision (FP32 for FP32 handles, over
+ * at most one work item's rows); each block reduces its sums in FP64 with
+ * warp shuffles and adds them to the case's entry with FP64 atomics, and
+ * the case's last block advances a ring of `history` entries. The sums
+ * agree with lb_reductions to FP64 rounding for FP64 handles and to about
+ * 1e-6 relative for FP32 ones. The order of the atomics is not fixed, so
+ * the last bits can differ between runs. While a buffer is attached,
+ * lb_step does not use the persistent launch and the autotuner's trial
+ * launches record nothing. lb_init_fields and lb_load restart a case's
+ * record at its new state. A case frozen by the instability flag (lb_step)
+ * stops recording.
+ *
+ * lb_step_stats_bytes: device bytes of a buffer with `history` entries per
+ *   case (1 <= history <= 2^20).
+ * lb_step_stats_attach: attach a caller-owned device buffer of at least that
+ *   size, 16-byte aligned. It is cleared here and never freed by the
+ *   library. d_buf NULL detaches. Recording starts at each case's current
+ *   state.
+ * lb_step_stats_range: the recorded states of case_id still held in the
+ *   ring: [*first_state, *first_state + *count). Synchronises the stream;
+ *   LB_E_STATE without a buffer.
+ * lb_step_stats_read: out[4*k + {0,1,2,3}] for state first_state + k,
+ *   0 <= k < count, all inside that range (else LB_E_INVALID). Host output;
+ *   synchronises the stream. */
+lb_status lb_step_stats_bytes(const lb_handle* h, int32_t history, size_t* bytes);
+lb_status lb_step_stats_attach(lb_handle* h, void* d_buf, size_t bytes, int32_t history);
+lb_status lb_step_stats_range(lb_handle* h, int32_t case_id, int64_t* first_state, int64_t* count);
+lb_status lb_step_stats_read(lb_handle* h, int32_t case_id, int64_t first_state, int32_t count, double* out);
+
 /* Coexistence-density averages (the rho_g / rho_l measurements of Sec. IV):
  * the mean of rho (Eq. 12) at the current step over each of nwin windows of
  * case case_id, with the node values in the storage precision and the sums

@@ -250,6 +250,16 @@ struct lb_handle {
     bool nb_ok = false;          // neighbour lists built for the current work-list
     int persist_grid = 0;
     long long spin_limit = kWaitCycles;
+    // per-step statistics (lb_step_stats_attach): the caller's device buffer
+    // ([ncases][2] int32 counters {ticket, recorded states}, then
+    // [ncases][st_hist] StepStat entries), whether the kernels see it (off
+    // while the autotuner times trial launches), the state index of each
+    // case's first recorded entry, and the work items per case of the list
+    uint8_t* st_buf = nullptr;
+    int st_hist = 0;
+    bool st_live = false;
+    std::vector<int64_t> st_base;
+    std::vector<int32_t> case_items;
     std::string err;
 
     void* fbuf(int b) const { return ws + L.f[b]; }
@@ -279,12 +289,28 @@ struct lb_handle {
         err = std::string(where) + ": " + cudaGetErrorString(e);
         return LB_E_CUDA;
     }
+    int32_t* st_ctr() const { return reinterpret_cast<int32_t*>(st_buf); }
+    StepStat* st_ring() const
+    {
+        return reinterpret_cast<StepStat*>(st_buf + align_up(2 * sizeof(int32_t) * cases.size(), kAlign));
+    }
+    template <typename T>
+    void set_stats(DevCase<T>& c, int i) const
+    {
+        if (!st_live || !st_buf) return;
+        c.st_hist = st_hist;
+        c.st_ring = st_ring() + (size_t)i * st_hist;
+        c.st_ctr = st_ctr() + 2 * i;
+        c.st_blocks = i < (int)case_items.size() ? case_items[i] : 0;
+    }
     lb_status upload_case(int i)
     {
         DevCase<float> c32 = dev_case<float>(cases[i], L.off[i], rho_ref[i]);
         DevCase<double> c64 = dev_case<double>(cases[i], L.off[i], rho_ref[i]);
         // a Lax-Wendroff case at step 0 holds f(0) itself (see pull_lw)
         c32.lw_first = c64.lw_first = cases[i].scheme == LB_LAX_WENDROFF && steps[i] == 0;
+        set_stats(c32, i);
+        set_stats(c64, i);
         lb_status s = cuda(cudaMemcpyAsync(dc32() + i, &c32, sizeof c32, cudaMemcpyHostToDevice, stream),
                            "upload case");
         if (s != LB_OK) return s;
@@ -377,6 +403,7 @@ void build_items(lb_handle* h)
                          [](const Item& a, const Item& b) { return a.h > b.h; });
         h->groups.push_back(g);
     };
+
     for (int s = 0; s < 5; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
@@ -400,6 +427,9 @@ void build_items(lb_handle* h)
                         emit(members, s, co, e, nu, tma, !tma ? kStepThreads : pair ? kPairWide : h->tma_threads);
                         emit(narrow, s, co, e, nu, tma, kPairNarrow);
                     }
+    // work items per case (the blocks one step of the case launches)
+    h->case_items.assign(h->cases.size(), 0);
+    for (const Item& it : h->items) ++h->case_items[it.case_id];
 }
 
 lb_status upload_items(lb_handle* h)
@@ -407,9 +437,43 @@ lb_status upload_items(lb_handle* h)
     h->nb_ok = false;
     if ((int64_t)h->items.size() > h->L.max_items)
         return h->fail(LB_E_STATE, "work-list larger than the workspace's item table");
-    return h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
-                                   cudaMemcpyHostToDevice, h->stream),
-                   "upload items");
+    lb_status s = h->cuda(cudaMemcpyAsync(h->ditems(), h->items.data(), h->items.size() * sizeof(Item),
+                                          cudaMemcpyHostToDevice, h->stream),
+                          "upload items");
+    // the statistics' tickets count the items of each case
+    for (int i = 0; s == LB_OK && h->st_live && i < (int)h->cases.size(); ++i) s = h->upload_case(i);
+    return s;
+}
+
+// Statistics recorded by the step launches or not: the case table is
+// uploaded again, and the captured graphs, whose launches name the kernel
+// variants without or with statistics, are dropped (captured again by the
+// next lb_step).
+lb_status stats_live(lb_handle* h, bool on)
+{
+    const bool want = on && h->st_buf;
+    if (h->st_live == want) return LB_OK;
+    h->st_live = want;
+    lb_status s = h->cuda(cudaStreamSynchronize(h->stream), "stats sync");
+    for (cudaGraphExec_t& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (int i = 0; s == LB_OK && i < (int)h->cases.size(); ++i) s = h->upload_case(i);
+    return s;
+}
+
+// Restart case i's statistics at its current state (a new or loaded state).
+lb_status stats_restart(lb_handle* h, int i)
+{
+    if (!h->st_buf) return LB_OK;
+    h->st_base[i] = h->steps[i];
+    lb_status s = h->cuda(cudaMemsetAsync(h->st_ctr() + 2 * i, 0, 2 * sizeof(int32_t), h->stream), "stats reset");
+    if (s == LB_OK)
+        s = h->cuda(cudaMemsetAsync(h->st_ring() + (size_t)i * h->st_hist, 0, sizeof(StepStat), h->stream),
+                    "stats reset");
+    return s;
 }
 
 lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
@@ -607,7 +671,7 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     if (s != LB_OK) return s;
     h->steps[case_id] = 0;
     h->inited[case_id] = 1;
-    return LB_OK;
+    return stats_restart(h, case_id);
 }
 
 // Enqueue one time step (every group) on stream st, reading buffer cur.
@@ -641,10 +705,11 @@ static lb_status enqueue_step(lb_handle* h, int cur, cudaStream_t st)
         if (h->prec == LB_FP32)
             e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, gs,
                                 (const float*)h->fbuf(cur), (float*)h->fbuf(cur ^ 1), h->dc32(),
-                                h->ditems() + g.first, h->status());
+                                h->ditems() + g.first, h->status(), h->st_live);
         else
             e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, gs, (const double*)h->fbuf(cur),
-                                (double*)h->fbuf(cur ^ 1), h->dc64(), h->ditems() + g.first, h->status());
+                                (double*)h->fbuf(cur ^ 1), h->dc64(), h->ditems() + g.first, h->status(),
+                                h->st_live);
         if (e != cudaSuccess) s = h->cuda(e, "step launch");
     }
     for (int b = 0; b < nb; ++b) {  // join every branch, even after a failed launch
@@ -711,8 +776,12 @@ static lb_status autotune(lb_handle* h)
         h->seg_rows = segs[k % kSegs];
         h->narrow = any_narrow ? k >= kSegs : narrow0;
     };
+    // trial launches record no statistics
+    const bool st_was = h->st_live;
+    lb_status s = stats_live(h, false);
+    if (s != LB_OK) return s;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    lb_status s = h->cuda(cudaEventCreate(&e0), "tune event");
+    s = h->cuda(cudaEventCreate(&e0), "tune event");
     if (s == LB_OK) s = h->cuda(cudaEventCreate(&e1), "tune event");
     float best_ms[2 * kSegs];
     for (float& b : best_ms) b = 1e30f;
@@ -744,6 +813,7 @@ static lb_status autotune(lb_handle* h)
     apply(best);
     build_items(h);
     lb_status u = upload_items(h);
+    if (u == LB_OK) u = stats_live(h, st_was);
     h->tuned = true;
     return s != LB_OK ? s : u;
 }
@@ -767,7 +837,7 @@ static bool circ_overlap(int a0, int la, int b0, int lb, int n)
 // group already runs the one-column kernel, so that results do not change).
 static bool persist_possible(const lb_handle* h, bool strict)
 {
-    if (h->groups.size() != 1) return false;
+    if (h->groups.size() != 1 || h->st_buf) return false;  // (per-step statistics need one launch per step)
     const Group& g = h->groups[0];
     if (strict && g.tma) return false;
     return occupancy_persist(h->prec, g.scheme, g.coll, g.eos, g.nu) > 0;
@@ -952,7 +1022,7 @@ lb_status lb_launch_mode(lb_handle* h, int32_t mode, int32_t* persistent)
     if (mode >= 0) {
         if (mode == 1 && !persist_possible(h, false))
             return h->fail(LB_E_INVALID, "lb_launch_mode: the persistent launch needs a handle whose cases all "
-                                         "share one kernel group");
+                                         "share one kernel group and no per-step statistics attached");
         h->persist_mode = mode;
         h->persist = mode == 1;
         h->persist_tuned = mode != 2;
@@ -1059,6 +1129,104 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
                                      "lb_reductions are unreliable");
     }
     if (unstable) return h->fail(LB_E_UNSTABLE, "a case has rho <= 0 or non-finite values");
+    return LB_OK;
+}
+
+constexpr int32_t kMaxStatHistory = 1 << 20;
+
+lb_status lb_step_stats_bytes(const lb_handle* h, int32_t history, size_t* bytes)
+{
+    if (!h || !bytes || history < 1 || history > kMaxStatHistory) return LB_E_INVALID;
+    *bytes = align_up(2 * sizeof(int32_t) * h->cases.size(), kAlign) +
+             (size_t)history * h->cases.size() * sizeof(StepStat);
+    return LB_OK;
+}
+
+lb_status lb_step_stats_attach(lb_handle* h, void* d_buf, size_t bytes, int32_t history)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    lb_status s = stats_live(h, false);  // the kernels stop seeing the previous buffer
+    if (s != LB_OK) return s;
+    h->st_buf = nullptr;
+    h->st_hist = 0;
+    if (!d_buf) return LB_OK;
+    size_t need = 0;
+    if (lb_step_stats_bytes(h, history, &need) != LB_OK)
+        return h->fail(LB_E_INVALID, "lb_step_stats_attach: history must be in [1, 2^20]");
+    if (bytes < need || (uintptr_t)d_buf % 16 != 0)
+        return h->fail(LB_E_INVALID, "lb_step_stats_attach: buffer smaller than lb_step_stats_bytes or not "
+                                     "16-byte aligned");
+    s = h->cuda(cudaMemsetAsync(d_buf, 0, need, h->stream), "stats clear");
+    if (s != LB_OK) return s;
+    h->st_buf = (uint8_t*)d_buf;
+    h->st_hist = history;
+    h->st_base.assign(h->steps.begin(), h->steps.end());
+    return stats_live(h, true);
+}
+
+// recorded states of case i still in the ring: [first, first + count)
+static lb_status stats_range(lb_handle* h, int32_t i, int64_t* first, int64_t* count, int32_t* recorded)
+{
+    int32_t n = 0;
+    lb_status s = h->cuda(cudaMemcpyAsync(&n, h->st_ctr() + 2 * i + 1, sizeof n, cudaMemcpyDeviceToHost, h->stream),
+                          "stats counter");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "stats sync");
+    if (s != LB_OK) return s;
+    const int64_t kept = std::min<int64_t>(n, h->st_hist);
+    *first = h->st_base[i] + n - kept;
+    *count = kept;
+    if (recorded) *recorded = n;
+    return LB_OK;
+}
+
+lb_status lb_step_stats_range(lb_handle* h, int32_t case_id, int64_t* first_state, int64_t* count)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size() || !first_state || !count)
+        return h->fail(LB_E_INVALID, "lb_step_stats_range: bad case id or null output");
+    if (!h->st_buf) return h->fail(LB_E_STATE, "lb_step_stats_range: no statistics buffer attached");
+    return stats_range(h, case_id, first_state, count, nullptr);
+}
+
+lb_status lb_step_stats_read(lb_handle* h, int32_t case_id, int64_t first_state, int32_t count, double* out)
+{
+    if (check_handle(h) != LB_OK) return LB_E_INVALID;
+    if (case_id < 0 || case_id >= (int)h->cases.size() || count < 0 || (count > 0 && !out))
+        return h->fail(LB_E_INVALID, "lb_step_stats_read: bad case id, count or output");
+    if (!h->st_buf) return h->fail(LB_E_STATE, "lb_step_stats_read: no statistics buffer attached");
+    int64_t first = 0, kept = 0;
+    int32_t n = 0;
+    lb_status s = stats_range(h, case_id, &first, &kept, &n);
+    if (s != LB_OK) return s;
+    if (first_state < first || first_state + count > first + kept)
+        return h->fail(LB_E_INVALID, "lb_step_stats_read: states outside the recorded range (lb_step_stats_range)");
+    if (count == 0) return LB_OK;
+    std::vector<StepStat> e((size_t)count);
+    const StepStat* ring = h->st_ring() + (size_t)case_id * h->st_hist;
+    // entry k of the case (k-th recorded state since the restart) is at ring[k % history]
+    const int64_t k0 = first_state - h->st_base[case_id];
+    const int64_t r0 = k0 % h->st_hist;
+    const int64_t n1 = std::min<int64_t>(count, h->st_hist - r0);
+    s = h->cuda(cudaMemcpyAsync(e.data(), ring + r0, n1 * sizeof(StepStat), cudaMemcpyDeviceToHost, h->stream),
+                "stats read");
+    if (s == LB_OK && n1 < count)
+        s = h->cuda(cudaMemcpyAsync(e.data() + n1, ring, (count - n1) * sizeof(StepStat), cudaMemcpyDeviceToHost,
+                                    h->stream),
+                    "stats read");
+    if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "stats sync");
+    if (s != LB_OK) return s;
+    const lb_case& c = h->cases[case_id];
+    // the share of rho_ref in the mass, with rho_ref as the kernels hold it
+    const double rr = h->prec == LB_FP32 ? (double)(float)h->rho_ref[case_id] : h->rho_ref[case_id];
+    const double base = (double)c.nx * c.ny * rr;
+    for (int32_t k = 0; k < count; ++k) {
+        double u2;
+        memcpy(&u2, &e[k].umax2, sizeof u2);
+        out[4 * k + 0] = base + e[k].dmass;
+        out[4 * k + 1] = 0.5 * e[k].ke2;
+        out[4 * k + 2] = std::sqrt(u2);
+        out[4 * k + 3] = (double)e[k].nodes;
+    }
     return LB_OK;
 }
 
@@ -1187,7 +1355,7 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
     if (s != LB_OK) return s;
     h->steps[case_id] = st;
     h->inited[case_id] = 1;
-    return LB_OK;
+    return stats_restart(h, case_id);
 }
 
 }  // extern "C"

@@ -17,6 +17,8 @@ constexpr int kQ = 9;
 // and 3 share the equilibrium, force and collision of Eqs. 24-28.
 __host__ __device__ constexpr bool improved_scheme(int s) { return s == 1 || s == 3; }
 
+struct StepStat;  // per-step statistics entry (below)
+
 // Per-case parameters as the kernels read them (one record per case, in the
 // arithmetic type T of the launch).
 template <typename T>
@@ -36,8 +38,78 @@ struct DevCase {
     // Eqs. A3-A4; dt (1 - 1/(2 tau)) of Eq. A1
     T lw_dt, lw_a0, lw_a1, lw_am1, lw_kT, lw_fd, lw_bt, lw_g;
     int32_t lw_first;  // 1: the stored populations are the pre-collision f(0) (step 0)
+    // per-step statistics (st_hist == 0: off): this case's ring of st_hist
+    // entries, its counters {ticket, recorded states} and the number of work
+    // items (blocks) that one step of the case launches
+    int32_t st_hist;
+    StepStat* st_ring;
+    int32_t* st_ctr;
+    int32_t st_blocks;
     int32_t pad_;
 };
+
+// One entry of the per-step statistics of a case: over the nodes of the
+// state a step starts from, the sums of rho - rho_ref and of rho |u|^2, the
+// largest |u|^2 (the bits of a non-negative double, which order like its
+// value) and the number of nodes summed.
+struct StepStat {
+    double dmass, ke2;
+    unsigned long long umax2;
+    unsigned long long nodes;
+};
+
+// Block end of the per-step statistics (Sec. II A: mass and kinetic energy of
+// the fields; the sums run in FP64 from here on). Every thread of the block
+// calls it with its partial sums over its stage D nodes; thread 0 adds the
+// block's sums to the case's current ring entry with FP64 atomics, and the
+// case's last block of the step (a ticket over st_blocks) clears the next
+// entry and advances the recorded-state counter. Kernel boundaries order the
+// steps, so the next launch reads the advanced counter. blockDim.x must be a
+// multiple of 32 and at most 1024.
+template <typename T>
+__device__ __forceinline__ void stats_block(const DevCase<T>& c, double dm, double k2, double u2,
+                                            unsigned long long nodes)
+{
+    __shared__ double s_m[32], s_k[32], s_u[32];
+    constexpr unsigned kFull = 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm += __shfl_xor_sync(kFull, dm, o);
+        k2 += __shfl_xor_sync(kFull, k2, o);
+        u2 = fmax(u2, __shfl_xor_sync(kFull, u2, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if (lane == 0) {
+        s_m[w] = dm;
+        s_k[w] = k2;
+        s_u[w] = u2;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 1; i < nw; ++i) {
+        dm += s_m[i];
+        k2 += s_k[i];
+        u2 = fmax(u2, s_u[i]);
+    }
+    int32_t* ctr = c.st_ctr;
+    StepStat* e = c.st_ring + (*(volatile int32_t*)(ctr + 1) % c.st_hist);
+    atomicAdd(&e->dmass, dm);
+    atomicAdd(&e->ke2, k2);
+    atomicMax(&e->umax2, (unsigned long long)__double_as_longlong(u2 > 0.0 ? u2 : 0.0));
+    atomicAdd(&e->nodes, nodes);
+    __threadfence();
+    if (atomicAdd(ctr, 1) == c.st_blocks - 1) {
+        const int32_t n = *(volatile int32_t*)(ctr + 1) + 1;
+        StepStat* nx = c.st_ring + (n % c.st_hist);
+        nx->dmass = 0.0;
+        nx->ke2 = 0.0;
+        nx->umax2 = 0ull;
+        nx->nodes = 0ull;
+        *(volatile int32_t*)ctr = 0;
+        __threadfence();
+        *(volatile int32_t*)(ctr + 1) = n;
+    }
+}
 
 
 // One block of work: output columns [x0, x0 + wv) and rows [y0, y0 + h) of a

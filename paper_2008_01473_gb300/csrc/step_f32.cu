@@ -1,6 +1,7 @@
 // Instantiations of the one-column FP32 step kernels (plain loads and the TMA
 // variant) and the FP32 launch; the packed kernels are instantiated per
-// scheme in the step_f32_pair<S>.cu units (compiled in parallel).
+// scheme in the step_f32_pair<S>[s].cu units and the plain-load kernel with
+// the per-step statistics in step_f32s.cu (compiled in parallel).
 #include "launch.h"
 #include "step_pair.cuh"
 
@@ -8,15 +9,22 @@ namespace lbfe {
 
 namespace {
 // the packed kernel (nullptr for the Lax-Wendroff scheme, which it does not run)
-void* pick_pair(int scheme, int coll, int eos, bool nu, bool narrow)
+template <bool ST>
+void* pick_pair_st(int scheme, int coll, int eos, bool nu, bool narrow)
 {
     switch (scheme) {
-    case 0: return pick_pair_scheme<0>(coll, eos, nu, narrow);
-    case 1: return pick_pair_scheme<1>(coll, eos, nu, narrow);
-    case 2: return pick_pair_scheme<2>(coll, eos, nu, narrow);
-    case 3: return pick_pair_scheme<3>(coll, eos, nu, narrow);
+    case 0: return pick_pair_scheme<0, ST>(coll, eos, nu, narrow);
+    case 1: return pick_pair_scheme<1, ST>(coll, eos, nu, narrow);
+    case 2: return pick_pair_scheme<2, ST>(coll, eos, nu, narrow);
+    case 3: return pick_pair_scheme<3, ST>(coll, eos, nu, narrow);
     default: return nullptr;
     }
+}
+
+void* pick_pair(int scheme, int coll, int eos, bool nu, bool narrow, bool stats)
+{
+    return stats ? pick_pair_st<true>(scheme, coll, eos, nu, narrow)
+                 : pick_pair_st<false>(scheme, coll, eos, nu, narrow);
 }
 
 // NT = kPairWide / kPairNarrow select the two-columns-per-thread packed
@@ -60,11 +68,12 @@ int block_threads(bool tma, int nt)
     return !tma ? kStepThreads : nt == kPairWide ? kPairThreads : nt == kPairNarrow ? kPairThreadsNarrow : nt + 32;
 }
 
-void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
+void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool stats = false)
 {
-    void* k = !tma           ? pick<false, kStepThreads>(scheme, coll, eos, nu)
-              : nt == kPairWide   ? pick_pair(scheme, coll, eos, nu, false)
-              : nt == kPairNarrow ? pick_pair(scheme, coll, eos, nu, true)
+    void* k = !tma                ? (stats ? pick_plain_stats_f32(scheme, coll, eos, nu)
+                                           : pick<false, kStepThreads>(scheme, coll, eos, nu))
+              : nt == kPairWide   ? pick_pair(scheme, coll, eos, nu, false, stats)
+              : nt == kPairNarrow ? pick_pair(scheme, coll, eos, nu, true, stats)
               : nt == 128    ? pick<true, 128>(scheme, coll, eos, nu)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;
@@ -80,9 +89,9 @@ void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt)
 
 cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, int nblocks,
                             cudaStream_t s, const float* fin, float* fout, const DevCase<float>* cases,
-                            const Item* items, int* status)
+                            const Item* items, int* status, bool stats)
 {
-    void* k = resolve(scheme, coll, eos, nu, tma, nt);
+    void* k = resolve(scheme, coll, eos, nu, tma, nt, stats);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
     // the TMA kernels add one producer warp to their compute threads

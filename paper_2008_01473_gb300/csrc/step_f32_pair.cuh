@@ -1,7 +1,8 @@
 // Instantiation table of the packed two-columns-per-thread FP32 step kernel
-// (step_pair.cuh) for one scheme, wide (128 threads) and narrow (64 threads);
-// each step_f32_pair<scheme>.cu unit instantiates one scheme, so that the
-// four compile in parallel.
+// (step_pair.cuh) for one scheme, wide (128 threads) and narrow (64 threads),
+// without (ST false) or with the per-step statistics (ST true); each
+// step_f32_pair<scheme>[s].cu unit instantiates one scheme and one ST, so
+// that the eight compile in parallel.
 #pragma once
 
 #include "launch.h"
@@ -9,18 +10,18 @@
 
 namespace lbfe {
 
-template <int S, int C, int E, bool NU>
+template <int S, int C, int E, bool NU, bool ST>
 void* pair_ptr(bool narrow)
 {
-    return narrow ? reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow>)
-                  : reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads>);
+    return narrow ? reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow, ST>)
+                  : reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads, ST>);
 }
 
-template <int S>
+template <int S, bool ST>
 void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow)
 {
 #define LBFE_PICK(C, E) \
-    if (coll == C && eos == E) return nu ? pair_ptr<S, C, E, true>(narrow) : pair_ptr<S, C, E, false>(narrow);
+    if (coll == C && eos == E) return nu ? pair_ptr<S, C, E, true, ST>(narrow) : pair_ptr<S, C, E, false, ST>(narrow);
     LBFE_PICK(0, 0) LBFE_PICK(0, 1) LBFE_PICK(1, 0) LBFE_PICK(1, 1)
 #undef LBFE_PICK
     return nullptr;

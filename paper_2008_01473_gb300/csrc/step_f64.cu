@@ -1,4 +1,5 @@
-// Instantiations of the fused step kernel with FP64 populations and arithmetic.
+// Instantiations of the fused step kernel with FP64 populations and arithmetic
+// (the variant with the per-step statistics: step_f64s.cu).
 #include "launch.h"
 #include "step_kernel.cuh"
 
@@ -28,9 +29,9 @@ void* pick(int scheme, int coll, int eos, bool nu)
 
 cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks, cudaStream_t s,
                             const double* fin, double* fout, const DevCase<double>* cases,
-                            const Item* items, int* status)
+                            const Item* items, int* status, bool stats)
 {
-    void* k = pick(scheme, coll, eos, nu);
+    void* k = stats ? pick_plain_stats_f64(scheme, coll, eos, nu) : pick(scheme, coll, eos, nu);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
     return cudaLaunchKernel(k, dim3(nblocks), dim3(kStepThreads), args, 0, s);

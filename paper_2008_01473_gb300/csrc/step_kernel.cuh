@@ -68,6 +68,22 @@ struct StepRegs {
     T ux[4], uy[4], Fx[4], Fy[4];  // stage C results of the last rows (improved schemes)
     T grx, gry;                    // stage B grad rho (standard)
     bool bad;                      // a stage D node had rho <= 0 or a non-finite density
+    T am, ak, au;                  // statistics of the stage D nodes: sums of rho - rho_ref, rho |u|^2; max |u|^2
+};
+
+template <typename T>
+__device__ __forceinline__ void node_stats(StepRegs<T>& R, T drho, T rho, T ux, T uy)
+{
+    const T u2 = ux * ux + uy * uy;
+    R.am += drho;
+    R.ak += rho * u2;
+    R.au = u2 > R.au ? u2 : R.au;
+}
+
+// per-thread statistics of one work item (returned by step_item)
+template <typename T>
+struct StepAcc {
+    T am, ak, au;
 };
 
 // rho > 0 and finite (NaN fails both comparisons)
@@ -211,7 +227,7 @@ __device__ __forceinline__ void pull_lw(T* F, const T* __restrict__ fin, const D
 // roles of x and y exchanged. The populations of row rd are pulled again
 // (L2-resident: stage A read them four iterations earlier) instead of being
 // kept in registers for four rows.
-template <typename T, int NT, int COLL, int EOS, bool NU, int SLOT, bool COHERENT>
+template <typename T, int NT, int COLL, int EOS, bool NU, int SLOT, bool COHERENT, bool ST>
 __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin, T* __restrict__ fout,
                                               const DevCase<T>& c, const StepLane& L, const StepRows& rows,
                                               StepSmem<T, NT, 3>& sm, StepRegs<T>& R)
@@ -254,6 +270,7 @@ __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin,
     const T rho = c.rho_ref + drho;
     R.bad |= !rho_ok(rho);
     const T mu = sm.mu[S0][t];  // row ra - 4
+    if constexpr (ST) node_stats(R, drho, rho, R.ux[S2], R.uy[S2]);
     T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
     if (NU) {
         lv = shear_rate<3, NU, T>(c, rho, mu);
@@ -267,7 +284,8 @@ __device__ __forceinline__ void step_d_smooth(int it, const T* __restrict__ fin,
     for (int a = 0; a < kQ; ++a) fout[a * P + o] = F[a];
 }
 
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A, bool COHERENT = false>
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, int SLOT, class A, bool COHERENT = false,
+          bool ST = false>
 __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restrict__ fin, T* __restrict__ fout,
                                           const DevCase<T>& c, const StepLane& L, StepRows& rows,
                                           StepSmem<T, NT, SCHEME>& sm, StepRegs<T>& R)
@@ -355,7 +373,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
         if constexpr (SCHEME == 3) {
             // -------------------------------------------------------- D (3)
             if (L.d && it >= G::ND)
-                step_d_smooth<T, NT, COLL, EOS, NU, SLOT, COHERENT>(it, fin, fout, c, L, rows, sm, R);
+                step_d_smooth<T, NT, COLL, EOS, NU, SLOT, COHERENT, ST>(it, fin, fout, c, L, rows, sm, R);
         } else {
         // ------------------------------------------------------------ D
         constexpr int U3 = (SLOT + 1) & 1;
@@ -372,6 +390,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T rho = c.rho_ref + drho;
             R.bad |= !rho_ok(rho);
             const T mu = sm.mu[S3][t];
+            if constexpr (ST) node_stats(R, drho, rho, R.ux[U3], R.uy[U3]);
             T le = c.lam_e, ls = c.lam_s, lq = c.lam_q, lv = c.lam_v;
             if (NU) {
                 lv = shear_rate<SCHEME, NU, T>(c, rho, mu);
@@ -419,6 +438,7 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
             const T half = SCHEME == 4 ? T(0.5) * c.lw_dt : T(0.5);  // Lax-Wendroff: time step dt = A
             const T ux = (R.jx[S2] + half * Fx) * inv;
             const T uy = (R.jy[S2] + half * Fy) * inv;
+            if constexpr (ST) node_stats(R, drho, rho, ux, uy);
             if constexpr (SCHEME == 4) {
                 collide_lw<T>(R.f[S2], drho, rho, ux, uy, Fx, Fy, c);
             } else {
@@ -443,10 +463,11 @@ __device__ __forceinline__ void step_iter(int it, const A& A_, const T* __restri
 // One work item of one time step (the body of step_kernel): the block walks
 // the item's rows through stages A-D, reading fin and writing fout, and
 // returns whether a stage D node had rho <= 0 or a non-finite density (the
-// same value in every thread). COHERENT selects L2-only population loads.
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, bool COHERENT>
+// same value in every thread). COHERENT selects L2-only population loads; ST
+// accumulates the thread's statistics of its stage D nodes into acc.
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, bool COHERENT, bool ST = false>
 __device__ __forceinline__ bool step_item(const T* __restrict__ fin, T* __restrict__ fout, const DevCase<T>& c,
-                                          const Item& item, StepSmem<T, NT, SCHEME>& sm)
+                                          const Item& item, StepSmem<T, NT, SCHEME>& sm, StepAcc<T>& acc)
 {
     using G = StepGeom<SCHEME>;
     fin += c.off;
@@ -471,21 +492,25 @@ __device__ __forceinline__ bool step_item(const T* __restrict__ fin, T* __restri
 
     StepRegs<T> R;
     R.bad = false;
+    R.am = R.ak = R.au = T(0);
     const int niter = item.h + 2 * G::HX;
     const PullGlobal<T, COHERENT> A;
     for (int base = 0; base < niter; base += 4) {
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0, PullGlobal<T, COHERENT>, COHERENT>(base, A, fin, fout, c, L, rows,
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 0, PullGlobal<T, COHERENT>, COHERENT, ST>(base, A, fin, fout, c, L, rows,
                                                                                      sm, R);
         if (base + 1 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1, PullGlobal<T, COHERENT>, COHERENT>(base + 1, A, fin, fout, c, L,
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 1, PullGlobal<T, COHERENT>, COHERENT, ST>(base + 1, A, fin, fout, c, L,
                                                                                      rows, sm, R);
         if (base + 2 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2, PullGlobal<T, COHERENT>, COHERENT>(base + 2, A, fin, fout, c, L,
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 2, PullGlobal<T, COHERENT>, COHERENT, ST>(base + 2, A, fin, fout, c, L,
                                                                                      rows, sm, R);
         if (base + 3 >= niter) break;
-        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3, PullGlobal<T, COHERENT>, COHERENT>(base + 3, A, fin, fout, c, L,
+        step_iter<T, NT, SCHEME, COLL, EOS, NU, 3, PullGlobal<T, COHERENT>, COHERENT, ST>(base + 3, A, fin, fout, c, L,
                                                                                      rows, sm, R);
     }
+    acc.am = R.am;
+    acc.ak = R.ak;
+    acc.au = R.au;
     return __syncthreads_or(R.bad) != 0;
 }
 
@@ -495,7 +520,9 @@ __device__ __forceinline__ bool step_item(const T* __restrict__ fin, T* __restri
 // up (TMA variants); status[1 + case]: set when a node of the case had
 // rho <= 0 or a non-finite density in stage D. The blocks of a flagged case
 // return at once, so it no longer advances while the other cases go on.
-template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU>
+// ST: the variant that also records the per-step statistics (stage D sums,
+// stats_block) of the cases whose record has st_hist != 0.
+template <typename T, int NT, int SCHEME, int COLL, int EOS, bool NU, bool ST = false>
 __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* __restrict__ fout,
                                                   const DevCase<T>* __restrict__ cases,
                                                   const Item* __restrict__ items, int* __restrict__ status)
@@ -505,8 +532,12 @@ __global__ void __launch_bounds__(NT) step_kernel(const T* __restrict__ fin, T* 
     // thread 0 decides for the block: another block may set the word meanwhile
     if (__syncthreads_or(threadIdx.x == 0 && status[1 + item.case_id] != 0)) return;
     const DevCase<T> c = cases[item.case_id];
-    const bool bad = step_item<T, NT, SCHEME, COLL, EOS, NU, false>(fin, fout, c, item, sm);
+    StepAcc<T> acc;
+    const bool bad = step_item<T, NT, SCHEME, COLL, EOS, NU, false, ST>(fin, fout, c, item, sm, acc);
     if (bad && threadIdx.x == 0) atomicOr(status + 1 + item.case_id, 1);
+    if (ST && c.st_hist)
+        stats_block(c, (double)acc.am, (double)acc.ak, (double)acc.au,
+                    (unsigned long long)item.wv * (unsigned long long)item.h);
 }
 
 }  // namespace lbfe

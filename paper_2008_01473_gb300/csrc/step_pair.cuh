@@ -284,7 +284,18 @@ struct PairRegs {
     float2 ux[SCHEME == 3 ? 4 : 2], uy[SCHEME == 3 ? 4 : 2];  // stage C results (improved)
     float2 Fx[SCHEME == 3 ? 4 : 2], Fy[SCHEME == 3 ? 4 : 2];
     float2 grx, gry;  // stage B grad rho (standard)
+    float2 am, ak;    // statistics of the stage D nodes: sums of rho - rho_ref and rho |u|^2
+    float au;         // and the largest |u|^2
 };
+
+template <int SCHEME>
+__device__ __forceinline__ void pair_stats(PairRegs<SCHEME>& R, float2 drho, float2 rho, float2 ux, float2 uy)
+{
+    const float2 u2 = fma2(ux, ux, uy * uy);
+    R.am = R.am + drho;
+    R.ak = fma2(rho, u2, R.ak);
+    R.au = fmaxf(R.au, fmaxf(u2.x, u2.y));
+}
 
 struct PairCtx {
     float* ring;        // [kPairSlots][9][ring columns]
@@ -399,7 +410,7 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64
     }
 }
 
-template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT>
+template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT, bool ST>
 __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME, 2 * NP>& sm,
                                           PairRegs<SCHEME>& R)
 {
@@ -539,6 +550,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                                      shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
                     if (COLL == 0) le = ls = lq = lv;
                 }
+                if constexpr (ST) pair_stats(R, drho, rho, R.ux[S2], R.uy[S2]);
                 collide2<SCHEME>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c, le,
                                  ls, lq, lv);
                 float* o = X.orow;
@@ -567,6 +579,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                                  shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
                 if (COLL == 0) le = ls = lq = lv;
             }
+            if constexpr (ST) pair_stats(R, drho, rho, R.ux[U3], R.uy[U3]);
             float2 d[kQ];
             collide2m<SCHEME>(d, R.m[S3], drho, rho, R.jx[S3], R.jy[S3], R.ux[U3], R.uy[U3], R.Fx[U3], R.Fy[U3],
                               mu, C1, C7, c, le, ls, lq, lv);
@@ -616,6 +629,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                                  shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
                 if (COLL == 0) le = ls = lq = lv;
             }
+            if constexpr (ST) pair_stats(R, drho, rho, ux, uy);
             float2 d[kQ];
             collide2m<SCHEME>(d, R.m[S2], drho, rho, R.jx[S2], R.jy[S2], ux, uy, Fx, Fy, mu, v2(0.0f), v2(0.0f), c,
                               le, ls, lq, lv);
@@ -660,8 +674,9 @@ constexpr size_t pair_dynamic_smem()
 // 64). Every case of the launch has nx % 4 == 0 (and nx >= 8 for scheme 3,
 // so that each margin of the ring is one copy run); every item x0 % 4 == 0,
 // wv % 4 == 0, wv + 2 M <= 2 NP with M = PairGeom<SCHEME>::M (4, or 8 for
-// scheme 3).
-template <int SCHEME, int COLL, int EOS, bool NU, int NP>
+// scheme 3). ST: the variant that also records the per-step statistics
+// (stats_block) of the cases whose record has st_hist != 0.
+template <int SCHEME, int COLL, int EOS, bool NU, int NP, bool ST = false>
 __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pair(const float* __restrict__ fin,
                                                                     float* __restrict__ fout,
                                                                     const DevCase<float>* __restrict__ cases,
@@ -751,18 +766,23 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     X.bad = &bad;
 
     PairRegs<SCHEME> R;
+    R.am = R.ak = v2(0.0f);
+    R.au = 0.0f;
     for (int base = 0; base < niter; base += 4) {
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 0>(base, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 0, ST>(base, X, c, sm, R);
         if (base + 1 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 1>(base + 1, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 1, ST>(base + 1, X, c, sm, R);
         if (base + 2 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 2>(base + 2, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 2, ST>(base + 2, X, c, sm, R);
         if (base + 3 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 3>(base + 3, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 3, ST>(base + 3, X, c, sm, R);
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
     __syncthreads();
     if (threadIdx.x == 0 && bad) atomicOr(status + 1 + item.case_id, 1);
+    if (ST && c.st_hist)
+        stats_block(c, (double)R.am.x + (double)R.am.y, (double)R.ak.x + (double)R.ak.y, (double)R.au,
+                    (unsigned long long)item.wv * (unsigned long long)item.h);
     if (threadIdx.x == 0 && flag) {
         for (int s = max(X.s0, X.s_last - kPairSlots + 1); s <= X.s_last; ++s) {
             const int i = s - X.s0;

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(NT) step_kernel_persist(T* buf0, T* buf1, cons
             const bool skip = __syncthreads_or(threadIdx.x == 0 && *(volatile const int*)(status + 1 + item.case_id));
             if (!skip) {
                 const DevCase<T> c = cases[item.case_id];
-                const bool bad = step_item<T, NT, SCHEME, COLL, EOS, NU, true>(fin, fout, c, item, sm);
+                StepAcc<T> acc;  // (handles with per-step statistics do not launch this kernel)
+                const bool bad = step_item<T, NT, SCHEME, COLL, EOS, NU, true>(fin, fout, c, item, sm, acc);
                 if (bad && threadIdx.x == 0) atomicOr(status + 1 + item.case_id, 1);
             }
             __syncthreads();  // every store of the item precedes the release below

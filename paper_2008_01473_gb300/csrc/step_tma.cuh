@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
 
     StepRegs<T> R;
     R.bad = false;
+    R.am = R.ak = R.au = T(0);
     if (threadIdx.x >= NT) {
         // producer warp
         if (threadIdx.x == NT) {
@@ -261,14 +262,15 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
         rows.rd = item.y0;
         rows.sa = item.y0 - G::HX;  // (this kernel never runs lattices with walls)
 
+        using Pull = PullTma<T, NT, SCHEME>;  // (accumulating statistics; the block end reads st_hist)
         for (int base = 0; base < niter; base += 4) {
-            step_iter<T, NT, SCHEME, COLL, EOS, NU, 0>(base, A, fin, fout, c, L, rows, sm, R);
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 0, Pull, false, true>(base, A, fin, fout, c, L, rows, sm, R);
             if (base + 1 >= niter) break;
-            step_iter<T, NT, SCHEME, COLL, EOS, NU, 1>(base + 1, A, fin, fout, c, L, rows, sm, R);
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 1, Pull, false, true>(base + 1, A, fin, fout, c, L, rows, sm, R);
             if (base + 2 >= niter) break;
-            step_iter<T, NT, SCHEME, COLL, EOS, NU, 2>(base + 2, A, fin, fout, c, L, rows, sm, R);
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 2, Pull, false, true>(base + 2, A, fin, fout, c, L, rows, sm, R);
             if (base + 3 >= niter) break;
-            step_iter<T, NT, SCHEME, COLL, EOS, NU, 3>(base + 3, A, fin, fout, c, L, rows, sm, R);
+            step_iter<T, NT, SCHEME, COLL, EOS, NU, 3, Pull, false, true>(base + 3, A, fin, fout, c, L, rows, sm, R);
         }
         // every issued row was waited on by stage A; after a timeout, drain (bounded)
         A.sync();
@@ -279,8 +281,11 @@ __global__ void __launch_bounds__(NT + 32) step_kernel_tma(const T* __restrict__
             }
         }
     }
-    // the producer warp joins with R.bad == false
+    // the producer warp joins with R.bad == false and zero statistics
     if (__syncthreads_or(R.bad) && threadIdx.x == 0) atomicOr(status + 1 + item.case_id, 1);
+    if (c.st_hist)
+        stats_block(c, (double)R.am, (double)R.ak, (double)R.au,
+                    (unsigned long long)item.wv * (unsigned long long)item.h);
 }
 
 }  // namespace lbfe

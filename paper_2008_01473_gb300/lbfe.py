@@ -113,14 +113,20 @@ def lib() -> C.CDLL:
         L.lb_launch_mode.argtypes = [vp, i32, C.POINTER(i32)]
         L.lb_persistent_selftest.argtypes = [vp, i64]
         L.lb_window_means.argtypes = [vp, i32, i32, C.POINTER(_CWindow), dp]
+        L.lb_step_stats_bytes.argtypes = [vp, i32, C.POINTER(sz)]
+        L.lb_step_stats_attach.argtypes = [vp, vp, sz, i32]
+        L.lb_step_stats_range.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
+        L.lb_step_stats_read.argtypes = [vp, i32, i64, i32, dp]
         L.lb_last_error.argtypes = [vp]
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
         for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
-                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist", "lb_wait_selftest", "lb_window_means", "lb_launch_mode", "lb_persistent_selftest",
-                     "lb_surface_tension", "lb_young_laplace"):
+                     "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist",
+                     "lb_wait_selftest", "lb_window_means", "lb_launch_mode", "lb_persistent_selftest",
+                     "lb_surface_tension", "lb_young_laplace", "lb_step_stats_bytes", "lb_step_stats_attach",
+                     "lb_step_stats_range", "lb_step_stats_read"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -284,6 +290,34 @@ class Lattice:
         if rc != 0 and (rc != 3 or raise_unstable):
             _check(rc, self._h)
         return out, st
+
+    def attach_step_stats(self, history: int = 1024):
+        """Record per-step statistics of every case (mass, kinetic energy,
+        max |u|, node count of the state each step starts from) in a device
+        ring of `history` entries per case; history 0 detaches."""
+        if history <= 0:
+            _check(lib().lb_step_stats_attach(self._h, None, 0, 0), self._h)
+            self._stats_buf = None
+            return
+        nb = C.c_size_t()
+        _check(lib().lb_step_stats_bytes(self._h, int(history), C.byref(nb)), self._h, "lb_step_stats_bytes")
+        buf = self._torch.empty(nb.value + 256, dtype=self._torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        _check(lib().lb_step_stats_attach(self._h, C.c_void_p(ptr), nb.value, int(history)), self._h)
+        self._stats_buf = buf  # the library does not own it
+
+    def step_stats(self, case_id: int, first=None, count=None):
+        """(first state, array[count, 4] of mass, kinetic energy, max |u|,
+        nodes) of the recorded states of case_id (all those still held by
+        default)."""
+        f, n = C.c_int64(), C.c_int64()
+        _check(lib().lb_step_stats_range(self._h, case_id, C.byref(f), C.byref(n)), self._h)
+        first = f.value if first is None else int(first)
+        count = f.value + n.value - first if count is None else int(count)
+        out = np.zeros((max(count, 0), 4))
+        _check(lib().lb_step_stats_read(self._h, case_id, first, count, out.ctypes.data_as(C.POINTER(C.c_double))),
+               self._h)
+        return first, out
 
     def adjoint(self, case_id: int, rho0, nsteps: int, u_from: int, s_final=None, ckpt_every: int = 0):
         """Loss L = sum_{n >= u_from} sum |u^n|^2 + sum s_final rho^N of a run from
