@@ -156,7 +156,9 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
 /* Set case case_id to f(0) = M^-1 m_eq(rho0, u0) of its scheme, with mu_c of
  * Eq. 2 evaluated on rho0 (the paper gives no initialisation rule).
  * rho0 [ny][nx] must be > 0; ux0/uy0 may be NULL (fluid at rest). Pointers
- * are device addresses if on_device, else host (copied synchronously). */
+ * are device addresses if on_device, else host (copied synchronously;
+ * page-locked host memory, as from cudaHostAlloc, is read by the first init
+ * kernel directly over the host link). */
 lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
                          const double* uy0, int32_t on_device);
 
@@ -230,7 +232,9 @@ lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, i
 /* Macroscopic fields of case case_id at the current step: rho and u of
  * Eq. 12 (u includes the F/2 shift) and mu_c of Eq. 2, computed per node in
  * the storage precision and returned as FP64; any output may be NULL.
- * Device outputs if on_device, else host (stream synchronised). */
+ * Device outputs if on_device, else host (stream synchronised; the export
+ * kernel writes page-locked host outputs, as from cudaHostAlloc, directly
+ * over the host link, pageable ones are staged in the workspace). */
 lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy,
                      double* mu, int32_t on_device);
 

@@ -478,6 +478,22 @@ lb_status stats_restart(lb_handle* h, int i)
 
 lb_status check_handle(lb_handle* h) { return h ? LB_OK : LB_E_INVALID; }
 
+// The device address of host memory that kernels can read and write
+// directly (page-locked and mapped, as cudaHostAlloc memory is under unified
+// addressing), or nullptr for pageable memory. Kernels then move the data
+// over the host link themselves, overlapping it with their arithmetic,
+// instead of a copy before or after them.
+template <typename P>
+P* mapped_view(P* p)
+{
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // a pageable pointer may leave an error behind on older runtimes
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<P*>(a.devicePointer) : nullptr;
+}
+
 // Failure-detection self-test: one thread waits, bounded like every wait of
 // the step kernels, on an mbarrier phase that nothing completes (no copy is
 // issued, no other thread arrives), then records the give-up in the status
@@ -650,8 +666,13 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
     lb_status s = LB_OK;
     const double* d_rho0 = rho0;
     if (!on_device) {
-        s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
-        d_rho0 = s0;
+        // page-locked host rho0 is read by rho0_kernel itself
+        const double* m = mapped_view(rho0);
+        if (m)
+            d_rho0 = m;
+        else
+            s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
+        if (!m) d_rho0 = s0;
     }
     const double* pux = nullptr;
     const double* puy = nullptr;
@@ -1074,12 +1095,22 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
     const size_t bytes = (size_t)c.nx * c.ny * sizeof(double);
     double* outs[4] = {rho, ux, uy, mu};
     double* dst[4];
-    for (int k = 0; k < 4; ++k) dst[k] = outs[k] ? (on_device ? outs[k] : h->scratch(4 + k)) : nullptr;
+    bool staged[4] = {false, false, false, false};
+    for (int k = 0; k < 4; ++k) {
+        dst[k] = outs[k];
+        if (outs[k] && !on_device) {
+            // page-locked host outputs are written by the export kernel itself
+            double* m = mapped_view(outs[k]);
+            staged[k] = m == nullptr;
+            dst[k] = m ? m : h->scratch(4 + k);
+        }
+    }
     lb_status s = fields_pass(h, case_id, dst[0], dst[1], dst[2], dst[3]);
     if (s != LB_OK) return s;
     if (!on_device) {
         for (int k = 0; k < 4 && s == LB_OK; ++k)
-            if (outs[k]) s = h->cuda(cudaMemcpyAsync(outs[k], dst[k], bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
+            if (staged[k])
+                s = h->cuda(cudaMemcpyAsync(outs[k], dst[k], bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
         if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "moments sync");
     }
     return s;

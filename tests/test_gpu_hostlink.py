@@ -1,0 +1,71 @@
+"""Host buffers of lb_init_fields and lb_moments: page-locked host memory is
+read and written by the kernels themselves over the host link, pageable
+memory is staged through the workspace; both give the same bits as device
+buffers."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import thermo
+from paper_2008_01473_gb300 import inputs, lbfe
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_01473_gb300 import build
+
+    build.build()
+
+
+def _pops(lat, nx, ny):
+    """Snapshot header and the stored populations at the lattice columns (the
+    row padding up to the pitch is never written)."""
+    snap = lat.save(0)
+    dt = np.float32 if lat.precision == lbfe.FP32 else np.float64
+    pitch = (nx + 31) // 32 * 32
+    raw = np.frombuffer(snap[16:], dtype=dt).reshape(9, ny, pitch)[:, :, :nx]
+    return np.concatenate([np.frombuffer(snap[:16], dtype=np.uint8).astype(np.float64),
+                           raw.astype(np.float64).ravel()])
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP32, lbfe.FP64])
+@pytest.mark.parametrize("shape", [(96, 72), (37, 29)])
+def test_pinned_host_buffers_match_pageable_and_device(precision, shape):
+    import torch
+
+    nx, ny = shape
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    case = lbfe.Case(nx=nx, ny=ny, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, R=1.0,
+                     T=T, kappa=0.02, tau_v=0.8)
+    rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=9)
+    pinned = torch.from_numpy(rho0.copy()).pin_memory()
+    a = lbfe.Lattice([case], precision=precision)
+    b = lbfe.Lattice([case], precision=precision)
+    a.init_fields(0, rho0)     # pageable: staged
+    b.init_fields(0, pinned)   # page-locked: read by the init kernel
+    assert np.array_equal(_pops(a, nx, ny), _pops(b, nx, ny))
+    a.step(7)
+    names = ("rho", "ux", "uy", "mu")
+    pin_out = {k: torch.empty((ny, nx), dtype=torch.float64).pin_memory() for k in names}
+    lbfe._check(lbfe.lib().lb_moments(a._h, 0, *[C.c_void_p(pin_out[k].data_ptr()) for k in names], 0), a._h)
+    host = a.moments(0)                    # pageable outputs
+    dev = a.moments(0, on_device=True)     # device outputs
+    for k in names:
+        assert np.array_equal(pin_out[k].numpy(), host[k]), k
+        assert np.array_equal(dev[k].cpu().numpy(), host[k]), k
+    # a subset of outputs (the others NULL), mixed page-locked and pageable
+    rho_only = torch.zeros((ny, nx), dtype=torch.float64).pin_memory()
+    uy_host = np.zeros((ny, nx))
+    lbfe._check(lbfe.lib().lb_moments(a._h, 0, C.c_void_p(rho_only.data_ptr()), None,
+                                      C.c_void_p(uy_host.ctypes.data), None, 0), a._h)
+    assert np.array_equal(rho_only.numpy(), host["rho"]) and np.array_equal(uy_host, host["uy"])
+    a.close()
+    b.close()
