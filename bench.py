@@ -401,6 +401,7 @@ def run_gpu(args):
                                     "narrow_blocks": narrow}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
+                         "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                          "traffic": _profiled_traffic(n_side) if dtype == "f32" else None,
                          "peak_source": src, "bytes_per_node": BYTES_PER_NODE[dtype],
                          "kernel_ms_mean": round(mean_ms, 4), "kernel_ms_min": round(min(per), 4)}
