@@ -114,8 +114,10 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * to the wall state's pressure (rho_wall / 3, or p_m of Eq. 24), so rho_wall
  * is the density of the fluid that touches the walls (rho_g for a droplet in
  * its vapour): another value drives that fluid at wall_u times the ratio of
- * the two pressures. Needs ny >= 8; runs on the one-column step kernel; no
- * adjoint and no lb_fields_static. */
+ * the two pressures. Needs ny >= 8. FP32 cases with nx % 4 == 0 (schemes
+ * other than LB_IMPROVED_SMOOTH) run on the packed kernel, whose row ring
+ * holds the ghost rows with their planes reflected; the others on the
+ * one-column step kernel. No adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
     int32_t scheme;      /* LB_STANDARD, LB_IMPROVED, LB_STANDARD_PT, LB_IMPROVED_SMOOTH or LB_LAX_WENDROFF */
@@ -164,12 +166,12 @@ lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, cons
 
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
  * Eq. 10): one fused kernel launch per step and per group of cases that
- * share scheme, collision, EOS, viscosity mode and nx % 4 == 0; each launch
+ * share scheme, collision, EOS, viscosity mode, nx % 4 == 0 and walls; each launch
  * runs a work-list of (case, column strip, row segment) items. FP32 cases
  * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
- * FP64 cases, other widths, walled cases, Lax-Wendroff cases and
- * LB_IMPROVED_SMOOTH cases narrower than 8 run the one-column plain-load
- * kernel. The first
+ * FP64 cases, other widths, Lax-Wendroff cases and LB_IMPROVED_SMOOTH cases
+ * narrower than 8 or with walls run the one-column plain-load kernel. The
+ * first
  * call with nsteps > 0 autotunes the work-list: it times one step under
  * several row-segment sizes, with and without narrow blocks for the lattices
  * that fit them better, and keeps the fastest (these trial launches read
@@ -203,8 +205,8 @@ lb_status lb_step(lb_handle* h, int64_t nsteps);
  * mode: 0 never; 1 always (an FP32 group with nx % 4 == 0 then leaves the
  * packed kernel for the one-column one, whose FP32 rounding differs in the
  * last bits); 2 (default) automatic: for a handle whose group already runs
- * the one-column kernel (FP64; FP32 with nx % 4 != 0, walls or
- * LB_IMPROVED_SMOOTH), the first lb_step of at least 40 steps times 16 steps
+ * the one-column kernel (FP64; FP32 with nx % 4 != 0, Lax-Wendroff or
+ * LB_IMPROVED_SMOOTH with walls or narrower than 8), the first lb_step of at least 40 steps times 16 steps
  * of graph replay against 16 persistent steps (its own steps: results are
  * identical either way) and keeps the faster; -1 leaves the mode unchanged.
  * *persistent (may be NULL) tells whether the persistent launch is in use.

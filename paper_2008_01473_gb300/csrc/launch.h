@@ -19,26 +19,28 @@ constexpr int kPairWide = 0, kPairNarrow = 1;  // packed-kernel shapes (nt value
 // The plain-load kernel always uses kStepThreads. stats: launch the variant
 // that records the per-step statistics (the packed and plain-load kernels;
 // the one-column TMA shapes always accumulate and check st_hist).
+// walls: the group holds lattices with walls (the packed kernel's variant
+// that runs them).
 cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, int nblocks,
                             cudaStream_t s, const float* fin, float* fout, const DevCase<float>* cases,
-                            const Item* items, int* status, bool stats = false);
+                            const Item* items, int* status, bool stats = false, bool walls = false);
 cudaError_t launch_step_f64(int scheme, int coll, int eos, bool nu, int nblocks, cudaStream_t s,
                             const double* fin, double* fout, const DevCase<double>* cases,
                             const Item* items, int* status, bool stats = false);
-int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt);
+int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool walls = false);
 // the packed FP32 kernel of scheme S for a collision / EOS / viscosity mode,
 // wide or narrow shape, without or with the per-step statistics
 // (instantiated in step_f32_pair<S>.cu and step_f32_pair<S>s.cu)
 template <int S, bool ST>
-void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow);
-extern template void* pick_pair_scheme<0, false>(int, int, bool, bool);
-extern template void* pick_pair_scheme<1, false>(int, int, bool, bool);
-extern template void* pick_pair_scheme<2, false>(int, int, bool, bool);
-extern template void* pick_pair_scheme<3, false>(int, int, bool, bool);
-extern template void* pick_pair_scheme<0, true>(int, int, bool, bool);
-extern template void* pick_pair_scheme<1, true>(int, int, bool, bool);
-extern template void* pick_pair_scheme<2, true>(int, int, bool, bool);
-extern template void* pick_pair_scheme<3, true>(int, int, bool, bool);
+void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow, bool walls);
+extern template void* pick_pair_scheme<0, false>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<1, false>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<2, false>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<3, false>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<0, true>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<1, true>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<2, true>(int, int, bool, bool, bool);
+extern template void* pick_pair_scheme<3, true>(int, int, bool, bool, bool);
 // the plain-load one-column kernel with the per-step statistics (step_f32s.cu,
 // step_f64s.cu); nullptr where it has no instantiation
 void* pick_plain_stats_f32(int scheme, int coll, int eos, bool nu);

@@ -31,12 +31,13 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
-// cases that only the one-column plain-load kernel runs: walls, the
-// Lax-Wendroff scheme, and the averaged correction on lattices narrower than
-// its 8-column ring margin
+// cases that only the one-column plain-load kernel runs: the Lax-Wendroff
+// scheme, and the averaged correction with walls (its stage D pulls rows
+// again from global memory) or on lattices narrower than its 8-column ring
+// margin
 bool one_column_only(const lb_case& c)
 {
-    return c.walls || c.scheme == LB_LAX_WENDROFF || (c.scheme == LB_IMPROVED_SMOOTH && c.nx < 8);
+    return c.scheme == LB_LAX_WENDROFF || (c.scheme == LB_IMPROVED_SMOOTH && (c.nx < 8 || c.walls));
 }
 
 // Widest strip of output columns a block of nt threads can own. Lattices with
@@ -213,6 +214,7 @@ struct Group {
     bool tma;              // TMA-staged kernel (FP32, every nx % 4 == 0)
     int nt;                // compute threads per block
     int64_t first, count;  // slice of the item array
+    bool walls = false;    // lattices with walls (the packed kernel's variant for them)
 };
 
 }  // namespace
@@ -351,7 +353,7 @@ void build_items(lb_handle* h)
     h->items.clear();
     h->groups.clear();
     // one group (one launch per step) per kernel variant and block shape
-    auto emit = [&](const std::vector<int>& members, int s, int co, int e, int nu, bool tma, int nt) {
+    auto emit = [&](const std::vector<int>& members, int s, int co, int e, int nu, bool tma, int nt, bool walls) {
         if (members.empty()) return;
         double nodes = 0;
         for (int i : members) nodes += (double)h->cases[i].nx * h->cases[i].ny;
@@ -359,10 +361,11 @@ void build_items(lb_handle* h)
                           : nt == kPairWide   ? kPairCols256
                           : nt == kPairNarrow ? kPairCols128
                                               : nt;  // columns per block
-        const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt)
+        const int occ = h->prec == LB_FP32 ? occupancy_step_f32(s, co, e, nu == 1, tma, nt, walls && tma)
                                            : occupancy_step_f64(s, co, e, nu == 1);
         const double slots = (double)sms * occ;
         Group g{s, co, e, nu == 1, tma, nt, (int64_t)h->items.size(), 0};
+        g.walls = walls && tma;
         for (int i : members) {
             const lb_case& c = h->cases[i];
             int ns = strips_of(c, width);
@@ -408,24 +411,27 @@ void build_items(lb_handle* h)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu)
-                    for (int al = 0; al < 3; ++al) {
-                        // al: lattices with nx % 4 == 0 (TMA-eligible), without, and
-                        // lattices with walls (the plain-load kernel pulls across them) or
-                        // with scheme 3 (whose wider stencil only that kernel has)
+                    for (int al = 0; al < 4; ++al) {
+                        // al: 0 lattices with nx % 4 != 0; 1 with nx % 4 == 0 (TMA-eligible);
+                        // 2 the cases only the plain-load kernel runs; 3 with nx % 4 == 0
+                        // and walls (the packed kernel's variant for walls)
                         // (the one-column TMA shapes of LBFE_STEP_THREADS do not run scheme 3)
-                        const bool tma = h->prec == LB_FP32 && h->path != 1 && al == 1 &&
+                        const bool tma = h->prec == LB_FP32 && h->path != 1 && (al == 1 || al == 3) &&
                                          !(s == LB_IMPROVED_SMOOTH && h->tma_threads != 0);
                         const bool pair = tma && h->tma_threads == 0;
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {
                             const lb_case& c = h->cases[i];
-                            const int kind = one_column_only(c) ? 2 : (c.nx % 4 == 0 ? 1 : 0);
+                            // (the one-column TMA shapes pull no walls)
+                            const bool plain = one_column_only(c) || (c.walls && h->tma_threads != 0);
+                            const int kind = plain ? 2 : c.nx % 4 != 0 ? 0 : c.walls ? 3 : 1;
                             if (c.scheme == s && c.collision == co && c.eos == e && (c.nu > 0) == (nu == 1) &&
                                 kind == al)
                                 (pair && h->narrow && prefers_narrow(c) ? narrow : members).push_back(i);
                         }
-                        emit(members, s, co, e, nu, tma, !tma ? kStepThreads : pair ? kPairWide : h->tma_threads);
-                        emit(narrow, s, co, e, nu, tma, kPairNarrow);
+                        emit(members, s, co, e, nu, tma, !tma ? kStepThreads : pair ? kPairWide : h->tma_threads,
+                             al == 3);
+                        emit(narrow, s, co, e, nu, tma, kPairNarrow, al == 3);
                     }
     // work items per case (the blocks one step of the case launches)
     h->case_items.assign(h->cases.size(), 0);
@@ -726,7 +732,7 @@ static lb_status enqueue_step(lb_handle* h, int cur, cudaStream_t st)
         if (h->prec == LB_FP32)
             e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, gs,
                                 (const float*)h->fbuf(cur), (float*)h->fbuf(cur ^ 1), h->dc32(),
-                                h->ditems() + g.first, h->status(), h->st_live);
+                                h->ditems() + g.first, h->status(), h->st_live, g.walls);
         else
             e = launch_step_f64(g.scheme, g.coll, g.eos, g.nu, (int)g.count, gs, (const double*)h->fbuf(cur),
                                 (double*)h->fbuf(cur ^ 1), h->dc64(), h->ditems() + g.first, h->status(),

@@ -10,21 +10,21 @@ namespace lbfe {
 namespace {
 // the packed kernel (nullptr for the Lax-Wendroff scheme, which it does not run)
 template <bool ST>
-void* pick_pair_st(int scheme, int coll, int eos, bool nu, bool narrow)
+void* pick_pair_st(int scheme, int coll, int eos, bool nu, bool narrow, bool walls)
 {
     switch (scheme) {
-    case 0: return pick_pair_scheme<0, ST>(coll, eos, nu, narrow);
-    case 1: return pick_pair_scheme<1, ST>(coll, eos, nu, narrow);
-    case 2: return pick_pair_scheme<2, ST>(coll, eos, nu, narrow);
-    case 3: return pick_pair_scheme<3, ST>(coll, eos, nu, narrow);
+    case 0: return pick_pair_scheme<0, ST>(coll, eos, nu, narrow, walls);
+    case 1: return pick_pair_scheme<1, ST>(coll, eos, nu, narrow, walls);
+    case 2: return pick_pair_scheme<2, ST>(coll, eos, nu, narrow, walls);
+    case 3: return pick_pair_scheme<3, ST>(coll, eos, nu, narrow, walls);
     default: return nullptr;
     }
 }
 
-void* pick_pair(int scheme, int coll, int eos, bool nu, bool narrow, bool stats)
+void* pick_pair(int scheme, int coll, int eos, bool nu, bool narrow, bool stats, bool walls)
 {
-    return stats ? pick_pair_st<true>(scheme, coll, eos, nu, narrow)
-                 : pick_pair_st<false>(scheme, coll, eos, nu, narrow);
+    return stats ? pick_pair_st<true>(scheme, coll, eos, nu, narrow, walls)
+                 : pick_pair_st<false>(scheme, coll, eos, nu, narrow, walls);
 }
 
 // NT = kPairWide / kPairNarrow select the two-columns-per-thread packed
@@ -68,12 +68,12 @@ int block_threads(bool tma, int nt)
     return !tma ? kStepThreads : nt == kPairWide ? kPairThreads : nt == kPairNarrow ? kPairThreadsNarrow : nt + 32;
 }
 
-void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool stats = false)
+void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool stats = false, bool walls = false)
 {
     void* k = !tma                ? (stats ? pick_plain_stats_f32(scheme, coll, eos, nu)
                                            : pick<false, kStepThreads>(scheme, coll, eos, nu))
-              : nt == kPairWide   ? pick_pair(scheme, coll, eos, nu, false, stats)
-              : nt == kPairNarrow ? pick_pair(scheme, coll, eos, nu, true, stats)
+              : nt == kPairWide   ? pick_pair(scheme, coll, eos, nu, false, stats, walls)
+              : nt == kPairNarrow ? pick_pair(scheme, coll, eos, nu, true, stats, walls)
               : nt == 128    ? pick<true, 128>(scheme, coll, eos, nu)
               : nt == 256    ? pick<true, 256>(scheme, coll, eos, nu)
                              : nullptr;
@@ -89,18 +89,18 @@ void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool sta
 
 cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, int nblocks,
                             cudaStream_t s, const float* fin, float* fout, const DevCase<float>* cases,
-                            const Item* items, int* status, bool stats)
+                            const Item* items, int* status, bool stats, bool walls)
 {
-    void* k = resolve(scheme, coll, eos, nu, tma, nt, stats);
+    void* k = resolve(scheme, coll, eos, nu, tma, nt, stats, walls);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
     // the TMA kernels add one producer warp to their compute threads
     return cudaLaunchKernel(k, dim3(nblocks), dim3(block_threads(tma, nt)), args, tma ? tma_smem(nt) : 0, s);
 }
 
-int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt)
+int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool walls)
 {
-    void* k = resolve(scheme, coll, eos, nu, tma, nt);
+    void* k = resolve(scheme, coll, eos, nu, tma, nt, false, walls);
     int n = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block_threads(tma, nt),
                                                             tma ? tma_smem(nt) : 0) != cudaSuccess)

@@ -10,18 +10,29 @@
 
 namespace lbfe {
 
-template <int S, int C, int E, bool NU, bool ST>
-void* pair_ptr(bool narrow)
+template <int S, int C, int E, bool NU, bool ST, bool WL>
+void* pair_ptr_w(bool narrow)
 {
-    return narrow ? reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow, ST>)
-                  : reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads, ST>);
+    return narrow ? reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreadsNarrow, ST, WL>)
+                  : reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads, ST, WL>);
+}
+
+// the variant for lattices with walls exists for schemes 0-2
+template <int S, int C, int E, bool NU, bool ST>
+void* pair_ptr(bool narrow, bool walls)
+{
+    if constexpr (S == 3)
+        return walls ? nullptr : pair_ptr_w<S, C, E, NU, ST, false>(narrow);
+    else
+        return walls ? pair_ptr_w<S, C, E, NU, ST, true>(narrow) : pair_ptr_w<S, C, E, NU, ST, false>(narrow);
 }
 
 template <int S, bool ST>
-void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow)
+void* pick_pair_scheme(int coll, int eos, bool nu, bool narrow, bool walls)
 {
-#define LBFE_PICK(C, E) \
-    if (coll == C && eos == E) return nu ? pair_ptr<S, C, E, true, ST>(narrow) : pair_ptr<S, C, E, false, ST>(narrow);
+#define LBFE_PICK(C, E)                                                                                 \
+    if (coll == C && eos == E)                                                                          \
+        return nu ? pair_ptr<S, C, E, true, ST>(narrow, walls) : pair_ptr<S, C, E, false, ST>(narrow, walls);
     LBFE_PICK(0, 0) LBFE_PICK(0, 1) LBFE_PICK(1, 0) LBFE_PICK(1, 1)
 #undef LBFE_PICK
     return nullptr;

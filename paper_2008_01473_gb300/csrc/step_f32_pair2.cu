@@ -2,5 +2,5 @@
 #include "step_f32_pair.cuh"
 
 namespace lbfe {
-template void* pick_pair_scheme<2, false>(int coll, int eos, bool nu, bool narrow);
+template void* pick_pair_scheme<2, false>(int coll, int eos, bool nu, bool narrow, bool walls);
 }  // namespace lbfe

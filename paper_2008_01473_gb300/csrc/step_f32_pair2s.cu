@@ -3,5 +3,5 @@
 #include "step_f32_pair.cuh"
 
 namespace lbfe {
-template void* pick_pair_scheme<2, true>(int coll, int eos, bool nu, bool narrow);
+template void* pick_pair_scheme<2, true>(int coll, int eos, bool nu, bool narrow, bool walls);
 }  // namespace lbfe

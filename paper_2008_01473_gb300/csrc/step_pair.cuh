@@ -326,6 +326,7 @@ struct PairCtx {
     // this thread's share of a row refill: one (plane, run) copy, or none
     const float* iss_src;  // source of the copy in row 0
     uint32_t iss_dst;      // ring offset of the copy within a slot (floats)
+    uint32_t iss_dst_refl; // the same for a ghost row beyond a wall (plane reflected in y)
     uint32_t iss_bytes;
     bool iss_on;
 };
@@ -391,26 +392,42 @@ __device__ __forceinline__ void pair_issue_setup(PairCtx& X, const DevCase<float
     const int g0 = r == 0 ? X.runs.g0[0] : (r == 1 ? X.runs.g0[1] : X.runs.g0[2]);
     const int j0 = r == 0 ? X.runs.j0[0] : (r == 1 ? X.runs.j0[1] : X.runs.j0[2]);
     const int len = r == 0 ? X.runs.len[0] : (r == 1 ? X.runs.len[1] : X.runs.len[2]);
+    constexpr int refl[kQ] = {0, 1, 4, 3, 2, 8, 7, 6, 5};  // e_a with e_y negated
     X.iss_src = X.fin + ((uint32_t)a * (uint32_t)c.plane + (uint32_t)g0);
     X.iss_dst = (uint32_t)(a * 2 * NP + j0);
+    X.iss_dst_refl = (uint32_t)(refl[a] * 2 * NP + j0);
     X.iss_bytes = (uint32_t)len * sizeof(float);
 }
 
+// Row offset of the stored row that fills window row s, and whether the slot
+// takes its planes reflected in y: periodic lattices wrap; with walls, a
+// ghost row beyond a wall is the mirror image of row nb_row(s) (R19), whose
+// populations the slot holds reflected (2 <-> 4, 5 <-> 8, 6 <-> 7), so that
+// the plain pull of stage A reads the mirrored state.
+__device__ __forceinline__ uint32_t window_row(const DevCase<float>& c, int s, bool& reflected)
+{
+    const int m = c.walls ? nb_row(c, s) : wrapi(s, c.ny);
+    reflected = c.walls && m != s;
+    return (uint32_t)m * c.pitch;
+}
+
 // Copy the stored row at row offset `row` (row * pitch) into a slot whose
-// mbarrier is `bar`. (A copy may complete before the arming arrive; the
-// phase cannot complete before it, since that arrive is the phase's only
-// one.) Called by the first pair_issuers(NP) threads only.
-__device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64_t* bar, uint32_t row)
+// mbarrier is `bar`, its planes reflected in y if `refl`. (A copy may
+// complete before the arming arrive; the phase cannot complete before it,
+// since that arrive is the phase's only one.) Called by the first
+// pair_issuers(NP) threads only.
+__device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64_t* bar, uint32_t row,
+                                           bool refl = false)
 {
     if (threadIdx.x == 0) mbar_expect_tx(bar, X.row_bytes);
     if (X.iss_on) {
         // order earlier generic-proxy reads of the slot before the async refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(slot + X.iss_dst, X.iss_src + row, X.iss_bytes, bar);
+        bulk_load(slot + (refl ? X.iss_dst_refl : X.iss_dst), X.iss_src + row, X.iss_bytes, bar);
     }
 }
 
-template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT, bool ST>
+template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT, bool ST, bool WL>
 __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME, 2 * NP>& sm,
                                           PairRegs<SCHEME>& R)
 {
@@ -443,6 +460,36 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jq]);
         F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jq]);
         F[8] = make_float2(Rp[8 * SW + jm], Rp[8 * SW + j]);
+        if (WL && c.walls) {
+            // With ghost rows held reflected, the plain pull above is the
+            // wall reading everywhere but for the diagonals that cross a wall
+            // (halfway bounce-back with the moving-wall term): on the wall
+            // rows themselves and, mirrored, on the ghost rows next to them.
+            // They are the wall row's own outgoing populations.
+            const int sa = X.s0 + it + 1;  // window row of stage A
+            const float2 wd = v2(c.wall_d);
+            if (sa == 0 || sa == -1) {
+                const float* W = sa == 0 ? R0 : Rp;  // slot of row 0
+                const float2 f7 = ld2(W + 7 * SW + j), f8 = ld2(W + 8 * SW + j);
+                if (sa == 0) {
+                    F[5] = f7 + wd;
+                    F[6] = f8 - wd;
+                } else {
+                    F[8] = f7 + wd;
+                    F[7] = f8 - wd;
+                }
+            } else if (sa == c.ny - 1 || sa == c.ny) {
+                const float* W = sa == c.ny - 1 ? R0 : Rm;  // slot of row ny - 1
+                const float2 f5 = ld2(W + 5 * SW + j), f6 = ld2(W + 6 * SW + j);
+                if (sa == c.ny - 1) {
+                    F[7] = f5 - wd;
+                    F[8] = f6 + wd;
+                } else {
+                    F[5] = f6 + wd;
+                    F[6] = f5 - wd;
+                }
+            }
+        }
         const float2 dr = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
         R.drho[S0] = dr;
         R.jx[S0] = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
@@ -642,7 +689,15 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     // stored row it (ra - 1) has had no reader since stage A's barrier: refill
     // its slot now, with the iteration's arithmetic issued (the copy still has
     // two iterations of lead before stage A needs it)
-    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last) pair_issue(X, X.pRm, X.fm, X.irow);
+    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last) {
+        if (WL && c.walls) {
+            bool refl;
+            const uint32_t row = window_row(c, X.s0 + it + kPairSlots, refl);
+            pair_issue(X, X.pRm, X.fm, row, refl);
+        } else {
+            pair_issue(X, X.pRm, X.fm, X.irow);
+        }
+    }
     // advance the ring, the refill row and the output row by one (wrapping
     // compares instead of row modulos and multiplies)
     X.irow = X.irow + c.pitch == X.plane_rows ? 0u : X.irow + c.pitch;
@@ -675,8 +730,9 @@ constexpr size_t pair_dynamic_smem()
 // so that each margin of the ring is one copy run); every item x0 % 4 == 0,
 // wv % 4 == 0, wv + 2 M <= 2 NP with M = PairGeom<SCHEME>::M (4, or 8 for
 // scheme 3). ST: the variant that also records the per-step statistics
-// (stats_block) of the cases whose record has st_hist != 0.
-template <int SCHEME, int COLL, int EOS, bool NU, int NP, bool ST = false>
+// (stats_block) of the cases whose record has st_hist != 0. WL: the variant
+// that also runs lattices with walls (schemes 0-2).
+template <int SCHEME, int COLL, int EOS, bool NU, int NP, bool ST = false, bool WL = false>
 __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pair(const float* __restrict__ fin,
                                                                     float* __restrict__ fout,
                                                                     const DevCase<float>* __restrict__ cases,
@@ -685,6 +741,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
 {
     using G = StepGeom<SCHEME>;
     static_assert(SCHEME != 4, "scheme 4 runs on the plain-load kernel only");
+    static_assert(!(WL && SCHEME == 3), "scheme 3 with walls runs on the plain-load kernel only");
     constexpr int M = PairGeom<SCHEME>::M;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
@@ -733,8 +790,11 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     }
     __syncthreads();
     if (threadIdx.x < pair_issuers(NP))
-        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i)
-            pair_issue(X, X.ring + i * kQ * (2 * NP), X.full + i, (uint32_t)wrapi(X.s0 + i, c.ny) * c.pitch);
+        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) {
+            bool refl;
+            const uint32_t row = window_row(c, X.s0 + i, refl);
+            pair_issue(X, X.ring + i * kQ * (2 * NP), X.full + i, row, refl);
+        }
 
     const int p = threadIdx.x;
     X.j = 2 * p;
@@ -769,13 +829,13 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     R.am = R.ak = v2(0.0f);
     R.au = 0.0f;
     for (int base = 0; base < niter; base += 4) {
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 0, ST>(base, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 0, ST, WL>(base, X, c, sm, R);
         if (base + 1 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 1, ST>(base + 1, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 1, ST, WL>(base + 1, X, c, sm, R);
         if (base + 2 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 2, ST>(base + 2, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 2, ST, WL>(base + 2, X, c, sm, R);
         if (base + 3 >= niter) break;
-        pair_iter<SCHEME, COLL, EOS, NU, NP, 3, ST>(base + 3, X, c, sm, R);
+        pair_iter<SCHEME, COLL, EOS, NU, NP, 3, ST, WL>(base + 3, X, c, sm, R);
     }
     // every issued row was waited on by stage A; after a timeout, drain (bounded)
     __syncthreads();
