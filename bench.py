@@ -286,6 +286,7 @@ def _host_link(rho0_pin, res, stream) -> dict:
 
 
 def run_gpu(args):
+    import numpy as np
     import torch
 
     from paper_2008_01473_gb300 import build, inputs, lbfe
@@ -355,18 +356,27 @@ def run_gpu(args):
     # ------------------------------------------------------------ end to end
     import ctypes as C
 
-    res = {k: torch.empty((n_side, n_side), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy")}
+    # The fields cross the host link in the handle's own precision: FP32
+    # handles compute every per-node field in FP32 (FP64 only in the global
+    # sums), so they take rho0 and return rho, u as FP32 (the _f32 calls).
+    f32_io = prec == lbfe.FP32
+    fdt = torch.float32 if f32_io else torch.float64
+    fbytes = 4 if f32_io else 8
+    e2e_rho0 = torch.from_numpy(rho0.astype(np.float32) if f32_io else rho0).pin_memory()
+    res = {k: torch.empty((n_side, n_side), dtype=fdt).pin_memory() for k in ("rho", "ux", "uy")}
+    init_fn = lbfe.lib().lb_init_fields_f32 if f32_io else lbfe.lib().lb_init_fields
+    moments_fn = lbfe.lib().lb_moments_f32 if f32_io else lbfe.lib().lb_moments
 
     def end_to_end():
-        lat.init_fields(0, rho0_pin)
+        lbfe._check(init_fn(lat._h, 0, C.c_void_p(e2e_rho0.data_ptr()), None, None, 0), lat._h)
         lat.step(args.steps)
-        rc = lbfe.lib().lb_moments(lat._h, 0, C.c_void_p(res["rho"].data_ptr()), C.c_void_p(res["ux"].data_ptr()),
-                                   C.c_void_p(res["uy"].data_ptr()), None, 0)
+        rc = moments_fn(lat._h, 0, C.c_void_p(res["rho"].data_ptr()), C.c_void_p(res["ux"].data_ptr()),
+                        C.c_void_p(res["uy"].data_ptr()), None, 0)
         lbfe._check(rc, lat._h)
 
     for _ in range(2):  # warm-up: graphs for both buffer parities, first use of the pinned outputs
         end_to_end()
-    link = _host_link(rho0_pin, res, stream)
+    link = _host_link(e2e_rho0, res, stream)
     barrier()
     e2e_passes = 3
     t0 = time.perf_counter()
@@ -425,11 +435,13 @@ def run_gpu(args):
             if dtype == "f32" else _fp64_roofline(nodes, mean_ms, achieved / peak),
             "clocks": clk,
             "e2e": {"value": round(_job_mlups(ws, nodes, args.steps, e2e_s * 1e3), 1), "unit": "MLUPS",
-                    "h2d_bytes_per_step": int(8 * nodes / args.steps),
-                    "d2h_bytes_per_step": int((3 * 8 * nodes + 40) / args.steps),
-                    "includes": "lb_init_fields from pinned host rho0 (validated on the device), K lb_step calls, "
-                                "lb_moments of rho, ux, uy to pinned host; mean of 3 passes after 2 warm-up passes",
-                    "host_link_bytes_per_pass": int(8 * nodes + 3 * 8 * nodes), "host_link": link},
+                    "h2d_bytes_per_step": int(fbytes * nodes / args.steps),
+                    "d2h_bytes_per_step": int(3 * fbytes * nodes / args.steps),
+                    "includes": f"lb_init_fields{'_f32' if f32_io else ''} from pinned host rho0 (validated on the "
+                                f"device), one lb_step(K) call, lb_moments{'_f32' if f32_io else ''} of rho, ux, uy "
+                                "to pinned host; mean of 3 passes after 2 warm-up passes",
+                    "field_dtype": "f32" if f32_io else "f64",
+                    "host_link_bytes_per_pass": int(fbytes * nodes + 3 * fbytes * nodes), "host_link": link},
             "gpu_launches": args.steps,
         }
         if cs is not None:

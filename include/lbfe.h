@@ -163,6 +163,13 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
  * kernel directly over the host link). */
 lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
                          const double* uy0, int32_t on_device);
+/* The same with FP32 fields: the state equals lb_init_fields' from the same
+ * values widened to FP64 (rho0 is checked and summed in FP64 all the same).
+ * For FP32 handles, whose per-node arithmetic is FP32 anyway (the precision
+ * pattern keeps FP64 for the global sums only), it halves the bytes that
+ * cross the host link. */
+lb_status lb_init_fields_f32(lb_handle* h, int32_t case_id, const float* rho0, const float* ux0,
+                             const float* uy0, int32_t on_device);
 
 /* Advance every case by nsteps time steps (Eqs. 9-14, 24-29, pull form of
  * Eq. 10): one fused kernel launch per step and per group of cases that
@@ -239,6 +246,10 @@ lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, i
  * over the host link, pageable ones are staged in the workspace). */
 lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy,
                      double* mu, int32_t on_device);
+/* The same with FP32 outputs: each value is lb_moments' rounded to FP32 (for
+ * FP32 handles the exact per-node FP32 value), at half the bytes. */
+lb_status lb_moments_f32(lb_handle* h, int32_t case_id, float* rho, float* ux, float* uy, float* mu,
+                         int32_t on_device);
 
 /* Reductions of every case's current state, FP64 sums in a fixed order:
  * out[5*c + {0,1,2,3,4}] = {mass sum rho, kinetic energy sum rho|u|^2/2,

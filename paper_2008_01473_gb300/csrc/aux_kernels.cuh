@@ -108,12 +108,13 @@ __device__ __forceinline__ void block_sums(double mass, double ke, double um2, i
     }
 }
 
-// Copy the FP64 initial density into C scratch and check it: one Partial per
-// block with the sum of rho0 and the count of values that are not finite,
-// not > 0, or outside the EOS domain (b rho < 1 for vdW, b rho / 4 < 1 for CS).
-template <typename C>
+// Copy the initial density (FP64, or FP32: I) into C scratch and check it:
+// one Partial per block with the sum of rho0 (FP64) and the count of values
+// that are not finite, not > 0, or outside the EOS domain (b rho < 1 for
+// vdW, b rho / 4 < 1 for CS).
+template <typename C, typename I = double>
 __global__ void __launch_bounds__(256) rho0_kernel(int nx, int ny, int eos, double b,
-                                                   const double* __restrict__ rho0, C* __restrict__ out,
+                                                   const I* __restrict__ rho0, C* __restrict__ out,
                                                    Partial* __restrict__ partials)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(256) rho0_kernel(int nx, int ny, int eos, doub
     if (x < nx)
         for (int y = y0; y < y1; ++y) {
             const int64_t i = (int64_t)y * nx + x;
-            const double r = rho0[i];
+            const double r = (double)rho0[i];
             const bool ok = r > 0.0 && r <= 1.7976931348623157e308 && bl * r < 1.0;
             sum += ok ? r : 0.0;
             bad += ok ? 0 : 1;
@@ -303,19 +304,19 @@ __global__ void __launch_bounds__(256) pull_moments_kernel(DevCase<T> c, const T
 }
 
 // Velocity of Eq. 12 from rho, j and the force of the case's scheme; writes
-// the requested FP64 outputs and one Partial per block (blockDim.x == 256,
-// grid field_grid(nx, ny)): per-node arithmetic in C, the thread's sums over
-// its kFieldRows nodes in FP64 registers, max |u|^2 in C, the bad-node count
-// as an integer. SCHEME 2 takes its force from the pressure tensor P (pxx,
-// pxy, pyy).
-template <int SCHEME, typename C>
+// the requested outputs (FP64, or FP32: O) and one Partial per block
+// (blockDim.x == 256, grid field_grid(nx, ny)): per-node arithmetic in C, the
+// thread's sums over its kFieldRows nodes in FP64 registers, max |u|^2 in C,
+// the bad-node count as an integer. SCHEME 2 takes its force from the
+// pressure tensor P (pxx, pxy, pyy).
+template <int SCHEME, typename C, typename O = double>
 __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* __restrict__ rho,
                                                        const C* __restrict__ jx, const C* __restrict__ jy,
                                                        const C* __restrict__ mu, const C* __restrict__ pxx,
                                                        const C* __restrict__ pxy, const C* __restrict__ pyy,
-                                                       double* __restrict__ out_rho,
-                                                       double* __restrict__ out_ux, double* __restrict__ out_uy,
-                                                       double* __restrict__ out_mu, Partial* __restrict__ partials)
+                                                       O* __restrict__ out_rho, O* __restrict__ out_ux,
+                                                       O* __restrict__ out_uy, O* __restrict__ out_mu,
+                                                       Partial* __restrict__ partials)
 {
     const int nx = cc.nx, ny = cc.ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,10 +364,10 @@ __global__ void __launch_bounds__(256) velocity_kernel(DevCase<C> cc, const C* _
             const C ux = (jx[i] + half * Fx) / r;
             const C uy = (jy[i] + half * Fy) / r;
             const C m = mu[i];
-            if (out_rho) out_rho[i] = (double)r;
-            if (out_ux) out_ux[i] = (double)ux;
-            if (out_uy) out_uy[i] = (double)uy;
-            if (out_mu) out_mu[i] = (double)m;
+            if (out_rho) out_rho[i] = (O)r;
+            if (out_ux) out_ux[i] = (O)ux;
+            if (out_uy) out_uy[i] = (O)uy;
+            if (out_mu) out_mu[i] = (O)m;
             const C u2 = ux * ux + uy * uy;
             mass += (double)r;
             ke += (double)(C(0.5) * r * u2);

@@ -516,8 +516,8 @@ __global__ void wait_selftest_kernel(int* status)
 // Pull-moment, chemical-potential and velocity passes for one case, in the
 // storage precision C per node (FP64 sums); outputs may be device pointers
 // or NULL. Partials of the case land in h->partials().
-template <typename T, typename C>
-lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
+template <typename T, typename C, typename O>
+lb_status fields_pass_t(lb_handle* h, int i, O* o_rho, O* o_ux, O* o_uy, O* o_mu)
 {
     const lb_case& c = h->cases[i];
     DevCase<T> ct = dev_case<T>(c, h->L.off[i], h->rho_ref[i]);
@@ -534,7 +534,7 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
     else
         mu_field_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, s3);
     if (improved_scheme(c.scheme)) {
-        velocity_kernel<1, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+        velocity_kernel<1, C, O><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
                                                           o_uy, o_mu, h->partials());
     } else if (c.scheme == LB_STANDARD_PT) {
         C* p0 = reinterpret_cast<C*>(h->scratch(8));
@@ -544,36 +544,46 @@ lb_status fields_pass_t(lb_handle* h, int i, double* o_rho, double* o_ux, double
             ptensor_kernel<C, 0><<<grd, blk, 0, h->stream>>>(cc, s0, p0, p1, p2);
         else
             ptensor_kernel<C, 1><<<grd, blk, 0, h->stream>>>(cc, s0, p0, p1, p2);
-        velocity_kernel<2, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, p0, p1, p2, o_rho, o_ux, o_uy, o_mu,
+        velocity_kernel<2, C, O><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, p0, p1, p2, o_rho, o_ux, o_uy, o_mu,
                                                           h->partials());
     } else if (c.scheme == LB_LAX_WENDROFF) {
-        velocity_kernel<4, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+        velocity_kernel<4, C, O><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
                                                           o_uy, o_mu, h->partials());
     } else {
-        velocity_kernel<0, C><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
+        velocity_kernel<0, C, O><<<grd, blk, 0, h->stream>>>(cc, s0, s1, s2, s3, nullptr, nullptr, nullptr, o_rho, o_ux,
                                                           o_uy, o_mu, h->partials());
     }
     return h->cuda(cudaGetLastError(), "fields pass");
 }
 
-lb_status fields_pass(lb_handle* h, int i, double* o_rho, double* o_ux, double* o_uy, double* o_mu)
+// outputs of the field type O: double, or float (lb_moments_f32)
+template <typename O>
+lb_status fields_pass(lb_handle* h, int i, O* o_rho, O* o_ux, O* o_uy, O* o_mu)
 {
-    return h->prec == LB_FP32 ? fields_pass_t<float, float>(h, i, o_rho, o_ux, o_uy, o_mu)
-                              : fields_pass_t<double, double>(h, i, o_rho, o_ux, o_uy, o_mu);
+    return h->prec == LB_FP32 ? fields_pass_t<float, float, O>(h, i, o_rho, o_ux, o_uy, o_mu)
+                              : fields_pass_t<double, double, O>(h, i, o_rho, o_ux, o_uy, o_mu);
 }
 
-// Initial populations of case i from the FP64 fields already in scratch
-// (u0 in scratch 1, 2 when given): rho0 -> C scratch 0 with a device-side
-// check, mu_c of rho0, then the equilibrium.
-template <typename T, typename C>
-lb_status init_pass_t(lb_handle* h, int i, const double* d_rho0, const double* pux, const double* puy)
+// FP32 field -> FP64 field (n values), for the FP32 initial velocities.
+__global__ void __launch_bounds__(256) widen_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// Initial populations of case i from rho0 (FP64 or FP32, I) on the device or
+// in mapped host memory and the FP64 u0 fields in scratch 1, 2 when given:
+// rho0 -> C scratch 4 with a device-side check, mu_c of rho0, then the
+// equilibrium.
+template <typename T, typename C, typename I>
+lb_status init_pass_t(lb_handle* h, int i, const I* d_rho0, const double* pux, const double* puy)
 {
     const lb_case& c = h->cases[i];
     const int64_t N = (int64_t)c.nx * c.ny;
     const dim3 blk(256), grd = field_grid(c.nx, c.ny);
     C* r0 = reinterpret_cast<C*>(h->scratch(4));
     C* mu = reinterpret_cast<C*>(h->scratch(5));
-    rho0_kernel<C><<<grd, blk, 0, h->stream>>>(c.nx, c.ny, c.eos, c.b, d_rho0, r0, h->partials());
+    rho0_kernel<C, I><<<grd, blk, 0, h->stream>>>(c.nx, c.ny, c.eos, c.b, d_rho0, r0, h->partials());
     finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials(), (int64_t)grd.x * grd.y, 0.0, h->red() + 8 * i);
     double chk[5];
     lb_status s = h->cuda(cudaMemcpyAsync(chk, h->red() + 8 * i, sizeof chk, cudaMemcpyDeviceToHost, h->stream),
@@ -657,48 +667,73 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
     return LB_OK;
 }
 
-lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
-                         const double* uy0, int32_t on_device)
+extern "C++" {
+// lb_init_fields and lb_init_fields_f32 (field type I)
+template <typename I>
+static lb_status init_fields_t(lb_handle* h, int32_t case_id, const I* rho0, const I* ux0, const I* uy0,
+                               int32_t on_device)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (case_id < 0 || case_id >= (int)h->cases.size() || !rho0)
         return h->fail(LB_E_INVALID, "lb_init_fields: bad case id or null rho0");
     const lb_case& c = h->cases[case_id];
     const int64_t N = (int64_t)c.nx * c.ny;
-    const size_t bytes = N * sizeof(double);
+    const size_t bytes = N * sizeof(I);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     double *s0 = h->scratch(0), *s1 = h->scratch(1), *s2 = h->scratch(2);
     h->steps[case_id] = 0;  // before the case table is uploaded (Lax-Wendroff step-0 flag)
     lb_status s = LB_OK;
-    const double* d_rho0 = rho0;
+    const I* d_rho0 = rho0;
     if (!on_device) {
         // page-locked host rho0 is read by rho0_kernel itself
-        const double* m = mapped_view(rho0);
+        const I* m = mapped_view(rho0);
         if (m)
             d_rho0 = m;
         else
             s = h->cuda(cudaMemcpyAsync(s0, rho0, bytes, kind, h->stream), "copy rho0");
-        if (!m) d_rho0 = s0;
+        if (!m) d_rho0 = reinterpret_cast<const I*>(s0);
     }
-    const double* pux = nullptr;
-    const double* puy = nullptr;
-    if (s == LB_OK && ux0) {
-        s = h->cuda(cudaMemcpyAsync(s1, ux0, bytes, kind, h->stream), "copy ux0");
-        pux = s1;
-    }
-    if (s == LB_OK && uy0) {
-        s = h->cuda(cudaMemcpyAsync(s2, uy0, bytes, kind, h->stream), "copy uy0");
-        puy = s2;
+    // u0 as FP64 in scratch 1, 2 (FP32 u0 is copied to scratch 6, 7, which
+    // the init pass does not use, and widened from there)
+    const double* pu[2] = {nullptr, nullptr};
+    const I* u0[2] = {ux0, uy0};
+    double* su[2] = {s1, s2};
+    for (int k = 0; k < 2 && s == LB_OK; ++k) {
+        if (!u0[k]) continue;
+        if constexpr (sizeof(I) == sizeof(double)) {
+            s = h->cuda(cudaMemcpyAsync(su[k], u0[k], bytes, kind, h->stream), "copy u0");
+        } else {
+            float* tmp = reinterpret_cast<float*>(h->scratch(6 + k));
+            s = h->cuda(cudaMemcpyAsync(tmp, u0[k], bytes, kind, h->stream), "copy u0");
+            if (s == LB_OK) {
+                widen_kernel<<<(unsigned)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, h->stream>>>(tmp, su[k], N);
+                s = h->cuda(cudaGetLastError(), "widen u0");
+            }
+        }
+        pu[k] = su[k];
     }
     if (s != LB_OK) return s;
-    s = h->prec == LB_FP32 ? init_pass_t<float, float>(h, case_id, d_rho0, pux, puy)
-                           : init_pass_t<double, double>(h, case_id, d_rho0, pux, puy);
+    s = h->prec == LB_FP32 ? init_pass_t<float, float, I>(h, case_id, d_rho0, pu[0], pu[1])
+                           : init_pass_t<double, double, I>(h, case_id, d_rho0, pu[0], pu[1]);
     if (s == LB_OK)  // a fresh state clears the case's instability flag
         s = h->cuda(cudaMemsetAsync(h->status() + 1 + case_id, 0, sizeof(int), h->stream), "clear case flag");
     if (s != LB_OK) return s;
     h->steps[case_id] = 0;
     h->inited[case_id] = 1;
     return stats_restart(h, case_id);
+}
+}  // extern "C++"
+
+lb_status lb_init_fields(lb_handle* h, int32_t case_id, const double* rho0, const double* ux0,
+                         const double* uy0, int32_t on_device)
+{
+    return init_fields_t<double>(h, case_id, rho0, ux0, uy0, on_device);
+}
+
+lb_status lb_init_fields_f32(lb_handle* h, int32_t case_id, const float* rho0, const float* ux0, const float* uy0,
+                             int32_t on_device)
+{
+    return init_fields_t<float>(h, case_id, rho0, ux0, uy0, on_device);
 }
 
 // Enqueue one time step (every group) on stream st, reading buffer cur.
@@ -1091,27 +1126,29 @@ lb_status lb_worklist(const lb_handle* h, int32_t* seg_rows, int64_t* n_items, i
     return LB_OK;
 }
 
-lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy, double* mu,
-                     int32_t on_device)
+extern "C++" {
+// lb_moments and lb_moments_f32 (field type O)
+template <typename O>
+static lb_status moments_t(lb_handle* h, int32_t case_id, O* rho, O* ux, O* uy, O* mu, int32_t on_device)
 {
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (case_id < 0 || case_id >= (int)h->cases.size()) return h->fail(LB_E_INVALID, "lb_moments: bad case id");
     if (!h->inited[case_id]) return h->fail(LB_E_STATE, "lb_moments: case not initialised");
     const lb_case& c = h->cases[case_id];
-    const size_t bytes = (size_t)c.nx * c.ny * sizeof(double);
-    double* outs[4] = {rho, ux, uy, mu};
-    double* dst[4];
+    const size_t bytes = (size_t)c.nx * c.ny * sizeof(O);
+    O* outs[4] = {rho, ux, uy, mu};
+    O* dst[4];
     bool staged[4] = {false, false, false, false};
     for (int k = 0; k < 4; ++k) {
         dst[k] = outs[k];
         if (outs[k] && !on_device) {
             // page-locked host outputs are written by the export kernel itself
-            double* m = mapped_view(outs[k]);
+            O* m = mapped_view(outs[k]);
             staged[k] = m == nullptr;
-            dst[k] = m ? m : h->scratch(4 + k);
+            dst[k] = m ? m : reinterpret_cast<O*>(h->scratch(4 + k));
         }
     }
-    lb_status s = fields_pass(h, case_id, dst[0], dst[1], dst[2], dst[3]);
+    lb_status s = fields_pass<O>(h, case_id, dst[0], dst[1], dst[2], dst[3]);
     if (s != LB_OK) return s;
     if (!on_device) {
         for (int k = 0; k < 4 && s == LB_OK; ++k)
@@ -1120,6 +1157,19 @@ lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, dou
         if (s == LB_OK) s = h->cuda(cudaStreamSynchronize(h->stream), "moments sync");
     }
     return s;
+}
+}  // extern "C++"
+
+lb_status lb_moments(lb_handle* h, int32_t case_id, double* rho, double* ux, double* uy, double* mu,
+                     int32_t on_device)
+{
+    return moments_t<double>(h, case_id, rho, ux, uy, mu, on_device);
+}
+
+lb_status lb_moments_f32(lb_handle* h, int32_t case_id, float* rho, float* ux, float* uy, float* mu,
+                         int32_t on_device)
+{
+    return moments_t<float>(h, case_id, rho, ux, uy, mu, on_device);
 }
 
 lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
@@ -1130,7 +1180,7 @@ lb_status lb_reductions(lb_handle* h, double* out, int32_t* case_status)
     for (int i = 0; i < n; ++i)
         if (!h->inited[i]) return h->fail(LB_E_STATE, "lb_reductions: case not initialised");
     for (int i = 0; i < n; ++i) {
-        lb_status s = fields_pass(h, i, nullptr, nullptr, nullptr, nullptr);
+        lb_status s = fields_pass<double>(h, i, nullptr, nullptr, nullptr, nullptr);
         if (s != LB_OK) return s;
         const lb_case& c = h->cases[i];
         const dim3 g = field_grid(c.nx, c.ny);
@@ -1301,7 +1351,7 @@ lb_status lb_window_means(lb_handle* h, int32_t case_id, int32_t nwin, const lb_
         bx[k] = ((bx[k] % c.nx) + c.nx) % c.nx;
         by[k] = ((by[k] % c.ny) + c.ny) % c.ny;
     }
-    lb_status s = fields_pass(h, case_id, nullptr, nullptr, nullptr, nullptr);  // rho -> scratch 0
+    lb_status s = fields_pass<double>(h, case_id, nullptr, nullptr, nullptr, nullptr);  // rho -> scratch 0
     if (s != LB_OK) return s;
     double* res = h->red() + 8 * case_id;  // the case's reduction slot, rewritten by lb_reductions
     std::vector<double> out(5);

@@ -95,6 +95,8 @@ def lib() -> C.CDLL:
         L.lb_workspace_bytes.argtypes = [cp, i32, i32, C.POINTER(sz)]
         L.lb_create.argtypes = [cp, i32, i32, vp, sz, vp, C.POINTER(vp)]
         L.lb_init_fields.argtypes = [vp, i32, vp, vp, vp, i32]
+        L.lb_init_fields_f32.argtypes = [vp, i32, vp, vp, vp, i32]
+        L.lb_moments_f32.argtypes = [vp, i32, vp, vp, vp, vp, i32]
         L.lb_step.argtypes = [vp, i64]
         L.lb_moments.argtypes = [vp, i32, vp, vp, vp, vp, i32]
         L.lb_reductions.argtypes = [vp, dp, C.POINTER(i32)]
@@ -121,7 +123,8 @@ def lib() -> C.CDLL:
         L.lb_last_error.restype = C.c_char_p
         L.lb_destroy.argtypes = [vp]
         L.lb_destroy.restype = None
-        for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_step", "lb_moments",
+        for name in ("lb_workspace_bytes", "lb_create", "lb_init_fields", "lb_init_fields_f32", "lb_step",
+                     "lb_moments", "lb_moments_f32",
                      "lb_reductions", "lb_snapshot_bytes", "lb_save", "lb_load", "lb_critical", "lb_maxwell",
                      "lb_fields_static", "lb_adjoint_workspace_bytes", "lb_adjoint_step", "lb_worklist",
                      "lb_wait_selftest", "lb_window_means", "lb_launch_mode", "lb_persistent_selftest",
@@ -195,16 +198,18 @@ class Lattice:
         self._h = h
 
     # ------------------------------------------------------------------ helpers
-    def _ptr_of(self, a, shape):
-        """(pointer, on_device, keepalive) for a host array or a CUDA tensor of FP64."""
+    def _ptr_of(self, a, shape, fp32: bool = False):
+        """(pointer, on_device, keepalive) for a host array or a CUDA tensor of
+        FP64 (FP32 with fp32)."""
         torch = self._torch
         if a is None:
             return None, 0, None
         if isinstance(a, torch.Tensor) and a.is_cuda:
-            t = a.detach().to(torch.float64).contiguous()
+            t = a.detach().to(torch.float32 if fp32 else torch.float64).contiguous()
             assert tuple(t.shape) == shape, (t.shape, shape)
             return C.c_void_p(t.data_ptr()), 1, t
-        h = _host_f64(a.cpu().numpy() if isinstance(a, torch.Tensor) else a)
+        h = a.cpu().numpy() if isinstance(a, torch.Tensor) else a
+        h = np.ascontiguousarray(np.asarray(h, dtype=np.float32)) if fp32 else _host_f64(h)
         assert h.shape == shape, (h.shape, shape)
         return C.c_void_p(h.ctypes.data), 0, h
 
@@ -213,14 +218,17 @@ class Lattice:
         return (c.ny, c.nx)
 
     # ---------------------------------------------------------------------- API
-    def init_fields(self, case_id: int, rho0, ux0=None, uy0=None):
+    def init_fields(self, case_id: int, rho0, ux0=None, uy0=None, fp32: bool = False):
+        """Initial state of case_id from rho0 (and u0): FP64 fields, or FP32
+        ones with fp32 (lb_init_fields_f32)."""
         sh = self._shape(case_id)
-        p, dev, k0 = self._ptr_of(rho0, sh)
-        pu, devu, k1 = self._ptr_of(ux0, sh)
-        pv, devv, k2 = self._ptr_of(uy0, sh)
+        p, dev, k0 = self._ptr_of(rho0, sh, fp32)
+        pu, devu, k1 = self._ptr_of(ux0, sh, fp32)
+        pv, devv, k2 = self._ptr_of(uy0, sh, fp32)
         if (ux0 is not None and devu != dev) or (uy0 is not None and devv != dev):
             raise ValueError("rho0, ux0 and uy0 must all be on the host or all on the device")
-        _check(lib().lb_init_fields(self._h, case_id, p, pu, pv, dev), self._h)
+        fn = lib().lb_init_fields_f32 if fp32 else lib().lb_init_fields
+        _check(fn(self._h, case_id, p, pu, pv, dev), self._h)
         del k0, k1, k2
 
     def step(self, nsteps: int = 1):
@@ -267,17 +275,20 @@ class Lattice:
         _check(lib().lb_worklist(self._h, C.byref(r), C.byref(n), C.byref(w)), self._h)
         return r.value, n.value, bool(w.value)
 
-    def moments(self, case_id: int, on_device: bool = False):
-        """dict rho, ux, uy, mu of the current state (numpy, or CUDA tensors)."""
+    def moments(self, case_id: int, on_device: bool = False, fp32: bool = False):
+        """dict rho, ux, uy, mu of the current state (numpy, or CUDA tensors);
+        FP64, or FP32 with fp32 (lb_moments_f32)."""
         sh = self._shape(case_id)
         torch = self._torch
         if on_device:
-            out = {k: torch.empty(sh, dtype=torch.float64, device=self.device) for k in ("rho", "ux", "uy", "mu")}
+            dt = torch.float32 if fp32 else torch.float64
+            out = {k: torch.empty(sh, dtype=dt, device=self.device) for k in ("rho", "ux", "uy", "mu")}
             ptrs = [C.c_void_p(out[k].data_ptr()) for k in ("rho", "ux", "uy", "mu")]
         else:
-            out = {k: np.empty(sh) for k in ("rho", "ux", "uy", "mu")}
+            out = {k: np.empty(sh, dtype=np.float32 if fp32 else np.float64) for k in ("rho", "ux", "uy", "mu")}
             ptrs = [C.c_void_p(out[k].ctypes.data) for k in ("rho", "ux", "uy", "mu")]
-        _check(lib().lb_moments(self._h, case_id, *ptrs, 1 if on_device else 0), self._h)
+        fn = lib().lb_moments_f32 if fp32 else lib().lb_moments
+        _check(fn(self._h, case_id, *ptrs, 1 if on_device else 0), self._h)
         return out
 
     def reductions(self, raise_unstable: bool = False):

@@ -69,3 +69,44 @@ def test_pinned_host_buffers_match_pageable_and_device(precision, shape):
     assert np.array_equal(rho_only.numpy(), host["rho"]) and np.array_equal(uy_host, host["uy"])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [lbfe.FP32, lbfe.FP64])
+def test_fp32_field_calls(precision):
+    """lb_init_fields_f32 gives the state lb_init_fields gives from the same
+    values widened to FP64 (pageable, page-locked and device inputs, with
+    FP32 initial velocities), and lb_moments_f32 returns lb_moments' values
+    rounded to FP32 (pageable, page-locked and device outputs)."""
+    import torch
+
+    nx, ny = 68, 37
+    e = thermo.vdw_paper()
+    T, rg, rl = thermo.maxwell_reduced(e, 0.8)
+    case = lbfe.Case(nx=nx, ny=ny, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, a=e.a, b=e.b, R=1.0,
+                     T=T, kappa=0.02, tau_v=0.8)
+    rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=4).astype(np.float32)
+    ux0 = (0.01 * (2 * inputs.splitmix_uniform(2, 0, nx, ny) - 1)).astype(np.float32)
+    uy0 = (0.01 * (2 * inputs.splitmix_uniform(3, 0, nx, ny) - 1)).astype(np.float32)
+    ref = lbfe.Lattice([case], precision=precision)
+    ref.init_fields(0, rho0.astype(np.float64), ux0.astype(np.float64), uy0.astype(np.float64))
+    want = _pops(ref, nx, ny)
+    pinned = [torch.from_numpy(a.copy()).pin_memory() for a in (rho0, ux0, uy0)]
+    device = [torch.from_numpy(a.copy()).cuda() for a in (rho0, ux0, uy0)]
+    for src in ((rho0, ux0, uy0), pinned, device):
+        lat = lbfe.Lattice([case], precision=precision)
+        lat.init_fields(0, *src, fp32=True)
+        assert np.array_equal(_pops(lat, nx, ny), want)
+        lat.close()
+    ref.step(9)
+    m64 = ref.moments(0)
+    names = ("rho", "ux", "uy", "mu")
+    host = ref.moments(0, fp32=True)
+    dev = ref.moments(0, on_device=True, fp32=True)
+    pin = {k: torch.empty((ny, nx), dtype=torch.float32).pin_memory() for k in names}
+    lbfe._check(lbfe.lib().lb_moments_f32(ref._h, 0, *[C.c_void_p(pin[k].data_ptr()) for k in names], 0), ref._h)
+    for k in names:
+        w = m64[k].astype(np.float32)
+        assert host[k].dtype == np.float32 and np.array_equal(host[k], w), k
+        assert np.array_equal(dev[k].cpu().numpy(), w), k
+        assert np.array_equal(pin[k].numpy(), w), k
+    ref.close()
