@@ -422,7 +422,7 @@ def run_gpu(args):
                                           "steps, and the improved scheme's vapour at 0.7 T_c is linearly "
                                           "unstable with the Eq. 17 discretisation of d(phi u); the CS kernel's "
                                           "throughput on a stable CS case is under eos_cs",
-                       "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows), "items": n_items,
+                       "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled", -2: "slot share, 2 waves", -3: "slot share, 4 waves"}.get(seg_rows, seg_rows), "items": n_items,
                                     "narrow_blocks": narrow}},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
@@ -569,7 +569,7 @@ def _batched_throughput(lbfe, steps: int, warmup: int, t_range=(0.8, 0.9), schem
     res = {"value": round(nodes * steps / (batched_ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "steps": steps,
            "ms_per_step": round(batched_ms / steps, 4), "n_cases": len(cases), "nodes": nodes,
            "stable_cases": int((st == 0).sum()), "t_over_tc": list(t_range),
-           "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled"}.get(seg_rows, seg_rows),
+           "worklist": {"segment_rows": {0: "slot share", -1: "slot share, filled", -2: "slot share, 2 waves", -3: "slot share, 4 waves"}.get(seg_rows, seg_rows),
                         "items": n_items, "narrow_blocks": narrow},
            "roofline": {"bound": "hbm", "achieved": round(72 * nodes / (batched_ms / steps * 1e-3) / 1e9, 1),
                         "peak": _peaks()[0], "unit": "GB/s",

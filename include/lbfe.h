@@ -231,8 +231,9 @@ lb_status lb_launch_mode(lb_handle* h, int32_t mode, int32_t* persistent);
  * one-group handle whose work-list has at least two items. */
 lb_status lb_persistent_selftest(lb_handle* h, int64_t nsteps);
 
-/* The work-list in use: rows per segment (0: slot-share rule, -1: the
- * filled slot-share rule), item count,
+/* The work-list in use: rows per segment (0: slot-share rule over one wave
+ * of blocks, -1: the filled slot-share rule, -2 / -3: the slot-share rule
+ * over two / four waves), item count,
  * and whether narrow blocks (64 threads, 128 columns) run the lattices that
  * fit them with fewer idle lanes. Before the first lb_step it is the untuned
  * default. Any pointer may be NULL. */

@@ -370,11 +370,15 @@ void build_items(lb_handle* h)
             const lb_case& c = h->cases[i];
             int ns = strips_of(c, width);
             const int q = c.nx % 4 == 0 ? 4 : 1;  // strip edges on multiples of q
-            const double share = slots * ((double)c.nx * c.ny) / nodes;
+            // the case's share of the block slots, over one wave of blocks
+            // (seg_rows 0, -1) or two and four waves (-2, -3), whose later
+            // waves fill the slots that short items free
+            const double waves = seg_rows == -2 ? 2.0 : seg_rows == -3 ? 4.0 : 1.0;
+            const double share = slots * waves * ((double)c.nx * c.ny) / nodes;
             const int min_rows = seg_rows > 0 ? std::max(kMinSegRows, std::min(kMinRows, seg_rows)) : kMinRows;
             const int max_seg = std::max(1, c.ny / min_rows);
             int nseg = seg_rows > 0 ? (c.ny + seg_rows / 2) / seg_rows : (int)std::floor(share / ns);
-            if (seg_rows < 0) {
+            if (seg_rows == -1) {
                 // slot share, filled: up to four more (narrower) strips when
                 // strips x segments then comes closer to the case's share
                 int best = std::min(std::max(1, nseg), max_seg) * ns;
@@ -647,7 +651,7 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
         h->tma_threads = (v == 128 || v == 256) ? v : 0;
     }
     if (const char* p = std::getenv("LBFE_SEG_ROWS")) {
-        h->seg_rows = std::max(-1, std::atoi(p));
+        h->seg_rows = std::max(-3, std::atoi(p));
         h->autotune = false;
     }
     if (const char* p = std::getenv("LBFE_PAIR_NARROW")) {
@@ -827,7 +831,7 @@ static lb_status autotune(lb_handle* h)
     // second half only when some lattice prefers narrow blocks
     // (short segments serve lattices small enough that a step is bound by the
     // latency of its row pipeline: fewer rows per item, more items at once)
-    static const int segs[] = {0, -1, 256, 128, 64, 32, 16, 8, 4, 2};
+    static const int segs[] = {0, -1, -2, -3, 256, 128, 64, 32, 16, 8, 4, 2};
     constexpr int kSegs = (int)(sizeof segs / sizeof segs[0]);
     bool any_narrow = false;
     if (h->prec == LB_FP32 && h->path != 1 && h->tma_threads == 0 && !h->narrow_fixed)

@@ -478,7 +478,7 @@ def test_autotuned_worklist_changes_no_result(monkeypatch):
                                a=e.a, b=e.b, T=T, kappa=0.02, tau_v=0.9))
         rhos.append(inputs.droplet(side, side + 8, 0.25 * side, rl, rg, noise=1e-3, case=side))
     snaps = {}
-    for seg in ("0", "-1", "16", "64", "2", None):
+    for seg in ("0", "-1", "-2", "-3", "16", "64", "2", None):
         if seg is None:
             monkeypatch.delenv("LBFE_SEG_ROWS", raising=False)
         else:
@@ -493,7 +493,7 @@ def test_autotuned_worklist_changes_no_result(monkeypatch):
         assert n_items >= len(cases)
         snaps[seg] = [lat.save(i) for i in range(len(cases))]
         lat.close()
-    for seg in ("-1", "16", "64", "2", None):
+    for seg in ("-1", "-2", "-3", "16", "64", "2", None):
         for i, c in enumerate(cases):
             pitch = (c.nx + 31) // 32 * 32
             a = np.frombuffer(snaps["0"][i][16:], dtype=np.float32).reshape(9, c.ny, pitch)[:, :, :c.nx]
