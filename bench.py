@@ -810,12 +810,14 @@ def _adjoint_check(lbfe, inputs, steps: int, window: int, ckpt: int, n: int = 25
 
 def run_adjoint(args):
     """Differentiation workload: the 256^2 droplet of radius 64, 2000 steps
-    checkpointed every 100, loss over the last 100 steps (_adjoint_check)."""
+    (--adjoint-steps) checkpointed every 100, loss over the last 100 steps
+    (_adjoint_check)."""
     from paper_2008_01473_gb300 import build, inputs, lbfe
 
     build.build()
-    line = {"metric": "adjoint gradient (lb_adjoint_step) vs central differences",
-            **_adjoint_check(lbfe, inputs, steps=2000, window=100, ckpt=100)}
+    n = args.adjoint_steps
+    line = {"metric": "adjoint gradient (lb_adjoint_step) vs central differences", "steps": n,
+            **_adjoint_check(lbfe, inputs, steps=n, window=min(100, n // 2), ckpt=min(100, n // 2))}
     print(json.dumps(line), flush=True)
 
 
@@ -1071,6 +1073,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=450)
+    ap.add_argument("--adjoint-steps", type=int, default=2000, help="horizon of --workload adjoint")
     ap.add_argument("--accuracy-steps", type=int, default=10000,
                     help="batched workload: steps of the FP32-vs-FP64 droplet check (0 skips it)")
     ap.add_argument("--no-cpu", action="store_true")

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) adj_fwd_force(DevCase<T> c, AdjFields<T> 
         F.B[n.i] = phi * uy;
         loss = w_u * ((double)ux * ux + (double)uy * uy) + (s_final ? s_final[n.i] * (double)r : 0.0);
     }
-    block_partial(loss, 0.0, 0.0, 0.0, partials);
+    block_partial<true>(loss, 0.0, 0.0, 0.0, partials);
 }
 
 template <typename T>
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256) adj_mu(DevCase<T> c, T R, AdjFields<T> F,
         gk = -(double)mub * (double)F.lap[i];
         gT = (double)mub * (double)dEf_dT_dev<EOS, T>(c, F.rho[i], R);
     }
-    block_partial(gk, gT, 0.0, 0.0, partials);
+    block_partial<true>(gk, gT, 0.0, 0.0, partials);
 }
 
 // lap transposed; lam(x)_a = lam_direct + rho-bar + e_a . j-bar (+ final density seed)
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) adj_init(DevCase<T> c, T R, AdjFields<T> 
         gk = -(double)mub * (double)F.lap[n.i];
         gT = (double)mub * (double)dEf_dT_dev<EOS, T>(c, r, R);
     }
-    block_partial(gk, gT, 0.0, 0.0, partials);
+    block_partial<true>(gk, gT, 0.0, 0.0, partials);
 }
 
 template <typename T>

@@ -41,7 +41,10 @@ struct Partial {
 };
 
 // Block reduction of one Partial per thread (blockDim.x == 256) into
-// partials[block index].
+// partials[block index]: stored, or with ADD added to the slot (its sums;
+// the max is kept), so that one slot per block accumulates over many
+// launches of the same grid in launch order.
+template <bool ADD = false>
 __device__ __forceinline__ void block_partial(double mass, double ke, double um, double bad,
                                               Partial* __restrict__ partials)
 {
@@ -68,7 +71,15 @@ __device__ __forceinline__ void block_partial(double mass, double ke, double um,
             p.umax2 = fmax(p.umax2, s[2][k]);
             p.bad += s[3][k];
         }
-        partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = p;
+        Partial& q = partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+        if (ADD) {
+            q.mass += p.mass;
+            q.ke += p.ke;
+            q.umax2 = fmax(q.umax2, p.umax2);
+            q.bad += p.bad;
+        } else {
+            q = p;
+        }
     }
 }
 

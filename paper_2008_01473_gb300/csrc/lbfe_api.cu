@@ -1455,7 +1455,7 @@ lb_status lb_load(lb_handle* h, int32_t case_id, const void* host_buf, size_t by
 namespace {
 
 struct AdjLayout {
-    size_t cases, items, ckpt, seg, lam, lamd, fields, partials, acc, rho0, sfin, grad, status, total;
+    size_t cases, items, ckpt, seg, lam, lamd, fields, partials, partials2, acc, rho0, sfin, grad, status, total;
     int64_t K, ncp, state, nitems, N, parts;
 };
 
@@ -1486,6 +1486,7 @@ AdjLayout adj_layout(const lb_case& c, int64_t nsteps, int64_t K, size_t es)
     L.lamd = take((size_t)kQ * L.N * es);
     L.fields = take((size_t)kAdjFields * align_up(L.N * es, kAlign));
     L.partials = take(L.parts * sizeof(Partial));
+    L.partials2 = take(L.parts * sizeof(Partial));
     L.acc = take(8 * sizeof(double));
     L.rho0 = take(L.N * sizeof(double));
     L.sfin = take(L.N * sizeof(double));
@@ -1519,7 +1520,10 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
     T* seg = reinterpret_cast<T*>(ws + L.seg);
     T* lam = reinterpret_cast<T*>(ws + L.lam);
     T* lamd = reinterpret_cast<T*>(ws + L.lamd);
+    // per-block slots that accumulate over the whole reverse sweep: the loss
+    // (parts) and the kappa / T gradients (parts2); folded once at the end
     Partial* parts = reinterpret_cast<Partial*>(ws + L.partials);
+    Partial* parts2 = reinterpret_cast<Partial*>(ws + L.partials2);
     double* acc = reinterpret_cast<double*>(ws + L.acc);
     const double* rho0 = reinterpret_cast<const double*>(ws + L.rho0);
     double* grad = reinterpret_cast<double*>(ws + L.grad);
@@ -1555,6 +1559,8 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
     }
     lb_status ms = h->cuda(cudaMemsetAsync(acc, 0, 4 * sizeof(double), st), "adjoint clear");
     if (ms == LB_OK) ms = h->cuda(cudaMemsetAsync(lam, 0, (size_t)kQ * L.N * sizeof(T), st), "adjoint clear");
+    if (ms == LB_OK) ms = h->cuda(cudaMemsetAsync(parts, 0, L.parts * sizeof(Partial), st), "adjoint clear");
+    if (ms == LB_OK) ms = h->cuda(cudaMemsetAsync(parts2, 0, L.parts * sizeof(Partial), st), "adjoint clear");
     if (ms != LB_OK) return ms;
     // reverse sweep over segments [s, e], states s+1..e rebuilt into seg
     for (int64_t s = (nsteps / L.K) * L.K, e = nsteps; s >= 0; e = s - 1, s -= L.K) {
@@ -1569,21 +1575,21 @@ lb_status adjoint_run(lb_handle* h, const lb_case& c, const AdjLayout& L, uint8_
             adj_fwd_mu<T, EOS><<<grd, blk, 0, st>>>(cd, F);
             adj_fwd_force<T, SCHEME><<<grd, blk, 0, st>>>(cd, F, n >= u_from ? 1.0 : 0.0,
                                                           n == nsteps ? s_fin : nullptr, parts);
-            adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 0, nullptr);
             if (SCHEME == 1) adj_fwd_corr<T><<<grd, blk, 0, st>>>(cd, F);
             adj_collide<T, SCHEME><<<grd, blk, 0, st>>>(cd, F, lam, n < nsteps, n >= u_from, lamd);
             adj_force<T, SCHEME><<<grd, blk, 0, st>>>(cd, F);
-            adj_mu<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, parts);
-            adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
+            adj_mu<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, parts2);
             adj_lambda<T><<<grd, blk, 0, st>>>(cd, F, lamd, n == nsteps ? s_fin : nullptr, lam);
         }
         if (s == 0) break;
     }
+    // the loss, before load_rho0's check partials overwrite parts
+    adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 0, nullptr);
     // initial populations
     load_rho0();
     adj_fwd_mu<T, EOS><<<grd, blk, 0, st>>>(cd, F);
-    adj_init<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, lam, parts);
-    adj_accumulate<<<1, 256, 0, st>>>(parts, L.parts, acc + 1, acc + 2);
+    adj_init<T, SCHEME, EOS><<<grd, blk, 0, st>>>(cd, R, F, lam, parts2);
+    adj_accumulate<<<1, 256, 0, st>>>(parts2, L.parts, acc + 1, acc + 2);
     adj_init_out<T><<<grd, blk, 0, st>>>(cd, F, grad);
     return h->cuda(cudaGetLastError(), "adjoint kernels");
 }
