@@ -649,9 +649,12 @@ def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
     """Launch-bound workloads that live in L2: the sweep's 16 periodic
     1024 x 8 strips (improved scheme, BGK tau 1, vdW at T/T_c 0.95 ... 0.75,
     131,072 nodes) in FP32 and FP64, and one 40 x 33 FP64 droplet, each timed
-    over `steps` steps with one launch per step (8-step graph replay) and with
-    the persistent launch (one cooperative launch for the steps); MLUPS and
-    microseconds per step."""
+    over `steps` steps with one launch per step (8-step graph replay), the
+    strips also with the row kernel off (the sliding-window kernels), and
+    with the persistent launch (one cooperative launch for the steps); MLUPS
+    and microseconds per step."""
+    import os
+
     import numpy as np
     import torch
 
@@ -672,8 +675,19 @@ def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
                                     ("droplet_40x33_fp64", drop, drop_rho, lbfe.FP64)):
         nodes = sum(c.nx * c.ny for c in cases)
         res = {"nodes": nodes}
-        for mode, key in ((0, "graph_replay"), (1, "persistent")):
-            lat = lbfe.Lattice(cases, precision=prec)
+        runs = [(0, "graph_replay", "1"), (1, "persistent", "1")]
+        if cases[0].ny <= 16:
+            runs.insert(1, (0, "sliding_window", "0"))
+        for mode, key, rows in runs:
+            old = os.environ.get("LBFE_ROWS")
+            os.environ["LBFE_ROWS"] = rows  # read when the handle is made
+            try:
+                lat = lbfe.Lattice(cases, precision=prec)
+            finally:
+                if old is None:
+                    os.environ.pop("LBFE_ROWS")
+                else:
+                    os.environ["LBFE_ROWS"] = old
             lat.launch_mode(mode)
             for i, r in enumerate(rhos):
                 lat.init_fields(i, r)
@@ -691,10 +705,13 @@ def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
                         "us_per_step": round(ms * 1e3 / steps, 2), "stable": bool((st == 0).all())}
         res["population_bytes_both_buffers"] = (72 if prec == lbfe.FP32 else 144) * nodes
         res["gain"] = round(res["persistent"]["MLUPS"] / res["graph_replay"]["MLUPS"], 3)
+        if "sliding_window" in res:
+            res["row_kernel_gain"] = round(res["graph_replay"]["MLUPS"] / res["sliding_window"]["MLUPS"], 3)
         out[name] = res
     out["note"] = ("L2-resident (both population buffers far below the 129 MB L2): bound by launch latency and "
-                   "the per-row pipeline latency of a step, not by HBM; FP32 strips run the packed kernel under "
-                   "graph replay and the one-column kernel when persistent")
+                   "the latency of a step's stages, not by HBM; the strips (ny 8) run the row kernel under graph "
+                   "replay, the packed (FP32) or one-column (FP64) sliding-window kernel with it off, and the "
+                   "one-column kernel when persistent; the droplet runs the one-column kernel")
     return out
 
 

@@ -151,7 +151,8 @@ lb_status lb_workspace_bytes(const lb_case* cases, int32_t ncases, int32_t preci
  * lattices all have nx % 4 == 0 use the TMA-staged step kernel, others the
  * plain-load one. Environment overrides read here, for tuning:
  * LBFE_STEP_PATH=ldg forces the plain-load kernel; LBFE_STEP_THREADS=128|256
- * sets the compute threads per block of the TMA kernel (default 128). */
+ * sets the compute threads per block of the TMA kernel (default 128);
+ * LBFE_ROWS=0 keeps short periodic lattices off the row kernel (lb_step). */
 lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, void* d_workspace,
                     size_t ws_bytes, void* cuda_stream, lb_handle** out);
 
@@ -177,7 +178,15 @@ lb_status lb_init_fields_f32(lb_handle* h, int32_t case_id, const float* rho0, c
  * runs a work-list of (case, column strip, row segment) items. FP32 cases
  * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
  * FP64 cases, other widths, Lax-Wendroff cases and LB_IMPROVED_SMOOTH cases
- * narrower than 8 or with walls run the one-column plain-load kernel. The
+ * narrower than 8 or with walls run the one-column plain-load kernel.
+ * Periodic LB_STANDARD and LB_IMPROVED cases with ny <= 16, in either
+ * precision, run the row kernel instead (one thread per node of a
+ * whole-height strip of 64 columns, 58 or 60 of them output, the stages
+ * separated by block barriers), except under the persistent launch: on
+ * lattices that short the sliding-window kernels are bound by the latency
+ * of their chain of row iterations. Its results agree with the other
+ * kernels' to rounding (FP64: the oracle's 1e-11; FP32: the storage's
+ * rounding), and are bit-identical between runs. The
  * first
  * call with nsteps > 0 autotunes the work-list: it times one step under
  * several row-segment sizes, with and without narrow blocks for the lattices
@@ -211,7 +220,8 @@ lb_status lb_step(lb_handle* h, int64_t nsteps);
  * by launch latency. The persistent kernel is the one-column kernel.
  * mode: 0 never; 1 always (an FP32 group with nx % 4 == 0 then leaves the
  * packed kernel for the one-column one, whose FP32 rounding differs in the
- * last bits); 2 (default) automatic: for a handle whose group already runs
+ * last bits; cases of the row kernel leave it too: entering or leaving mode
+ * 1 rebuilds the work-list, synchronising the stream); 2 (default) automatic: for a handle whose group already runs
  * the one-column kernel (FP64; FP32 with nx % 4 != 0, Lax-Wendroff or
  * LB_IMPROVED_SMOOTH with walls or narrower than 8), the first lb_step of at least 40 steps times 16 steps
  * of graph replay against 16 persistent steps (its own steps: results are

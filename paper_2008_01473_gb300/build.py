@@ -17,7 +17,7 @@ LIB = os.path.join(OUT_DIR, "liblbfe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
-CUDA_UNITS = ["step_f32.cu", "step_persist.cu", "step_f64.cu", "step_f64s.cu", "step_f32s.cu",
+CUDA_UNITS = ["step_f32.cu", "step_persist.cu", "step_f64.cu", "step_f64s.cu", "step_f32s.cu", "step_rows.cu",
               "step_f32_pair0.cu", "step_f32_pair1.cu", "step_f32_pair2.cu", "step_f32_pair3.cu",
               "step_f32_pair0s.cu", "step_f32_pair1s.cu", "step_f32_pair2s.cu", "step_f32_pair3s.cu",
               "lbfe_api.cu", "lbfe_static.cu"]

@@ -55,7 +55,15 @@ constexpr int kMinBlockThreads = 128;  // narrowest block any path uses
 
 int64_t max_items_of(const lb_case& c)
 {
-    return (int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinSegRows - 1) / kMinSegRows);
+    // (the row kernel's whole-height strips: at least rows_strip_width(1) wide)
+    return std::max<int64_t>((int64_t)strips_of(c, kMinBlockThreads) * ((c.ny + kMinSegRows - 1) / kMinSegRows),
+                             (c.nx + rows_strip_width(LB_IMPROVED) - 1) / rows_strip_width(LB_IMPROVED));
+}
+
+// periodic lattices of schemes 0 and 1 short enough for the row kernel
+bool rows_eligible(const lb_case& c)
+{
+    return !c.walls && (c.scheme == LB_STANDARD || c.scheme == LB_IMPROVED) && c.ny <= rows_max_ny();
 }
 
 constexpr int kMaxNeighbours = 32;  // neighbour items per item that the persistent launch tracks
@@ -215,6 +223,8 @@ struct Group {
     int nt;                // compute threads per block
     int64_t first, count;  // slice of the item array
     bool walls = false;    // lattices with walls (the packed kernel's variant for them)
+    bool rows = false;     // the row kernel (short periodic lattices, whole-height strips)
+    int ny_max = 0;        // row kernel: tallest lattice of the group
 };
 
 }  // namespace
@@ -239,6 +249,7 @@ struct lb_handle {
     int seg_rows = 0;       // work-list rows per segment, 0: share of the block slots
     bool autotune = true;   // pick seg_rows (and narrow) by timing on the first lb_step
     bool narrow = false;    // narrow packed blocks for the lattices that prefer them
+    bool rows_on = true;    // the row kernel runs the lattices it can (LBFE_ROWS=0: never)
     bool narrow_fixed = false;  // narrow set by LBFE_PAIR_NARROW, not tuned
     std::vector<cudaStream_t> aux;       // capture branches for groups after the first
     std::vector<cudaEvent_t> fork_join;  // [2 * branch]: fork, join
@@ -411,6 +422,9 @@ void build_items(lb_handle* h)
         h->groups.push_back(g);
     };
 
+    // short periodic lattices of schemes 0 and 1 run on the row kernel,
+    // except under the persistent launch (whose kernel runs every item)
+    const bool rows_ok = h->rows_on && h->persist_mode != 1;
     for (int s = 0; s < 5; ++s)
         for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
@@ -426,6 +440,7 @@ void build_items(lb_handle* h)
                         std::vector<int> members, narrow;
                         for (int i = 0; i < n; ++i) {
                             const lb_case& c = h->cases[i];
+                            if (rows_ok && rows_eligible(c)) continue;  // the row kernel's groups below
                             // (the one-column TMA shapes pull no walls)
                             const bool plain = one_column_only(c) || (c.walls && h->tma_threads != 0);
                             const int kind = plain ? 2 : c.nx % 4 != 0 ? 0 : c.walls ? 3 : 1;
@@ -437,6 +452,30 @@ void build_items(lb_handle* h)
                              al == 3);
                         emit(narrow, s, co, e, nu, tma, kPairNarrow, al == 3);
                     }
+    // the row kernel: one item per strip of at most rows_strip_width columns
+    // over the lattice's whole height, whatever the segment rule
+    for (int s = 0; rows_ok && s < 2; ++s)
+        for (int co = 0; co < 2; ++co)
+            for (int e = 0; e < 2; ++e)
+                for (int nu = 0; nu < 2; ++nu) {
+                    Group g{s, co, e, nu == 1, false, 0, (int64_t)h->items.size(), 0};
+                    g.rows = true;
+                    const int w = rows_strip_width(s);
+                    for (int i = 0; i < n; ++i) {
+                        const lb_case& c = h->cases[i];
+                        if (!rows_eligible(c) || c.scheme != s || c.collision != co || c.eos != e ||
+                            (c.nu > 0) != (nu == 1))
+                            continue;
+                        g.ny_max = std::max(g.ny_max, c.ny);
+                        const int ns = (c.nx + w - 1) / w;
+                        for (int k = 0; k < ns; ++k) {
+                            const int x0 = (int)((int64_t)c.nx * k / ns), x1 = (int)((int64_t)c.nx * (k + 1) / ns);
+                            h->items.push_back(Item{i, x0, x1 - x0, 0, c.ny, 0});
+                        }
+                    }
+                    g.count = (int64_t)h->items.size() - g.first;
+                    if (g.count > 0) h->groups.push_back(g);
+                }
     // work items per case (the blocks one step of the case launches)
     h->case_items.assign(h->cases.size(), 0);
     for (const Item& it : h->items) ++h->case_items[it.case_id];
@@ -654,6 +693,7 @@ lb_status lb_create(const lb_case* cases, int32_t ncases, int32_t precision, voi
         h->seg_rows = std::max(-3, std::atoi(p));
         h->autotune = false;
     }
+    if (const char* p = std::getenv("LBFE_ROWS")) h->rows_on = std::strcmp(p, "0") != 0;
     if (const char* p = std::getenv("LBFE_PAIR_NARROW")) {
         h->narrow = std::strcmp(p, "0") != 0;
         h->narrow_fixed = true;
@@ -768,7 +808,12 @@ static lb_status enqueue_step(lb_handle* h, int cur, cudaStream_t st)
         const Group& g = h->groups[k];
         const cudaStream_t gs = k == 0 ? st : h->aux[k - 1];
         cudaError_t e;
-        if (h->prec == LB_FP32)
+        if (g.rows)
+            e = launch_step_rows(h->prec, g.scheme, g.coll, g.eos, g.nu, g.ny_max, (int)g.count, gs, h->fbuf(cur),
+                                 h->fbuf(cur ^ 1),
+                                 h->prec == LB_FP32 ? (const void*)h->dc32() : (const void*)h->dc64(),
+                                 h->ditems() + g.first, h->status(), h->st_live);
+        else if (h->prec == LB_FP32)
             e = launch_step_f32(g.scheme, g.coll, g.eos, g.nu, g.tma, g.nt, (int)g.count, gs,
                                 (const float*)h->fbuf(cur), (float*)h->fbuf(cur ^ 1), h->dc32(),
                                 h->ditems() + g.first, h->status(), h->st_live, g.walls);
@@ -827,6 +872,13 @@ static lb_status tune_time(lb_handle* h, cudaEvent_t e0, cudaEvent_t e1, int rep
 
 static lb_status autotune(lb_handle* h)
 {
+    // the row kernel's work-lists do not depend on the segment rule
+    bool all_rows = true;
+    for (const Group& g : h->groups) all_rows = all_rows && g.rows;
+    if (all_rows) {
+        h->tuned = true;
+        return LB_OK;
+    }
     // candidates: row-segment rule x (narrow packed blocks off, on); the
     // second half only when some lattice prefers narrow blocks
     // (short segments serve lattices small enough that a step is bound by the
@@ -884,6 +936,20 @@ static lb_status autotune(lb_handle* h)
     return s != LB_OK ? s : u;
 }
 
+// Work-list built again after a change of the rules that shape it (the
+// captured graphs name the old groups and are dropped).
+static lb_status rebuild_worklist(lb_handle* h)
+{
+    lb_status s = h->cuda(cudaStreamSynchronize(h->stream), "work-list sync");
+    for (cudaGraphExec_t& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    build_items(h);
+    return s == LB_OK ? upload_items(h) : s;
+}
+
 // ------------------------------------------------------ persistent launch
 constexpr int kPersistChunk = 1024;  // steps per persistent launch
 
@@ -905,7 +971,7 @@ static bool persist_possible(const lb_handle* h, bool strict)
 {
     if (h->groups.size() != 1 || h->st_buf) return false;  // (per-step statistics need one launch per step)
     const Group& g = h->groups[0];
-    if (strict && g.tma) return false;
+    if (strict && (g.tma || g.rows)) return false;
     return occupancy_persist(h->prec, g.scheme, g.coll, g.eos, g.nu) > 0;
 }
 
@@ -1086,10 +1152,20 @@ lb_status lb_launch_mode(lb_handle* h, int32_t mode, int32_t* persistent)
     if (check_handle(h) != LB_OK) return LB_E_INVALID;
     if (mode < -1 || mode > 2) return h->fail(LB_E_INVALID, "lb_launch_mode: mode must be -1, 0, 1 or 2");
     if (mode >= 0) {
-        if (mode == 1 && !persist_possible(h, false))
+        // the row kernel's groups exist outside the persistent launch only:
+        // entering or leaving it rebuilds the work-list
+        bool any_rows = false;
+        for (const lb_case& c : h->cases) any_rows = any_rows || (h->rows_on && rows_eligible(c));
+        const int old = h->persist_mode;
+        h->persist_mode = mode;
+        lb_status s = any_rows && (old == 1) != (mode == 1) ? rebuild_worklist(h) : LB_OK;
+        if (s == LB_OK && mode == 1 && !persist_possible(h, false)) {
+            h->persist_mode = old;
+            if (any_rows && old != 1) rebuild_worklist(h);
             return h->fail(LB_E_INVALID, "lb_launch_mode: the persistent launch needs a handle whose cases all "
                                          "share one kernel group and no per-step statistics attached");
-        h->persist_mode = mode;
+        }
+        if (s != LB_OK) return s;
         h->persist = mode == 1;
         h->persist_tuned = mode != 2;
     }

@@ -2,7 +2,7 @@
 mass, kinetic energy and max |u| recorded for every state a step starts from
 agree with lb_reductions of the same state, for every step kernel (packed
 FP32, one-column FP32 and FP64, the averaged correction, walls, the
-Lax-Wendroff scheme), under graph replay and direct launches; the ring, the
+Lax-Wendroff scheme, the row kernel of short periodic lattices), under graph replay and direct launches; the ring, the
 restart at lb_init_fields and the persistent-launch exclusion behave as
 include/lbfe.h states."""
 import numpy as np
@@ -27,8 +27,9 @@ def _built():
 
 def _cases():
     """Uneven lattices that take different kernels: packed (nx % 4 == 0),
-    one-column (nx % 4 != 0), the averaged correction, walls and the
-    Lax-Wendroff scheme."""
+    one-column (nx % 4 != 0), the averaged correction, walls, the
+    Lax-Wendroff scheme and the row kernel (ny <= 16, two rows and one row
+    per thread)."""
     e = thermo.vdw_paper()
     T, rg, rl = thermo.maxwell_reduced(e, 0.8)
     base = dict(eos=lbfe.VDW, a=e.a, b=e.b, R=1.0, T=T, kappa=0.02, tau_v=0.8)
@@ -38,6 +39,8 @@ def _cases():
         dict(nx=96, ny=40, scheme=lbfe.IMPROVED_SMOOTH, collision=lbfe.MRT),
         dict(nx=48, ny=36, scheme=lbfe.IMPROVED, collision=lbfe.BGK, walls=1, wall_u=0.02, rho_wall=rg),
         dict(nx=40, ny=40, scheme=lbfe.LAX_WENDROFF, collision=lbfe.BGK, tau_v=1.0, lw_A=0.5, lw_B=-0.2),
+        dict(nx=150, ny=12, scheme=lbfe.IMPROVED, collision=lbfe.MRT),
+        dict(nx=72, ny=8, scheme=lbfe.STANDARD, collision=lbfe.BGK),
     ]
     cases, rho0s = [], []
     for k, kw in enumerate(specs):
