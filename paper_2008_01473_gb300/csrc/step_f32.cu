@@ -55,10 +55,15 @@ void* pick(int scheme, int coll, int eos, bool nu)
     return nullptr;
 }
 
-size_t tma_smem(int nt)
+// dynamic shared memory of a TMA-fed kernel (the packed kernel's scheme 3
+// has a ring of its own for stage D)
+size_t tma_smem(int nt, int scheme)
 {
-    return nt == kPairWide     ? pair_dynamic_smem<float, kPairThreads>()
-           : nt == kPairNarrow ? pair_dynamic_smem<float, kPairThreadsNarrow>()
+    const bool s3 = scheme == 3;
+    return nt == kPairWide     ? (s3 ? pair_dynamic_smem<float, kPairThreads, 3>()
+                                     : pair_dynamic_smem<float, kPairThreads, 1>())
+           : nt == kPairNarrow ? (s3 ? pair_dynamic_smem<float, kPairThreadsNarrow, 3>()
+                                     : pair_dynamic_smem<float, kPairThreadsNarrow, 1>())
            : nt == 128         ? tma_dynamic_smem<float, 128>()
                                : tma_dynamic_smem<float, 256>();
 }
@@ -80,7 +85,7 @@ void* resolve(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool sta
     if (k && tma) {
         // idempotent; needed once per kernel for more than 48 KB of dynamic smem,
         // and the largest shared-memory carveout so that several blocks fit per SM
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(nt));
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(nt, scheme));
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     return k;
@@ -95,7 +100,7 @@ cudaError_t launch_step_f32(int scheme, int coll, int eos, bool nu, bool tma, in
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&fin, (void*)&fout, (void*)&cases, (void*)&items, (void*)&status};
     // the TMA kernels add one producer warp to their compute threads
-    return cudaLaunchKernel(k, dim3(nblocks), dim3(block_threads(tma, nt)), args, tma ? tma_smem(nt) : 0, s);
+    return cudaLaunchKernel(k, dim3(nblocks), dim3(block_threads(tma, nt)), args, tma ? tma_smem(nt, scheme) : 0, s);
 }
 
 int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt, bool walls)
@@ -103,7 +108,7 @@ int occupancy_step_f32(int scheme, int coll, int eos, bool nu, bool tma, int nt,
     void* k = resolve(scheme, coll, eos, nu, tma, nt, false, walls);
     int n = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block_threads(tma, nt),
-                                                            tma ? tma_smem(nt) : 0) != cudaSuccess)
+                                                            tma ? tma_smem(nt, scheme) : 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }

@@ -13,13 +13,14 @@
 // j - 1 and j + 2 are read from the shared-memory field rows. Populations
 // are stored with 64-bit stores (x0 and wv are multiples of 4).
 //
-// Ring: kPairSlots slots of one stored row (nine planes over the block's
-// columns [x0 - 4, x0 + wv + 4)), one full-mbarrier each. Stored row i = s - s0
-// lives in slot i % kPairSlots, phase (i / kPairSlots) & 1. Stage A of
+// Ring: SL slots of one stored row (nine planes over the block's columns
+// [x0 - 4, x0 + wv + 4)), one full-mbarrier each (SL = PairGeom::SL: 5, or 4
+// for scheme 3). Stored row i = s - s0 lives in slot i % SL, phase (i / SL) &
+// 1. Stage A of
 // iteration it reads rows it .. it + 2; after the block barrier that follows
 // it, row it is dead, and at the end of the iteration (after stage D's
 // stores, off the path of the three barrier intervals) lanes of warps 0..2
-// refill its slot with row it + kPairSlots (one lane per plane and run), so no
+// refill its slot with row it + SL (one lane per plane and run), so no
 // producer warp is needed and three blocks fit on an SM. The slots, their
 // mbarriers and phases, the refill row and the output row advance by one per
 // iteration through wrapping pointer and offset updates: no row modulo or
@@ -48,10 +49,15 @@
 // 5 x 5 stencil) reaches one column and one row further: the ring spans
 // [x0 - 8, x0 + wv + 8) (a margin of 8 keeps the copies 16-byte aligned), phi u
 // is needed on [6, wv + 10), mu_c on [5, wv + 11), rho on [3, wv + 13); stage
-// D runs four rows behind stage A, on a six-row phi u ring, and pulls its
-// row's populations again from global memory (L2: stage A's bulk copies
-// brought those rows in four iterations earlier) instead of holding five rows
-// of them in registers, as the one-column kernel does for this scheme.
+// D runs four rows behind stage A, on a five-row phi u ring. Five rows of
+// pulled populations do not fit the registers of three blocks per SM, so
+// stage D reads its row's pull again, from a second ring of two slots: slot
+// m & 1 holds the pull of output row y0 + m (plane a copied from stored row
+// y0 + m - e_ay, so the nine planes of one slot come from three stored rows),
+// filled by bulk copies from L2 (stage A's copies brought those rows in four
+// iterations earlier) at the end of the iteration after the slot's previous
+// row was collided, three barrier intervals before stage D needs it. Both
+// rings then fit three blocks per SM with four slots in stage A's ring.
 #pragma once
 
 #include "step_tma.cuh"
@@ -61,7 +67,7 @@ namespace lbfe {
 constexpr int kPairThreads = 128;             // compute threads per block, wide shape
 constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block, wide shape
 constexpr int kPairThreadsNarrow = 64;        // the narrow shape
-constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight
+constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight (scheme 3: 4 and 1)
 
 // threads that issue a stored row's bulk copies: three warps (wide), two (narrow)
 __host__ __device__ constexpr int pair_issuers(int np) { return np == kPairThreads ? 96 : 64; }
@@ -265,7 +271,9 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
 template <int SCHEME>
 struct PairGeom {
     static constexpr int M = SCHEME == 3 ? 8 : 4;
-    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 6 : 4;  // rows of the phi u rings
+    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 5 : 4;  // rows of the phi u rings
+    static constexpr int SL = SCHEME == 3 ? 4 : kPairSlots;            // slots of stage A's ring
+    static constexpr int SD = SCHEME == 3 ? 2 : 0;                     // slots of stage D's ring
 };
 
 template <int SCHEME, int COLS>
@@ -298,7 +306,7 @@ __device__ __forceinline__ void pair_stats(PairRegs<SCHEME>& R, float2 drho, flo
 }
 
 struct PairCtx {
-    float* ring;        // [kPairSlots][9][ring columns]
+    float* ring;        // [SL][9][ring columns], then scheme 3's [SD][9][ring columns]
     uint64_t* full;
     int* flag;
     int* status;
@@ -316,13 +324,14 @@ struct PairCtx {
     float *pRm, *pR0, *pRp;
     uint64_t *fm, *f2;
     uint32_t par2;
-    uint32_t irow;      // row offset (row * pitch) of the next refill, stored row it + kPairSlots
+    uint32_t irow;      // row offset (row * pitch) of the next refill, stored row it + SL
     uint32_t plane_rows; // ny * pitch
     int rd;             // lattice row of stage D
     float* out;         // fout + column of the pair's first node (stage D pairs)
     float* orow;        // out + rd * pitch
     int* bad;           // shared: a stage D node had rho <= 0 or a non-finite density
-    int xc, xm1, xp2;   // scheme 3: lattice columns x (even), x - 1 and x + 2 of the pair
+    int pu;             // scheme 3: slot of the phi u ring that row ra - 6 occupies (it % 5)
+    uint32_t drow;      // scheme 3: row offset of this lane's plane for the next stage D copy
     // this thread's share of a row refill: one (plane, run) copy, or none
     const float* iss_src;  // source of the copy in row 0
     uint32_t iss_dst;      // ring offset of the copy within a slot (floats)
@@ -331,38 +340,25 @@ struct PairCtx {
     bool iss_on;
 };
 
-// Populations of the pair at lattice row r pulled from global memory (the
-// pull of Eq. 10): two columns per plane from one 64-bit load at the pair's
-// own columns and, for the planes that shift in x, one scalar load of the
-// column beyond it. Periodic lattices.
-__device__ __forceinline__ void pull_pair(float2 (&F)[kQ], const PairCtx& X, const DevCase<float>& c, int r)
+// The pull of Eq. 10 for the pair from ring rows holding stored rows y - 1
+// (Rm), y (R0) and y + 1 (Rp), or from one slot of stage D's ring that holds
+// each plane's source row already (Rm = R0 = Rp): plane a from the row of
+// y - e_ay, column x - e_ax. The planes that shift in x take one scalar load
+// per node, straight into its half of the pair (the outermost pairs of the
+// block read clamped columns jm, jq and produce unused values).
+template <int SW>
+__device__ __forceinline__ void pull_ring(float2 (&F)[kQ], const float* Rm, const float* R0, const float* Rp, int j,
+                                          int jm, int jq)
 {
-    const int ny = c.ny;
-    const uint32_t P = (uint32_t)c.plane;
-    const uint32_t r0 = (uint32_t)r * c.pitch;
-    const uint32_t rm = (uint32_t)(r == 0 ? ny - 1 : r - 1) * c.pitch;
-    const uint32_t rp = (uint32_t)(r + 1 == ny ? 0 : r + 1) * c.pitch;
-    const float* f = X.fin;
-    auto pair_at = [&](uint32_t a, uint32_t row) {
-        return __ldg(reinterpret_cast<const float2*>(f + a * P + row + (uint32_t)X.xc));
-    };
-    auto one_at = [&](uint32_t a, uint32_t row, int x) { return __ldg(f + a * P + row + (uint32_t)x); };
-    F[0] = pair_at(0, r0);
-    F[2] = pair_at(2, rm);
-    F[4] = pair_at(4, rp);
-    float2 t;
-    t = pair_at(1, r0);
-    F[1] = make_float2(one_at(1, r0, X.xm1), t.x);
-    t = pair_at(5, rm);
-    F[5] = make_float2(one_at(5, rm, X.xm1), t.x);
-    t = pair_at(8, rp);
-    F[8] = make_float2(one_at(8, rp, X.xm1), t.x);
-    t = pair_at(3, r0);
-    F[3] = make_float2(t.y, one_at(3, r0, X.xp2));
-    t = pair_at(6, rm);
-    F[6] = make_float2(t.y, one_at(6, rm, X.xp2));
-    t = pair_at(7, rp);
-    F[7] = make_float2(t.y, one_at(7, rp, X.xp2));
+    F[0] = ld2(R0 + 0 * SW + j);
+    F[1] = make_float2(R0[1 * SW + jm], R0[1 * SW + j]);
+    F[2] = ld2(Rm + 2 * SW + j);
+    F[3] = make_float2(R0[3 * SW + j + 1], R0[3 * SW + jq]);
+    F[4] = ld2(Rp + 4 * SW + j);
+    F[5] = make_float2(Rm[5 * SW + jm], Rm[5 * SW + j]);
+    F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jq]);
+    F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jq]);
+    F[8] = make_float2(Rp[8 * SW + jm], Rp[8 * SW + j]);
 }
 
 // rho > 0 and finite for both nodes of a pair (NaN fails both comparisons)
@@ -380,9 +376,10 @@ __device__ __forceinline__ void pair_timeout(const PairCtx& X)
 // This thread's share of every row copy, fixed for the block: thread 0 arms
 // a slot's mbarrier with the row's byte count, and each lane of an issuing
 // warp copies one (plane, run) pair: wide shape, warp w < 3 takes planes
-// 3w .. 3w + 2; narrow shape, warp 0 planes 0-4, warp 1 planes 5-8.
+// 3w .. 3w + 2; narrow shape, warp 0 planes 0-4, warp 1 planes 5-8. Returns
+// e_ay of the thread's plane (stage D's ring copies plane a from row y - e_ay).
 template <int NP>
-__device__ __forceinline__ void pair_issue_setup(PairCtx& X, const DevCase<float>& c)
+__device__ __forceinline__ int pair_issue_setup(PairCtx& X, const DevCase<float>& c)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int pw = NP == kPairThreads ? 3 : (w == 0 ? 5 : 4);  // planes of this warp
@@ -397,6 +394,7 @@ __device__ __forceinline__ void pair_issue_setup(PairCtx& X, const DevCase<float
     X.iss_dst = (uint32_t)(a * 2 * NP + j0);
     X.iss_dst_refl = (uint32_t)(refl[a] * 2 * NP + j0);
     X.iss_bytes = (uint32_t)len * sizeof(float);
+    return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0;  // e_ay of the plane
 }
 
 // Row offset of the stored row that fills window row s, and whether the slot
@@ -446,20 +444,8 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         const float* Rm = X.pRm;
         const float* R0 = X.pR0;
         const float* Rp = X.pRp;
-        // the planes that shift in x take one scalar load per node, straight
-        // into its half of the pair (the outermost pairs of the block read
-        // clamped columns and produce unused values)
-        const int jm = X.jm, jq = X.jq;
         float2 F[kQ];
-        F[0] = ld2(R0 + 0 * SW + j);
-        F[1] = make_float2(R0[1 * SW + jm], R0[1 * SW + j]);
-        F[2] = ld2(Rm + 2 * SW + j);
-        F[3] = make_float2(R0[3 * SW + j + 1], R0[3 * SW + jq]);
-        F[4] = ld2(Rp + 4 * SW + j);
-        F[5] = make_float2(Rm[5 * SW + jm], Rm[5 * SW + j]);
-        F[6] = make_float2(Rm[6 * SW + j + 1], Rm[6 * SW + jq]);
-        F[7] = make_float2(Rp[7 * SW + j + 1], Rp[7 * SW + jq]);
-        F[8] = make_float2(Rp[8 * SW + jm], Rp[8 * SW + j]);
+        pull_ring<SW>(F, Rm, R0, Rp, j, X.jm, X.jq);
         if (WL && c.walls) {
             // With ghost rows held reflected, the plain pull above is the
             // wall reading everywhere but for the diagonals that cross a wall
@@ -534,10 +520,12 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         // ------------------------------------------------------------ C
         // results of row ra - 2: u, F in registers (two rows deep; four for
         // scheme 3, whose stage D is two rows further behind) and phi u in
-        // the shared rows (a ring of six rows for scheme 3)
+        // the shared rows (scheme 3: a ring of five rows, row ra - 2 in slot
+        // (it + 4) % 5)
         constexpr int U2 = SCHEME == 3 ? SLOT : (SLOT & 1);
-        float* const pux_w = SCHEME == 3 ? sm.pux[(it + 4) % 6] : sm.pux[S2];
-        float* const puy_w = SCHEME == 3 ? sm.puy[(it + 4) % 6] : sm.puy[S2];
+        const int pw = X.pu == 0 ? 4 : X.pu - 1;
+        float* const pux_w = SCHEME == 3 ? sm.pux[pw] : sm.pux[S2];
+        float* const puy_w = SCHEME == 3 ? sm.puy[pw] : sm.puy[S2];
         if (X.c && it >= G::NC) {
             const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
             const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
@@ -572,7 +560,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                 float2 hx[5], sb[5];
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    const int slot = (it + k) % 6;  // phi u of row ra - 6 + k
+                    const int slot = X.pu + k < 5 ? X.pu + k : X.pu + k - 5;  // phi u of row ra - 6 + k
                     const float* a = sm.pux[slot] + j;
                     const float2 aL = ld2(a - 2), aO = ld2(a), aR = ld2(a + 2);
                     hx[k] = fma2(g1, make_float2(aO.y, aR.x) - make_float2(aL.y, aO.x), g2 * (aR - aL));
@@ -583,8 +571,14 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                 const float2 Ax = fma2(s0, hx[0] + hx[4], fma2(s1, hx[1] + hx[3], s2 * hx[2]));
                 const float2 By = fma2(g1, sb[3] - sb[1], g2 * (sb[4] - sb[0]));
                 const float2 C1 = Ax + By, C7 = Ax - By;
+                // the pull of row rd from stage D's ring: output row m = it - ND
+                // of the item in slot m & 1, phase (m / 2) & 1 (both fixed by
+                // SLOT, since ND is a multiple of 4)
+                constexpr int SLD = PairGeom<SCHEME>::SL + (SLOT & 1);
+                if (!mbar_wait(X.full + SLD, (uint32_t)(SLOT >> 1) & 1u)) pair_timeout(X);
+                const float* Dr = X.ring + SLD * (kQ * SW);
                 float2 F[kQ];
-                pull_pair(F, X, c, X.rd);
+                pull_ring<SW>(F, Dr, Dr, Dr, j, X.jm, X.jq);
                 const float2 drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
                 const float2 jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
                 const float2 jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
@@ -688,24 +682,38 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
     // stored row it (ra - 1) has had no reader since stage A's barrier: refill
     // its slot now, with the iteration's arithmetic issued (the copy still has
-    // two iterations of lead before stage A needs it)
-    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + kPairSlots <= X.s_last) {
+    // two iterations of lead before stage A needs it; one with scheme 3's
+    // four slots)
+    constexpr int SL = PairGeom<SCHEME>::SL;
+    if (threadIdx.x < pair_issuers(NP) && X.s0 + it + SL <= X.s_last) {
         if (WL && c.walls) {
             bool refl;
-            const uint32_t row = window_row(c, X.s0 + it + kPairSlots, refl);
+            const uint32_t row = window_row(c, X.s0 + it + SL, refl);
             pair_issue(X, X.pRm, X.fm, row, refl);
         } else {
             pair_issue(X, X.pRm, X.fm, X.irow);
         }
+    }
+    if constexpr (SCHEME == 3) {
+        // stage D's ring: output row m = it - ND + 1 goes to the slot of row
+        // m - 2, which stage D collided in the last iteration and no thread
+        // has read since stage A's barrier (rows 0 and 1 were issued at the
+        // start; m < h, i.e. it <= niter - 2)
+        constexpr int SLN = SL + ((SLOT + 1) & 1);
+        if (threadIdx.x < pair_issuers(NP) && it >= G::ND + 1 && X.s0 + it + 3 <= X.s_last) {
+            pair_issue(X, X.ring + SLN * (kQ * SW), X.full + SLN, X.drow);
+            X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
+        }
+        X.pu = X.pu == 4 ? 0 : X.pu + 1;
     }
     // advance the ring, the refill row and the output row by one (wrapping
     // compares instead of row modulos and multiplies)
     X.irow = X.irow + c.pitch == X.plane_rows ? 0u : X.irow + c.pitch;
     {
         constexpr int SLOTF = kQ * SW;
-        float* const ring_end = X.ring + kPairSlots * SLOTF;
-        X.fm = X.fm + 1 == X.full + kPairSlots ? X.full : X.fm + 1;
-        const bool wrap = X.f2 + 1 == X.full + kPairSlots;
+        float* const ring_end = X.ring + SL * SLOTF;
+        X.fm = X.fm + 1 == X.full + SL ? X.full : X.fm + 1;
+        const bool wrap = X.f2 + 1 == X.full + SL;
         X.f2 = wrap ? X.full : X.f2 + 1;
         X.par2 ^= wrap ? 1u : 0u;
         X.pRm = X.pR0;
@@ -719,10 +727,12 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
 }
 
-template <typename T, int NP>
+// stage A's ring, scheme 3's stage D ring, and one mbarrier per slot
+template <typename T, int NP, int SCHEME>
 constexpr size_t pair_dynamic_smem()
 {
-    return (size_t)kPairSlots * kQ * (2 * NP) * sizeof(T) + kPairSlots * sizeof(uint64_t);
+    constexpr int slots = PairGeom<SCHEME>::SL + PairGeom<SCHEME>::SD;
+    return (size_t)slots * kQ * (2 * NP) * sizeof(T) + slots * sizeof(uint64_t);
 }
 
 // FP32 step with NP threads of two columns each: blockDim.x == NP (128 or
@@ -743,6 +753,8 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     static_assert(SCHEME != 4, "scheme 4 runs on the plain-load kernel only");
     static_assert(!(WL && SCHEME == 3), "scheme 3 with walls runs on the plain-load kernel only");
     constexpr int M = PairGeom<SCHEME>::M;
+    constexpr int SL = PairGeom<SCHEME>::SL, SD = PairGeom<SCHEME>::SD;
+    constexpr int SLOTF = kQ * (2 * NP);
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(16) PairSmem<SCHEME, 2 * NP> sm;
     __shared__ int flag, bad;
@@ -757,7 +769,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
 
     PairCtx X;
     X.ring = reinterpret_cast<float*>(dsm);
-    X.full = reinterpret_cast<uint64_t*>(dsm + (size_t)kPairSlots * kQ * (2 * NP) * sizeof(float));
+    X.full = reinterpret_cast<uint64_t*>(dsm + (size_t)(SL + SD) * SLOTF * sizeof(float));
     X.flag = &flag;
     X.status = status;
     X.fin = fin;
@@ -781,20 +793,30 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
         }
         X.row_bytes = (uint32_t)(kQ * (end - start) * sizeof(float));
     }
-    pair_issue_setup<NP>(X, c);
+    const int ey = pair_issue_setup<NP>(X, c);
     if (threadIdx.x == 0) {
         flag = 0;
         bad = 0;
-        for (int k = 0; k < kPairSlots; ++k) mbar_init(X.full + k, 1);
+        for (int k = 0; k < SL + SD; ++k) mbar_init(X.full + k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x < pair_issuers(NP))
-        for (int i = 0; i < kPairSlots && X.s0 + i <= X.s_last; ++i) {
+    if (threadIdx.x < pair_issuers(NP)) {
+        for (int i = 0; i < SL && X.s0 + i <= X.s_last; ++i) {
             bool refl;
             const uint32_t row = window_row(c, X.s0 + i, refl);
-            pair_issue(X, X.ring + i * kQ * (2 * NP), X.full + i, row, refl);
+            pair_issue(X, X.ring + i * SLOTF, X.full + i, row, refl);
         }
+        if constexpr (SCHEME == 3) {
+            // stage D's ring: the pulls of output rows y0 and y0 + 1 (this
+            // thread's plane from stored row y - e_ay), then row y0 + 2's
+            // source row for the first refill
+            for (int m = 0; m < SD && m < item.h; ++m)
+                pair_issue(X, X.ring + (SL + m) * SLOTF, X.full + SL + m,
+                           (uint32_t)wrapi(item.y0 + m - ey, c.ny) * c.pitch);
+            X.drow = (uint32_t)wrapi(item.y0 + SD - ey, c.ny) * c.pitch;
+        }
+    }
 
     const int p = threadIdx.x;
     X.j = 2 * p;
@@ -810,19 +832,17 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     X.jm = X.j > 0 ? X.j - 1 : 0;
     X.jq = X.j + 2 < 2 * NP ? X.j + 2 : 2 * NP - 1;
     X.pRm = X.ring;
-    X.pR0 = X.ring + kQ * (2 * NP);
-    X.pRp = X.ring + 2 * kQ * (2 * NP);
+    X.pR0 = X.ring + SLOTF;
+    X.pRp = X.ring + 2 * SLOTF;
     X.fm = X.full;
     X.f2 = X.full + 2;
     X.par2 = 0;
     X.plane_rows = (uint32_t)c.ny * c.pitch;
-    X.irow = (uint32_t)wrapi(X.s0 + kPairSlots, c.ny) * c.pitch;
+    X.irow = (uint32_t)wrapi(X.s0 + SL, c.ny) * c.pitch;
     X.rd = item.y0;
     X.out = fout + (X.d ? item.x0 - M + 2 * p : 0);
     X.orow = X.out + (uint32_t)X.rd * c.pitch;
-    X.xc = X.d ? item.x0 - M + 2 * p : 0;
-    X.xm1 = X.xc == 0 ? c.nx - 1 : X.xc - 1;
-    X.xp2 = X.xc + 2 >= c.nx ? X.xc + 2 - c.nx : X.xc + 2;
+    X.pu = 0;
     X.bad = &bad;
 
     PairRegs<SCHEME> R;
@@ -844,10 +864,12 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
         stats_block(c, (double)R.am.x + (double)R.am.y, (double)R.ak.x + (double)R.ak.y, (double)R.au,
                     (unsigned long long)item.wv * (unsigned long long)item.h);
     if (threadIdx.x == 0 && flag) {
-        for (int s = max(X.s0, X.s_last - kPairSlots + 1); s <= X.s_last; ++s) {
+        for (int s = max(X.s0, X.s_last - SL + 1); s <= X.s_last; ++s) {
             const int i = s - X.s0;
-            mbar_wait(X.full + i % kPairSlots, (uint32_t)(i / kPairSlots) & 1u);
+            mbar_wait(X.full + i % SL, (uint32_t)(i / SL) & 1u);
         }
+        for (int m = max(0, item.h - SD); m < item.h; ++m)  // scheme 3: stage D's ring
+            mbar_wait(X.full + SL + (m & 1), (uint32_t)(m >> 1) & 1u);
     }
 }
 
