@@ -49,15 +49,17 @@
 // 5 x 5 stencil) reaches one column and one row further: the ring spans
 // [x0 - 8, x0 + wv + 8) (a margin of 8 keeps the copies 16-byte aligned), phi u
 // is needed on [6, wv + 10), mu_c on [5, wv + 11), rho on [3, wv + 13); stage
-// D runs four rows behind stage A, on a five-row phi u ring. Five rows of
-// pulled populations do not fit the registers of three blocks per SM, so
-// stage D reads its row's pull again, from a second ring of two slots: slot
-// m & 1 holds the pull of output row y0 + m (plane a copied from stored row
-// y0 + m - e_ay, so the nine planes of one slot come from three stored rows),
-// filled by bulk copies from L2 (stage A's copies brought those rows in four
-// iterations earlier) at the end of the iteration after the slot's previous
-// row was collided, three barrier intervals before stage D needs it. Both
-// rings then fit three blocks per SM with four slots in stage A's ring.
+// D runs four rows behind stage A. The stencil factors into an x-part per
+// phi u row and a y-combination of five rows: each iteration takes the
+// x-part of the newest row (one shared phi u row) and keeps those of the last
+// four rows in registers. Five rows of pulled populations do not fit the
+// registers of three blocks per SM, so stage D reads its row's pull again,
+// from a second ring of two slots: slot m & 1 holds the pull of output row
+// y0 + m (plane a copied from stored row y0 + m - e_ay, so the nine planes of
+// one slot come from three stored rows), filled by bulk copies from L2
+// (stage A's copies brought those rows in four iterations earlier) at the end
+// of the iteration after the slot's previous row was collided, three barrier
+// intervals before stage D needs it.
 #pragma once
 
 #include "step_tma.cuh"
@@ -67,7 +69,7 @@ namespace lbfe {
 constexpr int kPairThreads = 128;             // compute threads per block, wide shape
 constexpr int kPairCols = 2 * kPairThreads;   // ring / field columns per block, wide shape
 constexpr int kPairThreadsNarrow = 64;        // the narrow shape
-constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight (scheme 3: 4 and 1)
+constexpr int kPairSlots = 5;                 // ring slots: 3 rows in use, 2 in flight
 
 // threads that issue a stored row's bulk copies: three warps (wide), two (narrow)
 __host__ __device__ constexpr int pair_issuers(int np) { return np == kPairThreads ? 96 : 64; }
@@ -271,9 +273,9 @@ __device__ __forceinline__ void collide2(float2 (&d)[kQ], float2 drho, float2 rh
 template <int SCHEME>
 struct PairGeom {
     static constexpr int M = SCHEME == 3 ? 8 : 4;
-    static constexpr int NPU = SCHEME == 0 ? 1 : SCHEME == 3 ? 5 : 4;  // rows of the phi u rings
-    static constexpr int SL = SCHEME == 3 ? 4 : kPairSlots;            // slots of stage A's ring
-    static constexpr int SD = SCHEME == 3 ? 2 : 0;                     // slots of stage D's ring
+    static constexpr int NPU = SCHEME == 0 || SCHEME == 3 ? 1 : 4;  // rows of the phi u rings
+    static constexpr int SL = kPairSlots;                           // slots of stage A's ring
+    static constexpr int SD = SCHEME == 3 ? 2 : 0;                  // slots of stage D's ring
 };
 
 template <int SCHEME, int COLS>
@@ -292,6 +294,8 @@ struct PairRegs {
     float2 ux[SCHEME == 3 ? 4 : 2], uy[SCHEME == 3 ? 4 : 2];  // stage C results (improved)
     float2 Fx[SCHEME == 3 ? 4 : 2], Fy[SCHEME == 3 ? 4 : 2];
     float2 grx, gry;  // stage B grad rho (standard)
+    // scheme 3: x-parts of the correction's stencil of phi u rows ra - 6 .. ra - 3
+    float2 hx[SCHEME == 3 ? 4 : 1], sb[SCHEME == 3 ? 4 : 1];
     float2 am, ak;    // statistics of the stage D nodes: sums of rho - rho_ref and rho |u|^2
     float au;         // and the largest |u|^2
 };
@@ -330,7 +334,6 @@ struct PairCtx {
     float* out;         // fout + column of the pair's first node (stage D pairs)
     float* orow;        // out + rd * pitch
     int* bad;           // shared: a stage D node had rho <= 0 or a non-finite density
-    int pu;             // scheme 3: slot of the phi u ring that row ra - 6 occupies (it % 5)
     uint32_t drow;      // scheme 3: row offset of this lane's plane for the next stage D copy
     // this thread's share of a row refill: one (plane, run) copy, or none
     const float* iss_src;  // source of the copy in row 0
@@ -520,12 +523,11 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         // ------------------------------------------------------------ C
         // results of row ra - 2: u, F in registers (two rows deep; four for
         // scheme 3, whose stage D is two rows further behind) and phi u in
-        // the shared rows (scheme 3: a ring of five rows, row ra - 2 in slot
-        // (it + 4) % 5)
+        // the shared rows (scheme 3: one row, read by stage D of the same
+        // iteration)
         constexpr int U2 = SCHEME == 3 ? SLOT : (SLOT & 1);
-        const int pw = X.pu == 0 ? 4 : X.pu - 1;
-        float* const pux_w = SCHEME == 3 ? sm.pux[pw] : sm.pux[S2];
-        float* const puy_w = SCHEME == 3 ? sm.puy[pw] : sm.puy[S2];
+        float* const pux_w = SCHEME == 3 ? sm.pux[0] : sm.pux[S2];
+        float* const puy_w = SCHEME == 3 ? sm.puy[0] : sm.puy[S2];
         if (X.c && it >= G::NC) {
             const Row2 Mm = row2(sm.mu[S3], j, R.mu[S3]);
             const Row2 Mc = row2(sm.mu[S2], j, R.mu[S2]);
@@ -553,51 +555,58 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             // gradient of the averages factors into
             //   d_x A' = sum_dy s(dy) [(A(x+1) - A(x-1))/3 + (A(x+2) - A(x-2))/12](y + dy)
             // with s = (1, 8, 18, 8, 1)/36 over dy = -2 .. 2, and d_y B' with
-            // the roles of x and y exchanged.
-            if (X.d && it >= G::ND) {
-                const float2 g1 = v2(1.0f / 3.0f), g2 = v2(1.0f / 12.0f);
-                const float2 s0 = v2(1.0f / 36.0f), s1 = v2(8.0f / 36.0f), s2 = v2(18.0f / 36.0f);
-                float2 hx[5], sb[5];
+            // the roles of x and y exchanged. The x-parts (the bracket for A,
+            // the s-weighted sum over x for B) of row ra - 2 are taken here
+            // once; those of rows ra - 6 .. ra - 3 are in registers.
+            const float2 g1 = v2(1.0f / 3.0f), g2 = v2(1.0f / 12.0f);
+            const float2 s0 = v2(1.0f / 36.0f), s1 = v2(8.0f / 36.0f), s2 = v2(18.0f / 36.0f);
+            if (X.d && it >= G::NC) {
+                const float* a = sm.pux[0] + j;
+                const float2 aL = ld2(a - 2), aO = ld2(a), aR = ld2(a + 2);
+                const float2 hx4 = fma2(g1, make_float2(aO.y, aR.x) - make_float2(aL.y, aO.x), g2 * (aR - aL));
+                const float* b = sm.puy[0] + j;
+                const float2 bL = ld2(b - 2), bO = ld2(b), bR = ld2(b + 2);
+                const float2 sb4 =
+                    fma2(s0, bL + bR, fma2(s1, make_float2(bL.y, bO.x) + make_float2(bO.y, bR.x), s2 * bO));
+                if (it >= G::ND) {
+                    const float2 Ax = fma2(s0, R.hx[0] + hx4, fma2(s1, R.hx[1] + R.hx[3], s2 * R.hx[2]));
+                    const float2 By = fma2(g1, R.sb[3] - R.sb[1], g2 * (sb4 - R.sb[0]));
+                    const float2 C1 = Ax + By, C7 = Ax - By;
+                    // the pull of row rd from stage D's ring: output row m = it - ND
+                    // of the item in slot m & 1, phase (m / 2) & 1 (both fixed by
+                    // SLOT, since ND is a multiple of 4)
+                    constexpr int SLD = PairGeom<SCHEME>::SL + (SLOT & 1);
+                    if (!mbar_wait(X.full + SLD, (uint32_t)(SLOT >> 1) & 1u)) pair_timeout(X);
+                    const float* Dr = X.ring + SLD * (kQ * SW);
+                    float2 F[kQ];
+                    pull_ring<SW>(F, Dr, Dr, Dr, j, X.jm, X.jq);
+                    const float2 drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
+                    const float2 jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
+                    const float2 jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
+                    const float2 rho = v2(c.rho_ref) + drho;
+                    if (!pair_ok(rho)) *X.bad = 1;
+                    const float2 mu = R.mu[S0];  // row ra - 4
+                    float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
+                    if (NU) {
+                        lv = make_float2(shear_rate<SCHEME, NU, float>(c, rho.x, mu.x),
+                                         shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
+                        if (COLL == 0) le = ls = lq = lv;
+                    }
+                    if constexpr (ST) pair_stats(R, drho, rho, R.ux[S2], R.uy[S2]);
+                    collide2<SCHEME>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c, le,
+                                     ls, lq, lv);
+                    float* o = X.orow;
+                    const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const int slot = X.pu + k < 5 ? X.pu + k : X.pu + k - 5;  // phi u of row ra - 6 + k
-                    const float* a = sm.pux[slot] + j;
-                    const float2 aL = ld2(a - 2), aO = ld2(a), aR = ld2(a + 2);
-                    hx[k] = fma2(g1, make_float2(aO.y, aR.x) - make_float2(aL.y, aO.x), g2 * (aR - aL));
-                    const float* b = sm.puy[slot] + j;
-                    const float2 bL = ld2(b - 2), bO = ld2(b), bR = ld2(b + 2);
-                    sb[k] = fma2(s0, bL + bR, fma2(s1, make_float2(bL.y, bO.x) + make_float2(bO.y, bR.x), s2 * bO));
+                    for (int a = 0; a < kQ; ++a) st2(o + a * P, F[a]);
                 }
-                const float2 Ax = fma2(s0, hx[0] + hx[4], fma2(s1, hx[1] + hx[3], s2 * hx[2]));
-                const float2 By = fma2(g1, sb[3] - sb[1], g2 * (sb[4] - sb[0]));
-                const float2 C1 = Ax + By, C7 = Ax - By;
-                // the pull of row rd from stage D's ring: output row m = it - ND
-                // of the item in slot m & 1, phase (m / 2) & 1 (both fixed by
-                // SLOT, since ND is a multiple of 4)
-                constexpr int SLD = PairGeom<SCHEME>::SL + (SLOT & 1);
-                if (!mbar_wait(X.full + SLD, (uint32_t)(SLOT >> 1) & 1u)) pair_timeout(X);
-                const float* Dr = X.ring + SLD * (kQ * SW);
-                float2 F[kQ];
-                pull_ring<SW>(F, Dr, Dr, Dr, j, X.jm, X.jq);
-                const float2 drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
-                const float2 jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
-                const float2 jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
-                const float2 rho = v2(c.rho_ref) + drho;
-                if (!pair_ok(rho)) *X.bad = 1;
-                const float2 mu = R.mu[S0];  // row ra - 4
-                float2 le = v2(c.lam_e), ls = v2(c.lam_s), lq = v2(c.lam_q), lv = v2(c.lam_v);
-                if (NU) {
-                    lv = make_float2(shear_rate<SCHEME, NU, float>(c, rho.x, mu.x),
-                                     shear_rate<SCHEME, NU, float>(c, rho.y, mu.y));
-                    if (COLL == 0) le = ls = lq = lv;
-                }
-                if constexpr (ST) pair_stats(R, drho, rho, R.ux[S2], R.uy[S2]);
-                collide2<SCHEME>(F, drho, rho, jx, jy, R.ux[S2], R.uy[S2], R.Fx[S2], R.Fy[S2], mu, C1, C7, c, le,
-                                 ls, lq, lv);
-                float* o = X.orow;
-                const uint32_t P = (uint32_t)c.plane;
 #pragma unroll
-                for (int a = 0; a < kQ; ++a) st2(o + a * P, F[a]);
+                for (int k = 0; k < 3; ++k) {
+                    R.hx[k] = R.hx[k + 1];
+                    R.sb[k] = R.sb[k + 1];
+                }
+                R.hx[3] = hx4;
+                R.sb[3] = sb4;
             }
         } else {
         // ------------------------------------------------------------ D
@@ -704,7 +713,6 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             pair_issue(X, X.ring + SLN * (kQ * SW), X.full + SLN, X.drow);
             X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
         }
-        X.pu = X.pu == 4 ? 0 : X.pu + 1;
     }
     // advance the ring, the refill row and the output row by one (wrapping
     // compares instead of row modulos and multiplies)
@@ -842,7 +850,6 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     X.rd = item.y0;
     X.out = fout + (X.d ? item.x0 - M + 2 * p : 0);
     X.orow = X.out + (uint32_t)X.rd * c.pitch;
-    X.pu = 0;
     X.bad = &bad;
 
     PairRegs<SCHEME> R;
