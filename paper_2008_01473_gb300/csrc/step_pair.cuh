@@ -57,9 +57,9 @@
 // from a second ring of two slots: slot m & 1 holds the pull of output row
 // y0 + m (plane a copied from stored row y0 + m - e_ay, so the nine planes of
 // one slot come from three stored rows), filled by bulk copies from L2
-// (stage A's copies brought those rows in four iterations earlier) at the end
-// of the iteration after the slot's previous row was collided, three barrier
-// intervals before stage D needs it.
+// (stage A's copies brought those rows in four iterations earlier) right after
+// the first barrier that follows the collision of the slot's previous row,
+// six barrier intervals before stage D needs it.
 #pragma once
 
 #include "step_tma.cuh"
@@ -428,6 +428,25 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64
     }
 }
 
+// Scheme 3: refill stage D's ring, right after stage A's barrier. Output row
+// m = it - ND + 1 goes to the slot of row m - 2, which stage D collided in the
+// last iteration and no thread has read since that barrier (rows 0 and 1 were
+// issued at the start; m < h, i.e. it <= niter - 2). The copy has six stage
+// intervals of lead (issued at the end of the iteration, three, it arrived
+// late: 56.5 k instead of 59.7 k MLUPS at 4096^2).
+template <int SCHEME, int NP, int SLOT>
+__device__ __forceinline__ void pair_issue_d(int it, PairCtx& X, const DevCase<float>& c)
+{
+    if constexpr (SCHEME == 3) {
+        using G = StepGeom<SCHEME>;
+        constexpr int SLN = PairGeom<SCHEME>::SL + ((SLOT + 1) & 1);
+        if (threadIdx.x < pair_issuers(NP) && it >= G::ND + 1 && X.s0 + it + 3 <= X.s_last) {
+            pair_issue(X, X.ring + SLN * (kQ * 2 * NP), X.full + SLN, X.drow);
+            X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
+        }
+    }
+}
+
 template <int SCHEME, int COLL, int EOS, bool NU, int NP, int SLOT, bool ST, bool WL>
 __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<float>& c, PairSmem<SCHEME, 2 * NP>& sm,
                                           PairRegs<SCHEME>& R)
@@ -487,6 +506,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         if constexpr (SCHEME != 3) moments2(F, R.m[S0]);  // scheme 3 keeps only the sums
     }
     __syncthreads();
+    pair_issue_d<SCHEME, NP, SLOT>(it, X, c);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -691,8 +711,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
     }
     // stored row it (ra - 1) has had no reader since stage A's barrier: refill
     // its slot now, with the iteration's arithmetic issued (the copy still has
-    // two iterations of lead before stage A needs it; one with scheme 3's
-    // four slots)
+    // two iterations of lead before stage A needs it)
     constexpr int SL = PairGeom<SCHEME>::SL;
     if (threadIdx.x < pair_issuers(NP) && X.s0 + it + SL <= X.s_last) {
         if (WL && c.walls) {
@@ -701,17 +720,6 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             pair_issue(X, X.pRm, X.fm, row, refl);
         } else {
             pair_issue(X, X.pRm, X.fm, X.irow);
-        }
-    }
-    if constexpr (SCHEME == 3) {
-        // stage D's ring: output row m = it - ND + 1 goes to the slot of row
-        // m - 2, which stage D collided in the last iteration and no thread
-        // has read since stage A's barrier (rows 0 and 1 were issued at the
-        // start; m < h, i.e. it <= niter - 2)
-        constexpr int SLN = SL + ((SLOT + 1) & 1);
-        if (threadIdx.x < pair_issuers(NP) && it >= G::ND + 1 && X.s0 + it + 3 <= X.s_last) {
-            pair_issue(X, X.ring + SLN * (kQ * SW), X.full + SLN, X.drow);
-            X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
         }
     }
     // advance the ring, the refill row and the output row by one (wrapping
