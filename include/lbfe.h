@@ -68,8 +68,9 @@ typedef enum {
  * that instability and keeps 0.7 T_c stable for tau_v >= 0.8, or with MRT at
  * the constant kinematic viscosity 0.04 of Table II. Same steady states as
  * LB_IMPROVED (C vanishes at u = 0). FP32 cases with nx % 4 == 0 and
- * nx >= 8 run on the packed kernel (its stage D pulls the row's populations
- * a second time from L2), the others on the one-column plain-load kernel;
+ * nx >= 8 run on the packed kernel (its stage D reads the row's pull a
+ * second time, from a shared-memory ring that bulk copies fill out of L2),
+ * the others on the one-column plain-load kernel;
  * no lb_adjoint_step. */
 /* LB_LAX_WENDROFF: the comparison scheme of Appendix A (Lou and Guo's
  * Lax-Wendroff propagation): the standard force (Eq. 13 right), velocity
