@@ -294,7 +294,8 @@ struct PairRegs {
     float2 ux[SCHEME == 3 ? 4 : 2], uy[SCHEME == 3 ? 4 : 2];  // stage C results (improved)
     float2 Fx[SCHEME == 3 ? 4 : 2], Fy[SCHEME == 3 ? 4 : 2];
     float2 grx, gry;  // stage B grad rho (standard)
-    // scheme 3: x-parts of the correction's stencil of phi u rows ra - 6 .. ra - 3
+    // scheme 3: x-parts of the correction's stencil of phi u rows ra - 6 .. ra - 3;
+    // row ra - 2 - d (taken d iterations ago) in slot (SLOT - d) & 3
     float2 hx[SCHEME == 3 ? 4 : 1], sb[SCHEME == 3 ? 4 : 1];
     float2 am, ak;    // statistics of the stage D nodes: sums of rho - rho_ref and rho |u|^2
     float au;         // and the largest |u|^2
@@ -577,20 +578,23 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
             // with s = (1, 8, 18, 8, 1)/36 over dy = -2 .. 2, and d_y B' with
             // the roles of x and y exchanged. The x-parts (the bracket for A,
             // the s-weighted sum over x for B) of row ra - 2 are taken here
-            // once; those of rows ra - 6 .. ra - 3 are in registers.
+            // once; those of rows ra - 6 .. ra - 3 are in a register ring of
+            // four, row ra - 2 - d in slot (SLOT - d) & 3, so row ra - 2 takes
+            // the slot of row ra - 6 once that is read.
             const float2 g1 = v2(1.0f / 3.0f), g2 = v2(1.0f / 12.0f);
             const float2 s0 = v2(1.0f / 36.0f), s1 = v2(8.0f / 36.0f), s2 = v2(18.0f / 36.0f);
             if (X.d && it >= G::NC) {
+                constexpr int K6 = SLOT, K5 = (SLOT + 1) & 3, K4 = (SLOT + 2) & 3, K3 = (SLOT + 3) & 3;
                 const float* a = sm.pux[0] + j;
                 const float2 aL = ld2(a - 2), aO = ld2(a), aR = ld2(a + 2);
-                const float2 hx4 = fma2(g1, make_float2(aO.y, aR.x) - make_float2(aL.y, aO.x), g2 * (aR - aL));
+                // the shifted differences and sums as scalar halves (no pair assembly)
+                const float2 hx4 = fma2(g1, make_float2(aO.y - aL.y, aR.x - aO.x), g2 * (aR - aL));
                 const float* b = sm.puy[0] + j;
                 const float2 bL = ld2(b - 2), bO = ld2(b), bR = ld2(b + 2);
-                const float2 sb4 =
-                    fma2(s0, bL + bR, fma2(s1, make_float2(bL.y, bO.x) + make_float2(bO.y, bR.x), s2 * bO));
+                const float2 sb4 = fma2(s0, bL + bR, fma2(s1, make_float2(bL.y + bO.y, bO.x + bR.x), s2 * bO));
                 if (it >= G::ND) {
-                    const float2 Ax = fma2(s0, R.hx[0] + hx4, fma2(s1, R.hx[1] + R.hx[3], s2 * R.hx[2]));
-                    const float2 By = fma2(g1, R.sb[3] - R.sb[1], g2 * (sb4 - R.sb[0]));
+                    const float2 Ax = fma2(s0, R.hx[K6] + hx4, fma2(s1, R.hx[K5] + R.hx[K3], s2 * R.hx[K4]));
+                    const float2 By = fma2(g1, R.sb[K3] - R.sb[K5], g2 * (sb4 - R.sb[K6]));
                     const float2 C1 = Ax + By, C7 = Ax - By;
                     // the pull of row rd from stage D's ring: output row m = it - ND
                     // of the item in slot m & 1, phase (m / 2) & 1 (both fixed by
@@ -620,13 +624,8 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
 #pragma unroll
                     for (int a = 0; a < kQ; ++a) st2(o + a * P, F[a]);
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    R.hx[k] = R.hx[k + 1];
-                    R.sb[k] = R.sb[k + 1];
-                }
-                R.hx[3] = hx4;
-                R.sb[3] = sb4;
+                R.hx[K6] = hx4;
+                R.sb[K6] = sb4;
             }
         } else {
         // ------------------------------------------------------------ D
