@@ -9,7 +9,7 @@ step of the whole lattice (one fused kernel launch). The populations (1.2 GB
 per step read + write) exceed the 129 MB L2, so no flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--scheme improved|improved_smooth|standard|standard_pt] [--side N]
+                    [--scheme improved|improved_smooth|standard|standard_pt] [--walls] [--side N]
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on a
 bounded 256 x 256 sample of the same workload on the host cores.
@@ -349,8 +349,10 @@ def run_gpu(args):
     rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], T)
     n_side = args.side
     scheme = getattr(lbfe, SCHEMES[args.scheme][0])
+    # --walls: no-slip plates at rest half a node outside rows 0 and ny - 1 (Sec. IV C's walls)
+    wall_kw = dict(walls=1, wall_u=0.0, rho_wall=0.5 * (rg + rl)) if args.walls else {}
     case = lbfe.Case(nx=n_side, ny=n_side, scheme=scheme, collision=lbfe.MRT, eos=lbfe.VDW, T=T,
-                     kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW)
+                     kappa=0.02, tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW, **wall_kw)
     nodes = n_side * n_side
     rho0 = inputs.spinodal(n_side, n_side, 0.5 * (rg + rl), 0.01, seed=1 + rank)
     rho0_pin = torch.from_numpy(rho0).pin_memory()
@@ -430,9 +432,10 @@ def run_gpu(args):
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_passes, ws, f"cuda:{local}")
     seg_rows, n_items, narrow = lat.worklist()
     lat.close()
-    cs = _cs_variant(lbfe, inputs, n_side, prec, local, rank) if ws == 1 and args.scheme == "improved" else None
+    cs = _cs_variant(lbfe, inputs, n_side, prec, local, rank) if ws == 1 and args.scheme == "improved" and not args.walls else None
     extras = {}
-    if ws == 1 and dtype == "f32" and not args.no_extras and args.scheme == "improved":
+    default_case = args.scheme == "improved" and not args.walls
+    if ws == 1 and dtype == "f32" and not args.no_extras and default_case:
         # the other measured targets, outside the timed region, a few seconds each
         extras["batched"] = _batched_throughput(lbfe, steps=20, warmup=16)
         # the same batch down to 0.65 T_c with the averaged correction (one-column kernel)
@@ -455,7 +458,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD.replace(f"{N_SIDE}x{N_SIDE}", f"{n_side}x{n_side}").replace(
                            "FP32 deviation storage", "FP32 deviation storage" if dtype == "f32" else "FP64").replace(
-                           "improved scheme", SCHEMES[args.scheme][1]),
+                           "improved scheme", SCHEMES[args.scheme][1]).replace(
+                           "periodic", "between no-slip walls at rest (y), periodic in x" if args.walls else "periodic"),
                        "nx": n_side, "ny": n_side, "nodes_per_gpu": nodes,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single",
                        "l2": f"populations {BYTES_PER_NODE[dtype] * nodes / 1e9:.2f} GB per step vs 129 MB L2 "
@@ -474,7 +478,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
                          "frac_of_nominal_7900": round(achieved / 7900.0, 4),
-                         "traffic": _profiled_traffic(n_side) if dtype == "f32" and args.scheme == "improved" else None,
+                         "traffic": _profiled_traffic(n_side) if dtype == "f32" and default_case else None,
                          "peak_source": src, "bytes_per_node": BYTES_PER_NODE[dtype],
                          "kernel_ms_mean": round(mean_ms, 4),
                          "single_launch_ms": {"min": round(min(per), 4), "max": round(max(per), 4),
@@ -1145,6 +1149,8 @@ def main():
                     help="default workload: skip the batched, fp64 and adjoint sub-measurements")
     ap.add_argument("--side", type=int, default=N_SIDE, help="lattice side (profiling of smaller cases)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--walls", action="store_true",
+                    help="spinodal workload: no-slip walls at rest across y (the walled kernels)")
     ap.add_argument("--scheme", default="improved", choices=list(SCHEMES),
                     help="spinodal workload: the scheme of the lattice (the sub-measurements run with improved only)")
     ap.add_argument("--workload", default="spinodal", choices=["spinodal", "batched", "adjoint", "sweep", "galilean"],

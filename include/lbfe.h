@@ -115,9 +115,9 @@ enum { LB_FP64 = 0, LB_FP32 = 1 };          /* population storage and arithmetic
  * to the wall state's pressure (rho_wall / 3, or p_m of Eq. 24), so rho_wall
  * is the density of the fluid that touches the walls (rho_g for a droplet in
  * its vapour): another value drives that fluid at wall_u times the ratio of
- * the two pressures. Needs ny >= 8. FP32 cases with nx % 4 == 0 (schemes
- * other than LB_IMPROVED_SMOOTH) run on the packed kernel, whose row ring
- * holds the ghost rows with their planes reflected; the others on the
+ * the two pressures. Needs ny >= 8. FP32 cases with nx % 4 == 0 (and
+ * nx >= 8 for LB_IMPROVED_SMOOTH) run on the packed kernel, whose row rings
+ * hold the ghost rows with their planes reflected; the others on the
  * one-column step kernel. No adjoint and no lb_fields_static. */
 typedef struct {
     int32_t nx, ny;      /* >= 3 each */
@@ -179,7 +179,7 @@ lb_status lb_init_fields_f32(lb_handle* h, int32_t case_id, const float* rho0, c
  * runs a work-list of (case, column strip, row segment) items. FP32 cases
  * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
  * FP64 cases, other widths, Lax-Wendroff cases and LB_IMPROVED_SMOOTH cases
- * narrower than 8 or with walls run the one-column plain-load kernel.
+ * narrower than 8 run the one-column plain-load kernel.
  * Periodic LB_STANDARD and LB_IMPROVED cases with ny <= 16, in either
  * precision, run the row kernel instead (one thread per node of a
  * whole-height strip of 64 columns, 58 or 60 of them output, the stages

@@ -32,12 +32,11 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int halo_of(int scheme) { return scheme == LB_IMPROVED_SMOOTH ? 4 : scheme == LB_IMPROVED ? 3 : 2; }
 
 // cases that only the one-column plain-load kernel runs: the Lax-Wendroff
-// scheme, and the averaged correction with walls (its stage D pulls rows
-// again from global memory) or on lattices narrower than its 8-column ring
-// margin
+// scheme, and the averaged correction on lattices narrower than its 8-column
+// ring margin
 bool one_column_only(const lb_case& c)
 {
-    return c.scheme == LB_LAX_WENDROFF || (c.scheme == LB_IMPROVED_SMOOTH && (c.nx < 8 || c.walls));
+    return c.scheme == LB_LAX_WENDROFF || (c.scheme == LB_IMPROVED_SMOOTH && c.nx < 8);
 }
 
 // Widest strip of output columns a block of nt threads can own. Lattices with

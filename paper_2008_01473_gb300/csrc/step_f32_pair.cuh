@@ -17,14 +17,11 @@ void* pair_ptr_w(bool narrow)
                   : reinterpret_cast<void*>(&step_kernel_pair<S, C, E, NU, kPairThreads, ST, WL>);
 }
 
-// the variant for lattices with walls exists for schemes 0-2
+// lattices with walls run the WL variant
 template <int S, int C, int E, bool NU, bool ST>
 void* pair_ptr(bool narrow, bool walls)
 {
-    if constexpr (S == 3)
-        return walls ? nullptr : pair_ptr_w<S, C, E, NU, ST, false>(narrow);
-    else
-        return walls ? pair_ptr_w<S, C, E, NU, ST, true>(narrow) : pair_ptr_w<S, C, E, NU, ST, false>(narrow);
+    return walls ? pair_ptr_w<S, C, E, NU, ST, true>(narrow) : pair_ptr_w<S, C, E, NU, ST, false>(narrow);
 }
 
 template <int S, bool ST>

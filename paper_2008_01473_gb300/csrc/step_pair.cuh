@@ -56,7 +56,9 @@
 // registers of three blocks per SM, so stage D reads its row's pull again,
 // from a second ring of two slots: slot m & 1 holds the pull of output row
 // y0 + m (plane a copied from stored row y0 + m - e_ay, so the nine planes of
-// one slot come from three stored rows), filled by bulk copies from L2
+// one slot come from three stored rows; with walls, a source row beyond a
+// wall is taken as the mirror row's reflected plane, as in stage A's ring),
+// filled by bulk copies from L2
 // (stage A's copies brought those rows in four iterations earlier) right after
 // the first barrier that follows the collision of the slot's previous row,
 // six barrier intervals before stage D needs it.
@@ -341,6 +343,7 @@ struct PairCtx {
     uint32_t iss_dst;      // ring offset of the copy within a slot (floats)
     uint32_t iss_dst_refl; // the same for a ghost row beyond a wall (plane reflected in y)
     uint32_t iss_bytes;
+    int iss_ey;            // e_ay of the copy's plane (stage D's ring of scheme 3, with walls)
     bool iss_on;
 };
 
@@ -398,7 +401,7 @@ __device__ __forceinline__ int pair_issue_setup(PairCtx& X, const DevCase<float>
     X.iss_dst = (uint32_t)(a * 2 * NP + j0);
     X.iss_dst_refl = (uint32_t)(refl[a] * 2 * NP + j0);
     X.iss_bytes = (uint32_t)len * sizeof(float);
-    return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0;  // e_ay of the plane
+    return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0;
 }
 
 // Row offset of the stored row that fills window row s, and whether the slot
@@ -435,15 +438,41 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64
 // issued at the start; m < h, i.e. it <= niter - 2). The copy has six stage
 // intervals of lead (issued at the end of the iteration, three, it arrived
 // late: 56.5 k instead of 59.7 k MLUPS at 4096^2).
-template <int SCHEME, int NP, int SLOT>
+// With walls, a plane whose source row y - e_ay lies beyond a wall is the
+// mirror row's reflected plane (R19): the thread of plane b copies it, from
+// row nb_row(y + e_by), into the position of refl(b), where the plain pull
+// reads it; it copies its own plane only when y - e_by is inside. Every
+// position gets one copy, so the row's byte count is the periodic one.
+// Called by the first pair_issuers(NP) threads only; lattice row y, not
+// wrapped (walled items lie inside [0, ny)).
+__device__ __forceinline__ void pair_issue_walls(const PairCtx& X, const DevCase<float>& c, float* slot,
+                                                 uint64_t* bar, int y)
+{
+    if (threadIdx.x == 0) mbar_expect_tx(bar, X.row_bytes);
+    if (X.iss_on) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int sn = y - X.iss_ey, sg = y + X.iss_ey;
+        if (sn >= 0 && sn < c.ny)
+            bulk_load(slot + X.iss_dst, X.iss_src + (uint32_t)sn * c.pitch, X.iss_bytes, bar);
+        if (sg < 0 || sg >= c.ny)
+            bulk_load(slot + X.iss_dst_refl, X.iss_src + (uint32_t)nb_row(c, sg) * c.pitch, X.iss_bytes, bar);
+    }
+}
+
+template <int SCHEME, int NP, int SLOT, bool WL>
 __device__ __forceinline__ void pair_issue_d(int it, PairCtx& X, const DevCase<float>& c)
 {
     if constexpr (SCHEME == 3) {
         using G = StepGeom<SCHEME>;
         constexpr int SLN = PairGeom<SCHEME>::SL + ((SLOT + 1) & 1);
         if (threadIdx.x < pair_issuers(NP) && it >= G::ND + 1 && X.s0 + it + 3 <= X.s_last) {
-            pair_issue(X, X.ring + SLN * (kQ * 2 * NP), X.full + SLN, X.drow);
-            X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
+            float* const slot = X.ring + SLN * (kQ * 2 * NP);
+            if (WL && c.walls) {
+                pair_issue_walls(X, c, slot, X.full + SLN, X.rd + 1);  // X.rd: the row of this iteration's D
+            } else {
+                pair_issue(X, slot, X.full + SLN, X.drow);
+                X.drow = X.drow + c.pitch == X.plane_rows ? 0u : X.drow + c.pitch;
+            }
         }
     }
 }
@@ -507,7 +536,7 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
         if constexpr (SCHEME != 3) moments2(F, R.m[S0]);  // scheme 3 keeps only the sums
     }
     __syncthreads();
-    pair_issue_d<SCHEME, NP, SLOT>(it, X, c);
+    pair_issue_d<SCHEME, NP, SLOT, WL>(it, X, c);
 
     // ---------------------------------------------------------------- B
     if (X.b && it >= G::NB) {
@@ -604,6 +633,20 @@ __device__ __forceinline__ void pair_iter(int it, PairCtx& X, const DevCase<floa
                     const float* Dr = X.ring + SLD * (kQ * SW);
                     float2 F[kQ];
                     pull_ring<SW>(F, Dr, Dr, Dr, j, X.jm, X.jq);
+                    if (WL && c.walls) {
+                        // the diagonals that cross a wall (as in stage A): the
+                        // wall row's own outgoing populations, which the slot
+                        // holds at the reflected positions (7 -> 6, 8 -> 5 at
+                        // row 0; 5 -> 8, 6 -> 7 at row ny - 1)
+                        const float2 wd = v2(c.wall_d);
+                        if (X.rd == 0) {
+                            F[5] = ld2(Dr + 6 * SW + j) + wd;
+                            F[6] = ld2(Dr + 5 * SW + j) - wd;
+                        } else if (X.rd == c.ny - 1) {
+                            F[7] = ld2(Dr + 8 * SW + j) - wd;
+                            F[8] = ld2(Dr + 7 * SW + j) + wd;
+                        }
+                    }
                     const float2 drho = ((F[0] + (F[1] + F[3])) + (F[2] + F[4])) + ((F[5] + F[7]) + (F[6] + F[8]));
                     const float2 jx = (F[1] - F[3]) + ((F[5] - F[7]) + (F[8] - F[6]));
                     const float2 jy = (F[2] - F[4]) + ((F[5] - F[7]) + (F[6] - F[8]));
@@ -756,7 +799,7 @@ constexpr size_t pair_dynamic_smem()
 // wv % 4 == 0, wv + 2 M <= 2 NP with M = PairGeom<SCHEME>::M (4, or 8 for
 // scheme 3). ST: the variant that also records the per-step statistics
 // (stats_block) of the cases whose record has st_hist != 0. WL: the variant
-// that also runs lattices with walls (schemes 0-2).
+// that also runs lattices with walls.
 template <int SCHEME, int COLL, int EOS, bool NU, int NP, bool ST = false, bool WL = false>
 __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pair(const float* __restrict__ fin,
                                                                     float* __restrict__ fout,
@@ -766,7 +809,6 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
 {
     using G = StepGeom<SCHEME>;
     static_assert(SCHEME != 4, "scheme 4 runs on the plain-load kernel only");
-    static_assert(!(WL && SCHEME == 3), "scheme 3 with walls runs on the plain-load kernel only");
     constexpr int M = PairGeom<SCHEME>::M;
     constexpr int SL = PairGeom<SCHEME>::SL, SD = PairGeom<SCHEME>::SD;
     constexpr int SLOTF = kQ * (2 * NP);
@@ -809,6 +851,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
         X.row_bytes = (uint32_t)(kQ * (end - start) * sizeof(float));
     }
     const int ey = pair_issue_setup<NP>(X, c);
+    if constexpr (WL) X.iss_ey = ey;
     if (threadIdx.x == 0) {
         flag = 0;
         bad = 0;
@@ -826,9 +869,13 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
             // stage D's ring: the pulls of output rows y0 and y0 + 1 (this
             // thread's plane from stored row y - e_ay), then row y0 + 2's
             // source row for the first refill
-            for (int m = 0; m < SD && m < item.h; ++m)
-                pair_issue(X, X.ring + (SL + m) * SLOTF, X.full + SL + m,
-                           (uint32_t)wrapi(item.y0 + m - ey, c.ny) * c.pitch);
+            for (int m = 0; m < SD && m < item.h; ++m) {
+                if (WL && c.walls)
+                    pair_issue_walls(X, c, X.ring + (SL + m) * SLOTF, X.full + SL + m, item.y0 + m);
+                else
+                    pair_issue(X, X.ring + (SL + m) * SLOTF, X.full + SL + m,
+                               (uint32_t)wrapi(item.y0 + m - ey, c.ny) * c.pitch);
+            }
             X.drow = (uint32_t)wrapi(item.y0 + SD - ey, c.ny) * c.pitch;
         }
     }

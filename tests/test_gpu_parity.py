@@ -748,17 +748,18 @@ def _wall_droplet(nx, ny, scheme, collision):
     return kw, rho0, ux0, uy0
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("shape,seg", [((64, 8), "0"), ((128, 41), "4"), ((96, 24), "0"), ((260, 33), "2")])
 def test_fp32_walls_packed_kernel(scheme, collision, shape, seg, monkeypatch):
     """Walled FP32 lattices with nx % 4 == 0 run on the packed kernel, whose
     row ring holds the ghost rows beyond a wall with their planes reflected
     and whose stage A replaces the diagonals that cross a wall by the
-    bounce-back ones. Its populations after 25 steps agree with the
-    one-column plain-load kernel to FP32 rounding (row segments of 2 and 4
-    rows put ghost rows at the edges of many items), and rho, u with the FP64
-    oracle to the FP32 storage's precision."""
+    bounce-back ones (with the averaged correction, stage D's own ring of
+    pulled rows does the same at the wall rows). Its populations after 25
+    steps agree with the one-column plain-load kernel to FP32 rounding (row
+    segments of 2 and 4 rows put ghost rows at the edges of many items), and
+    rho, u with the FP64 oracle to the FP32 storage's precision."""
     nx, ny = shape
     kw, rho0, ux0, uy0 = _wall_droplet(nx, ny, scheme, collision)
     snaps, moms = {}, {}
