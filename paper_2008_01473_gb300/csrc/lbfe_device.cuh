@@ -65,12 +65,14 @@ struct StepStat {
 // case's last block of the step (a ticket over st_blocks) clears the next
 // entry and advances the recorded-state counter. Kernel boundaries order the
 // steps, so the next launch reads the advanced counter. blockDim.x must be a
-// multiple of 32 and at most 1024.
-template <typename T>
+// multiple of 32 and at most 32 W (W: the warps the block's shared partials
+// hold; the packed kernel passes its own warp count so that the narrow
+// shape's shared memory still fits six blocks per SM).
+template <typename T, int W = 32>
 __device__ __forceinline__ void stats_block(const DevCase<T>& c, double dm, double k2, double u2,
                                             unsigned long long nodes)
 {
-    __shared__ double s_m[32], s_k[32], s_u[32];
+    __shared__ double s_m[W], s_k[W], s_u[W];
     constexpr unsigned kFull = 0xffffffffu;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(NP, NP == kPairThreads ? 3 : 6) step_kernel_pa
     __syncthreads();
     if (threadIdx.x == 0 && bad) atomicOr(status + 1 + item.case_id, 1);
     if (ST && c.st_hist)
-        stats_block(c, (double)R.am.x + (double)R.am.y, (double)R.ak.x + (double)R.ak.y, (double)R.au,
+        stats_block<float, NP / 32>(c, (double)R.am.x + (double)R.am.y, (double)R.ak.x + (double)R.ak.y, (double)R.au,
                     (unsigned long long)item.wv * (unsigned long long)item.h);
     if (threadIdx.x == 0 && flag) {
         for (int s = max(X.s0, X.s_last - SL + 1); s <= X.s_last; ++s) {
