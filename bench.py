@@ -699,7 +699,8 @@ def _step_stats_cost(lbfe, case, rho0_pin, local: int, steps: int) -> dict:
 def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
     """Launch-bound workloads that live in L2: the sweep's 16 periodic
     1024 x 8 strips (improved scheme, BGK tau 1, vdW at T/T_c 0.95 ... 0.75,
-    131,072 nodes) in FP32 and FP64, and one 40 x 33 FP64 droplet, each timed
+    131,072 nodes) in FP32 and FP64, the same strips with the averaged
+    correction at T/T_c 0.95 ... 0.65 in FP32, and one 40 x 33 FP64 droplet, each timed
     over `steps` steps with one launch per step (8-step graph replay), the
     strips also with the row kernel off (the sliding-window kernels), and
     with the persistent launch (one cooperative launch for the steps); MLUPS
@@ -716,6 +717,12 @@ def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
         strips.append(lbfe.Case(nx=1024, ny=8, scheme=lbfe.IMPROVED, collision=lbfe.BGK, eos=lbfe.VDW, T=t * tc,
                                 kappa=0.02, tau_v=1.0, **VDW))
         strip_rho.append(inputs.slab(1024, 8, rl, rg))
+    smooth, smooth_rho = [], []
+    for t in np.linspace(0.95, 0.65, 16):
+        rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], t * tc)
+        smooth.append(lbfe.Case(nx=1024, ny=8, scheme=lbfe.IMPROVED_SMOOTH, collision=lbfe.BGK, eos=lbfe.VDW,
+                                T=t * tc, kappa=0.02, tau_v=1.0, **VDW))
+        smooth_rho.append(inputs.slab(1024, 8, rl, rg))
     rg, rl = lbfe.maxwell(lbfe.VDW, VDW["a"], VDW["b"], VDW["R"], 0.8 * tc)
     drop = [lbfe.Case(nx=40, ny=33, scheme=lbfe.IMPROVED, collision=lbfe.MRT, eos=lbfe.VDW, T=0.8 * tc, kappa=0.02,
                       tau_v=0.8, tau_e=1.0, tau_s=1.0, tau_q=1.1, **VDW)]
@@ -723,6 +730,7 @@ def _small_lattices(lbfe, inputs, steps: int = 400) -> dict:
     out = {}
     for name, cases, rhos, prec in (("sweep_strips_fp32", strips, strip_rho, lbfe.FP32),
                                     ("sweep_strips_fp64", strips, strip_rho, lbfe.FP64),
+                                    ("sweep_strips_smooth_fp32", smooth, smooth_rho, lbfe.FP32),
                                     ("droplet_40x33_fp64", drop, drop_rho, lbfe.FP64)):
         nodes = sum(c.nx * c.ny for c in cases)
         res = {"nodes": nodes}

@@ -10,8 +10,9 @@
 // pull plus the stage arithmetic of one node; the sliding window of
 // step_kernel.cuh instead walks ny + 2 HX rows as a chain of dependent row
 // iterations, and with the short segments that its latency favours on small
-// lattices it recomputes most rows of stages A-C several times. Schemes 0
-// and 1 (the chemical-potential forces), periodic lattices.
+// lattices it recomputes most rows of stages A-C several times. Schemes 0,
+// 1 and 3 (the chemical-potential forces; scheme 3 takes Eq. 29's derivatives
+// of the lattice-weight average of phi u), periodic lattices.
 #pragma once
 
 #include "step_kernel.cuh"
@@ -32,11 +33,12 @@ __host__ __device__ constexpr int rows_pass(int ny_max)
 }
 
 // Shared memory of a block: rho, mu_c, phi u_x, phi u_y (the last two for
-// the improved scheme only), each [rows_pass * RPT][NT].
+// the improved schemes only), each [rows_pass * RPT][NT].
 template <typename T, int SCHEME>
 __host__ __device__ constexpr size_t rows_dynamic_smem(int ny_max)
 {
-    return (size_t)(SCHEME == 1 ? 4 : 2) * rows_pass(ny_max) * rows_per_thread(ny_max) * kRowsCols * sizeof(T);
+    return (size_t)(improved_scheme(SCHEME) ? 4 : 2) * rows_pass(ny_max) * rows_per_thread(ny_max) * kRowsCols *
+           sizeof(T);
 }
 
 // Same contract as step_kernel (one block per work item, status words,
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
     step_kernel_rows(const T* __restrict__ fin, T* __restrict__ fout, const DevCase<T>* __restrict__ cases,
                      const Item* __restrict__ items, int* __restrict__ status)
 {
-    static_assert(SCHEME == 0 || SCHEME == 1, "the row kernel runs the chemical-potential forces");
+    static_assert(SCHEME == 0 || SCHEME == 1 || SCHEME == 3, "the row kernel runs the chemical-potential forces");
     constexpr int HX = StepGeom<SCHEME>::HX;
     extern __shared__ __align__(16) unsigned char rows_dsm[];
     const Item item = items[blockIdx.x];
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
     const int stride = RY * RPT * NT;  // words of one shared field
     T* const s_rho = reinterpret_cast<T*>(rows_dsm);
     T* const s_mu = s_rho + stride;
-    T* const s_ax = s_mu + stride;  // phi u_x, phi u_y (scheme 1)
+    T* const s_ax = s_mu + stride;  // phi u_x, phi u_y (schemes 1 and 3)
     T* const s_ay = s_ax + stride;
     const int span = item.wv + 2 * HX;  // active columns of the strip
     const int xw = item.x0 - HX + t;
@@ -117,9 +119,9 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();
 
     // ---------------------------------------------------------------- C
-    // improved scheme: F = (1/3 - rho) grad mu_c, u, and phi u for the
+    // improved schemes: F = (1/3 - rho) grad mu_c, u, and phi u for the
     // correction terms of stage D; the standard scheme takes its force in D
-    if constexpr (SCHEME == 1) {
+    if constexpr (improved_scheme(SCHEME)) {
 #pragma unroll
         for (int k = 0; k < RPT; ++k)
             if (in_c && vk[k]) {
@@ -163,6 +165,28 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
                 const T* Bp = s_ay + yp * NT;
                 const T Ax = gradx9<T>(Ac[t + 1], Ac[t - 1], Ap[t + 1], Ap[t - 1], Am[t + 1], Am[t - 1]);
                 const T By = grady9<T>(Bp[t], Bm[t], Bp[t + 1], Bp[t - 1], Bm[t + 1], Bm[t - 1]);
+                C1 = Ax + By;
+                C7 = Ax - By;
+            } else if constexpr (SCHEME == 3) {
+                // the derivatives of the lattice-weight averages A' = sum_a
+                // w_a (phi u_x)(x + e_a), B' likewise, through the factored
+                // 5 x 5 stencil of step_d_smooth (same order of operations):
+                //   d_x A' = sum_dy s(dy) [(A(x+1) - A(x-1))/3 + (A(x+2) - A(x-2))/12](y + dy)
+                // with s = (1, 8, 18, 8, 1)/36, d_y B' with x and y exchanged;
+                // rows y - 2 .. y + 2 wrap periodically within the strip
+                const int yr[5] = {dec_wrap(ym, ny), ym, y, yp, inc_wrap(yp, ny)};
+                const T s0 = T(1.0 / 36.0), s1 = T(8.0 / 36.0), s2 = T(18.0 / 36.0);
+                const T g1 = T(1.0 / 3.0), g2 = T(1.0 / 12.0);
+                T hx[5], sb[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const T* a = s_ax + yr[q] * NT;
+                    hx[q] = g1 * (a[t + 1] - a[t - 1]) + g2 * (a[t + 2] - a[t - 2]);
+                    const T* b = s_ay + yr[q] * NT;
+                    sb[q] = s0 * (b[t - 2] + b[t + 2]) + s1 * (b[t - 1] + b[t + 1]) + s2 * b[t];
+                }
+                const T Ax = s0 * (hx[0] + hx[4]) + s1 * (hx[1] + hx[3]) + s2 * hx[2];
+                const T By = g1 * (sb[3] - sb[1]) + g2 * (sb[4] - sb[0]);
                 C1 = Ax + By;
                 C7 = Ax - By;
             } else {

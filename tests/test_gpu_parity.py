@@ -95,10 +95,16 @@ def test_fp64_droplet_64_1000_steps(scheme):
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("eos", ["vdw", "cs"])
 @pytest.mark.parametrize("shape", [(530, 37), (7, 300), (3, 3), (5, 4), (257, 9)])
-def test_fp64_ragged_shapes(scheme, collision, eos, shape):
+@pytest.mark.parametrize("rows", ["1", "0"])
+def test_fp64_ragged_shapes(scheme, collision, eos, shape, rows, monkeypatch):
     """Several strips and row segments, ragged tails, and degenerate lattices
-    (3 x 3 wraps the halo more than once): 12 FP64 steps, element-wise."""
+    (3 x 3 wraps the halo more than once): 12 FP64 steps, element-wise. The
+    lattices of at most 16 rows run on the row kernel (schemes 0, 1, 3) and,
+    with it off, on the sliding window."""
     nx, ny = shape
+    if rows == "0" and ny > 16:
+        pytest.skip("the row kernel takes only lattices of at most 16 rows")
+    monkeypatch.setenv("LBFE_ROWS", rows)
     gc, oc, rg, rl = _pair(nx, ny, scheme, collision, eos=eos, t=0.9)
     rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=5)
     ux0 = 0.01 * (2 * inputs.splitmix_uniform(2, 0, nx, ny) - 1)
@@ -327,6 +333,7 @@ def test_fp32_kernel_shapes_agree(scheme, shape, monkeypatch):
     nx, ny = shape
     gc, _, rg, rl = _pair(nx, ny, scheme, lbfe.MRT, t=0.85)
     rho0 = inputs.droplet(nx, ny, 0.3 * min(nx, ny), rl, rg, width=3.0, noise=1e-3, seed=6)
+    monkeypatch.setenv("LBFE_ROWS", "0")  # the sliding-window kernels, also on the short lattices
     snaps = {}
     for path, threads in (("ldg", "128"), ("tma", "128"), ("tma", "256"), ("tma", "0")):
         monkeypatch.setenv("LBFE_STEP_PATH", path)
