@@ -180,9 +180,9 @@ lb_status lb_init_fields_f32(lb_handle* h, int32_t case_id, const float* rho0, c
  * with nx % 4 == 0 run the packed two-column kernel fed by bulk copies;
  * FP64 cases, other widths, Lax-Wendroff cases and LB_IMPROVED_SMOOTH cases
  * narrower than 8 run the one-column plain-load kernel.
- * Periodic LB_STANDARD, LB_IMPROVED and LB_IMPROVED_SMOOTH cases with
- * ny <= 16, in either precision, run the row kernel instead (one thread per
- * node of a whole-height strip of 64 columns, 56, 58 or 60 of them output, the stages
+ * Periodic cases with ny <= 16 (every scheme but LB_LAX_WENDROFF), in
+ * either precision, run the row kernel instead (one thread per node of a
+ * whole-height strip of 64 columns, 56, 58 or 60 of them output, the stages
  * separated by block barriers), except under the persistent launch: on
  * lattices that short the sliding-window kernels are bound by the latency
  * of their chain of row iterations. Its results agree with the other

@@ -48,7 +48,7 @@ void* pick_plain_stats_f64(int scheme, int coll, int eos, bool nu);
 int occupancy_step_f64(int scheme, int coll, int eos, bool nu);
 
 // The row-resident kernel for short periodic lattices (step_rows.cuh):
-// schemes 0, 1 and 3, every case of the launch periodic with ny <= ny_max <=
+// schemes 0-3, every case of the launch periodic with ny <= ny_max <=
 // rows_max_ny(), one item per column strip of at most rows_strip_width(scheme)
 // output columns spanning the whole height. prec: LB_FP32 (1) or LB_FP64 (0).
 cudaError_t launch_step_rows(int prec, int scheme, int coll, int eos, bool nu, int ny_max, int nblocks,

@@ -59,11 +59,10 @@ int64_t max_items_of(const lb_case& c)
                              (c.nx + rows_strip_width(LB_IMPROVED_SMOOTH) - 1) / rows_strip_width(LB_IMPROVED_SMOOTH));
 }
 
-// periodic lattices of schemes 0, 1 and 3 short enough for the row kernel
+// periodic lattices of schemes 0-3 short enough for the row kernel
 bool rows_eligible(const lb_case& c)
 {
-    return !c.walls && (c.scheme == LB_STANDARD || c.scheme == LB_IMPROVED || c.scheme == LB_IMPROVED_SMOOTH) &&
-           c.ny <= rows_max_ny();
+    return !c.walls && c.scheme != LB_LAX_WENDROFF && c.ny <= rows_max_ny();
 }
 
 constexpr int kMaxNeighbours = 32;  // neighbour items per item that the persistent launch tracks
@@ -422,7 +421,7 @@ void build_items(lb_handle* h)
         h->groups.push_back(g);
     };
 
-    // short periodic lattices of schemes 0, 1 and 3 run on the row kernel,
+    // short periodic lattices of schemes 0-3 run on the row kernel,
     // except under the persistent launch (whose kernel runs every item)
     const bool rows_ok = h->rows_on && h->persist_mode != 1;
     for (int s = 0; s < 5; ++s)
@@ -455,7 +454,7 @@ void build_items(lb_handle* h)
     // the row kernel: one item per strip of at most rows_strip_width columns
     // over the lattice's whole height, whatever the segment rule
     for (int s = 0; rows_ok && s < 4; ++s)
-        for (int co = 0; s != LB_STANDARD_PT && co < 2; ++co)
+        for (int co = 0; co < 2; ++co)
             for (int e = 0; e < 2; ++e)
                 for (int nu = 0; nu < 2; ++nu) {
                     Group g{s, co, e, nu == 1, false, 0, (int64_t)h->items.size(), 0};

@@ -16,6 +16,7 @@ void* pick_rows(int scheme, int coll, int eos, bool nu)
                   : reinterpret_cast<void*>(&step_kernel_rows<T, kRowsCols, RPT, S, C, E, false, ST>);
     LBFE_PICK(0, 0, 0) LBFE_PICK(0, 0, 1) LBFE_PICK(0, 1, 0) LBFE_PICK(0, 1, 1)
     LBFE_PICK(1, 0, 0) LBFE_PICK(1, 0, 1) LBFE_PICK(1, 1, 0) LBFE_PICK(1, 1, 1)
+    LBFE_PICK(2, 0, 0) LBFE_PICK(2, 0, 1) LBFE_PICK(2, 1, 0) LBFE_PICK(2, 1, 1)
     LBFE_PICK(3, 0, 0) LBFE_PICK(3, 0, 1) LBFE_PICK(3, 1, 0) LBFE_PICK(3, 1, 1)
 #undef LBFE_PICK
     return nullptr;
@@ -32,14 +33,14 @@ int rows_max_ny() { return kRowsMax; }
 
 int rows_strip_width(int scheme)
 {
-    return kRowsCols - 2 * (scheme == 3 ? StepGeom<3>::HX : scheme == 1 ? StepGeom<1>::HX : StepGeom<0>::HX);
+    return kRowsCols - 2 * (scheme == 3 ? StepGeom<3>::HX : scheme == 1 ? StepGeom<1>::HX : StepGeom<0>::HX);  // 56, 58, 60
 }
 
 cudaError_t launch_step_rows(int prec, int scheme, int coll, int eos, bool nu, int ny_max, int nblocks,
                              cudaStream_t s, const void* fin, void* fout, const void* cases, const Item* items,
                              int* status, bool stats)
 {
-    if ((scheme != 0 && scheme != 1 && scheme != 3) || ny_max < 1 || ny_max > kRowsMax) return cudaErrorInvalidValue;
+    if (scheme < 0 || scheme > 3 || ny_max < 1 || ny_max > kRowsMax) return cudaErrorInvalidValue;
     const int rpt = rows_per_thread(ny_max), threads = kRowsCols * rows_pass(ny_max);
     void* k;
     size_t smem;

@@ -10,9 +10,10 @@
 // pull plus the stage arithmetic of one node; the sliding window of
 // step_kernel.cuh instead walks ny + 2 HX rows as a chain of dependent row
 // iterations, and with the short segments that its latency favours on small
-// lattices it recomputes most rows of stages A-C several times. Schemes 0,
-// 1 and 3 (the chemical-potential forces; scheme 3 takes Eq. 29's derivatives
-// of the lattice-weight average of phi u), periodic lattices.
+// lattices it recomputes most rows of stages A-C several times. Schemes
+// 0-3 (the chemical-potential forces, the pressure-tensor force, and scheme
+// 3's Eq. 29 derivatives of the lattice-weight average of phi u), periodic
+// lattices.
 #pragma once
 
 #include "step_kernel.cuh"
@@ -33,12 +34,12 @@ __host__ __device__ constexpr int rows_pass(int ny_max)
 }
 
 // Shared memory of a block: rho, mu_c, phi u_x, phi u_y (the last two for
-// the improved schemes only), each [rows_pass * RPT][NT].
+// the improved schemes), or rho, P_xx, P_xy, P_yy (the pressure-tensor force),
+// or rho and mu_c (the standard scheme); each [rows_pass * RPT][NT].
 template <typename T, int SCHEME>
 __host__ __device__ constexpr size_t rows_dynamic_smem(int ny_max)
 {
-    return (size_t)(improved_scheme(SCHEME) ? 4 : 2) * rows_pass(ny_max) * rows_per_thread(ny_max) * kRowsCols *
-           sizeof(T);
+    return (size_t)(SCHEME == 0 ? 2 : 4) * rows_pass(ny_max) * rows_per_thread(ny_max) * kRowsCols * sizeof(T);
 }
 
 // Same contract as step_kernel (one block per work item, status words,
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
     step_kernel_rows(const T* __restrict__ fin, T* __restrict__ fout, const DevCase<T>* __restrict__ cases,
                      const Item* __restrict__ items, int* __restrict__ status)
 {
-    static_assert(SCHEME == 0 || SCHEME == 1 || SCHEME == 3, "the row kernel runs the chemical-potential forces");
+    static_assert(SCHEME >= 0 && SCHEME <= 3, "the row kernel runs schemes 0-3");
     constexpr int HX = StepGeom<SCHEME>::HX;
     extern __shared__ __align__(16) unsigned char rows_dsm[];
     const Item item = items[blockIdx.x];
@@ -64,8 +65,8 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
     const int t = (int)(threadIdx.x % NT), ty = (int)(threadIdx.x / NT), RY = (int)(blockDim.x / NT);
     const int stride = RY * RPT * NT;  // words of one shared field
     T* const s_rho = reinterpret_cast<T*>(rows_dsm);
-    T* const s_mu = s_rho + stride;
-    T* const s_ax = s_mu + stride;  // phi u_x, phi u_y (schemes 1 and 3)
+    T* const s_mu = s_rho + stride;  // mu_c, or P_xx (scheme 2)
+    T* const s_ax = s_mu + stride;   // phi u_x, phi u_y (schemes 1 and 3), or P_xy, P_yy (scheme 2)
     T* const s_ay = s_ax + stride;
     const int span = item.wv + 2 * HX;  // active columns of the strip
     const int xw = item.x0 - HX + t;
@@ -113,8 +114,20 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
             const T rc = Sc[t];
             const T lap = lap9<T>(rc, Sc[t + 1], Sc[t - 1], Sp[t], Sm[t], Sp[t + 1], Sp[t - 1], Sm[t + 1],
                                   Sm[t - 1]);
-            mu[k] = dEf<EOS, T>(c, rc) - c.kappa * lap;
-            s_mu[y * NT + t] = mu[k];
+            if constexpr (SCHEME == 2) {
+                // the pressure tensor of Eqs. 4-5 (P_xx in the mu_c field)
+                const T gx = gradx9<T>(Sc[t + 1], Sc[t - 1], Sp[t + 1], Sp[t - 1], Sm[t + 1], Sm[t - 1]);
+                const T gy = grady9<T>(Sp[t], Sm[t], Sp[t + 1], Sp[t - 1], Sm[t + 1], Sm[t - 1]);
+                T Pxx, Pxy, Pyy;
+                pressure_tensor<T>(pEOS<EOS, T>(c, rc), rc, gx, gy, lap, c.kappa, Pxx, Pxy, Pyy);
+                mu[k] = T(0);  // the standard collision does not use mu_c
+                s_mu[y * NT + t] = Pxx;
+                s_ax[y * NT + t] = Pxy;
+                s_ay[y * NT + t] = Pyy;
+            } else {
+                mu[k] = dEf<EOS, T>(c, rc) - c.kappa * lap;
+                s_mu[y * NT + t] = mu[k];
+            }
         }
     __syncthreads();
 
@@ -199,10 +212,25 @@ __global__ void __launch_bounds__(NT * kRowsPassMax, sizeof(T) == 4 ? 2 : 1)
                 const T* Mp = s_mu + yp * NT;
                 const T grx = gradx9<T>(Qc[t + 1], Qc[t - 1], Qp[t + 1], Qp[t - 1], Qm[t + 1], Qm[t - 1]);
                 const T gry = grady9<T>(Qp[t], Qm[t], Qp[t + 1], Qp[t - 1], Qm[t + 1], Qm[t - 1]);
-                const T gmx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
-                const T gmy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
-                fx[k] = grx * T(1.0 / 3.0) - rho * gmx;
-                fy[k] = gry * T(1.0 / 3.0) - rho * gmy;
+                if constexpr (SCHEME == 2) {
+                    // F = grad(rho/3) - div P, each component of P through Eq. 17
+                    const T* Xm = s_ax + ym * NT;
+                    const T* Xc = s_ax + y * NT;
+                    const T* Xp = s_ax + yp * NT;
+                    const T* Ym = s_ay + ym * NT;
+                    const T* Yp = s_ay + yp * NT;
+                    const T divx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]) +
+                                   grady9<T>(Xp[t], Xm[t], Xp[t + 1], Xp[t - 1], Xm[t + 1], Xm[t - 1]);
+                    const T divy = gradx9<T>(Xc[t + 1], Xc[t - 1], Xp[t + 1], Xp[t - 1], Xm[t + 1], Xm[t - 1]) +
+                                   grady9<T>(Yp[t], Ym[t], Yp[t + 1], Yp[t - 1], Ym[t + 1], Ym[t - 1]);
+                    fx[k] = grx * T(1.0 / 3.0) - divx;
+                    fy[k] = gry * T(1.0 / 3.0) - divy;
+                } else {
+                    const T gmx = gradx9<T>(Mc[t + 1], Mc[t - 1], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+                    const T gmy = grady9<T>(Mp[t], Mm[t], Mp[t + 1], Mp[t - 1], Mm[t + 1], Mm[t - 1]);
+                    fx[k] = grx * T(1.0 / 3.0) - rho * gmx;
+                    fy[k] = gry * T(1.0 / 3.0) - rho * gmy;
+                }
                 const T inv = rcp_fast<T>(rho);
                 ux[k] = (jx[k] + T(0.5) * fx[k]) * inv;
                 uy[k] = (jy[k] + T(0.5) * fy[k]) * inv;

@@ -1,6 +1,7 @@
-"""The row kernel for short periodic lattices (ny <= 16, standard and
-improved scheme, and the improved scheme with the averaged correction): one
-thread per node of a whole-height strip, the stages separated by block
+"""The row kernel for short periodic lattices (ny <= 16; the standard
+scheme with either force form, the improved scheme, and the improved scheme
+with the averaged correction): one thread per node of a whole-height strip,
+the stages separated by block
 barriers. FP64 against the oracle (1e-11), FP32 against the sliding-window
 kernels that run the same lattices with the row kernel off (LBFE_ROWS=0) to
 FP32 rounding, its work-list (one item per strip of at most 56, 58 or 60
@@ -60,7 +61,7 @@ def _strips(nx, scheme):
     return (nx + w - 1) // w
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.IMPROVED_SMOOTH])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 @pytest.mark.parametrize("collision", [lbfe.BGK, lbfe.MRT])
 @pytest.mark.parametrize("shape", [(64, 8), (130, 13), (37, 3), (203, 16), (11, 5)])
 def test_fp64_rows_kernel_matches_oracle(scheme, collision, shape):
@@ -94,7 +95,7 @@ def test_fp64_rows_kernel_eos_and_variable_viscosity(eos, nu):
     """The Carnahan-Starling equation of state and the density-dependent
     viscosity (nu > 0) on the row kernel, against the oracle."""
     nx, ny = 96, 12
-    for scheme in (lbfe.STANDARD, lbfe.IMPROVED, lbfe.IMPROVED_SMOOTH):
+    for scheme in (lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH):
         kw, rg, rl = _case(nx, ny, scheme, lbfe.MRT, eos=eos, nu=nu)
         rho0 = _rho0(nx, ny, rl, rg, 11)
         lat = lbfe.Lattice([lbfe.Case(**kw)], precision=lbfe.FP64)
@@ -122,7 +123,7 @@ def _run(cases, rhos, steps, precision, rows, monkeypatch):
     return out, items
 
 
-@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.IMPROVED_SMOOTH])
+@pytest.mark.parametrize("scheme", [lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH])
 def test_fp32_rows_kernel_matches_sliding_window(scheme, monkeypatch):
     """FP32: one launch over lattices of one row per thread (ny <= 8) and
     two (ny 9 ... 16) of uneven widths; after 40 steps rho (about 0.8 to 6.8)
