@@ -13,15 +13,14 @@
 // j - 1 and j + 2 are read from the shared-memory field rows. Populations
 // are stored with 64-bit stores (x0 and wv are multiples of 4).
 //
-// Ring: SL slots of one stored row (nine planes over the block's columns
-// [x0 - 4, x0 + wv + 4)), one full-mbarrier each (SL = PairGeom::SL: 5, or 4
-// for scheme 3). Stored row i = s - s0 lives in slot i % SL, phase (i / SL) &
-// 1. Stage A of
-// iteration it reads rows it .. it + 2; after the block barrier that follows
-// it, row it is dead, and at the end of the iteration (after stage D's
-// stores, off the path of the three barrier intervals) lanes of warps 0..2
-// refill its slot with row it + SL (one lane per plane and run), so no
-// producer warp is needed and three blocks fit on an SM. The slots, their
+// Ring: SL = 5 slots of one stored row (nine planes over the block's columns
+// [x0 - 4, x0 + wv + 4)), one full-mbarrier each. Stored row i = s - s0 lives
+// in slot i % SL, phase (i / SL) & 1. Stage A of iteration it reads rows
+// it .. it + 2; after the block barrier that follows it, row it is dead, and
+// at the end of the iteration (after stage D's stores, off the path of the
+// three barrier intervals) lanes of warps 0..2 refill its slot with row
+// it + SL (one lane per plane and run), so no producer warp is needed and
+// three blocks fit on an SM. The slots, their
 // mbarriers and phases, the refill row and the output row advance by one per
 // iteration through wrapping pointer and offset updates: no row modulo or
 // multiply sits on the iteration's path.
@@ -58,10 +57,10 @@
 // y0 + m (plane a copied from stored row y0 + m - e_ay, so the nine planes of
 // one slot come from three stored rows; with walls, a source row beyond a
 // wall is taken as the mirror row's reflected plane, as in stage A's ring),
-// filled by bulk copies from L2
-// (stage A's copies brought those rows in four iterations earlier) right after
-// the first barrier that follows the collision of the slot's previous row,
-// six barrier intervals before stage D needs it.
+// filled by bulk copies from L2 (stage A's copies brought those rows in four
+// iterations earlier) right after the first barrier that follows the
+// collision of the slot's previous row, six barrier intervals before stage D
+// needs it.
 #pragma once
 
 #include "step_tma.cuh"
@@ -432,12 +431,6 @@ __device__ __forceinline__ void pair_issue(const PairCtx& X, float* slot, uint64
     }
 }
 
-// Scheme 3: refill stage D's ring, right after stage A's barrier. Output row
-// m = it - ND + 1 goes to the slot of row m - 2, which stage D collided in the
-// last iteration and no thread has read since that barrier (rows 0 and 1 were
-// issued at the start; m < h, i.e. it <= niter - 2). The copy has six stage
-// intervals of lead (issued at the end of the iteration, three, it arrived
-// late: 56.5 k instead of 59.7 k MLUPS at 4096^2).
 // With walls, a plane whose source row y - e_ay lies beyond a wall is the
 // mirror row's reflected plane (R19): the thread of plane b copies it, from
 // row nb_row(y + e_by), into the position of refl(b), where the plain pull
@@ -459,6 +452,12 @@ __device__ __forceinline__ void pair_issue_walls(const PairCtx& X, const DevCase
     }
 }
 
+// Scheme 3: refill stage D's ring, right after stage A's barrier. Output row
+// m = it - ND + 1 goes to the slot of row m - 2, which stage D collided in the
+// last iteration and no thread has read since that barrier (rows 0 and 1 were
+// issued at the start; m < h, i.e. it <= niter - 2). The copy has six stage
+// intervals of lead (issued at the end of the iteration, three, it arrived
+// late: 56.5 k instead of 59.7 k MLUPS at 4096^2).
 template <int SCHEME, int NP, int SLOT, bool WL>
 __device__ __forceinline__ void pair_issue_d(int it, PairCtx& X, const DevCase<float>& c)
 {
