@@ -52,3 +52,13 @@ def test_gpu_ids_follow_the_pci_location_not_the_cuda_ordinal():
     smi, sysfs = bench._pci_ids(Props())
     assert smi == "00000000:1B:00.0"
     assert sysfs == "0000:1b:00.0"
+
+
+def test_scheme_option_names_library_schemes():
+    """Every --scheme choice names a scheme code of the binding, and the
+    workload text that the line reports names it."""
+    from paper_2008_01473_gb300 import lbfe
+
+    codes = {getattr(lbfe, attr) for attr, _ in bench.SCHEMES.values()}
+    assert codes == {lbfe.STANDARD, lbfe.IMPROVED, lbfe.STANDARD_PT, lbfe.IMPROVED_SMOOTH}
+    assert "improved scheme" in bench.WORKLOAD  # the text the option replaces
