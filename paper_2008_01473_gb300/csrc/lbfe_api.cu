@@ -348,8 +348,11 @@ constexpr int kGraphSteps = 8;  // steps per captured graph (even: buffer parity
 // fewer idle lanes than the wide (128-thread, 256-column) ones.
 bool prefers_narrow(const lb_case& c)
 {
-    const int wide = (c.nx + kPairCols256 - 9) / (kPairCols256 - 8) * kPairCols256;
-    const int narrow = (c.nx + kPairCols128 - 9) / (kPairCols128 - 8) * kPairCols128;
+    // block columns each shape spends on the lattice (its strips are at most
+    // strip_width: ring margins of 4, or 8 for the averaged correction)
+    const int ww = strip_width(c, kPairCols256), wn = strip_width(c, kPairCols128);
+    const int wide = (c.nx + ww - 1) / ww * kPairCols256;
+    const int narrow = (c.nx + wn - 1) / wn * kPairCols128;
     return narrow < wide;
 }
 
