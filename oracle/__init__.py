@@ -38,6 +38,7 @@ FLAG_ADJOINT_DROP_C = 4
 FLAG_WALL_EVEN_JY = 8
 FLAG_NU_SWAPPED = 16
 FLAG_NU_STANDARD_MAP = 32
+FLAG_MEQ_DROP_U2 = 64  # the standard e-equilibrium without its rho |u|^2 term
 
 
 class _CCase(C.Structure):

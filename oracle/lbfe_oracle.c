@@ -254,7 +254,7 @@ void orc_meq(const orc_case* c, double rho, double ux, double uy, double mu, dou
     double u2 = ux * ux + uy * uy;
     if (!improved(c)) {
         meq[0] = rho;
-        meq[1] = rho * (-2.0 + 3.0 * u2);
+        meq[1] = rho * (-2.0 + ((c->flags & 64) ? 0.0 : 3.0 * u2));  /* hook 64: the kinetic term dropped */
         meq[2] = rho * (1.0 - 3.0 * u2);
         meq[3] = rho * ux;
         meq[4] = -rho * ux;

@@ -325,6 +325,39 @@ def test_mrt_equal_rates_is_bgk():
     np.testing.assert_allclose(f1, f2, atol=1e-13)
 
 
+@pytest.mark.parametrize("collision,flags", [(O.BGK, 0), (O.MRT, 0), (O.MRT, O.FLAG_MEQ_DROP_U2)])
+def test_uniform_flow_relaxes_to_textbook_equilibrium(collision, flags):
+    """A uniform state has no force (grad mu_c = 0) and streams onto itself,
+    so the step reduces to the collision map, whose fixed point for the
+    standard scheme is the textbook second-order D2Q9 equilibrium
+    w_a rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u^2) (Eq. 11, Sec. II A). Start
+    from that state at u = (0.12, -0.07) with a uniform perturbation that
+    carries no mass or momentum; with distinct MRT rates (Eq. 8) every
+    non-conserved moment relaxes at its own rate to its Eq. 11 value, so
+    after 300 steps the populations are the closed form to round-off. Pins
+    the MRT collision with its velocity-dependent equilibrium beyond linear
+    order (the equal-rate and brute-force tests cover BGK); a planted
+    equilibrium without its rho |u|^2 term misses."""
+    nx, ny, rho, ux, uy = 6, 5, 1.7, 0.12, -0.07
+    c, _, _ = vdw_case(0.8, scheme=O.STANDARD, nx=nx, ny=ny, collision=collision, tau_v=0.7, tau_e=1.3,
+                       tau_s=0.6, tau_q=1.7, flags=flags)
+    f = O.init(c, np.full((ny, nx), rho), np.full((ny, nx), ux), np.full((ny, nx), uy))
+    eu = EX * ux + EY * uy
+    feq = W * rho * (1 + 3 * eu + 4.5 * eu**2 - 1.5 * (ux * ux + uy * uy))
+    # a perturbation orthogonal to 1, e_x and e_y (no mass or momentum)
+    r = np.array([0.3, -0.1, 0.25, 0.05, -0.2, 0.15, -0.05, 0.1, -0.3])
+    B = np.stack([np.ones(9), EX, EY]).astype(float)
+    r = r - B.T @ np.linalg.solve(B @ B.T, B @ r)
+    f += 0.02 * r[:, None, None]
+    assert np.abs(f - feq[:, None, None]).max() > 1e-3
+    assert O.step(c, f, 300) == 300
+    err = np.abs(f - feq[:, None, None]).max()
+    if flags:
+        assert err > 1e-4
+    else:
+        assert err < 1e-13
+
+
 # ------------------------------------------------------------------ invariants
 @pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.STANDARD_PT])
 @pytest.mark.parametrize("collision", [O.BGK, O.MRT])
