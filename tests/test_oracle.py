@@ -358,6 +358,38 @@ def test_uniform_flow_relaxes_to_textbook_equilibrium(collision, flags):
         assert err < 1e-13
 
 
+@pytest.mark.parametrize("collision", [O.BGK, O.MRT])
+def test_improved_uniform_flow_relaxes_to_eq25_eq26_moments(collision):
+    """The improved scheme on a uniform flow: mu_c = E_f'(rho) is uniform, so
+    F and the correction C vanish and the step is the collision map. From a
+    perturbed state at u = (-0.09, 0.14), with distinct MRT rates, the state
+    it reaches has the moments that Eqs. 25 and 26 give its equilibrium:
+    sum f = rho, sum e f = rho u, sum e_i e_j f = p_m delta_ij + rho u_i u_j
+    with p_m = (c0 + mu_c)/3 (Eq. 24), and the third moments, to 1e-13."""
+    nx, ny, rho, ux, uy = 5, 4, 2.3, -0.09, 0.14
+    c, _, _ = vdw_case(0.8, scheme=O.IMPROVED, nx=nx, ny=ny, collision=collision, tau_v=0.75, tau_e=1.4,
+                       tau_s=0.65, tau_q=1.6)
+    f = O.init(c, np.full((ny, nx), rho), np.full((ny, nx), ux), np.full((ny, nx), uy))
+    r = np.array([-0.2, 0.1, 0.3, -0.15, 0.05, 0.2, -0.1, 0.25, -0.05])
+    B = np.stack([np.ones(9), EX, EY]).astype(float)
+    r = r - B.T @ np.linalg.solve(B @ B.T, B @ r)
+    f += 0.02 * r[:, None, None]
+    assert O.step(c, f, 300) == 300
+    g = f[:, 0, 0]
+    assert np.abs(f - g[:, None, None]).max() < 1e-14  # still uniform
+    pm = (c.pm_c0 + O.dEf(c, rho)) / 3
+    u, E = (ux, uy), (EX, EY)
+    assert abs(g.sum() - rho) < 1e-13
+    for i in range(2):
+        assert abs((E[i] * g).sum() - rho * u[i]) < 1e-13
+        for j in range(2):
+            assert abs((E[i] * E[j] * g).sum() - (pm * (i == j) + rho * u[i] * u[j])) < 1e-13
+            for k in range(2):
+                s = u[i] * (j == k) + u[j] * (i == k) + u[k] * (i == j)
+                ref = (rho / 3 if i == j == k else pm) * s
+                assert abs((E[i] * E[j] * E[k] * g).sum() - ref) < 1e-13
+
+
 # ------------------------------------------------------------------ invariants
 @pytest.mark.parametrize("scheme", [O.STANDARD, O.IMPROVED, O.STANDARD_PT])
 @pytest.mark.parametrize("collision", [O.BGK, O.MRT])
